@@ -1,0 +1,79 @@
+"""Pricing rule of Section 3.4 with an exact selection contract.
+
+Test infrastructure only (see ``oracle/__init__.py``).
+
+Section 3.4: the reduced cost of column (i, j) is c_ij - y_{k1j} - y_{k2j}, i.e. with the
+duals y = (u, v) of the row and column constraints, d_ij = c_ij - u_i - v_j.  Section 3.2
+(support enlargement) adds the most negative reduced costs to the support, at most m per
+iteration (end of Section 3.2).
+
+Exact contract (the reading used everywhere in this project):
+  * d_ij = (c_ij - u_i) - v_j evaluated in IEEE-754 float64, round to nearest, in exactly
+    that order (no fused multiply-add);
+  * candidates: (i, j) not in the support with d_ij < 0;
+  * order by (d_ij, jlin) ascending with jlin = i + j*m, the 0-based column-major position
+    of p_ij in vec(P) (Section 2.1); keep the first min(kmax, #candidates).
+The set kept is unique; tests compare sets bit for bit.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .costs import Cost
+
+
+def reduced_costs(cost: Cost, u: np.ndarray, v: np.ndarray, i0: int = 0, i1: int | None = None) -> np.ndarray:
+    """Rows i0..i1-1 of d = (c - u) - v in float64."""
+    i1 = cost.m if i1 is None else i1
+    c = cost.block(i0, i1)
+    return (c - u[i0:i1, None]) - v[None, :]
+
+
+def select(cost: Cost, u: np.ndarray, v: np.ndarray, support_i: np.ndarray,
+           support_j: np.ndarray, kmax: int, rows_per_chunk: int | None = None):
+    """Return (I, J, d) of the selected columns, ordered by (d, jlin)."""
+    m, n = cost.m, cost.n
+    in_support = set(zip(support_i.tolist(), support_j.tolist())) if m * n > (1 << 26) else None
+    key_support = None
+    if in_support is None:
+        key_support = np.zeros(m * n, dtype=bool)
+        key_support[np.asarray(support_i, np.int64) * n + np.asarray(support_j, np.int64)] = True
+    if rows_per_chunk is None:
+        rows_per_chunk = max(1, (1 << 23) // max(n, 1))
+    Is, Js, Ds = [], [], []
+    for i0 in range(0, m, rows_per_chunk):
+        i1 = min(m, i0 + rows_per_chunk)
+        d = reduced_costs(cost, u, v, i0, i1)
+        ii, jj = np.nonzero(d < 0.0)
+        if ii.size == 0:
+            continue
+        gi = ii + i0
+        if key_support is not None:
+            keep = ~key_support[gi.astype(np.int64) * n + jj]
+        else:
+            keep = np.array([(int(x), int(y)) not in in_support for x, y in zip(gi, jj)], dtype=bool)
+        Is.append(gi[keep]); Js.append(jj[keep]); Ds.append(d[ii[keep], jj[keep]])
+    if not Is:
+        e = np.zeros(0, dtype=np.int64)
+        return e, e.copy(), np.zeros(0)
+    I = np.concatenate(Is).astype(np.int64)
+    J = np.concatenate(Js).astype(np.int64)
+    D = np.concatenate(Ds)
+    jlin = I + J * m
+    order = np.lexsort((jlin, D))[:kmax]
+    return I[order], J[order], D[order]
+
+
+def select_bruteforce(C: np.ndarray, u, v, support: set, kmax: int):
+    """Pure-Python loops over every pair; for tiny inputs only."""
+    m, n = C.shape
+    cand = []
+    for j in range(n):
+        for i in range(m):
+            if (i, j) in support:
+                continue
+            d = (float(C[i, j]) - float(u[i])) - float(v[j])
+            if d < 0.0:
+                cand.append((d, i + j * m, i, j))
+    cand.sort()
+    return [(i, j) for _, _, i, j in cand[:kmax]]
