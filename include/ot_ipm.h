@@ -1,0 +1,202 @@
+/*
+ * ot_ipm.h -- C ABI of the GB300 (sm_103a) hybrid interior-point / column-generation solver
+ * for the Kantorovich optimal-transport linear program.
+ *
+ * Method: Zanetti & Gondzio, "An Interior-Point-Inspired algorithm for Linear Programs arising
+ * in Discrete Optimal Transport" (arXiv:2206.11009).  Section numbers below refer to it.
+ *
+ * Conventions shared by every entry point
+ *   - Return value: an ot_status code; OT_OK == 0.  On failure the handle (when there is one)
+ *     keeps a message readable with ot_ipm_last_error(); nothing is left half-written in the
+ *     caller's output buffers except where stated.
+ *   - Ownership: the caller owns every pointer it passes; the library copies what it needs and
+ *     never keeps or frees a caller pointer.  A handle owns all device memory it allocates and
+ *     releases it in ot_ipm_destroy().
+ *   - Indices are 0-based.  Source i in [0, m), target j in [0, n).  The column of the LP
+ *     that carries the flow p_ij is jlin = i + j*m (column-major vec(P), Section 2.1).
+ *   - Masses a, b: nonnegative doubles with sum(a) == sum(b) up to a relative 1e-12 (b is then
+ *     rescaled by sum(a)/sum(b)); otherwise OT_ERR_ARG.
+ *   - Device pointers (the ot_price_* / ot_ipm_*_dev entry points) must live on the current
+ *     CUDA device; `stream` is a cudaStream_t (NULL = the legacy default stream).
+ *   - Host-buffer entry points synchronise the handle's stream before returning.
+ */
+#ifndef OT_IPM_H
+#define OT_IPM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    OT_OK = 0,
+    OT_ERR_ARG = 1,           /* invalid argument (sizes, masses, null pointers, options)     */
+    OT_ERR_CUDA = 2,          /* a CUDA runtime call failed                                   */
+    OT_ERR_OOM = 3,           /* device allocation failed                                      */
+    OT_ERR_MAXITER = 4,       /* iteration limit reached before the stopping test held        */
+    OT_ERR_NUMERIC = 5,       /* NaN/Inf or breakdown in mu, step length or a linear solve    */
+    OT_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up (grid barrier)            */
+    OT_ERR_BUF_TOO_SMALL = 7, /* caller buffer too small; the needed size is still returned   */
+    OT_ERR_UNSUPPORTED = 8    /* valid request this build does not implement                  */
+} ot_status;
+
+/* Cost c_ij between source point i and target point j (Section 5.1 lists the L1, Euclidean
+ * and L-infinity pixel distances; the squared Euclidean distance is the default here). */
+typedef enum {
+    OT_COST_SQEUCLID = 0,     /* (dx)^2 + (dy)^2, computed on the fly, never stored           */
+    OT_COST_EUCLID = 1,       /* sqrt(dx^2 + dy^2)                                            */
+    OT_COST_L1 = 2,           /* |dx| + |dy|                                                  */
+    OT_COST_LINF = 3,         /* max(|dx|, |dy|)                                              */
+    OT_COST_DENSE = 4         /* explicit matrix C (tests and small problems)                 */
+} ot_cost_kind;
+
+/* Problem statement (Section 2: a in R^m_+, b in R^n_+, cost matrix C in R^{m x n}_+).
+ * All pointers are HOST pointers; they are copied by ot_ipm_create. */
+typedef struct {
+    int32_t m, n;
+    const double *a;          /* m source masses                                              */
+    const double *b;          /* n target masses                                              */
+    int32_t cost;             /* ot_cost_kind                                                 */
+    /* point coordinates for the distance kinds: integers with |x|,|y| < 2^14.  When all four
+     * are NULL the points are pixel grids: source i sits at (i mod src_w, i div src_w), target j
+     * at (j mod dst_w, j div dst_w) (m = src_w*src_h, n = dst_w*dst_h). */
+    const int32_t *src_x, *src_y, *dst_x, *dst_y;
+    int32_t src_w, dst_w;
+    const double *C;          /* OT_COST_DENSE only: m x n row-major, C[i*n + j]              */
+} ot_problem;
+
+typedef struct {
+    double tol;               /* 1e-6: feasibility and optimality tolerance (Section 5.2)     */
+    double feas_l1;           /* 1e-8: ||f - A p||_1 bound in the caller's mass units         */
+    double cg_tol_pred;       /* 1e-6: PCG relative residual for predictors (Section 5.2)     */
+    double cg_tol_corr;       /* 1e-3: PCG relative residual for correctors (Section 5.2)     */
+    int32_t max_iter;         /* 200 (Section 5.2)                                            */
+    int32_t max_cg;           /* 1000 CG iterations per call (Section 5.2)                    */
+    int32_t max_corr;         /* 3 centrality correctors (Section 5.2)                        */
+    double step_scale;        /* 0.995 (Section 3.3)                                          */
+    int32_t precision;        /* 0: plain FP64 everywhere; 1: FP32 scan + FP64 recheck and    */
+                              /*    FP32 PCG + FP64 iterative refinement                      */
+    int32_t linear_solver;    /* 0: PCG then switch to the sparse LDL^T (Section 4.2-4.3)     */
+                              /* 1: PCG only; 2: LDL^T only                                  */
+    double init_cost;         /* 2.0: initial support {c_ij <= init_cost} (Section 3.2 end)   */
+    double rm_mu_frac;        /* 1e-3: removal phase once mu <= rm_mu_frac * mu_0             */
+    double rm_p_frac;         /* 1e-3: remove when p < rm_p_frac*min(a_i,b_j) and theta < 1   */
+    int32_t add_max;          /* 0 = m: pairs added per pricing (end of Section 3.2)          */
+    int32_t verbose;          /* 0: silent; 1: one line per iteration on stderr               */
+    void *stream;             /* cudaStream_t to run on; NULL = a stream the handle creates   */
+} ot_options;
+
+/* One outer iteration (Section 3.4's commented listing). */
+typedef struct {
+    int32_t iter;             /* iteration index                                              */
+    int64_t psi;              /* support size before the support update                       */
+    double mu;                /* p^T s / psi before the step                                  */
+    double crit;              /* stopping measure before the step                             */
+    double alpha_p, alpha_s;  /* step lengths taken                                           */
+    double sigma;             /* centring parameter                                           */
+    int32_t ncorr;            /* centrality correctors accepted                               */
+    int32_t cg_iters;         /* CG iterations in this iteration (all solves)                 */
+    int32_t direct;           /* 1 if the Newton systems were solved by LDL^T                 */
+    int64_t added, removed;   /* support changes                                              */
+    int32_t done;             /* 1 when the stopping test held (no step was taken)            */
+} ot_iter_info;
+
+typedef struct {
+    int32_t status;           /* ot_status of the solve                                       */
+    double obj;               /* c^T p (caller's units)                                       */
+    double lower_bound;       /* c-transform bound a^T u~ + b^T v <= OPT (caller's units)     */
+    double rel_gap;           /* (obj - lower_bound) / (1 + |obj|)                            */
+    double r1_l1;             /* ||f - A p||_1 (caller's units)                               */
+    double mu;
+    int32_t iters, cg_iters, direct_iters;
+    int64_t psi;              /* final support size                                           */
+    double max_fill;          /* max nnz(L)/n^2 * 100 over direct iterations (Table 3's fill)  */
+    double seconds;           /* device time of the solve (CUDA events)                       */
+} ot_result;
+
+typedef struct ot_ipm ot_ipm_t;
+
+/* Fill *opt with the paper's defaults (Section 5.2) and this library's readings. */
+void ot_options_default(ot_options *opt);
+
+/* Validate and copy the problem to the device, build the initial support (Section 3.2 end) and
+ * the initial point.  On success *out owns all device state.  Errors: OT_ERR_ARG, OT_ERR_OOM,
+ * OT_ERR_CUDA, OT_ERR_UNSUPPORTED (cost kind not built). */
+int ot_ipm_create(const ot_problem *prob, const ot_options *opt, ot_ipm_t **out);
+
+/* One outer iteration: residuals, stopping test, predictor-corrector Newton direction,
+ * step, pricing, support update (Section 3.4's listing).  info may be NULL.  Returns OT_OK
+ * (info->done tells whether the stopping test held), or an error status. */
+int ot_ipm_step(ot_ipm_t *h, ot_iter_info *info);
+
+/* Iterate to the stopping test (or max_iter) and fill *res (may be NULL). */
+int ot_ipm_solve(ot_ipm_t *h, ot_result *res);
+
+/* Copy the current coupling (support pairs and their flows, caller's units) and the duals u, v
+ * into caller HOST buffers of capacity cap.  *nnz receives the support size even when cap is
+ * too small (then OT_ERR_BUF_TOO_SMALL and nothing else is written).  u (m), v (n) may be NULL. */
+int ot_ipm_get_solution(ot_ipm_t *h, int32_t *i, int32_t *j, double *p, int64_t cap,
+                        int64_t *nnz, double *u, double *v);
+
+/* Full iterate in the solver's internal scaling (masses scaled by m/sum(a)): support pairs
+ * sorted by (i, j), p, s, and u, v.  Same buffer rules as ot_ipm_get_solution.  Used for
+ * checkpoints and to compare single steps with a reference. */
+int ot_ipm_get_state(ot_ipm_t *h, int32_t *i, int32_t *j, double *p, double *s, int64_t cap,
+                     int64_t *psi, double *u, double *v);
+
+/* Replace the iterate (host buffers, internal scaling).  Pairs must be distinct, in range and
+ * sorted by (i, j); p, s > 0.  Resets the iteration counter's mu_0 reference only if
+ * reset_mu0 != 0. */
+int ot_ipm_set_state(ot_ipm_t *h, const int32_t *i, const int32_t *j, const double *p,
+                     const double *s, int64_t psi, const double *u, const double *v,
+                     int32_t reset_mu0);
+
+/* Internal scale factor sigma_f = m / sum(a) (masses are multiplied by it). */
+double ot_ipm_mass_scale(const ot_ipm_t *h);
+
+/* Release everything the handle owns.  NULL is accepted. */
+void ot_ipm_destroy(ot_ipm_t *h);
+
+/* Message of the last failure on this handle ("" if none).  Valid until the next call. */
+const char *ot_ipm_last_error(const ot_ipm_t *h);
+
+/* Message of the last failure of a handle-less entry point on the calling thread. */
+const char *ot_last_error(void);
+
+/* ---------------------------------------------------------------------------------------
+ * Pricing (Section 3.4, with the support enlargement of Section 3.2) on device buffers.
+ *
+ * Computes d_ij = c_ij - u_i - v_j for ALL m*n pairs of a squared-Euclidean point set, costs
+ * evaluated on the fly from integer coordinates, and selects the pairs outside the support
+ * with d_ij < 0, at most kmax of them, smallest first.  The selected SET is exactly the one of
+ * this rule: d_ij = (c_ij - u_i) - v_j in IEEE float64 round-to-nearest in that order (no
+ * fusion); order by (d_ij, jlin = i + j*m) ascending; keep the first min(kmax, #candidates).
+ * precision 1 scans in FP32 and rechecks every pair inside a proven error window in FP64;
+ * precision 0 scans in FP64.  Both return the same set.
+ *
+ *   sx, sy (m) / tx, ty (n): int32 coordinates, |value| < 2^14      (device)
+ *   u (m), v (n): float64 duals                                      (device)
+ *   sup_i, sup_j (psi): support pairs sorted by (i, j), distinct     (device, may be NULL if psi==0)
+ *   out_i, out_j, out_d (kmax): selected pairs in (d, jlin) order    (device, caller-owned)
+ *   out_count: number selected (device int32)
+ * Scratch is allocated from the stream-ordered pool and released before return.
+ * Errors: OT_ERR_ARG (sizes, m*n > 2^32, null pointers), OT_ERR_OOM, OT_ERR_CUDA.
+ * ------------------------------------------------------------------------------------- */
+int ot_price_topk(int32_t m, int32_t n, const int32_t *sx, const int32_t *sy,
+                  const int32_t *tx, const int32_t *ty, const double *u, const double *v,
+                  const int32_t *sup_i, const int32_t *sup_j, int64_t psi, int32_t kmax,
+                  int32_t precision, int32_t *out_i, int32_t *out_j, double *out_d,
+                  int32_t *out_count, void *stream);
+
+/* Number of kernels this library launched since load (for launch accounting). */
+int64_t ot_kernel_launches(void);
+
+/* sizeof(ot_problem), sizeof(ot_options), sizeof(ot_iter_info), sizeof(ot_result) written to
+ * out[0..3] (count >= 4), so bindings can check their struct layouts.  Returns 4. */
+int ot_abi_struct_sizes(int64_t *out, int32_t count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OT_IPM_H */

@@ -374,58 +374,80 @@ def stop_measure(prob: Problem, res: Residuals, psi: int) -> float:
 # the whole iteration
 # ---------------------------------------------------------------------------------------
 
+@dataclass
+class Tracker:
+    """Cross-iteration quantities of the outer loop."""
+    mu0: float | None = None
+    strong: int = 1          # pricing candidates below -tol(1 + max c_red) at the last pricing
+    lb: float = -np.inf
+
+
+def stop_test(prob: Problem, st: State, opt: Options, tr: Tracker):
+    """Stopping test of Section 3.2 (with this project's readings); returns (stop, res, crit)."""
+    from .certificate import c_transform_lower_bound
+    res = residuals(prob, st)
+    psi = len(st.p)
+    if tr.mu0 is None:
+        tr.mu0 = res.mu
+    crit = stop_measure(prob, res, psi)
+    r1_l1 = (np.abs(res.r1a).sum() + np.abs(res.r1b).sum()) / prob.sigma_f
+    if crit < opt.tol and r1_l1 <= opt.feas_l1 and tr.strong == 0:
+        tr.lb = c_transform_lower_bound(prob.cost, prob.as_, prob.bs, st.v)
+        if (res.ctp - tr.lb) / (1.0 + abs(res.ctp)) <= opt.tol:
+            return True, res, crit
+    return False, res, crit
+
+
+def one_iteration(prob: Problem, st: State, res: Residuals, opt: Options, tr: Tracker, it: int = 0):
+    """Newton step, pricing and support update (the body of Section 3.4's listing)."""
+    m, n = prob.m, prob.n
+    psi = len(st.p)
+    kadd = opt.add_max or m
+    d, ap, as_, sigma, ncorr = predictor_corrector(prob, st, res, opt)
+    st = State(st.I, st.J, st.p + ap * d.dp, st.s + as_ * d.ds, st.u + as_ * d.du, st.v + as_ * d.dv)
+    mu_new = float(st.p @ st.s) / psi
+    aI, aJ, aD = pricing.select(prob.cost, st.u, st.v, st.I, st.J, kadd)
+    c_red_max = float(np.abs(res.c_red).max()) if psi else 0.0
+    tr.strong = int((aD < -opt.tol * (1.0 + c_red_max)).sum())
+    if mu_new <= opt.rm_mu_frac * tr.mu0:
+        rem = removal_select(prob, st, opt, m)
+    else:
+        rem = np.zeros(0, dtype=np.int64)
+    stepped = st
+    st = update_support(st, rem, aI, aJ, math.sqrt(mu_new), n)
+    log = IterLog(it, psi, res.mu, stop_measure(prob, res, psi), ap, as_, sigma, ncorr, len(aI), len(rem))
+    return st, log, stepped, (aI, aJ, aD), rem
+
+
 def solve(cost: Cost, a, b, opt: Options | None = None, state: State | None = None,
           verbose: bool = False) -> Result:
     from .certificate import c_transform_lower_bound
     opt = opt or Options()
     prob = Problem(cost, a, b)
-    m, n = prob.m, prob.n
-    kadd = opt.add_max or m
     if state is None:
         I, J = initial_support(prob, opt)
         st = initial_point(prob, I, J)
     else:
         st = state
-    mu0 = None
-    strong = 1
+    tr = Tracker()
     log = []
     status = "maxiter"
-    lb = -np.inf
     it = 0
     while True:
-        res = residuals(prob, st)
-        psi = len(st.p)
-        if mu0 is None:
-            mu0 = res.mu
-        crit = stop_measure(prob, res, psi)
-        r1_l1 = (np.abs(res.r1a).sum() + np.abs(res.r1b).sum()) / prob.sigma_f
-        if crit < opt.tol and r1_l1 <= opt.feas_l1 and strong == 0:
-            lb = c_transform_lower_bound(cost, prob.as_, prob.bs, st.v)
-            if (res.ctp - lb) / (1.0 + abs(res.ctp)) <= opt.tol:
-                status = "optimal"
-                break
+        stop, res, crit = stop_test(prob, st, opt, tr)
+        if stop:
+            status = "optimal"
+            break
         if it >= opt.max_iter:
             break
-        d, ap, as_, sigma, ncorr = predictor_corrector(prob, st, res, opt)
-        st = State(st.I, st.J, st.p + ap * d.dp, st.s + as_ * d.ds, st.u + as_ * d.du,
-                   st.v + as_ * d.dv)
-        mu_new = float(st.p @ st.s) / psi
-        aI, aJ, aD = pricing.select(cost, st.u, st.v, st.I, st.J, kadd)
-        c_red_max = float(np.abs(res.c_red).max()) if psi else 0.0
-        strong = int((aD < -opt.tol * (1.0 + c_red_max)).sum())
-        if mu_new <= opt.rm_mu_frac * mu0:
-            rem = removal_select(prob, st, opt, m)
-        else:
-            rem = np.zeros(0, dtype=np.int64)
-        st = update_support(st, rem, aI, aJ, math.sqrt(mu_new), n)
-        log.append(IterLog(it, psi, res.mu, crit, ap, as_, sigma, ncorr, len(aI), len(rem)))
+        st, lg, _, _, _ = one_iteration(prob, st, res, opt, tr, it)
+        log.append(lg)
         if verbose:
-            print(f"it {it:3d} psi {psi:7d} mu {res.mu:.3e} crit {crit:.3e} ap {ap:.3f} "
-                  f"as {as_:.3f} sig {sigma:.2e} corr {ncorr} +{len(aI)} -{len(rem)}")
+            print(f"it {it:3d} psi {lg.psi:7d} mu {lg.mu:.3e} crit {lg.crit:.3e} ap {lg.alpha_p:.3f} "
+                  f"as {lg.alpha_s:.3f} sig {lg.sigma:.2e} corr {lg.ncorr} +{lg.added} -{lg.removed}")
         it += 1
     res = residuals(prob, st)
     r1_l1 = (np.abs(res.r1a).sum() + np.abs(res.r1b).sum()) / prob.sigma_f
-    if not np.isfinite(lb):
-        lb = c_transform_lower_bound(cost, prob.as_, prob.bs, st.v)
+    lb = tr.lb if np.isfinite(tr.lb) else c_transform_lower_bound(cost, prob.as_, prob.bs, st.v)
     gap = (res.ctp - lb) / (1.0 + abs(res.ctp))
     return Result(status, res.ctp / prob.sigma_f, lb / prob.sigma_f, gap, r1_l1, it, st, log)

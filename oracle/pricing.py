@@ -33,11 +33,7 @@ def select(cost: Cost, u: np.ndarray, v: np.ndarray, support_i: np.ndarray,
            support_j: np.ndarray, kmax: int, rows_per_chunk: int | None = None):
     """Return (I, J, d) of the selected columns, ordered by (d, jlin)."""
     m, n = cost.m, cost.n
-    in_support = set(zip(support_i.tolist(), support_j.tolist())) if m * n > (1 << 26) else None
-    key_support = None
-    if in_support is None:
-        key_support = np.zeros(m * n, dtype=bool)
-        key_support[np.asarray(support_i, np.int64) * n + np.asarray(support_j, np.int64)] = True
+    sup_key = np.sort(np.asarray(support_i, np.int64) * n + np.asarray(support_j, np.int64))
     if rows_per_chunk is None:
         rows_per_chunk = max(1, (1 << 23) // max(n, 1))
     Is, Js, Ds = [], [], []
@@ -48,10 +44,11 @@ def select(cost: Cost, u: np.ndarray, v: np.ndarray, support_i: np.ndarray,
         if ii.size == 0:
             continue
         gi = ii + i0
-        if key_support is not None:
-            keep = ~key_support[gi.astype(np.int64) * n + jj]
-        else:
-            keep = np.array([(int(x), int(y)) not in in_support for x, y in zip(gi, jj)], dtype=bool)
+        key = gi.astype(np.int64) * n + jj
+        pos = np.searchsorted(sup_key, key)
+        member = (pos < len(sup_key)) & (sup_key[np.minimum(pos, len(sup_key) - 1)] == key) \
+            if len(sup_key) else np.zeros(len(key), bool)
+        keep = ~member
         Is.append(gi[keep]); Js.append(jj[keep]); Ds.append(d[ii[keep], jj[keep]])
     if not Is:
         e = np.zeros(0, dtype=np.int64)

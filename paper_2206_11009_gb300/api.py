@@ -1,0 +1,178 @@
+"""Python front end of the GB300 OT solver: marshals arguments to the C ABI, nothing more.
+
+Every step of the method runs in the CUDA library; this module only converts arrays to the
+pointers and structs of ``include/ot_ipm.h``.  Device buffers (for ``price_topk``) are torch
+CUDA tensors; the solver handle takes host arrays and owns its device state.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _lib
+from ._lib import OtIterInfo, OtOptions, OtProblem, OtResult, check
+
+
+def _ptr(a: np.ndarray | None):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def default_options(**overrides) -> OtOptions:
+    lib = _lib.load()
+    o = OtOptions()
+    lib.ot_options_default(ctypes.byref(o))
+    for k, v in overrides.items():
+        if not hasattr(o, k):
+            raise KeyError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+@dataclass
+class Result:
+    status: int
+    obj: float
+    lower_bound: float
+    rel_gap: float
+    r1_l1: float
+    mu: float
+    iters: int
+    cg_iters: int
+    direct_iters: int
+    psi: int
+    max_fill: float
+    seconds: float
+
+
+class Solver:
+    """One OT instance on the GPU (``ot_ipm_create`` ... ``ot_ipm_destroy``).
+
+    a, b: masses (host arrays).  Points: either ``grid=(src_w, dst_w)`` (pixel grids, pixel
+    i at (i mod w, i div w)) or ``coords=(sx, sy, tx, ty)`` integer arrays.
+    """
+
+    def __init__(self, a, b, grid=None, coords=None, stream=None, **options):
+        self._lib = _lib.load()
+        self.a = np.ascontiguousarray(a, dtype=np.float64)
+        self.b = np.ascontiguousarray(b, dtype=np.float64)
+        self.m, self.n = len(self.a), len(self.b)
+        prob = OtProblem()
+        prob.m, prob.n = self.m, self.n
+        prob.a, prob.b = _ptr(self.a), _ptr(self.b)
+        prob.cost = _lib.COST[options.pop("cost", "sqeuclid")]
+        self._keep = []
+        if coords is not None:
+            cs = [np.ascontiguousarray(c, dtype=np.int32) for c in coords]
+            self._keep += cs
+            prob.src_x, prob.src_y, prob.dst_x, prob.dst_y = [_ptr(c) for c in cs]
+        else:
+            if grid is None:
+                k = int(round(np.sqrt(self.m)))
+                grid = (k, int(round(np.sqrt(self.n))))
+            prob.src_w, prob.dst_w = grid
+        if stream is not None:
+            options["stream"] = stream
+        self.options = default_options(**options)
+        h = ctypes.c_void_p()
+        check(self._lib.ot_ipm_create(ctypes.byref(prob), ctypes.byref(self.options), ctypes.byref(h)))
+        self.h = h
+
+    # -- iteration -----------------------------------------------------------------
+    def step(self) -> dict:
+        info = OtIterInfo()
+        check(self._lib.ot_ipm_step(self.h, ctypes.byref(info)), self.h)
+        return {f: getattr(info, f) for f, _ in OtIterInfo._fields_}
+
+    def solve(self, raise_on_error: bool = True) -> Result:
+        r = OtResult()
+        code = self._lib.ot_ipm_solve(self.h, ctypes.byref(r))
+        if raise_on_error and code not in (_lib.OT_OK,):
+            check(code, self.h)
+        return Result(*[getattr(r, f) for f, _ in OtResult._fields_])
+
+    # -- results -------------------------------------------------------------------
+    def solution(self):
+        nnz = ctypes.c_int64(0)
+        self._lib.ot_ipm_get_solution(self.h, None, None, None, 0, ctypes.byref(nnz), None, None)
+        k = nnz.value
+        I = np.zeros(k, np.int32)
+        J = np.zeros(k, np.int32)
+        P = np.zeros(k)
+        u = np.zeros(self.m)
+        v = np.zeros(self.n)
+        check(self._lib.ot_ipm_get_solution(self.h, _ptr(I), _ptr(J), _ptr(P), k, ctypes.byref(nnz),
+                                            _ptr(u), _ptr(v)), self.h)
+        return I, J, P, u, v
+
+    def state(self):
+        psi = ctypes.c_int64(0)
+        self._lib.ot_ipm_get_state(self.h, None, None, None, None, 0, ctypes.byref(psi), None, None)
+        k = psi.value
+        I = np.zeros(k, np.int32)
+        J = np.zeros(k, np.int32)
+        P = np.zeros(k)
+        S = np.zeros(k)
+        u = np.zeros(self.m)
+        v = np.zeros(self.n)
+        check(self._lib.ot_ipm_get_state(self.h, _ptr(I), _ptr(J), _ptr(P), _ptr(S), k, ctypes.byref(psi),
+                                         _ptr(u), _ptr(v)), self.h)
+        return I, J, P, S, u, v
+
+    def set_state(self, I, J, P, S, u, v, reset_mu0: bool = False):
+        arrs = [np.ascontiguousarray(I, np.int32), np.ascontiguousarray(J, np.int32),
+                np.ascontiguousarray(P, np.float64), np.ascontiguousarray(S, np.float64),
+                np.ascontiguousarray(u, np.float64), np.ascontiguousarray(v, np.float64)]
+        check(self._lib.ot_ipm_set_state(self.h, _ptr(arrs[0]), _ptr(arrs[1]), _ptr(arrs[2]), _ptr(arrs[3]),
+                                         len(arrs[0]), _ptr(arrs[4]), _ptr(arrs[5]), int(reset_mu0)), self.h)
+
+    @property
+    def mass_scale(self) -> float:
+        return self._lib.ot_ipm_mass_scale(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.ot_ipm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def price_topk(sx, sy, tx, ty, u, v, sup_i, sup_j, kmax: int, precision: int = 1, stream=None):
+    """Pricing + selection on device tensors (torch, cuda, contiguous): int32 coordinates,
+    float64 duals, int32 support pairs sorted by (i, j).  Returns (I, J, D) device tensors."""
+    import torch
+    lib = _lib.load()
+    m, n = int(sx.numel()), int(tx.numel())
+    dev = u.device
+    out_i = torch.empty(max(kmax, 1), dtype=torch.int32, device=dev)
+    out_j = torch.empty(max(kmax, 1), dtype=torch.int32, device=dev)
+    out_d = torch.empty(max(kmax, 1), dtype=torch.float64, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int32, device=dev)
+    for t, dt in ((sx, torch.int32), (sy, torch.int32), (tx, torch.int32), (ty, torch.int32),
+                  (u, torch.float64), (v, torch.float64), (sup_i, torch.int32), (sup_j, torch.int32)):
+        if t.dtype != dt or not t.is_contiguous() or not t.is_cuda:
+            raise TypeError("price_topk: expected contiguous CUDA tensors of the documented dtypes")
+    s = stream if stream is not None else torch.cuda.current_stream(dev).cuda_stream
+    psi = int(sup_i.numel())
+    check(lib.ot_price_topk(m, n, sx.data_ptr(), sy.data_ptr(), tx.data_ptr(), ty.data_ptr(), u.data_ptr(),
+                            v.data_ptr(), sup_i.data_ptr() if psi else None, sup_j.data_ptr() if psi else None,
+                            psi, kmax, precision, out_i.data_ptr(), out_j.data_ptr(), out_d.data_ptr(),
+                            cnt.data_ptr(), ctypes.c_void_p(s)))
+    k = int(cnt.item())
+    return out_i[:k], out_j[:k], out_d[:k]
+
+
+def kernel_launches() -> int:
+    return int(_lib.load().ot_kernel_launches())

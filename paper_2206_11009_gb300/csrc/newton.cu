@@ -1,0 +1,925 @@
+// Newton direction of the restricted IPM (eq. redsystem) through the normal equations
+// (eq. normalequationsipm) and the Schur complement S_M = N - V^T M^-1 V (Section 4), solved
+// matrix-free by PCG.  All reductions are deterministic (fixed-order two-stage sums).
+#include "newton.cuh"
+#include "primitives.cuh"
+
+#include <cmath>
+#include <vector>
+
+namespace ot {
+namespace {
+
+constexpr int kT = 256;
+
+inline unsigned grid_of(int64_t work, int sms) {
+    int64_t g = ceil_div(work, kT);
+    int64_t cap = std::min<int64_t>(kMaxPartBlocks, 4LL * std::max(sms, 1));
+    return (unsigned)std::max<int64_t>(1, std::min(g, cap));
+}
+
+#define GRID_STRIDE(var, count) \
+    for (int64_t var = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; var < (count); var += (int64_t)gridDim.x * blockDim.x)
+
+// stage-1 partial: thread 0 of each block writes part[slot*kMaxPartBlocks + blockIdx.x]
+__device__ __forceinline__ void put_sum(double x, double *part, int slot, double *sh) {
+    double r = block_sum(x, sh);
+    if (threadIdx.x == 0) part[(int64_t)slot * kMaxPartBlocks + blockIdx.x] = r;
+}
+__device__ __forceinline__ void put_min(double x, double *part, int slot, double *sh) {
+    double r = block_min(x, sh);
+    if (threadIdx.x == 0) part[(int64_t)slot * kMaxPartBlocks + blockIdx.x] = r;
+}
+__device__ __forceinline__ void put_max(double x, double *part, int slot, double *sh) {
+    double r = -block_min(-x, sh);
+    if (threadIdx.x == 0) part[(int64_t)slot * kMaxPartBlocks + blockIdx.x] = r;
+}
+
+// stage 2: block b reduces slot slots[b] over nblk[b] partials with op ops[b] (0 sum, 1 min, 2 max)
+struct Finish {
+    int count;
+    int slot[8];
+    int nblk[8];
+    int op[8];
+};
+
+__global__ void finish_kernel(Finish f, const double *__restrict__ part, double *__restrict__ scal) {
+    __shared__ double sh[kT / 32];
+    const int b = blockIdx.x;
+    if (b >= f.count) return;
+    const int slot = f.slot[b], nb = f.nblk[b], op = f.op[b];
+    double acc = op == 0 ? 0.0 : (op == 1 ? INFINITY : -INFINITY);
+    for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+        double x = part[(int64_t)slot * kMaxPartBlocks + k];
+        acc = op == 0 ? acc + x : (op == 1 ? fmin(acc, x) : fmax(acc, x));
+    }
+    double r;
+    if (op == 0) r = block_sum(acc, sh);
+    else if (op == 1) r = block_min(acc, sh);
+    else r = -block_min(-acc, sh);
+    if (threadIdx.x == 0) scal[slot] = r;
+}
+
+Error finish(const Finish &f, Newton &W, cudaStream_t st) {
+    finish_kernel<<<f.count, kT, 0, st>>>(f, W.part, W.scal);
+    OT_LAUNCHED();
+    return ok();
+}
+
+// ------------------------------------------------------------------------ support costs
+__global__ void support_cost_kernel(CostDev cd, int64_t psi, const int32_t *__restrict__ si,
+                                    const int32_t *__restrict__ sj, double *__restrict__ c) {
+    GRID_STRIDE(e, psi) c[e] = cost_at(cd, si[e], sj[e]);
+}
+
+// ------------------------------------------------------------------------ residuals
+__global__ void res_rows_kernel(int m, const int32_t *__restrict__ rp, const double *__restrict__ p,
+                                const double *__restrict__ a, double *__restrict__ r1a, double *part) {
+    __shared__ double sh[kT / 32];
+    double sq = 0, l1 = 0;
+    GRID_STRIDE(i, m) {
+        double acc = 0;
+        for (int e = rp[i]; e < rp[i + 1]; ++e) acc += p[e];
+        const double r = a[i] - acc;
+        r1a[i] = r;
+        sq += r * r;
+        l1 += fabs(r);
+    }
+    put_sum(sq, part, SC_R1A_SQ, sh);
+    put_sum(l1, part, SC_R1A_L1, sh);
+}
+
+__global__ void res_cols_kernel(int n, const int32_t *__restrict__ cp, const int32_t *__restrict__ perm,
+                                const double *__restrict__ p, const double *__restrict__ b,
+                                double *__restrict__ r1b, double *part) {
+    __shared__ double sh[kT / 32];
+    double sq = 0, l1 = 0;
+    GRID_STRIDE(j, n) {
+        double acc = 0;
+        for (int k = cp[j]; k < cp[j + 1]; ++k) acc += p[perm[k]];
+        const double r = b[j] - acc;
+        r1b[j] = r;
+        sq += r * r;
+        l1 += fabs(r);
+    }
+    put_sum(sq, part, SC_R1B_SQ, sh);
+    put_sum(l1, part, SC_R1B_L1, sh);
+}
+
+__global__ void res_entries_kernel(int64_t psi, const int32_t *__restrict__ si, const int32_t *__restrict__ sj,
+                                   const double *__restrict__ c, const double *__restrict__ p,
+                                   const double *__restrict__ s, const double *__restrict__ u,
+                                   const double *__restrict__ v, double *__restrict__ r2, double *part) {
+    __shared__ double sh[kT / 32];
+    double r2sq = 0, ps = 0, cp = 0, csq = 0, cmax = 0;
+    GRID_STRIDE(e, psi) {
+        const double ce = c[e];
+        const double r = ((ce - u[si[e]]) - v[sj[e]]) - s[e];
+        r2[e] = r;
+        r2sq += r * r;
+        ps += p[e] * s[e];
+        cp += ce * p[e];
+        csq += ce * ce;
+        cmax = fmax(cmax, fabs(ce));
+    }
+    put_sum(r2sq, part, SC_R2SQ, sh);
+    put_sum(ps, part, SC_PS, sh);
+    put_sum(cp, part, SC_CP, sh);
+    put_sum(csq, part, SC_CSQ, sh);
+    put_max(cmax, part, SC_CMAX, sh);
+}
+
+// ------------------------------------------------------------------------ Schur setup
+__global__ void theta_kernel(int64_t psi, const double *__restrict__ p, const double *__restrict__ s,
+                             double *__restrict__ th, float *__restrict__ th32) {
+    GRID_STRIDE(e, psi) {
+        const double t = p[e] / s[e];
+        th[e] = t;
+        th32[e] = (float)t;
+    }
+}
+
+// M_i = sum_j theta_ij; excl_ij = sum of the OTHER entries of row i (prefix + suffix, never a
+// subtraction, so a dominant theta does not cancel: S_jj = sum_i theta_ij excl_ij / M_i).
+__global__ void theta_rows_kernel(int m, const int32_t *__restrict__ rp, const double *__restrict__ th,
+                                  double *__restrict__ excl, double *__restrict__ M, double *__restrict__ Minv,
+                                  float *__restrict__ Minv32) {
+    GRID_STRIDE(i, m) {
+        const int lo = rp[i], hi = rp[i + 1];
+        double pre = 0;
+        for (int e = lo; e < hi; ++e) { excl[e] = pre; pre += th[e]; }
+        double suf = 0;
+        for (int e = hi - 1; e >= lo; --e) { excl[e] += suf; suf += th[e]; }
+        M[i] = pre;
+        const double mi = pre > 0 ? 1.0 / pre : 0.0;
+        Minv[i] = mi;
+        Minv32[i] = (float)mi;
+    }
+}
+
+__global__ void theta_cols_kernel(int n, const int32_t *__restrict__ cp, const int32_t *__restrict__ perm,
+                                  const int32_t *__restrict__ crow, const double *__restrict__ th,
+                                  const double *__restrict__ excl, const double *__restrict__ Minv,
+                                  double *__restrict__ thc, float *__restrict__ thc32, double *__restrict__ N,
+                                  double *__restrict__ Dinv, float *__restrict__ Dinv32) {
+    GRID_STRIDE(j, n) {
+        double nsum = 0, d = 0;
+        for (int k = cp[j]; k < cp[j + 1]; ++k) {
+            const int e = perm[k];
+            const double t = th[e];
+            thc[k] = t;
+            thc32[k] = (float)t;
+            nsum += t;
+            d += t * excl[e] * Minv[crow[k]];
+        }
+        N[j] = nsum;
+        const double di = d > 0 ? 1.0 / d : 0.0;  // columns with D = 0 are private stars: masked
+        Dinv[j] = di;
+        Dinv32[j] = (float)di;
+    }
+}
+
+// Connected components of the bipartite support graph (nodes: rows 0..m-1, columns m..m+n-1)
+// by lock-free union-find: hooking always points the larger root at the smaller, so every
+// root is the smallest node id of its component.
+__device__ __forceinline__ int uf_find(int32_t *parent, int x) {
+    int p = parent[x];
+    while (p != x) {
+        const int gp = parent[p];
+        if (gp != p) parent[x] = gp;  // path halving (benign race: only moves to an ancestor)
+        x = p;
+        p = gp;
+    }
+    return x;
+}
+
+__global__ void uf_init_kernel(int nn, int32_t *parent) {
+    GRID_STRIDE(v, nn) parent[v] = (int32_t)v;
+}
+
+__global__ void uf_hook_kernel(int64_t psi, int m, const int32_t *__restrict__ si, const int32_t *__restrict__ sj,
+                               int32_t *parent) {
+    GRID_STRIDE(e, psi) {
+        int a = si[e], b = m + sj[e];
+        for (int guard = 0; guard < (1 << 20); ++guard) {
+            a = uf_find(parent, a);
+            b = uf_find(parent, b);
+            if (a == b) break;
+            if (a < b) { int t = a; a = b; b = t; }
+            if (atomicCAS(&parent[a], a, b) == a) break;
+        }
+    }
+}
+
+__global__ void uf_final_kernel(int nn, int32_t *parent) {
+    GRID_STRIDE(v, nn) parent[v] = uf_find(parent, (int)v);
+}
+
+// SC_ONECOMP <- number of columns whose label differs from column 0's (0: one component)
+__global__ void onecomp_kernel(int m, int n, const int32_t *__restrict__ parent, double *part) {
+    __shared__ double sh[kT / 32];
+    double diff = 0;
+    const int l0 = parent[m];
+    GRID_STRIDE(j, n) diff += parent[m + j] != l0 ? 1.0 : 0.0;
+    put_sum(diff, part, SC_ONECOMP, sh);
+}
+
+// ------------------------------------------------------------------------ right-hand side
+__global__ void g_kernel(int64_t psi, const double *__restrict__ th, const double *__restrict__ p,
+                         const double *__restrict__ r2, const double *__restrict__ r3, double *__restrict__ g) {
+    GRID_STRIDE(e, psi) {
+        const double a = r2 ? r2[e] : 0.0;
+        const double b = r3 ? r3[e] / p[e] : 0.0;
+        g[e] = th[e] * (a - b);
+    }
+}
+
+__global__ void beta1_kernel(int m, const int32_t *__restrict__ rp, const double *__restrict__ g,
+                             const double *__restrict__ r1a, double *__restrict__ beta1) {
+    GRID_STRIDE(i, m) {
+        double acc = r1a ? r1a[i] : 0.0;
+        for (int e = rp[i]; e < rp[i + 1]; ++e) acc += g[e];
+        beta1[i] = acc;
+    }
+}
+
+// beta2_j = r1b_j + sum_i g_ij ; rhs_j = beta2_j - sum_i theta_ij beta1_i / M_i
+__global__ void rhs_kernel(int n, const int32_t *__restrict__ cp, const int32_t *__restrict__ perm,
+                           const int32_t *__restrict__ crow, const double *__restrict__ g,
+                           const double *__restrict__ thc, const double *__restrict__ Minv,
+                           const double *__restrict__ beta1, const double *__restrict__ r1b,
+                           double *__restrict__ beta2, double *__restrict__ rhs, double *part) {
+    __shared__ double sh[kT / 32];
+    double tot = 0;
+    GRID_STRIDE(j, n) {
+        double b2 = r1b ? r1b[j] : 0.0;
+        double vt = 0;
+        for (int k = cp[j]; k < cp[j + 1]; ++k) {
+            b2 += g[perm[k]];
+            const int i = crow[k];
+            vt += thc[k] * (Minv[i] * beta1[i]);
+        }
+        beta2[j] = b2;
+        const double r = b2 - vt;
+        rhs[j] = r;
+        tot += r;
+    }
+    put_sum(tot, part, SC_SUM_A, sh);
+}
+
+__global__ void sum_kernel(int n, const double *__restrict__ x, double *part, int slot) {
+    __shared__ double sh[kT / 32];
+    double t = 0;
+    GRID_STRIDE(j, n) t += x[j];
+    put_sum(t, part, slot, sh);
+}
+
+// one component: subtract the mean (scal[slot] / n)
+__global__ void center_kernel(int n, double *__restrict__ x, const double *__restrict__ scal, int slot) {
+    const double mean = scal[slot] / (double)n;
+    GRID_STRIDE(j, n) x[j] -= mean;
+}
+
+// several components: per-label sums by atomics, then subtract the label mean
+__global__ void comp_accum_kernel(int m, int n, const int32_t *__restrict__ parent, const double *__restrict__ x,
+                                  double *comp_sum, double *comp_cnt) {
+    GRID_STRIDE(j, n) {
+        const int l = parent[m + j];
+        atomicAdd(&comp_sum[l], x[j]);
+        atomicAdd(&comp_cnt[l], 1.0);
+    }
+}
+__global__ void comp_center_kernel(int m, int n, const int32_t *__restrict__ parent, double *__restrict__ x,
+                                   const double *__restrict__ comp_sum, const double *__restrict__ comp_cnt) {
+    GRID_STRIDE(j, n) {
+        const int l = parent[m + j];
+        x[j] -= comp_sum[l] / comp_cnt[l];
+    }
+}
+
+// ------------------------------------------------------------------------ PCG on S_M
+template <typename T>
+struct PcgArgs {
+    int m, n;
+    const int32_t *rp, *sj, *cp, *crow;
+    const T *th, *thc, *Minv, *Dinv;
+    const T *b;
+    T *x, *r, *z, *p, *q, *w;
+    double *part;  // 3 slots x gridDim
+    unsigned *bar;
+    int *err;
+    double tol;
+    int maxit;
+    double *scal;  // SC_PCG_ITERS, SC_PCG_RELRES
+};
+
+// Jacobi-preconditioned CG, persistent cooperative kernel.  One iteration:
+//   w = M^-1 V p          (rows)      | barrier
+//   q = S_M p = sum_i theta_ij (p_j - w_i)  and  p.q  (columns)  | barrier
+//   x += a p, r -= a q, z = D^-1 r, r.z, r.r          | barrier
+//   p = z + b p                                         | barrier
+// Dot products are accumulated in double in every precision.
+template <typename T>
+__global__ void __launch_bounds__(kT) pcg_kernel(PcgArgs<T> A) {
+    __shared__ double sh[kT / 32];
+    __shared__ double s_val[3];
+    const unsigned G = gridDim.x;
+    const int n = A.n, m = A.m;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)G * blockDim.x;
+    double *P0 = A.part, *P1 = A.part + G, *P2 = A.part + 2 * G;
+
+    double bb = 0, rz = 0;
+    for (int64_t j = tid; j < n; j += stride) {
+        const T bj = A.b[j];
+        A.x[j] = (T)0;
+        A.r[j] = bj;
+        const T zj = A.Dinv[j] * bj;
+        A.z[j] = zj;
+        A.p[j] = zj;
+        bb += (double)bj * (double)bj;
+        rz += (double)bj * (double)zj;
+    }
+    {
+        double s0 = block_sum(bb, sh), s1 = block_sum(rz, sh);
+        if (threadIdx.x == 0) { P0[blockIdx.x] = s0; P1[blockIdx.x] = s1; }
+    }
+    if (!grid_barrier(A.bar, G, A.err)) return;
+    if (threadIdx.x == 0) {
+        double a0 = 0, a1 = 0;
+        for (unsigned k = 0; k < G; ++k) { a0 += P0[k]; a1 += P1[k]; }
+        s_val[0] = a0; s_val[1] = a1;
+    }
+    __syncthreads();
+    bb = s_val[0];
+    rz = s_val[1];
+    const double tol2 = A.tol * A.tol * bb;
+    int it = 0;
+    double rr = bb;
+    if (bb > 0.0 && rz > 0.0) {
+        for (it = 0; it < A.maxit;) {
+            // w = M^-1 V p
+            for (int64_t i = tid; i < m; i += stride) {
+                T acc = (T)0;
+                for (int e = A.rp[i]; e < A.rp[i + 1]; ++e) acc += A.th[e] * A.p[A.sj[e]];
+                A.w[i] = A.Minv[i] * acc;
+            }
+            if (!grid_barrier(A.bar, G, A.err)) return;
+            double pq = 0;
+            for (int64_t j = tid; j < n; j += stride) {
+                const T pj = A.p[j];
+                T acc = (T)0;
+                for (int k = A.cp[j]; k < A.cp[j + 1]; ++k) acc += A.thc[k] * (pj - A.w[A.crow[k]]);
+                A.q[j] = acc;
+                pq += (double)pj * (double)acc;
+            }
+            {
+                double s0 = block_sum(pq, sh);
+                if (threadIdx.x == 0) P0[blockIdx.x] = s0;
+            }
+            if (!grid_barrier(A.bar, G, A.err)) return;
+            if (threadIdx.x == 0) {
+                double a0 = 0;
+                for (unsigned k = 0; k < G; ++k) a0 += P0[k];
+                s_val[0] = a0;
+            }
+            __syncthreads();
+            pq = s_val[0];
+            if (!(pq > 0.0)) break;  // breakdown (exact zero direction or loss of definiteness)
+            const double alpha = rz / pq;
+            double rzn = 0, rrn = 0;
+            for (int64_t j = tid; j < n; j += stride) {
+                const T xj = A.x[j] + (T)alpha * A.p[j];
+                const T rj = A.r[j] - (T)alpha * A.q[j];
+                const T zj = A.Dinv[j] * rj;
+                A.x[j] = xj;
+                A.r[j] = rj;
+                A.z[j] = zj;
+                rzn += (double)rj * (double)zj;
+                rrn += (double)rj * (double)rj;
+            }
+            {
+                double s1 = block_sum(rzn, sh), s2 = block_sum(rrn, sh);
+                if (threadIdx.x == 0) { P1[blockIdx.x] = s1; P2[blockIdx.x] = s2; }
+            }
+            if (!grid_barrier(A.bar, G, A.err)) return;
+            if (threadIdx.x == 0) {
+                double a1 = 0, a2 = 0;
+                for (unsigned k = 0; k < G; ++k) { a1 += P1[k]; a2 += P2[k]; }
+                s_val[1] = a1; s_val[2] = a2;
+            }
+            __syncthreads();
+            rzn = s_val[1];
+            rr = s_val[2];
+            ++it;
+            if (rr <= tol2 || !(rzn > 0.0)) break;
+            const double beta = rzn / rz;
+            rz = rzn;
+            for (int64_t j = tid; j < n; j += stride) A.p[j] = A.z[j] + (T)beta * A.p[j];
+            if (!grid_barrier(A.bar, G, A.err)) return;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        A.scal[SC_PCG_ITERS] = (double)it;
+        A.scal[SC_PCG_RELRES] = bb > 0 ? sqrt(rr / bb) : 0.0;
+    }
+}
+
+template <typename T>
+Error launch_pcg(Newton &W, const Support &S, const T *th, const T *thc, const T *Minv, const T *Dinv,
+                 const T *b, T *x, T *r, T *z, T *p, T *q, T *w, double tol, int maxit, cudaStream_t st) {
+    int dev;
+    OT_CUDA(cudaGetDevice(&dev));
+    int per_sm = 0;
+    OT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg_kernel<T>, kT, 0));
+    int maxg = std::max(1, per_sm) * W.num_sms;
+    int G = W.pcg_grid > 0 ? W.pcg_grid
+                           : (int)std::max<int64_t>(1, ceil_div(std::max<int64_t>(W.m, W.n), 512));
+    G = std::min(G, std::min(maxg, kMaxPartBlocks / 3));
+    OT_CUDA(cudaMemsetAsync(W.bar, 0, 2 * sizeof(unsigned), st));
+    OT_CUDA(cudaMemsetAsync(W.err, 0, sizeof(int), st));
+    PcgArgs<T> A{W.m, W.n, S.row_ptr, S.j, S.col_ptr, S.col_row, th, thc, Minv, Dinv, b, x, r, z, p, q, w,
+                 W.part, W.bar, W.err, tol, maxit, W.scal};
+    void *args[] = {&A};
+    OT_CUDA(cudaLaunchCooperativeKernel((void *)pcg_kernel<T>, dim3(G), dim3(kT), args, 0, st));
+    OT_LAUNCHED();
+    return ok();
+}
+
+// ------------------------------------------------------------------------ FP64 matvec / refinement
+__global__ void mv_rows_kernel(int m, const int32_t *__restrict__ rp, const int32_t *__restrict__ sj,
+                               const double *__restrict__ th, const double *__restrict__ Minv,
+                               const double *__restrict__ x, double *__restrict__ w) {
+    GRID_STRIDE(i, m) {
+        double acc = 0;
+        for (int e = rp[i]; e < rp[i + 1]; ++e) acc += th[e] * x[sj[e]];
+        w[i] = Minv[i] * acc;
+    }
+}
+
+// res = rhs - S_M x ; partial ||res||^2
+__global__ void mv_cols_res_kernel(int n, const int32_t *__restrict__ cp, const int32_t *__restrict__ crow,
+                                   const double *__restrict__ thc, const double *__restrict__ w,
+                                   const double *__restrict__ x, const double *__restrict__ rhs,
+                                   double *__restrict__ res, double *part) {
+    __shared__ double sh[kT / 32];
+    double sq = 0;
+    GRID_STRIDE(j, n) {
+        const double xj = x[j];
+        double acc = 0;
+        for (int k = cp[j]; k < cp[j + 1]; ++k) acc += thc[k] * (xj - w[crow[k]]);
+        const double r = rhs[j] - acc;
+        res[j] = r;
+        sq += r * r;
+    }
+    put_sum(sq, part, SC_NORM_A, sh);
+}
+
+__global__ void norm_kernel(int n, const double *__restrict__ x, double *part, int slot) {
+    __shared__ double sh[kT / 32];
+    double sq = 0;
+    GRID_STRIDE(j, n) sq += x[j] * x[j];
+    put_sum(sq, part, slot, sh);
+}
+
+__global__ void to_f32_kernel(int n, const double *__restrict__ x, float *__restrict__ y) {
+    GRID_STRIDE(j, n) y[j] = (float)x[j];
+}
+
+__global__ void axpy_f32_kernel(int n, const float *__restrict__ d, double *__restrict__ x) {
+    GRID_STRIDE(j, n) x[j] += (double)d[j];
+}
+
+__global__ void copy_kernel(int n, const double *__restrict__ a, double *__restrict__ b) {
+    GRID_STRIDE(j, n) b[j] = a[j];
+}
+
+// ------------------------------------------------------------------------ back-substitution
+__global__ void du_kernel(int m, const int32_t *__restrict__ rp, const int32_t *__restrict__ sj,
+                          const double *__restrict__ th, const double *__restrict__ Minv,
+                          const double *__restrict__ beta1, const double *__restrict__ dv, double *__restrict__ du) {
+    GRID_STRIDE(i, m) {
+        double acc = 0;
+        for (int e = rp[i]; e < rp[i + 1]; ++e) acc += th[e] * dv[sj[e]];
+        du[i] = Minv[i] * (beta1[i] - acc);
+    }
+}
+
+__global__ void dsdp_kernel(int64_t psi, const int32_t *__restrict__ si, const int32_t *__restrict__ sj,
+                            const double *__restrict__ p, const double *__restrict__ s,
+                            const double *__restrict__ r2, const double *__restrict__ r3,
+                            const double *__restrict__ du, const double *__restrict__ dv,
+                            double *__restrict__ ds, double *__restrict__ dp) {
+    GRID_STRIDE(e, psi) {
+        const double d = (r2 ? r2[e] : 0.0) - du[si[e]] - dv[sj[e]];
+        ds[e] = d;
+        dp[e] = ((r3 ? r3[e] : 0.0) - p[e] * d) / s[e];
+    }
+}
+
+// ------------------------------------------------------------------------ steps etc.
+__global__ void ratio_kernel(int64_t psi, const double *__restrict__ p, const double *__restrict__ dp,
+                             const double *__restrict__ s, const double *__restrict__ ds, double *part) {
+    __shared__ double sh[kT / 32];
+    double rp = INFINITY, rs = INFINITY;
+    GRID_STRIDE(e, psi) {
+        if (dp[e] < 0) rp = fmin(rp, -p[e] / dp[e]);
+        if (ds[e] < 0) rs = fmin(rs, -s[e] / ds[e]);
+    }
+    put_min(rp, part, SC_AP, sh);
+    put_min(rs, part, SC_AS, sh);
+}
+
+__global__ void trial_kernel(int64_t psi, const double *__restrict__ p, const double *__restrict__ dp,
+                             const double *__restrict__ s, const double *__restrict__ ds, double ap, double as,
+                             double *part) {
+    __shared__ double sh[kT / 32];
+    double acc = 0;
+    GRID_STRIDE(e, psi) acc += (p[e] + ap * dp[e]) * (s[e] + as * ds[e]);
+    put_sum(acc, part, SC_MUAFF, sh);
+}
+
+__global__ void corr_r3_kernel(int64_t psi, const double *__restrict__ p, const double *__restrict__ s,
+                               const double *__restrict__ dpa, const double *__restrict__ dsa, double smu,
+                               double *__restrict__ r3) {
+    GRID_STRIDE(e, psi) r3[e] = smu - p[e] * s[e] - (dpa ? dpa[e] * dsa[e] : 0.0);
+}
+
+__global__ void centr_r3_kernel(int64_t psi, const double *__restrict__ p, const double *__restrict__ s,
+                                const double *__restrict__ dp, const double *__restrict__ ds, double tp,
+                                double ts, double lo, double hi, double *__restrict__ r3) {
+    GRID_STRIDE(e, psi) {
+        const double vv = (p[e] + tp * dp[e]) * (s[e] + ts * ds[e]);
+        double t = fmin(fmax(vv, lo), hi) - vv;
+        r3[e] = fmax(t, -hi);
+    }
+}
+
+__global__ void add_kernel(int64_t count, double *__restrict__ x, const double *__restrict__ y) {
+    GRID_STRIDE(k, count) x[k] += y[k];
+}
+
+__global__ void step_entries_kernel(int64_t psi, double *__restrict__ p, double *__restrict__ s,
+                                    const double *__restrict__ dp, const double *__restrict__ ds, double ap,
+                                    double as, double *part) {
+    __shared__ double sh[kT / 32];
+    double acc = 0;
+    GRID_STRIDE(e, psi) {
+        const double pn = p[e] + ap * dp[e], sn = s[e] + as * ds[e];
+        p[e] = pn;
+        s[e] = sn;
+        acc += pn * sn;
+    }
+    put_sum(acc, part, SC_PSNEW, sh);
+}
+
+__global__ void axpy_kernel(int64_t count, double a, const double *__restrict__ y, double *__restrict__ x) {
+    GRID_STRIDE(k, count) x[k] += a * y[k];
+}
+
+template <typename T>
+Error dev_alloc(T **p, int64_t count) {
+    OT_CUDA(cudaMalloc((void **)p, sizeof(T) * (size_t)std::max<int64_t>(count, 1)));
+    return ok();
+}
+
+}  // namespace
+
+// =====================================================================================
+Error newton_alloc(Newton &W, int32_t m, int32_t n, int64_t cap, int num_sms) {
+    W.m = m;
+    W.n = n;
+    W.num_sms = num_sms;
+    OT_TRY(newton_grow(W, cap));
+    for (double **p : {&W.r1a, &W.beta1, &W.M, &W.Minv, &W.du, &W.du2, &W.du3, &W.w64}) OT_TRY(dev_alloc(p, m));
+    for (float **p : {&W.Minv32, &W.w32}) OT_TRY(dev_alloc(p, m));
+    for (double **p : {&W.r1b, &W.beta2, &W.N, &W.Dinv, &W.rhs, &W.dv, &W.dv2, &W.dv3, &W.res64, &W.y64, &W.x64,
+                       &W.r64, &W.z64, &W.p64, &W.q64})
+        OT_TRY(dev_alloc(p, n));
+    for (float **p : {&W.Dinv32, &W.b32, &W.x32, &W.r32, &W.z32, &W.p32, &W.q32}) OT_TRY(dev_alloc(p, n));
+    OT_TRY(dev_alloc(&W.parent, (int64_t)m + n));
+    OT_TRY(dev_alloc(&W.comp_sum, (int64_t)m + n));
+    OT_TRY(dev_alloc(&W.comp_cnt, (int64_t)m + n));
+    OT_TRY(dev_alloc(&W.part, (int64_t)SC_COUNT * kMaxPartBlocks));
+    OT_TRY(dev_alloc(&W.scal, SC_COUNT));
+    OT_TRY(dev_alloc(&W.bar, 2));
+    OT_TRY(dev_alloc(&W.err, 1));
+    return ok();
+}
+
+Error newton_grow(Newton &W, int64_t cap) {
+    if (cap <= W.cap) return ok();
+    double **d[] = {&W.c, &W.theta, &W.excl, &W.r2, &W.r3, &W.g, &W.dp, &W.ds, &W.dp2, &W.ds2, &W.dp3, &W.ds3,
+                    &W.theta_col};
+    for (double **p : d) { if (*p) cudaFree(*p); *p = nullptr; OT_TRY(dev_alloc(p, cap)); }
+    for (float **p : {&W.theta32, &W.theta32_col}) { if (*p) cudaFree(*p); *p = nullptr; OT_TRY(dev_alloc(p, cap)); }
+    if (W.flag) cudaFree(W.flag);
+    W.flag = nullptr;
+    OT_TRY(dev_alloc(&W.flag, cap));
+    W.cap = cap;
+    return ok();
+}
+
+void newton_free(Newton &W) {
+    void *ptrs[] = {W.c, W.theta, W.excl, W.r2, W.r3, W.g, W.dp, W.ds, W.dp2, W.ds2, W.dp3, W.ds3, W.theta32,
+                    W.theta_col, W.theta32_col, W.flag, W.r1a, W.beta1, W.M, W.Minv, W.du, W.du2, W.du3, W.w64,
+                    W.Minv32, W.w32, W.r1b, W.beta2, W.N, W.Dinv, W.rhs, W.dv, W.dv2, W.dv3, W.res64, W.y64,
+                    W.x64, W.r64, W.z64, W.p64, W.q64, W.Dinv32, W.b32, W.x32, W.r32, W.z32, W.p32, W.q32,
+                    W.parent, W.comp_sum, W.comp_cnt, W.part, W.scal, W.bar, W.err};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    W = Newton();
+}
+
+Error support_costs(Newton &W, const CostDev &cd, const Support &S, cudaStream_t st) {
+    if (S.psi == 0) return ok();
+    support_cost_kernel<<<grid_of(S.psi, W.num_sms), kT, 0, st>>>(cd, S.psi, S.i, S.j, W.c);
+    OT_LAUNCHED();
+    return ok();
+}
+
+Error residuals(Newton &W, const Support &S, const double *a_s, const double *b_s, const double *u,
+                const double *v, cudaStream_t st) {
+    const unsigned gm = grid_of(W.m, W.num_sms), gn = grid_of(W.n, W.num_sms), ge = grid_of(S.psi, W.num_sms);
+    res_rows_kernel<<<gm, kT, 0, st>>>(W.m, S.row_ptr, S.p, a_s, W.r1a, W.part);
+    OT_LAUNCHED();
+    res_cols_kernel<<<gn, kT, 0, st>>>(W.n, S.col_ptr, S.col_perm, S.p, b_s, W.r1b, W.part);
+    OT_LAUNCHED();
+    res_entries_kernel<<<ge, kT, 0, st>>>(S.psi, S.i, S.j, W.c, S.p, S.s, u, v, W.r2, W.part);
+    OT_LAUNCHED();
+    Finish f{8,
+             {SC_R1A_SQ, SC_R1A_L1, SC_R1B_SQ, SC_R1B_L1, SC_R2SQ, SC_PS, SC_CP, SC_CSQ},
+             {(int)gm, (int)gm, (int)gn, (int)gn, (int)ge, (int)ge, (int)ge, (int)ge},
+             {0, 0, 0, 0, 0, 0, 0, 0}};
+    OT_TRY(finish(f, W, st));
+    Finish f2{1, {SC_CMAX}, {(int)ge}, {2}};
+    OT_TRY(finish(f2, W, st));
+    return ok();
+}
+
+Error schur_setup(Newton &W, const Support &S, cudaStream_t st) {
+    const unsigned gm = grid_of(W.m, W.num_sms), gn = grid_of(W.n, W.num_sms), ge = grid_of(S.psi, W.num_sms);
+    theta_kernel<<<ge, kT, 0, st>>>(S.psi, S.p, S.s, W.theta, W.theta32);
+    OT_LAUNCHED();
+    theta_rows_kernel<<<gm, kT, 0, st>>>(W.m, S.row_ptr, W.theta, W.excl, W.M, W.Minv, W.Minv32);
+    OT_LAUNCHED();
+    theta_cols_kernel<<<gn, kT, 0, st>>>(W.n, S.col_ptr, S.col_perm, S.col_row, W.theta, W.excl, W.Minv,
+                                         W.theta_col, W.theta32_col, W.N, W.Dinv, W.Dinv32);
+    OT_LAUNCHED();
+    const int nn = W.m + W.n;
+    const unsigned gnn = grid_of(nn, W.num_sms);
+    uf_init_kernel<<<gnn, kT, 0, st>>>(nn, W.parent);
+    OT_LAUNCHED();
+    uf_hook_kernel<<<ge, kT, 0, st>>>(S.psi, W.m, S.i, S.j, W.parent);
+    OT_LAUNCHED();
+    uf_final_kernel<<<gnn, kT, 0, st>>>(nn, W.parent);
+    OT_LAUNCHED();
+    onecomp_kernel<<<gn, kT, 0, st>>>(W.m, W.n, W.parent, W.part);
+    OT_LAUNCHED();
+    Finish f{1, {SC_ONECOMP}, {(int)gn}, {0}};
+    OT_TRY(finish(f, W, st));
+    return ok();
+}
+
+// project x to mean zero on every connected component (reads scal[SC_ONECOMP] on the host)
+static Error project(Newton &W, double *x, bool one_comp, cudaStream_t st) {
+    const unsigned gn = grid_of(W.n, W.num_sms);
+    if (one_comp) {
+        sum_kernel<<<gn, kT, 0, st>>>(W.n, x, W.part, SC_SUM_B);
+        OT_LAUNCHED();
+        Finish f{1, {SC_SUM_B}, {(int)gn}, {0}};
+        OT_TRY(finish(f, W, st));
+        center_kernel<<<gn, kT, 0, st>>>(W.n, x, W.scal, SC_SUM_B);
+        OT_LAUNCHED();
+    } else {
+        const int nn = W.m + W.n;
+        OT_CUDA(cudaMemsetAsync(W.comp_sum, 0, sizeof(double) * nn, st));
+        OT_CUDA(cudaMemsetAsync(W.comp_cnt, 0, sizeof(double) * nn, st));
+        comp_accum_kernel<<<gn, kT, 0, st>>>(W.m, W.n, W.parent, x, W.comp_sum, W.comp_cnt);
+        OT_LAUNCHED();
+        comp_center_kernel<<<gn, kT, 0, st>>>(W.m, W.n, W.parent, x, W.comp_sum, W.comp_cnt);
+        OT_LAUNCHED();
+    }
+    return ok();
+}
+
+Error newton_solve(Newton &W, const Support &S, const Rhs &R, double cg_tol, int max_cg, int precision,
+                   double *du, double *dv, double *ds, double *dp, SolveStats *stats, cudaStream_t st) {
+    const unsigned gm = grid_of(W.m, W.num_sms), gn = grid_of(W.n, W.num_sms), ge = grid_of(S.psi, W.num_sms);
+    g_kernel<<<ge, kT, 0, st>>>(S.psi, W.theta, S.p, R.r2, R.r3, W.g);
+    OT_LAUNCHED();
+    beta1_kernel<<<gm, kT, 0, st>>>(W.m, S.row_ptr, W.g, R.r1a, W.beta1);
+    OT_LAUNCHED();
+    rhs_kernel<<<gn, kT, 0, st>>>(W.n, S.col_ptr, S.col_perm, S.col_row, W.g, W.theta_col, W.Minv, W.beta1, R.r1b,
+                                  W.beta2, W.rhs, W.part);
+    OT_LAUNCHED();
+    double hs[SC_COUNT];
+    OT_CUDA(cudaMemcpyAsync(hs, W.scal, sizeof(hs), cudaMemcpyDeviceToHost, st));
+    OT_CUDA(cudaStreamSynchronize(st));
+    const bool one = hs[SC_ONECOMP] == 0.0;
+    OT_TRY(project(W, W.rhs, one, st));
+
+    SolveStats ss;
+    if (precision == 0) {
+        OT_TRY(launch_pcg<double>(W, S, W.theta, W.theta_col, W.Minv, W.Dinv, W.rhs, W.x64, W.r64, W.z64, W.p64,
+                                  W.q64, W.w64, cg_tol, max_cg, st));
+        OT_CUDA(cudaMemcpyAsync(hs, W.scal, sizeof(hs), cudaMemcpyDeviceToHost, st));
+        OT_CUDA(cudaStreamSynchronize(st));
+        int errv = 0;
+        OT_CUDA(cudaMemcpy(&errv, W.err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (errv) return fail(OT_ERR_TIMEOUT, "pcg: grid barrier wait limit reached");
+        ss.cg_iters = (int)hs[SC_PCG_ITERS];
+        ss.relres = hs[SC_PCG_RELRES];
+        copy_kernel<<<gn, kT, 0, st>>>(W.n, W.x64, dv);
+        OT_LAUNCHED();
+    } else {
+        // FP32 PCG inside FP64 iterative refinement: dv = 0, res = rhs, repeat
+        //   solve S32 d = float(res) ; dv += d ; res = rhs - S64 dv
+        const double inner = std::max(cg_tol, 1e-4);
+        OT_CUDA(cudaMemsetAsync(dv, 0, sizeof(double) * W.n, st));
+        copy_kernel<<<gn, kT, 0, st>>>(W.n, W.rhs, W.res64);
+        OT_LAUNCHED();
+        norm_kernel<<<gn, kT, 0, st>>>(W.n, W.rhs, W.part, SC_NORM_B);
+        OT_LAUNCHED();
+        Finish f{1, {SC_NORM_B}, {(int)gn}, {0}};
+        OT_TRY(finish(f, W, st));
+        OT_CUDA(cudaMemcpyAsync(hs, W.scal, sizeof(hs), cudaMemcpyDeviceToHost, st));
+        OT_CUDA(cudaStreamSynchronize(st));
+        const double nrm0 = std::sqrt(hs[SC_NORM_B]);
+        double nrm = nrm0;
+        int budget = max_cg;
+        for (int ref = 0; ref < 12 && nrm > cg_tol * nrm0 && budget > 0; ++ref) {
+            to_f32_kernel<<<gn, kT, 0, st>>>(W.n, W.res64, W.b32);
+            OT_LAUNCHED();
+            OT_TRY(launch_pcg<float>(W, S, W.theta32, W.theta32_col, W.Minv32, W.Dinv32, W.b32, W.x32, W.r32,
+                                     W.z32, W.p32, W.q32, W.w32, inner, budget, st));
+            axpy_f32_kernel<<<gn, kT, 0, st>>>(W.n, W.x32, dv);
+            OT_LAUNCHED();
+            mv_rows_kernel<<<gm, kT, 0, st>>>(W.m, S.row_ptr, S.j, W.theta, W.Minv, dv, W.w64);
+            OT_LAUNCHED();
+            mv_cols_res_kernel<<<gn, kT, 0, st>>>(W.n, S.col_ptr, S.col_row, W.theta_col, W.w64, dv, W.rhs,
+                                                  W.res64, W.part);
+            OT_LAUNCHED();
+            Finish f2{1, {SC_NORM_A}, {(int)gn}, {0}};
+            OT_TRY(finish(f2, W, st));
+            OT_CUDA(cudaMemcpyAsync(hs, W.scal, sizeof(hs), cudaMemcpyDeviceToHost, st));
+            OT_CUDA(cudaStreamSynchronize(st));
+            int errv = 0;
+            OT_CUDA(cudaMemcpy(&errv, W.err, sizeof(int), cudaMemcpyDeviceToHost));
+            if (errv) return fail(OT_ERR_TIMEOUT, "pcg: grid barrier wait limit reached");
+            const int its = (int)hs[SC_PCG_ITERS];
+            ss.cg_iters += its;
+            budget -= std::max(its, 1);
+            ss.refinements = ref + 1;
+            const double prev = nrm;
+            nrm = std::sqrt(hs[SC_NORM_A]);
+            if (!(nrm < 0.9 * prev)) break;  // refinement stagnates
+        }
+        ss.relres = nrm0 > 0 ? nrm / nrm0 : 0.0;
+    }
+    OT_TRY(project(W, dv, one, st));
+    du_kernel<<<gm, kT, 0, st>>>(W.m, S.row_ptr, S.j, W.theta, W.Minv, W.beta1, dv, du);
+    OT_LAUNCHED();
+    dsdp_kernel<<<ge, kT, 0, st>>>(S.psi, S.i, S.j, S.p, S.s, R.r2, R.r3, du, dv, ds, dp);
+    OT_LAUNCHED();
+    if (stats) *stats = ss;
+    return ok();
+}
+
+Error step_lengths(Newton &W, const Support &S, const double *dp, const double *ds, double, cudaStream_t st) {
+    const unsigned ge = grid_of(S.psi, W.num_sms);
+    ratio_kernel<<<ge, kT, 0, st>>>(S.psi, S.p, dp, S.s, ds, W.part);
+    OT_LAUNCHED();
+    Finish f{2, {SC_AP, SC_AS}, {(int)ge, (int)ge}, {1, 1}};
+    return finish(f, W, st);
+}
+
+Error trial_complementarity(Newton &W, const Support &S, const double *dp, const double *ds, double ap, double as,
+                            cudaStream_t st) {
+    const unsigned ge = grid_of(S.psi, W.num_sms);
+    trial_kernel<<<ge, kT, 0, st>>>(S.psi, S.p, dp, S.s, ds, ap, as, W.part);
+    OT_LAUNCHED();
+    Finish f{1, {SC_MUAFF}, {(int)ge}, {0}};
+    return finish(f, W, st);
+}
+
+Error corrector_r3(Newton &W, const Support &S, double smu, const double *dpa, const double *dsa, cudaStream_t st) {
+    corr_r3_kernel<<<grid_of(S.psi, W.num_sms), kT, 0, st>>>(S.psi, S.p, S.s, dpa, dsa, smu, W.r3);
+    OT_LAUNCHED();
+    return ok();
+}
+
+Error centrality_r3(Newton &W, const Support &S, const double *dp, const double *ds, double tp, double ts,
+                    double lo, double hi, cudaStream_t st) {
+    centr_r3_kernel<<<grid_of(S.psi, W.num_sms), kT, 0, st>>>(S.psi, S.p, S.s, dp, ds, tp, ts, lo, hi, W.r3);
+    OT_LAUNCHED();
+    return ok();
+}
+
+Error add_direction(Newton &W, const Support &S, double *dp, double *ds, double *du, double *dv,
+                    const double *dp2, const double *ds2, const double *du2, const double *dv2, cudaStream_t st) {
+    add_kernel<<<grid_of(S.psi, W.num_sms), kT, 0, st>>>(S.psi, dp, dp2);
+    OT_LAUNCHED();
+    add_kernel<<<grid_of(S.psi, W.num_sms), kT, 0, st>>>(S.psi, ds, ds2);
+    OT_LAUNCHED();
+    add_kernel<<<grid_of(W.m, W.num_sms), kT, 0, st>>>(W.m, du, du2);
+    OT_LAUNCHED();
+    add_kernel<<<grid_of(W.n, W.num_sms), kT, 0, st>>>(W.n, dv, dv2);
+    OT_LAUNCHED();
+    return ok();
+}
+
+Error take_step(Newton &W, Support &S, double *u, double *v, const double *dp, const double *ds, const double *du,
+                const double *dv, double ap, double as, cudaStream_t st) {
+    const unsigned ge = grid_of(S.psi, W.num_sms);
+    step_entries_kernel<<<ge, kT, 0, st>>>(S.psi, S.p, S.s, dp, ds, ap, as, W.part);
+    OT_LAUNCHED();
+    axpy_kernel<<<grid_of(W.m, W.num_sms), kT, 0, st>>>(W.m, as, du, u);
+    OT_LAUNCHED();
+    axpy_kernel<<<grid_of(W.n, W.num_sms), kT, 0, st>>>(W.n, as, dv, v);
+    OT_LAUNCHED();
+    Finish f{1, {SC_PSNEW}, {(int)ge}, {0}};
+    return finish(f, W, st);
+}
+
+Error read_scalars(Newton &W, double *host, cudaStream_t st) {
+    OT_CUDA(cudaMemcpyAsync(host, W.scal, sizeof(double) * SC_COUNT, cudaMemcpyDeviceToHost, st));
+    OT_CUDA(cudaStreamSynchronize(st));
+    return ok();
+}
+
+// ------------------------------------------------------------------------ Mehrotra start
+namespace {
+__global__ void fill_kernel(int64_t count, double val, double *__restrict__ x) {
+    GRID_STRIDE(k, count) x[k] = val;
+}
+__global__ void start_min_kernel(int64_t psi, const double *__restrict__ pt, const double *__restrict__ st_,
+                                 double *part) {
+    __shared__ double sh[kT / 32];
+    double a = INFINITY, b = INFINITY;
+    GRID_STRIDE(e, psi) { a = fmin(a, pt[e]); b = fmin(b, st_[e]); }
+    put_min(a, part, SC_SUM_A, sh);
+    put_min(b, part, SC_SUM_B, sh);
+}
+__global__ void start_shift_kernel(int64_t psi, double *__restrict__ pt, double *__restrict__ st_, double dp,
+                                   double ds, double *part) {
+    __shared__ double sh[kT / 32];
+    double ps = 0, sp = 0, ss = 0;
+    GRID_STRIDE(e, psi) {
+        const double a = pt[e] + dp, b = st_[e] + ds;
+        pt[e] = a;
+        st_[e] = b;
+        ps += a * b;
+        sp += a;
+        ss += b;
+    }
+    put_sum(ps, part, SC_NORM_A, sh);
+    put_sum(sp, part, SC_SUM_A, sh);
+    put_sum(ss, part, SC_SUM_B, sh);
+}
+__global__ void add_const2_kernel(int64_t psi, double *__restrict__ p, double *__restrict__ s, double dp, double ds) {
+    GRID_STRIDE(e, psi) { p[e] += dp; s[e] += ds; }
+}
+}  // namespace
+
+Error mehrotra_start(Newton &W, Support &S, const double *a_s, const double *b_s, double *u, double *v,
+                     int precision, double cg_tol, int max_cg, int *cg_iters, cudaStream_t st) {
+    const unsigned ge = grid_of(S.psi, W.num_sms);
+    fill_kernel<<<ge, kT, 0, st>>>(S.psi, 1.0, S.p);
+    OT_LAUNCHED();
+    fill_kernel<<<ge, kT, 0, st>>>(S.psi, 1.0, S.s);
+    OT_LAUNCHED();
+    OT_TRY(schur_setup(W, S, st));
+    SolveStats s1, s2;
+    // p~ = A^T (A A^T)^+ f : with theta = 1, r1 = f, r2 = r3 = 0 the direction has dp = A^T dy
+    Rhs Rf{a_s, b_s, nullptr, nullptr};
+    OT_TRY(newton_solve(W, S, Rf, cg_tol, max_cg, precision, W.du, W.dv, W.ds, W.dp, &s1, st));
+    // y~ = (A A^T)^+ A c : r2 = c gives dy = y~ and ds = c - A^T y~ = s~
+    Rhs Rc{nullptr, nullptr, W.c, nullptr};
+    OT_TRY(newton_solve(W, S, Rc, cg_tol, max_cg, precision, u, v, W.ds2, W.dp2, &s2, st));
+    if (cg_iters) *cg_iters = s1.cg_iters + s2.cg_iters;
+    // dp holds p~, ds2 holds s~
+    start_min_kernel<<<ge, kT, 0, st>>>(S.psi, W.dp, W.ds2, W.part);
+    OT_LAUNCHED();
+    Finish f{2, {SC_SUM_A, SC_SUM_B}, {(int)ge, (int)ge}, {1, 1}};
+    OT_TRY(finish(f, W, st));
+    double hs[SC_COUNT];
+    OT_TRY(read_scalars(W, hs, st));
+    const double dpv = std::max(-1.5 * hs[SC_SUM_A], 0.0), dsv = std::max(-1.5 * hs[SC_SUM_B], 0.0);
+    start_shift_kernel<<<ge, kT, 0, st>>>(S.psi, W.dp, W.ds2, dpv, dsv, W.part);
+    OT_LAUNCHED();
+    Finish f2{3, {SC_NORM_A, SC_SUM_A, SC_SUM_B}, {(int)ge, (int)ge, (int)ge}, {0, 0, 0}};
+    OT_TRY(finish(f2, W, st));
+    OT_TRY(read_scalars(W, hs, st));
+    const double ps = hs[SC_NORM_A];
+    const double dp2 = 0.5 * ps / hs[SC_SUM_B], ds2 = 0.5 * ps / hs[SC_SUM_A];
+    add_const2_kernel<<<ge, kT, 0, st>>>(S.psi, W.dp, W.ds2, dp2, ds2);
+    OT_LAUNCHED();
+    OT_CUDA(cudaMemcpyAsync(S.p, W.dp, sizeof(double) * S.psi, cudaMemcpyDeviceToDevice, st));
+    OT_CUDA(cudaMemcpyAsync(S.s, W.ds2, sizeof(double) * S.psi, cudaMemcpyDeviceToDevice, st));
+    if (!(ps > 0) || !std::isfinite(dp2) || !std::isfinite(ds2))
+        return fail(OT_ERR_NUMERIC, "initial point: degenerate starting point");
+    return ok();
+}
+
+}  // namespace ot

@@ -1,0 +1,675 @@
+// Solver driver and C ABI: the outer iteration of the hybrid IPM / column-generation method
+// (Section 3.4's commented listing: residuals, mu, sigma and r3, Newton direction, step lengths,
+// update, pricing, support update), with the readings stated in ot_ipm.h.
+#include "newton.cuh"
+#include "pricing.cuh"
+#include "primitives.cuh"
+#include "support.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <vector>
+
+namespace ot {
+
+std::atomic<int64_t> g_launches{0};
+
+static thread_local std::string t_last_error;
+void set_thread_error(const char *msg) { t_last_error = msg ? msg : ""; }
+
+namespace {
+
+constexpr double kBetaMin = 0.1, kBetaMax = 10.0, kAlphaBoost = 0.1, kAcceptGain = 1.01;
+
+// c-transform lower bound (weak duality): ubar_i = min_j (c_ij - v_j); LB = a^T ubar + b^T v.
+__global__ void ctrans_kernel(CostDev cd, const double *__restrict__ v, unsigned long long *__restrict__ rowmin) {
+    const int m = cd.m, n = cd.n;
+    constexpr int CH = 256;
+    const int nch = (n + CH - 1) / CH;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.y + threadIdx.y; t < (int64_t)m * nch;
+         t += (int64_t)gridDim.x * blockDim.y) {
+        const int i = (int)(t / nch), c0 = (int)(t % nch) * CH;
+        double best = INFINITY;
+        for (int j = c0 + threadIdx.x; j < min(n, c0 + CH); j += blockDim.x)
+            best = fmin(best, __dsub_rn(cost_at(cd, i, j), v[j]));
+        best = warp_min(best);
+        if (threadIdx.x == 0) atomicMin(&rowmin[i], f64_key(best));
+    }
+}
+
+__global__ void lb_kernel(int m, int n, const unsigned long long *__restrict__ rowmin, const double *__restrict__ a,
+                          const double *__restrict__ b, const double *__restrict__ v, double *out) {
+    __shared__ double sh[32];
+    double acc = 0;
+    for (int64_t k = threadIdx.x; k < (int64_t)m + n; k += blockDim.x)
+        acc += k < m ? a[k] * f64_from_key(rowmin[k]) : b[k - m] * v[k - m];
+    double r = block_sum(acc, sh);
+    if (threadIdx.x == 0) *out = r;
+}
+
+__global__ void count_below_kernel(const int32_t *__restrict__ cnt, const double *__restrict__ d, double thr,
+                                   int *__restrict__ out) {
+    int c = 0;
+    for (int k = threadIdx.x; k < *cnt; k += blockDim.x) c += d[k] < thr ? 1 : 0;
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+    __shared__ int sh[32];
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+        *out = t;
+    }
+}
+
+__global__ void scale_copy_kernel(int64_t count, const double *__restrict__ x, double f, double *__restrict__ y) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count; k += (int64_t)gridDim.x * blockDim.x)
+        y[k] = x[k] * f;
+}
+
+}  // namespace
+}  // namespace ot
+
+using namespace ot;
+
+struct ot_ipm {
+    int32_t m = 0, n = 0;
+    ot_options opt{};
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    int num_sms = 0;
+    double sigma_f = 1.0, fnorm = 0.0;
+    // device problem
+    double *a_s = nullptr, *b_s = nullptr, *C = nullptr;
+    int32_t *sx = nullptr, *sy = nullptr, *tx = nullptr, *ty = nullptr;
+    int32_t ox = 0, oy = 0;
+    CostDev cd;
+    double *u = nullptr, *v = nullptr;
+    Support S[2];
+    int cur = 0;
+    Newton W;
+    int32_t *pi = nullptr, *pj = nullptr, *pcount = nullptr;
+    double *pd = nullptr;
+    int *pstrong = nullptr;
+    unsigned long long *rowmin = nullptr;
+    double *lbv = nullptr;
+    // iteration state
+    int iter = 0;
+    double mu0 = -1.0;
+    int strong = 1;
+    bool done = false;
+    int64_t cg_total = 0;
+    int direct_total = 0;
+    double last_lb = -INFINITY, last_gap = INFINITY, last_mu = 0.0;
+    std::string err;
+};
+
+namespace {
+
+Error support_alloc(Support &S, int64_t cap, int32_t m, int32_t n) {
+    OT_CUDA(cudaMalloc((void **)&S.i, sizeof(int32_t) * cap));
+    OT_CUDA(cudaMalloc((void **)&S.j, sizeof(int32_t) * cap));
+    OT_CUDA(cudaMalloc((void **)&S.p, sizeof(double) * cap));
+    OT_CUDA(cudaMalloc((void **)&S.s, sizeof(double) * cap));
+    OT_CUDA(cudaMalloc((void **)&S.col_perm, sizeof(int32_t) * cap));
+    OT_CUDA(cudaMalloc((void **)&S.col_row, sizeof(int32_t) * cap));
+    if (!S.row_ptr) OT_CUDA(cudaMalloc((void **)&S.row_ptr, sizeof(int32_t) * ((int64_t)m + 1)));
+    if (!S.col_ptr) OT_CUDA(cudaMalloc((void **)&S.col_ptr, sizeof(int32_t) * ((int64_t)n + 1)));
+    S.cap = cap;
+    return ok();
+}
+
+void support_free_arrays(Support &S) {
+    for (void *p : {(void *)S.i, (void *)S.j, (void *)S.p, (void *)S.s, (void *)S.col_perm, (void *)S.col_row})
+        if (p) cudaFree(p);
+    S.i = S.j = S.col_perm = S.col_row = nullptr;
+    S.p = S.s = nullptr;
+}
+
+void support_free(Support &S) {
+    support_free_arrays(S);
+    if (S.row_ptr) cudaFree(S.row_ptr);
+    if (S.col_ptr) cudaFree(S.col_ptr);
+    S = Support();
+}
+
+// grow both support buffers (and the work arrays) to hold `need` entries
+Error ensure_capacity(ot_ipm *h, int64_t need) {
+    if (need <= h->S[0].cap && need <= h->S[1].cap) return ok();
+    const int64_t cap = std::max<int64_t>(need, (int64_t)(1.5 * std::max(h->S[0].cap, h->S[1].cap)));
+    Support &A = h->S[h->cur];
+    Support &B = h->S[1 - h->cur];
+    // B is scratch: reallocate; A holds data: copy into a fresh allocation
+    support_free_arrays(B);
+    OT_TRY(support_alloc(B, cap, h->m, h->n));
+    Support nA;
+    nA.row_ptr = A.row_ptr;
+    nA.col_ptr = A.col_ptr;
+    OT_TRY(support_alloc(nA, cap, h->m, h->n));
+    const int64_t psi = A.psi;
+    OT_CUDA(cudaMemcpyAsync(nA.i, A.i, sizeof(int32_t) * psi, cudaMemcpyDeviceToDevice, h->st));
+    OT_CUDA(cudaMemcpyAsync(nA.j, A.j, sizeof(int32_t) * psi, cudaMemcpyDeviceToDevice, h->st));
+    OT_CUDA(cudaMemcpyAsync(nA.p, A.p, sizeof(double) * psi, cudaMemcpyDeviceToDevice, h->st));
+    OT_CUDA(cudaMemcpyAsync(nA.s, A.s, sizeof(double) * psi, cudaMemcpyDeviceToDevice, h->st));
+    OT_CUDA(cudaMemcpyAsync(nA.col_perm, A.col_perm, sizeof(int32_t) * psi, cudaMemcpyDeviceToDevice, h->st));
+    OT_CUDA(cudaMemcpyAsync(nA.col_row, A.col_row, sizeof(int32_t) * psi, cudaMemcpyDeviceToDevice, h->st));
+    OT_CUDA(cudaStreamSynchronize(h->st));
+    support_free_arrays(A);
+    nA.psi = psi;
+    A = nA;
+    OT_TRY(newton_grow(h->W, cap));
+    return ok();
+}
+
+Error lower_bound(ot_ipm *h, double *lb) {
+    OT_CUDA(cudaMemsetAsync(h->rowmin, 0xff, sizeof(unsigned long long) * h->m, h->st));
+    dim3 blk(32, 8);
+    const int64_t work = (int64_t)h->m * ceil_div(h->n, 256);
+    ctrans_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(work, 8), 16LL * h->num_sms)), blk, 0,
+                    h->st>>>(h->cd, h->v, h->rowmin);
+    OT_LAUNCHED();
+    lb_kernel<<<1, 1024, 0, h->st>>>(h->m, h->n, h->rowmin, h->a_s, h->b_s, h->v, h->lbv);
+    OT_LAUNCHED();
+    OT_CUDA(cudaMemcpyAsync(lb, h->lbv, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    OT_CUDA(cudaStreamSynchronize(h->st));
+    return ok();
+}
+
+Error price_support(ot_ipm *h, const Support &S, int32_t kmax, int32_t *count, PriceStats *ps) {
+    if (h->cd.kind != OT_COST_SQEUCLID)
+        return fail(OT_ERR_UNSUPPORTED, "pricing: only the squared-Euclidean cost is built");
+    PriceInput in;
+    in.m = h->m; in.n = h->n;
+    in.sx = h->sx; in.sy = h->sy; in.tx = h->tx; in.ty = h->ty;
+    in.u = h->u; in.v = h->v;
+    in.sup_i = S.i; in.sup_j = S.j; in.row_ptr = S.row_ptr; in.psi = S.psi;
+    in.kmax = kmax;
+    in.precision = h->opt.precision;
+    in.origin_x = h->ox; in.origin_y = h->oy;
+    in.num_sms = h->num_sms;
+    OT_TRY(price_topk(in, h->pi, h->pj, h->pd, h->pcount, ps, h->st));
+    OT_CUDA(cudaMemcpyAsync(count, h->pcount, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st));
+    OT_CUDA(cudaStreamSynchronize(h->st));
+    return ok();
+}
+
+double step_of(double ratio, double scale) { return std::min(1.0, scale * ratio); }
+
+Error do_step(ot_ipm *h, ot_iter_info *info) {
+    const ot_options &o = h->opt;
+    cudaStream_t st = h->st;
+    Newton &W = h->W;
+    Support &S = h->S[h->cur];
+    const int32_t m = h->m, n = h->n;
+    ot_iter_info inf{};
+    inf.iter = h->iter;
+    inf.psi = S.psi;
+    double hs[SC_COUNT];
+
+    OT_TRY(residuals(W, S, h->a_s, h->b_s, h->u, h->v, st));
+    OT_TRY(read_scalars(W, hs, st));
+    const double psi = (double)S.psi;
+    const double mu = hs[SC_PS] / psi;
+    const double ctp = hs[SC_CP];
+    const double r1n = std::sqrt(hs[SC_R1A_SQ] + hs[SC_R1B_SQ]);
+    const double crit = std::max({r1n / (1.0 + h->fnorm), std::sqrt(hs[SC_R2SQ]) / (1.0 + std::sqrt(hs[SC_CSQ])),
+                                  psi * mu / (1.0 + std::fabs(ctp))});
+    const double r1_l1 = (hs[SC_R1A_L1] + hs[SC_R1B_L1]) / h->sigma_f;
+    const double cmax_red = hs[SC_CMAX];
+    if (!std::isfinite(mu) || !std::isfinite(crit)) return fail(OT_ERR_NUMERIC, "non-finite mu or residual");
+    if (h->mu0 < 0) h->mu0 = mu;
+    h->last_mu = mu;
+    inf.mu = mu;
+    inf.crit = crit;
+    if (crit < o.tol && r1_l1 <= o.feas_l1 && h->strong == 0) {
+        double lb;
+        OT_TRY(lower_bound(h, &lb));
+        const double gap = (ctp - lb) / (1.0 + std::fabs(ctp));
+        h->last_lb = lb;
+        h->last_gap = gap;
+        if (gap <= o.tol) {
+            h->done = true;
+            inf.done = 1;
+            if (info) *info = inf;
+            return ok();
+        }
+    }
+    if (h->iter >= o.max_iter) {
+        if (info) *info = inf;
+        return fail(OT_ERR_MAXITER, "iteration limit reached");
+    }
+
+    // ---- Newton direction: Mehrotra predictor-corrector + centrality correctors
+    OT_TRY(schur_setup(W, S, st));
+    int cg = 0;
+    SolveStats ss;
+    OT_TRY(corrector_r3(W, S, 0.0, nullptr, nullptr, st));  // r3 = -p s
+    Rhs R{W.r1a, W.r1b, W.r2, W.r3};
+    OT_TRY(newton_solve(W, S, R, o.cg_tol_pred, o.max_cg, o.precision, W.du, W.dv, W.ds, W.dp, &ss, st));
+    cg += ss.cg_iters;
+    OT_TRY(step_lengths(W, S, W.dp, W.ds, o.step_scale, st));
+    OT_TRY(read_scalars(W, hs, st));
+    const double apa = step_of(hs[SC_AP], o.step_scale), asa = step_of(hs[SC_AS], o.step_scale);
+    OT_TRY(trial_complementarity(W, S, W.dp, W.ds, apa, asa, st));
+    OT_TRY(read_scalars(W, hs, st));
+    const double mu_aff = hs[SC_MUAFF] / psi;
+    const double sigma = std::min(1.0, std::max(0.0, std::pow(mu_aff / mu, 3.0)));
+    OT_TRY(corrector_r3(W, S, sigma * mu, W.dp, W.ds, st));
+    double *d_du = W.du2, *d_dv = W.dv2, *d_ds = W.ds2, *d_dp = W.dp2;  // current direction
+    double *c_du = W.du3, *c_dv = W.dv3, *c_ds = W.ds3, *c_dp = W.dp3;  // corrector scratch
+    OT_TRY(newton_solve(W, S, R, o.cg_tol_pred, o.max_cg, o.precision, d_du, d_dv, d_ds, d_dp, &ss, st));
+    cg += ss.cg_iters;
+    OT_TRY(step_lengths(W, S, d_dp, d_ds, o.step_scale, st));
+    OT_TRY(read_scalars(W, hs, st));
+    double ap = step_of(hs[SC_AP], o.step_scale), as = step_of(hs[SC_AS], o.step_scale);
+    int ncorr = 0;
+    for (int k = 0; k < o.max_corr; ++k) {
+        if (std::min(ap, as) >= 1.0) break;
+        const double tp = std::min(1.0, ap + kAlphaBoost), ts = std::min(1.0, as + kAlphaBoost);
+        OT_TRY(centrality_r3(W, S, d_dp, d_ds, tp, ts, kBetaMin * sigma * mu, kBetaMax * sigma * mu, st));
+        Rhs Rc{nullptr, nullptr, nullptr, W.r3};
+        OT_TRY(newton_solve(W, S, Rc, o.cg_tol_corr, o.max_cg, o.precision, c_du, c_dv, c_ds, c_dp, &ss, st));
+        cg += ss.cg_iters;
+        OT_TRY(add_direction(W, S, c_dp, c_ds, c_du, c_dv, d_dp, d_ds, d_du, d_dv, st));
+        OT_TRY(step_lengths(W, S, c_dp, c_ds, o.step_scale, st));
+        OT_TRY(read_scalars(W, hs, st));
+        const double ap2 = step_of(hs[SC_AP], o.step_scale), as2 = step_of(hs[SC_AS], o.step_scale);
+        if (std::min(ap2, as2) >= kAcceptGain * std::min(ap, as)) {
+            std::swap(d_du, c_du); std::swap(d_dv, c_dv); std::swap(d_ds, c_ds); std::swap(d_dp, c_dp);
+            ap = ap2;
+            as = as2;
+            ++ncorr;
+        } else {
+            break;
+        }
+    }
+    OT_TRY(take_step(W, S, h->u, h->v, d_dp, d_ds, d_du, d_dv, ap, as, st));
+    OT_TRY(read_scalars(W, hs, st));
+    const double mu_new = hs[SC_PSNEW] / psi;
+    if (!std::isfinite(mu_new) || !(mu_new > 0)) return fail(OT_ERR_NUMERIC, "non-finite or non-positive mu");
+
+    // ---- pricing (Section 3.4) and support update (Section 3.2)
+    const int32_t kadd = o.add_max > 0 ? o.add_max : m;
+    int32_t added = 0;
+    PriceStats ps;
+    OT_TRY(price_support(h, S, kadd, &added, &ps));
+    {
+        count_below_kernel<<<1, 256, 0, st>>>(h->pcount, h->pd, -o.tol * (1.0 + cmax_red), h->pstrong);
+        OT_LAUNCHED();
+        OT_CUDA(cudaMemcpyAsync(&h->strong, h->pstrong, sizeof(int), cudaMemcpyDeviceToHost, st));
+    }
+    // grow first: growing reallocates the work arrays, the removal flags included
+    OT_TRY(ensure_capacity(h, S.psi + added));
+    int64_t removed = 0;
+    const bool removing = mu_new <= o.rm_mu_frac * h->mu0;
+    if (removing) OT_TRY(removal_flags(S, m, n, h->a_s, h->b_s, o.rm_p_frac, m, W.flag, &removed, st));
+    Support &S0 = h->S[h->cur];
+    Support &T = h->S[1 - h->cur];
+    OT_TRY(merge_support(S0, removing ? W.flag : nullptr, h->pi, h->pj, added, std::sqrt(mu_new), m, n, T, st));
+    h->cur = 1 - h->cur;
+    OT_TRY(support_costs(W, h->cd, T, st));
+    OT_CUDA(cudaStreamSynchronize(st));
+
+    h->iter++;
+    h->cg_total += cg;
+    inf.alpha_p = ap;
+    inf.alpha_s = as;
+    inf.sigma = sigma;
+    inf.ncorr = ncorr;
+    inf.cg_iters = cg;
+    inf.added = added;
+    inf.removed = removed;
+    if (o.verbose)
+        fprintf(stderr, "it %3d psi %8lld mu %.3e crit %.3e ap %.3f as %.3f sig %.2e corr %d cg %d +%d -%lld\n",
+                inf.iter, (long long)inf.psi, mu, crit, ap, as, sigma, ncorr, cg, added, (long long)removed);
+    if (info) *info = inf;
+    return ok();
+}
+
+int record(ot_ipm *h, const Error &e) {
+    if (e.code != OT_OK) h->err = e.msg;
+    return e.code;
+}
+
+Error create_impl(const ot_problem *P, const ot_options *O, ot_ipm *h) {
+    if (!P || P->m <= 0 || P->n <= 0 || !P->a || !P->b) return fail(OT_ERR_ARG, "problem: sizes or masses missing");
+    const int32_t m = P->m, n = P->n;
+    if ((uint64_t)m * (uint64_t)n > (1ull << 32)) return fail(OT_ERR_ARG, "problem: m*n exceeds 2^32");
+    if (O) h->opt = *O; else ot_options_default(&h->opt);
+    ot_options &o = h->opt;
+    if (!(o.tol > 0) || o.max_iter < 0 || o.max_cg <= 0 || o.max_corr < 0 || !(o.step_scale > 0 && o.step_scale < 1) ||
+        (o.precision != 0 && o.precision != 1))
+        return fail(OT_ERR_ARG, "options: out of range");
+    double sa = 0, sb = 0;
+    for (int i = 0; i < m; ++i) {
+        if (!(P->a[i] >= 0) || !std::isfinite(P->a[i])) return fail(OT_ERR_ARG, "problem: negative or non-finite mass in a");
+        sa += P->a[i];
+    }
+    for (int j = 0; j < n; ++j) {
+        if (!(P->b[j] >= 0) || !std::isfinite(P->b[j])) return fail(OT_ERR_ARG, "problem: negative or non-finite mass in b");
+        sb += P->b[j];
+    }
+    if (!(sa > 0) || std::fabs(sa - sb) > 1e-12 * sa) return fail(OT_ERR_ARG, "problem: sum(a) != sum(b)");
+    if (P->cost < 0 || P->cost > OT_COST_DENSE) return fail(OT_ERR_ARG, "problem: unknown cost kind");
+    if (P->cost == OT_COST_DENSE && !P->C) return fail(OT_ERR_ARG, "problem: dense cost without C");
+    if (P->cost != OT_COST_SQEUCLID)
+        return fail(OT_ERR_UNSUPPORTED, "problem: only the squared-Euclidean cost is built");
+    h->m = m;
+    h->n = n;
+    h->sigma_f = (double)m / sa;
+    std::vector<double> as(m), bs(n);
+    double f2 = 0;
+    for (int i = 0; i < m; ++i) { as[i] = P->a[i] * h->sigma_f; f2 += as[i] * as[i]; }
+    for (int j = 0; j < n; ++j) { bs[j] = P->b[j] * (sa / sb) * h->sigma_f; f2 += bs[j] * bs[j]; }
+    h->fnorm = std::sqrt(f2);
+    // coordinates
+    std::vector<int32_t> hx(m), hy(m), gx(n), gy(n);
+    const bool have = P->src_x && P->src_y && P->dst_x && P->dst_y;
+    if (!have && (P->src_w <= 0 || P->dst_w <= 0 || m % P->src_w || n % P->dst_w))
+        return fail(OT_ERR_ARG, "problem: no coordinates and no valid grid widths");
+    for (int i = 0; i < m; ++i) { hx[i] = have ? P->src_x[i] : i % P->src_w; hy[i] = have ? P->src_y[i] : i / P->src_w; }
+    for (int j = 0; j < n; ++j) { gx[j] = have ? P->dst_x[j] : j % P->dst_w; gy[j] = have ? P->dst_y[j] : j / P->dst_w; }
+    int xmin = INT32_MAX, xmax = INT32_MIN, ymin = INT32_MAX, ymax = INT32_MIN;
+    for (int i = 0; i < m; ++i) { xmin = std::min(xmin, hx[i]); xmax = std::max(xmax, hx[i]); ymin = std::min(ymin, hy[i]); ymax = std::max(ymax, hy[i]); }
+    for (int j = 0; j < n; ++j) { xmin = std::min(xmin, gx[j]); xmax = std::max(xmax, gx[j]); ymin = std::min(ymin, gy[j]); ymax = std::max(ymax, gy[j]); }
+    if (xmin <= -(1 << 14) || ymin <= -(1 << 14) || xmax >= (1 << 14) || ymax >= (1 << 14))
+        return fail(OT_ERR_ARG, "problem: coordinates must satisfy |x|, |y| < 2^14");
+    h->ox = (int32_t)(((int64_t)xmin + xmax) / 2);
+    h->oy = (int32_t)(((int64_t)ymin + ymax) / 2);
+
+    int dev;
+    OT_CUDA(cudaGetDevice(&dev));
+    OT_CUDA(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev));
+    {
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t thr = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+    }
+    if (o.stream) {
+        h->st = (cudaStream_t)o.stream;
+    } else {
+        OT_CUDA(cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking));
+        h->own_stream = true;
+    }
+    cudaStream_t st = h->st;
+    OT_CUDA(cudaMalloc((void **)&h->a_s, sizeof(double) * m));
+    OT_CUDA(cudaMalloc((void **)&h->b_s, sizeof(double) * n));
+    OT_CUDA(cudaMalloc((void **)&h->u, sizeof(double) * m));
+    OT_CUDA(cudaMalloc((void **)&h->v, sizeof(double) * n));
+    OT_CUDA(cudaMalloc((void **)&h->sx, sizeof(int32_t) * m));
+    OT_CUDA(cudaMalloc((void **)&h->sy, sizeof(int32_t) * m));
+    OT_CUDA(cudaMalloc((void **)&h->tx, sizeof(int32_t) * n));
+    OT_CUDA(cudaMalloc((void **)&h->ty, sizeof(int32_t) * n));
+    OT_CUDA(cudaMalloc((void **)&h->pi, sizeof(int32_t) * std::max(m, 1)));
+    OT_CUDA(cudaMalloc((void **)&h->pj, sizeof(int32_t) * std::max(m, 1)));
+    OT_CUDA(cudaMalloc((void **)&h->pd, sizeof(double) * std::max(m, 1)));
+    OT_CUDA(cudaMalloc((void **)&h->pcount, sizeof(int32_t)));
+    OT_CUDA(cudaMalloc((void **)&h->pstrong, sizeof(int)));
+    OT_CUDA(cudaMalloc((void **)&h->rowmin, sizeof(unsigned long long) * m));
+    OT_CUDA(cudaMalloc((void **)&h->lbv, sizeof(double)));
+    if (o.add_max > m) o.add_max = m;
+    OT_CUDA(cudaMemcpyAsync(h->a_s, as.data(), sizeof(double) * m, cudaMemcpyHostToDevice, st));
+    OT_CUDA(cudaMemcpyAsync(h->b_s, bs.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
+    OT_CUDA(cudaMemcpyAsync(h->sx, hx.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, st));
+    OT_CUDA(cudaMemcpyAsync(h->sy, hy.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, st));
+    OT_CUDA(cudaMemcpyAsync(h->tx, gx.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
+    OT_CUDA(cudaMemcpyAsync(h->ty, gy.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
+    h->cd.kind = P->cost;
+    h->cd.m = m;
+    h->cd.n = n;
+    h->cd.sx = h->sx; h->cd.sy = h->sy; h->cd.tx = h->tx; h->cd.ty = h->ty;
+
+    // initial support (Section 3.2 end) and Mehrotra's starting point
+    int32_t *ii = nullptr, *jj = nullptr;
+    int64_t psi0 = 0;
+    OT_TRY(initial_support(h->cd, o.init_cost, &ii, &jj, &psi0, st));
+    const int64_t cap = std::max<int64_t>(2 * psi0, psi0 + 8LL * m);
+    Error e = support_alloc(h->S[0], cap, m, n);
+    if (e.code == OT_OK) e = support_alloc(h->S[1], cap, m, n);
+    if (e.code == OT_OK) {
+        cudaMemcpyAsync(h->S[0].i, ii, sizeof(int32_t) * psi0, cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(h->S[0].j, jj, sizeof(int32_t) * psi0, cudaMemcpyDeviceToDevice, st);
+        cudaStreamSynchronize(st);
+    }
+    cudaFree(ii);
+    cudaFree(jj);
+    OT_TRY(e);
+    h->S[0].psi = psi0;
+    OT_TRY(rebuild_views(h->S[0], m, n, st));
+    OT_TRY(newton_alloc(h->W, m, n, cap, h->num_sms));
+    OT_TRY(support_costs(h->W, h->cd, h->S[0], st));
+    int cgs = 0;
+    OT_TRY(mehrotra_start(h->W, h->S[0], h->a_s, h->b_s, h->u, h->v, o.precision, o.cg_tol_pred, 20 * o.max_cg,
+                          &cgs, st));
+    h->cg_total += cgs;
+    OT_CUDA(cudaStreamSynchronize(st));
+    return ok();
+}
+
+}  // namespace
+
+// ======================================================================== C ABI
+extern "C" {
+
+void ot_options_default(ot_options *o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->tol = 1e-6;
+    o->feas_l1 = 1e-8;
+    o->cg_tol_pred = 1e-6;
+    o->cg_tol_corr = 1e-3;
+    o->max_iter = 200;
+    o->max_cg = 1000;
+    o->max_corr = 3;
+    o->step_scale = 0.995;
+    o->precision = 1;
+    o->linear_solver = 1;
+    o->init_cost = 2.0;
+    o->rm_mu_frac = 1e-3;
+    o->rm_p_frac = 1e-3;
+    o->add_max = 0;
+    o->verbose = 0;
+    o->stream = nullptr;
+}
+
+int ot_ipm_create(const ot_problem *prob, const ot_options *opt, ot_ipm_t **out) {
+    if (!out) { set_thread_error("ot_ipm_create: out is NULL"); return OT_ERR_ARG; }
+    *out = nullptr;
+    ot_ipm *h = new (std::nothrow) ot_ipm();
+    if (!h) { set_thread_error("ot_ipm_create: host allocation failed"); return OT_ERR_OOM; }
+    Error e = create_impl(prob, opt, h);
+    if (e.code != OT_OK) {
+        set_thread_error(e.msg.c_str());
+        ot_ipm_destroy(h);
+        return e.code;
+    }
+    *out = h;
+    return OT_OK;
+}
+
+int ot_ipm_step(ot_ipm_t *h, ot_iter_info *info) {
+    if (!h) return OT_ERR_ARG;
+    if (h->done) {
+        if (info) { memset(info, 0, sizeof(*info)); info->done = 1; info->iter = h->iter; }
+        return OT_OK;
+    }
+    return record(h, do_step(h, info));
+}
+
+int ot_ipm_solve(ot_ipm_t *h, ot_result *res) {
+    if (!h) return OT_ERR_ARG;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, h->st);
+    int rc = OT_OK;
+    ot_iter_info inf{};
+    while (!h->done) {
+        rc = ot_ipm_step(h, &inf);
+        if (rc != OT_OK) break;
+    }
+    cudaEventRecord(e1, h->st);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (res) {
+        memset(res, 0, sizeof(*res));
+        res->status = rc;
+        double hs[SC_COUNT];
+        Error e = residuals(h->W, h->S[h->cur], h->a_s, h->b_s, h->u, h->v, h->st);
+        if (e.code == OT_OK) e = read_scalars(h->W, hs, h->st);
+        if (e.code == OT_OK) {
+            double lb = h->last_lb;
+            if (!h->done) {
+                Error e2 = lower_bound(h, &lb);
+                if (e2.code != OT_OK) lb = NAN;
+            }
+            const double ctp = hs[SC_CP];
+            res->obj = ctp / h->sigma_f;
+            res->lower_bound = lb / h->sigma_f;
+            res->rel_gap = (ctp - lb) / (1.0 + std::fabs(ctp));
+            res->r1_l1 = (hs[SC_R1A_L1] + hs[SC_R1B_L1]) / h->sigma_f;
+            res->mu = hs[SC_PS] / (double)h->S[h->cur].psi;
+        } else if (rc == OT_OK) {
+            rc = record(h, e);
+            res->status = rc;
+        }
+        res->iters = h->iter;
+        res->cg_iters = (int32_t)h->cg_total;
+        res->direct_iters = h->direct_total;
+        res->psi = h->S[h->cur].psi;
+        res->seconds = ms * 1e-3;
+    }
+    return rc;
+}
+
+int ot_ipm_get_solution(ot_ipm_t *h, int32_t *i, int32_t *j, double *p, int64_t cap, int64_t *nnz, double *u,
+                        double *v) {
+    if (!h || !nnz) return OT_ERR_ARG;
+    const Support &S = h->S[h->cur];
+    *nnz = S.psi;
+    if (cap < S.psi) { h->err = "ot_ipm_get_solution: buffer too small"; return OT_ERR_BUF_TOO_SMALL; }
+    if ((!i || !j || !p) && S.psi > 0) return OT_ERR_ARG;
+    Error e = ok();
+    double *tmp = nullptr;
+    if (cudaMalloc((void **)&tmp, sizeof(double) * std::max<int64_t>(S.psi, 1)) != cudaSuccess) return OT_ERR_OOM;
+    scale_copy_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(S.psi, 256), 1024)), 256, 0, h->st>>>(
+        S.psi, S.p, 1.0 / h->sigma_f, tmp);
+    g_launches.fetch_add(1);
+    cudaMemcpyAsync(i, S.i, sizeof(int32_t) * S.psi, cudaMemcpyDeviceToHost, h->st);
+    cudaMemcpyAsync(j, S.j, sizeof(int32_t) * S.psi, cudaMemcpyDeviceToHost, h->st);
+    cudaMemcpyAsync(p, tmp, sizeof(double) * S.psi, cudaMemcpyDeviceToHost, h->st);
+    if (u) cudaMemcpyAsync(u, h->u, sizeof(double) * h->m, cudaMemcpyDeviceToHost, h->st);
+    if (v) cudaMemcpyAsync(v, h->v, sizeof(double) * h->n, cudaMemcpyDeviceToHost, h->st);
+    cudaError_t ce = cudaStreamSynchronize(h->st);
+    cudaFree(tmp);
+    if (ce != cudaSuccess) return record(h, fail(OT_ERR_CUDA, cudaGetErrorString(ce)));
+    return record(h, e);
+}
+
+int ot_ipm_get_state(ot_ipm_t *h, int32_t *i, int32_t *j, double *p, double *s, int64_t cap, int64_t *psi,
+                     double *u, double *v) {
+    if (!h || !psi) return OT_ERR_ARG;
+    const Support &S = h->S[h->cur];
+    *psi = S.psi;
+    if (cap < S.psi) { h->err = "ot_ipm_get_state: buffer too small"; return OT_ERR_BUF_TOO_SMALL; }
+    if (i) cudaMemcpyAsync(i, S.i, sizeof(int32_t) * S.psi, cudaMemcpyDeviceToHost, h->st);
+    if (j) cudaMemcpyAsync(j, S.j, sizeof(int32_t) * S.psi, cudaMemcpyDeviceToHost, h->st);
+    if (p) cudaMemcpyAsync(p, S.p, sizeof(double) * S.psi, cudaMemcpyDeviceToHost, h->st);
+    if (s) cudaMemcpyAsync(s, S.s, sizeof(double) * S.psi, cudaMemcpyDeviceToHost, h->st);
+    if (u) cudaMemcpyAsync(u, h->u, sizeof(double) * h->m, cudaMemcpyDeviceToHost, h->st);
+    if (v) cudaMemcpyAsync(v, h->v, sizeof(double) * h->n, cudaMemcpyDeviceToHost, h->st);
+    cudaError_t ce = cudaStreamSynchronize(h->st);
+    if (ce != cudaSuccess) return record(h, fail(OT_ERR_CUDA, cudaGetErrorString(ce)));
+    return OT_OK;
+}
+
+int ot_ipm_set_state(ot_ipm_t *h, const int32_t *i, const int32_t *j, const double *p, const double *s, int64_t psi,
+                     const double *u, const double *v, int32_t reset_mu0) {
+    if (!h || psi <= 0 || !i || !j || !p || !s || !u || !v) return OT_ERR_ARG;
+    for (int64_t e = 0; e < psi; ++e) {
+        if (i[e] < 0 || i[e] >= h->m || j[e] < 0 || j[e] >= h->n || !(p[e] > 0) || !(s[e] > 0))
+            return record(h, fail(OT_ERR_ARG, "ot_ipm_set_state: entry out of range or nonpositive"));
+        if (e > 0 && ((int64_t)i[e] * h->n + j[e]) <= ((int64_t)i[e - 1] * h->n + j[e - 1]))
+            return record(h, fail(OT_ERR_ARG, "ot_ipm_set_state: pairs not sorted by (i, j) or repeated"));
+    }
+    Error e = ensure_capacity(h, psi);
+    if (e.code != OT_OK) return record(h, e);
+    Support &S = h->S[h->cur];
+    cudaMemcpyAsync(S.i, i, sizeof(int32_t) * psi, cudaMemcpyHostToDevice, h->st);
+    cudaMemcpyAsync(S.j, j, sizeof(int32_t) * psi, cudaMemcpyHostToDevice, h->st);
+    cudaMemcpyAsync(S.p, p, sizeof(double) * psi, cudaMemcpyHostToDevice, h->st);
+    cudaMemcpyAsync(S.s, s, sizeof(double) * psi, cudaMemcpyHostToDevice, h->st);
+    cudaMemcpyAsync(h->u, u, sizeof(double) * h->m, cudaMemcpyHostToDevice, h->st);
+    cudaMemcpyAsync(h->v, v, sizeof(double) * h->n, cudaMemcpyHostToDevice, h->st);
+    S.psi = psi;
+    e = rebuild_views(S, h->m, h->n, h->st);
+    if (e.code == OT_OK) e = support_costs(h->W, h->cd, S, h->st);
+    cudaError_t ce = cudaStreamSynchronize(h->st);
+    if (e.code == OT_OK && ce != cudaSuccess) e = fail(OT_ERR_CUDA, cudaGetErrorString(ce));
+    if (reset_mu0) h->mu0 = -1.0;
+    h->done = false;
+    h->strong = 1;
+    return record(h, e);
+}
+
+double ot_ipm_mass_scale(const ot_ipm_t *h) { return h ? h->sigma_f : 0.0; }
+
+void ot_ipm_destroy(ot_ipm_t *h) {
+    if (!h) return;
+    if (h->st) cudaStreamSynchronize(h->st);
+    support_free(h->S[0]);
+    support_free(h->S[1]);
+    newton_free(h->W);
+    void *ptrs[] = {h->a_s, h->b_s, h->C, h->sx, h->sy, h->tx, h->ty, h->u, h->v, h->pi, h->pj, h->pd,
+                    h->pcount, h->pstrong, h->rowmin, h->lbv};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (h->own_stream && h->st) cudaStreamDestroy(h->st);
+    delete h;
+}
+
+const char *ot_ipm_last_error(const ot_ipm_t *h) { return h ? h->err.c_str() : "null handle"; }
+
+const char *ot_last_error(void) { return t_last_error.c_str(); }
+
+int ot_price_topk(int32_t m, int32_t n, const int32_t *sx, const int32_t *sy, const int32_t *tx, const int32_t *ty,
+                  const double *u, const double *v, const int32_t *sup_i, const int32_t *sup_j, int64_t psi,
+                  int32_t kmax, int32_t precision, int32_t *out_i, int32_t *out_j, double *out_d,
+                  int32_t *out_count, void *stream) {
+    if (m <= 0 || n <= 0 || kmax < 0 || psi < 0 || !sx || !sy || !tx || !ty || !u || !v || !out_i || !out_j ||
+        !out_count || (psi > 0 && (!sup_i || !sup_j)) || (precision != 0 && precision != 1)) {
+        set_thread_error("ot_price_topk: invalid argument");
+        return OT_ERR_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    PriceInput in;
+    in.m = m; in.n = n;
+    in.sx = sx; in.sy = sy; in.tx = tx; in.ty = ty;
+    in.u = u; in.v = v;
+    in.sup_i = sup_i; in.sup_j = sup_j; in.psi = psi;
+    in.kmax = kmax;
+    in.precision = precision;
+    Error e = coord_origin(m, n, sx, sy, tx, ty, &in.origin_x, &in.origin_y, st);
+    if (e.code == OT_OK) e = price_topk(in, out_i, out_j, out_d, out_count, nullptr, st);
+    if (e.code != OT_OK) set_thread_error(e.msg.c_str());
+    return e.code;
+}
+
+int64_t ot_kernel_launches(void) { return g_launches.load(); }
+
+int ot_abi_struct_sizes(int64_t *out, int32_t count) {
+    if (!out || count < 4) return OT_ERR_ARG;
+    out[0] = sizeof(ot_problem);
+    out[1] = sizeof(ot_options);
+    out[2] = sizeof(ot_iter_info);
+    out[3] = sizeof(ot_result);
+    return 4;
+}
+
+}  // extern "C"

@@ -1,0 +1,94 @@
+"""Pricing parity (Section 3.4 + Section 3.2 selection): the CUDA path against the oracle's
+exact rule, bit for bit -- same pairs, same order, same float64 reduced costs."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from oracle import costs, pricing
+from tests import gpu_util as U
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _run(sx, sy, tx, ty, u, v, si, sj, kmax, precision):
+    from paper_2206_11009_gb300 import price_topk
+    T = U.cuda_tensors(sx, sy, tx, ty, u, v, si, sj)
+    gi, gj, gd = price_topk(*T, kmax=kmax, precision=precision)
+    return gi.cpu().numpy(), gj.cpu().numpy(), gd.cpu().numpy()
+
+
+def _oracle(sx, sy, tx, ty, u, v, si, sj, kmax):
+    c = costs.Cost.points(sx, sy, tx, ty, "sqeuclid")
+    return pricing.select(c, u, v, si.astype(np.int64), sj.astype(np.int64), kmax)
+
+
+def _check(sx, sy, tx, ty, u, v, si, sj, kmax, precision):
+    gi, gj, gd = _run(sx, sy, tx, ty, u, v, si, sj, kmax, precision)
+    oi, oj, od = _oracle(sx, sy, tx, ty, u, v, si, sj, kmax)
+    assert len(gi) == len(oi)
+    assert np.array_equal(gi, oi) and np.array_equal(gj, oj)
+    assert np.array_equal(gd, od)           # bit-exact float64 reduced costs
+    return len(oi)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("shape", [((13, 11), (9, 17), (-3, 5)), ((16, 16), (16, 16), (0, 0)),
+                                   ((37, 29), (31, 41), (100, -50)), ((1, 1), (1, 7), (0, 0))])
+@pytest.mark.parametrize("kmax_mode", ["one", "m", "huge"])
+def test_ragged_shapes_banded_duals(precision, shape, kmax_mode):
+    (ws, hs), (wt, ht), (x0, y0) = shape
+    sx, sy = U.rect_coords(ws, hs, x0, y0)
+    tx, ty = U.rect_coords(wt, ht, x0 + 2, y0 - 1)
+    m, n = len(sx), len(tx)
+    u, v = U.banded_duals(sx, sy, tx, ty, seed=ws * 7 + wt, amp=6.0, noise=3.0)
+    si, sj = U.random_support(m, n, 0.05, seed=m + n)
+    kmax = {"one": 1, "m": m, "huge": m * n}[kmax_mode]
+    _check(sx, sy, tx, ty, u, v, si, sj, kmax, precision)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_exact_ties_broken_by_jlin(precision):
+    # integer duals: many reduced costs are exactly equal; order must follow jlin = i + j*m
+    sx, sy = U.rect_coords(12, 12)
+    u = np.floor(U.banded_duals(sx, sy, sx, sy, 3, 4.0, 0.0)[0])
+    v = -u + 1.0
+    si = np.zeros(0, np.int32)
+    n = _check(sx, sy, sx, sy, u, v, si, si, 100, precision)
+    assert n == 100
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_degenerate_cases(precision):
+    sx, sy = U.rect_coords(10, 10)
+    m = len(sx)
+    # no negative reduced cost at all
+    u = np.zeros(m)
+    v = np.zeros(m)
+    assert _check(sx, sy, sx, sy, u, v, np.zeros(0, np.int32), np.zeros(0, np.int32), m, precision) == 0
+    # kmax = 0
+    u = np.full(m, 50.0)
+    assert _check(sx, sy, sx, sy, u, v, np.zeros(0, np.int32), np.zeros(0, np.int32), 0, precision) == 0
+    # every pair negative, support = all pairs: nothing may be selected
+    si, sj = U.random_support(m, m, 2.0, 1)
+    assert _check(sx, sy, sx, sy, u, v, si, sj, m, precision) == 0
+    # every pair negative (d = c - 250), empty support, kmax < count: the 7 cheapest pairs,
+    # all with c = 0 (ties at d = -250) in jlin order
+    assert _check(sx, sy, sx, sy, u, v + 200.0, np.zeros(0, np.int32), np.zeros(0, np.int32), 7, precision) == 7
+
+
+@pytest.mark.parametrize("k", [64, 128])
+def test_full_size_configs(k):
+    """Configs at full size (64x64: 16.8M pairs, 128x128: 268M pairs), FP32 scan + FP64 recheck,
+    kmax = m, support = the initial 3x3 neighbourhood, banded duals of the IPM's structure."""
+    sx, sy = U.rect_coords(k, k)
+    u, v = U.banded_duals(sx, sy, sx, sy, seed=k, amp=k / 8.0, noise=2.0)
+    si, sj = U.neighbourhood_support(sx, sy, sx, sy)
+    n = _check(sx, sy, sx, sy, u, v, si, sj, k * k, 1)
+    assert n > 0
