@@ -1,0 +1,57 @@
+// Direct branch (Sections 4.2-4.3): assembled Schur complement S_M, minimum-degree ordering,
+// LDL^T factorisation in FP64 with the "small pivot -> infinity" rule, triangular solves.
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+#include "newton.cuh"
+#include "support.cuh"
+
+namespace ot {
+
+struct Chol {
+    int32_t n = 0;
+    // assembled S_M (off-diagonal, CSR, both triangles) + diagonal
+    int64_t nnzA = 0, capA = 0;
+    int32_t *Ap = nullptr, *Aj = nullptr;
+    double *Ax = nullptr;
+    double *Adiag = nullptr;            // S_jj (cancellation-free form)
+    int64_t *a2l = nullptr;             // per A entry: position in Lx (lower part) or -1
+    // symbolic (device)
+    int64_t nnzL = 0, capL = 0;
+    int32_t *perm = nullptr, *iperm = nullptr;
+    int32_t *Lp = nullptr, *Li = nullptr;    // CSC of strictly lower L (permuted indices)
+    int32_t *Rp = nullptr, *Rj = nullptr;    // CSR of strictly lower L
+    int64_t *Rpos = nullptr;                 // Lx position of (row, Rj)
+    double *Lx = nullptr, *D = nullptr, *dperm = nullptr;
+    double *z = nullptr, *x = nullptr, *y = nullptr;
+    int *done = nullptr;
+    unsigned *counter = nullptr;
+    int *err = nullptr;
+    bool have_symbolic = false;
+    double fill_pct = 0.0;              // nnz(L) / n^2 * 100
+    int64_t max_nnzL = 0;               // symbolic gives up beyond this (too much fill)
+    // host copy of the pattern used by the current symbolic analysis
+    std::vector<int32_t> hAp, hAj;
+};
+
+Error chol_alloc(Chol &C, int32_t n);
+void chol_free(Chol &C);
+
+// Assemble S_M = N - V^T M^-1 V (off-diagonal part by rows of V, diagonal from the
+// cancellation-free form) for the current theta.  Sets *pattern_changed.
+Error chol_assemble(Chol &C, Newton &W, const Support &S, bool *pattern_changed, cudaStream_t st);
+
+// Minimum-degree ordering and the pattern of L (host), uploaded to the device.  Returns
+// OT_ERR_UNSUPPORTED when nnz(L) would exceed C.max_nnzL (the caller keeps using PCG).
+Error chol_symbolic(Chol &C, cudaStream_t st);
+
+// Numeric LDL^T of the assembled S_M; pivots d <= eps * S_jj become +infinity.
+Error chol_numeric(Chol &C, double eps, cudaStream_t st);
+
+// x = S_M^+ b through L D L^T (+inf pivots ground one node per component), b and x device
+// vectors of length n (natural order).  x may alias nothing.
+Error chol_solve(Chol &C, const double *b, double *x, cudaStream_t st);
+
+}  // namespace ot

@@ -2,6 +2,7 @@
 // (eq. normalequationsipm) and the Schur complement S_M = N - V^T M^-1 V (Section 4), solved
 // matrix-free by PCG.  All reductions are deterministic (fixed-order two-stage sums).
 #include "newton.cuh"
+#include "chol.cuh"
 #include "primitives.cuh"
 
 #include <cmath>
@@ -161,7 +162,7 @@ __global__ void theta_cols_kernel(int n, const int32_t *__restrict__ cp, const i
                                   const int32_t *__restrict__ crow, const double *__restrict__ th,
                                   const double *__restrict__ excl, const double *__restrict__ Minv,
                                   double *__restrict__ thc, float *__restrict__ thc32, double *__restrict__ N,
-                                  double *__restrict__ Dinv, float *__restrict__ Dinv32) {
+                                  double *__restrict__ Dinv, float *__restrict__ Dinv32, double *__restrict__ Sdiag) {
     GRID_STRIDE(j, n) {
         double nsum = 0, d = 0;
         for (int k = cp[j]; k < cp[j + 1]; ++k) {
@@ -173,6 +174,7 @@ __global__ void theta_cols_kernel(int n, const int32_t *__restrict__ cp, const i
             d += t * excl[e] * Minv[crow[k]];
         }
         N[j] = nsum;
+        Sdiag[j] = d;
         const double di = d > 0 ? 1.0 / d : 0.0;  // columns with D = 0 are private stars: masked
         Dinv[j] = di;
         Dinv32[j] = (float)di;
@@ -585,6 +587,112 @@ Error dev_alloc(T **p, int64_t count) {
 
 }  // namespace
 
+// ------------------------------------------------------------------------ S_M x = rhs
+static Error residual_norm(Newton &W, const Support &S, const double *x, double *res, double *nrm, cudaStream_t st) {
+    const unsigned gm = grid_of(W.m, W.num_sms), gn = grid_of(W.n, W.num_sms);
+    mv_rows_kernel<<<gm, kT, 0, st>>>(W.m, S.row_ptr, S.j, W.theta, W.Minv, x, W.w64);
+    OT_LAUNCHED();
+    mv_cols_res_kernel<<<gn, kT, 0, st>>>(W.n, S.col_ptr, S.col_row, W.theta_col, W.w64, x, W.rhs, res, W.part);
+    OT_LAUNCHED();
+    Finish f{1, {SC_NORM_A}, {(int)gn}, {0}};
+    OT_TRY(finish(f, W, st));
+    double hs[SC_COUNT];
+    OT_TRY(read_scalars(W, hs, st));
+    *nrm = std::sqrt(hs[SC_NORM_A]);
+    return ok();
+}
+
+static Error rhs_norm(Newton &W, double *nrm, cudaStream_t st) {
+    const unsigned gn = grid_of(W.n, W.num_sms);
+    norm_kernel<<<gn, kT, 0, st>>>(W.n, W.rhs, W.part, SC_NORM_B);
+    OT_LAUNCHED();
+    Finish f{1, {SC_NORM_B}, {(int)gn}, {0}};
+    OT_TRY(finish(f, W, st));
+    double hs[SC_COUNT];
+    OT_TRY(read_scalars(W, hs, st));
+    *nrm = std::sqrt(hs[SC_NORM_B]);
+    return ok();
+}
+
+static Error solve_pcg64(Newton &W, const Support &S, double tol, int max_cg, double *dv, SolveStats *ss,
+                         cudaStream_t st) {
+    const unsigned gn = grid_of(W.n, W.num_sms);
+    OT_TRY(launch_pcg<double>(W, S, W.theta, W.theta_col, W.Minv, W.Dinv, W.rhs, W.x64, W.r64, W.z64, W.p64,
+                              W.q64, W.w64, tol, max_cg, st));
+    double hs[SC_COUNT];
+    OT_TRY(read_scalars(W, hs, st));
+    int errv = 0;
+    OT_CUDA(cudaMemcpy(&errv, W.err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (errv) return fail(OT_ERR_TIMEOUT, "pcg: grid barrier wait limit reached");
+    ss->cg_iters = (int)hs[SC_PCG_ITERS];
+    ss->relres = hs[SC_PCG_RELRES];
+    copy_kernel<<<gn, kT, 0, st>>>(W.n, W.x64, dv);
+    OT_LAUNCHED();
+    return ok();
+}
+
+// FP32 PCG inside FP64 iterative refinement: dv = 0, res = rhs; repeat
+//   solve S32 d = float(res) ; dv += d ; res = rhs - S64 dv      until |res| <= tol |rhs|
+static Error solve_mixed(Newton &W, const Support &S, double tol, int max_cg, double *dv, SolveStats *ss,
+                         cudaStream_t st) {
+    const unsigned gn = grid_of(W.n, W.num_sms);
+    const double inner = std::max(tol, 1e-4);
+    OT_CUDA(cudaMemsetAsync(dv, 0, sizeof(double) * W.n, st));
+    copy_kernel<<<gn, kT, 0, st>>>(W.n, W.rhs, W.res64);
+    OT_LAUNCHED();
+    double nrm0;
+    OT_TRY(rhs_norm(W, &nrm0, st));
+    double nrm = nrm0;
+    int budget = max_cg;
+    for (int ref = 0; ref < 12 && nrm > tol * nrm0 && budget > 0; ++ref) {
+        to_f32_kernel<<<gn, kT, 0, st>>>(W.n, W.res64, W.b32);
+        OT_LAUNCHED();
+        OT_TRY(launch_pcg<float>(W, S, W.theta32, W.theta32_col, W.Minv32, W.Dinv32, W.b32, W.x32, W.r32, W.z32,
+                                 W.p32, W.q32, W.w32, inner, budget, st));
+        axpy_f32_kernel<<<gn, kT, 0, st>>>(W.n, W.x32, dv);
+        OT_LAUNCHED();
+        const double prev = nrm;
+        OT_TRY(residual_norm(W, S, dv, W.res64, &nrm, st));
+        double hs[SC_COUNT];
+        OT_TRY(read_scalars(W, hs, st));
+        int errv = 0;
+        OT_CUDA(cudaMemcpy(&errv, W.err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (errv) return fail(OT_ERR_TIMEOUT, "pcg: grid barrier wait limit reached");
+        const int its = (int)hs[SC_PCG_ITERS];
+        ss->cg_iters += its;
+        budget -= std::max(its, 1);
+        ss->refinements = ref + 1;
+        if (!(nrm < 0.9 * prev)) break;  // refinement stagnates
+    }
+    ss->relres = nrm0 > 0 ? nrm / nrm0 : 0.0;
+    return ok();
+}
+
+// LDL^T solve with FP64 iterative refinement (the factorisation may have +inf pivots)
+static Error solve_direct(Newton &W, const Support &S, double tol, double *dv, SolveStats *ss, cudaStream_t st) {
+    const unsigned gn = grid_of(W.n, W.num_sms);
+    Chol &C = *W.direct;
+    double nrm0;
+    OT_TRY(rhs_norm(W, &nrm0, st));
+    OT_TRY(chol_solve(C, W.rhs, dv, st));
+    double nrm;
+    OT_TRY(residual_norm(W, S, dv, W.res64, &nrm, st));
+    const double target = std::min(tol, 1e-10);
+    for (int ref = 0; ref < 3 && nrm > target * nrm0; ++ref) {
+        OT_TRY(chol_solve(C, W.res64, W.x64, st));
+        add_kernel<<<gn, kT, 0, st>>>(W.n, dv, W.x64);
+        OT_LAUNCHED();
+        const double prev = nrm;
+        OT_TRY(residual_norm(W, S, dv, W.res64, &nrm, st));
+        ss->refinements = ref + 1;
+        if (!(nrm < 0.5 * prev)) break;
+    }
+    ss->direct = 1;
+    ss->relres = nrm0 > 0 ? nrm / nrm0 : 0.0;
+    return ok();
+}
+
+
 // =====================================================================================
 Error newton_alloc(Newton &W, int32_t m, int32_t n, int64_t cap, int num_sms) {
     W.m = m;
@@ -593,7 +701,7 @@ Error newton_alloc(Newton &W, int32_t m, int32_t n, int64_t cap, int num_sms) {
     OT_TRY(newton_grow(W, cap));
     for (double **p : {&W.r1a, &W.beta1, &W.M, &W.Minv, &W.du, &W.du2, &W.du3, &W.w64}) OT_TRY(dev_alloc(p, m));
     for (float **p : {&W.Minv32, &W.w32}) OT_TRY(dev_alloc(p, m));
-    for (double **p : {&W.r1b, &W.beta2, &W.N, &W.Dinv, &W.rhs, &W.dv, &W.dv2, &W.dv3, &W.res64, &W.y64, &W.x64,
+    for (double **p : {&W.r1b, &W.beta2, &W.N, &W.Dinv, &W.Sdiag, &W.rhs, &W.dv, &W.dv2, &W.dv3, &W.res64, &W.y64, &W.x64,
                        &W.r64, &W.z64, &W.p64, &W.q64})
         OT_TRY(dev_alloc(p, n));
     for (float **p : {&W.Dinv32, &W.b32, &W.x32, &W.r32, &W.z32, &W.p32, &W.q32}) OT_TRY(dev_alloc(p, n));
@@ -623,7 +731,7 @@ Error newton_grow(Newton &W, int64_t cap) {
 void newton_free(Newton &W) {
     void *ptrs[] = {W.c, W.theta, W.excl, W.r2, W.r3, W.g, W.dp, W.ds, W.dp2, W.ds2, W.dp3, W.ds3, W.theta32,
                     W.theta_col, W.theta32_col, W.flag, W.r1a, W.beta1, W.M, W.Minv, W.du, W.du2, W.du3, W.w64,
-                    W.Minv32, W.w32, W.r1b, W.beta2, W.N, W.Dinv, W.rhs, W.dv, W.dv2, W.dv3, W.res64, W.y64,
+                    W.Minv32, W.w32, W.r1b, W.beta2, W.N, W.Dinv, W.Sdiag, W.rhs, W.dv, W.dv2, W.dv3, W.res64, W.y64,
                     W.x64, W.r64, W.z64, W.p64, W.q64, W.Dinv32, W.b32, W.x32, W.r32, W.z32, W.p32, W.q32,
                     W.parent, W.comp_sum, W.comp_cnt, W.part, W.scal, W.bar, W.err};
     for (void *p : ptrs)
@@ -664,7 +772,7 @@ Error schur_setup(Newton &W, const Support &S, cudaStream_t st) {
     theta_rows_kernel<<<gm, kT, 0, st>>>(W.m, S.row_ptr, W.theta, W.excl, W.M, W.Minv, W.Minv32);
     OT_LAUNCHED();
     theta_cols_kernel<<<gn, kT, 0, st>>>(W.n, S.col_ptr, S.col_perm, S.col_row, W.theta, W.excl, W.Minv,
-                                         W.theta_col, W.theta32_col, W.N, W.Dinv, W.Dinv32);
+                                         W.theta_col, W.theta32_col, W.N, W.Dinv, W.Dinv32, W.Sdiag);
     OT_LAUNCHED();
     const int nn = W.m + W.n;
     const unsigned gnn = grid_of(nn, W.num_sms);
@@ -720,62 +828,20 @@ Error newton_solve(Newton &W, const Support &S, const Rhs &R, double cg_tol, int
     OT_TRY(project(W, W.rhs, one, st));
 
     SolveStats ss;
-    if (precision == 0) {
-        OT_TRY(launch_pcg<double>(W, S, W.theta, W.theta_col, W.Minv, W.Dinv, W.rhs, W.x64, W.r64, W.z64, W.p64,
-                                  W.q64, W.w64, cg_tol, max_cg, st));
-        OT_CUDA(cudaMemcpyAsync(hs, W.scal, sizeof(hs), cudaMemcpyDeviceToHost, st));
-        OT_CUDA(cudaStreamSynchronize(st));
-        int errv = 0;
-        OT_CUDA(cudaMemcpy(&errv, W.err, sizeof(int), cudaMemcpyDeviceToHost));
-        if (errv) return fail(OT_ERR_TIMEOUT, "pcg: grid barrier wait limit reached");
-        ss.cg_iters = (int)hs[SC_PCG_ITERS];
-        ss.relres = hs[SC_PCG_RELRES];
-        copy_kernel<<<gn, kT, 0, st>>>(W.n, W.x64, dv);
-        OT_LAUNCHED();
+    if (W.direct) {
+        OT_TRY(solve_direct(W, S, cg_tol, dv, &ss, st));
+    } else if (precision == 0) {
+        OT_TRY(solve_pcg64(W, S, cg_tol, max_cg, dv, &ss, st));
     } else {
-        // FP32 PCG inside FP64 iterative refinement: dv = 0, res = rhs, repeat
-        //   solve S32 d = float(res) ; dv += d ; res = rhs - S64 dv
-        const double inner = std::max(cg_tol, 1e-4);
-        OT_CUDA(cudaMemsetAsync(dv, 0, sizeof(double) * W.n, st));
-        copy_kernel<<<gn, kT, 0, st>>>(W.n, W.rhs, W.res64);
-        OT_LAUNCHED();
-        norm_kernel<<<gn, kT, 0, st>>>(W.n, W.rhs, W.part, SC_NORM_B);
-        OT_LAUNCHED();
-        Finish f{1, {SC_NORM_B}, {(int)gn}, {0}};
-        OT_TRY(finish(f, W, st));
-        OT_CUDA(cudaMemcpyAsync(hs, W.scal, sizeof(hs), cudaMemcpyDeviceToHost, st));
-        OT_CUDA(cudaStreamSynchronize(st));
-        const double nrm0 = std::sqrt(hs[SC_NORM_B]);
-        double nrm = nrm0;
-        int budget = max_cg;
-        for (int ref = 0; ref < 12 && nrm > cg_tol * nrm0 && budget > 0; ++ref) {
-            to_f32_kernel<<<gn, kT, 0, st>>>(W.n, W.res64, W.b32);
-            OT_LAUNCHED();
-            OT_TRY(launch_pcg<float>(W, S, W.theta32, W.theta32_col, W.Minv32, W.Dinv32, W.b32, W.x32, W.r32,
-                                     W.z32, W.p32, W.q32, W.w32, inner, budget, st));
-            axpy_f32_kernel<<<gn, kT, 0, st>>>(W.n, W.x32, dv);
-            OT_LAUNCHED();
-            mv_rows_kernel<<<gm, kT, 0, st>>>(W.m, S.row_ptr, S.j, W.theta, W.Minv, dv, W.w64);
-            OT_LAUNCHED();
-            mv_cols_res_kernel<<<gn, kT, 0, st>>>(W.n, S.col_ptr, S.col_row, W.theta_col, W.w64, dv, W.rhs,
-                                                  W.res64, W.part);
-            OT_LAUNCHED();
-            Finish f2{1, {SC_NORM_A}, {(int)gn}, {0}};
-            OT_TRY(finish(f2, W, st));
-            OT_CUDA(cudaMemcpyAsync(hs, W.scal, sizeof(hs), cudaMemcpyDeviceToHost, st));
-            OT_CUDA(cudaStreamSynchronize(st));
-            int errv = 0;
-            OT_CUDA(cudaMemcpy(&errv, W.err, sizeof(int), cudaMemcpyDeviceToHost));
-            if (errv) return fail(OT_ERR_TIMEOUT, "pcg: grid barrier wait limit reached");
-            const int its = (int)hs[SC_PCG_ITERS];
-            ss.cg_iters += its;
-            budget -= std::max(its, 1);
-            ss.refinements = ref + 1;
-            const double prev = nrm;
-            nrm = std::sqrt(hs[SC_NORM_A]);
-            if (!(nrm < 0.9 * prev)) break;  // refinement stagnates
+        OT_TRY(solve_mixed(W, S, cg_tol, max_cg, dv, &ss, st));
+        if (W.fp64_fallback && !(ss.relres <= cg_tol)) {
+            // FP32 cannot resolve this system (condition beyond ~1/eps32): redo it in FP64
+            SolveStats s64;
+            OT_TRY(solve_pcg64(W, S, cg_tol, max_cg, dv, &s64, st));
+            s64.cg_iters += ss.cg_iters;
+            ss = s64;
+            W.fallbacks++;
         }
-        ss.relres = nrm0 > 0 ? nrm / nrm0 : 0.0;
     }
     OT_TRY(project(W, dv, one, st));
     du_kernel<<<gm, kT, 0, st>>>(W.m, S.row_ptr, S.j, W.theta, W.Minv, W.beta1, dv, du);

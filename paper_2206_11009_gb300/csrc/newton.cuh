@@ -31,7 +31,8 @@ struct Newton {
            *du3 = nullptr, *w64 = nullptr;
     float *Minv32 = nullptr, *w32 = nullptr;
     // cols (n)
-    double *r1b = nullptr, *beta2 = nullptr, *N = nullptr, *Dinv = nullptr, *rhs = nullptr, *dv = nullptr,
+    double *r1b = nullptr, *beta2 = nullptr, *N = nullptr, *Dinv = nullptr, *Sdiag = nullptr, *rhs = nullptr,
+           *dv = nullptr,
            *dv2 = nullptr, *dv3 = nullptr, *res64 = nullptr, *y64 = nullptr;
     double *x64 = nullptr, *r64 = nullptr, *z64 = nullptr, *p64 = nullptr, *q64 = nullptr;
     float *Dinv32 = nullptr, *b32 = nullptr, *x32 = nullptr, *r32 = nullptr, *z32 = nullptr, *p32 = nullptr,
@@ -45,6 +46,10 @@ struct Newton {
     unsigned *bar = nullptr;
     int *err = nullptr;
     int pcg_grid = 0;
+    // direct branch: when set, S_M x = rhs is solved by its LDL^T factorisation (chol.cuh)
+    struct Chol *direct = nullptr;
+    int fallbacks = 0;        // mixed-precision solves redone in FP64
+    bool fp64_fallback = true;  // redo a failed mixed-precision solve with FP64 PCG
 };
 
 constexpr int kMaxPartBlocks = 2048;
@@ -73,6 +78,7 @@ struct SolveStats {
     int cg_iters = 0;
     double relres = 0.0;
     int refinements = 0;
+    int direct = 0;
 };
 
 // Direction (du, dv, ds, dp) of eq. normalequationsipm for the given right-hand sides.

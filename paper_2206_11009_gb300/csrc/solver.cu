@@ -1,6 +1,7 @@
 // Solver driver and C ABI: the outer iteration of the hybrid IPM / column-generation method
 // (Section 3.4's commented listing: residuals, mu, sigma and r3, Newton direction, step lengths,
 // update, pricing, support update), with the readings stated in ot_ipm.h.
+#include "chol.cuh"
 #include "newton.cuh"
 #include "pricing.cuh"
 #include "primitives.cuh"
@@ -21,6 +22,13 @@ void set_thread_error(const char *msg) { t_last_error = msg ? msg : ""; }
 namespace {
 
 constexpr double kBetaMin = 0.1, kBetaMax = 10.0, kAlphaBoost = 0.1, kAcceptGain = 1.01;
+// Section 4.3: switch to LDL^T once psi fell by kSwitchDrop over the last 5 iterations; switch back
+// (the remark after Section 4.3) when psi grows kSwitchBack above its minimum since the switch.
+constexpr double kSwitchDrop = 0.1, kSwitchBack = 1.05;
+// Section 4.2: a pivot that kept less than kPivotEps of its diagonal becomes +infinity.
+constexpr double kPivotEps = 1e-12;
+// a PCG result with relative residual above kPcgFail x tolerance counts as a failed solve
+constexpr double kPcgFail = 10.0;
 
 // c-transform lower bound (weak duality): ubar_i = min_j (c_ij - v_j); LB = a^T ubar + b^T v.
 __global__ void ctrans_kernel(CostDev cd, const double *__restrict__ v, unsigned long long *__restrict__ rowmin) {
@@ -89,6 +97,11 @@ struct ot_ipm {
     Support S[2];
     int cur = 0;
     Newton W;
+    Chol chol;
+    std::vector<int64_t> psi_hist;
+    bool direct_mode = false;
+    int64_t psi_min = 0;
+    double max_fill = 0.0;
     int32_t *pi = nullptr, *pj = nullptr, *pcount = nullptr;
     double *pd = nullptr;
     int *pstrong = nullptr;
@@ -242,12 +255,63 @@ Error do_step(ot_ipm *h, ot_iter_info *info) {
 
     // ---- Newton direction: Mehrotra predictor-corrector + centrality correctors
     OT_TRY(schur_setup(W, S, st));
+    // iterative (PCG) or direct (LDL^T) solves of S_M, Section 4.3
+    h->psi_hist.push_back(S.psi);
+    bool use_direct = o.linear_solver == 2;
+    if (o.linear_solver == 0) {
+        const size_t L = h->psi_hist.size();
+        if (!h->direct_mode && L >= 6) {
+            const double p5 = (double)h->psi_hist[L - 6], p0 = (double)h->psi_hist[L - 1];
+            if ((p5 - p0) / p5 >= kSwitchDrop) { h->direct_mode = true; h->psi_min = S.psi; }
+        }
+        if (h->direct_mode) {
+            h->psi_min = std::min(h->psi_min, S.psi);
+            if ((double)S.psi > kSwitchBack * (double)h->psi_min) h->direct_mode = false;
+        }
+        use_direct = h->direct_mode;
+    }
+    W.direct = nullptr;
+    // factor S_M once for every solve of this iteration; false when the fill is over budget
+    auto enable_direct = [&]() -> Error {
+        bool changed = false;
+        OT_TRY(chol_assemble(h->chol, W, S, &changed, st));
+        Error e = ok();
+        if (changed || !h->chol.have_symbolic) e = chol_symbolic(h->chol, st);
+        if (e.code == OT_OK) {
+            OT_TRY(chol_numeric(h->chol, kPivotEps, st));
+            W.direct = &h->chol;
+            h->max_fill = std::max(h->max_fill, h->chol.fill_pct);
+            h->direct_total++;
+            inf.direct = 1;
+            return ok();
+        }
+        return e.code == OT_ERR_UNSUPPORTED ? ok() : e;
+    };
+    if (use_direct) OT_TRY(enable_direct());
     int cg = 0;
     SolveStats ss;
+    // a PCG solve that misses its tolerance by more than kPcgFail switches this iteration (and,
+    // through direct_mode, the following ones) to the LDL^T branch when its fill is acceptable
+    auto solve = [&](const Rhs &R, double tol, double *du, double *dv, double *ds, double *dp) -> Error {
+        W.fp64_fallback = o.linear_solver != 0;  // in auto mode a failed solve escalates to LDL^T
+        OT_TRY(newton_solve(W, S, R, tol, o.max_cg, o.precision, du, dv, ds, dp, &ss, st));
+        cg += ss.cg_iters;
+        if (!W.direct && o.linear_solver == 0 && !(ss.relres <= kPcgFail * tol)) {
+            OT_TRY(enable_direct());
+            if (W.direct) {
+                h->direct_mode = true;
+                h->psi_min = S.psi;
+                OT_TRY(newton_solve(W, S, R, tol, o.max_cg, o.precision, du, dv, ds, dp, &ss, st));
+            } else if (o.precision == 1) {  // fill over budget: FP64 PCG as the last resort
+                OT_TRY(newton_solve(W, S, R, tol, o.max_cg, 0, du, dv, ds, dp, &ss, st));
+                cg += ss.cg_iters;
+            }
+        }
+        return ok();
+    };
     OT_TRY(corrector_r3(W, S, 0.0, nullptr, nullptr, st));  // r3 = -p s
     Rhs R{W.r1a, W.r1b, W.r2, W.r3};
-    OT_TRY(newton_solve(W, S, R, o.cg_tol_pred, o.max_cg, o.precision, W.du, W.dv, W.ds, W.dp, &ss, st));
-    cg += ss.cg_iters;
+    OT_TRY(solve(R, o.cg_tol_pred, W.du, W.dv, W.ds, W.dp));
     OT_TRY(step_lengths(W, S, W.dp, W.ds, o.step_scale, st));
     OT_TRY(read_scalars(W, hs, st));
     const double apa = step_of(hs[SC_AP], o.step_scale), asa = step_of(hs[SC_AS], o.step_scale);
@@ -258,8 +322,7 @@ Error do_step(ot_ipm *h, ot_iter_info *info) {
     OT_TRY(corrector_r3(W, S, sigma * mu, W.dp, W.ds, st));
     double *d_du = W.du2, *d_dv = W.dv2, *d_ds = W.ds2, *d_dp = W.dp2;  // current direction
     double *c_du = W.du3, *c_dv = W.dv3, *c_ds = W.ds3, *c_dp = W.dp3;  // corrector scratch
-    OT_TRY(newton_solve(W, S, R, o.cg_tol_pred, o.max_cg, o.precision, d_du, d_dv, d_ds, d_dp, &ss, st));
-    cg += ss.cg_iters;
+    OT_TRY(solve(R, o.cg_tol_pred, d_du, d_dv, d_ds, d_dp));
     OT_TRY(step_lengths(W, S, d_dp, d_ds, o.step_scale, st));
     OT_TRY(read_scalars(W, hs, st));
     double ap = step_of(hs[SC_AP], o.step_scale), as = step_of(hs[SC_AS], o.step_scale);
@@ -269,8 +332,7 @@ Error do_step(ot_ipm *h, ot_iter_info *info) {
         const double tp = std::min(1.0, ap + kAlphaBoost), ts = std::min(1.0, as + kAlphaBoost);
         OT_TRY(centrality_r3(W, S, d_dp, d_ds, tp, ts, kBetaMin * sigma * mu, kBetaMax * sigma * mu, st));
         Rhs Rc{nullptr, nullptr, nullptr, W.r3};
-        OT_TRY(newton_solve(W, S, Rc, o.cg_tol_corr, o.max_cg, o.precision, c_du, c_dv, c_ds, c_dp, &ss, st));
-        cg += ss.cg_iters;
+        OT_TRY(solve(Rc, o.cg_tol_corr, c_du, c_dv, c_ds, c_dp));
         OT_TRY(add_direction(W, S, c_dp, c_ds, c_du, c_dv, d_dp, d_ds, d_du, d_dv, st));
         OT_TRY(step_lengths(W, S, c_dp, c_ds, o.step_scale, st));
         OT_TRY(read_scalars(W, hs, st));
@@ -321,8 +383,9 @@ Error do_step(ot_ipm *h, ot_iter_info *info) {
     inf.added = added;
     inf.removed = removed;
     if (o.verbose)
-        fprintf(stderr, "it %3d psi %8lld mu %.3e crit %.3e ap %.3f as %.3f sig %.2e corr %d cg %d +%d -%lld\n",
-                inf.iter, (long long)inf.psi, mu, crit, ap, as, sigma, ncorr, cg, added, (long long)removed);
+        fprintf(stderr, "it %3d psi %8lld mu %.3e crit %.3e ap %.3f as %.3f sig %.2e corr %d cg %d %s +%d -%lld\n",
+                inf.iter, (long long)inf.psi, mu, crit, ap, as, sigma, ncorr, cg, inf.direct ? "LDL" : "PCG", added,
+                (long long)removed);
     if (info) *info = inf;
     return ok();
 }
@@ -440,6 +503,7 @@ Error create_impl(const ot_problem *P, const ot_options *O, ot_ipm *h) {
     h->S[0].psi = psi0;
     OT_TRY(rebuild_views(h->S[0], m, n, st));
     OT_TRY(newton_alloc(h->W, m, n, cap, h->num_sms));
+    OT_TRY(chol_alloc(h->chol, n));
     OT_TRY(support_costs(h->W, h->cd, h->S[0], st));
     int cgs = 0;
     OT_TRY(mehrotra_start(h->W, h->S[0], h->a_s, h->b_s, h->u, h->v, o.precision, o.cg_tol_pred, 20 * o.max_cg,
@@ -466,7 +530,7 @@ void ot_options_default(ot_options *o) {
     o->max_corr = 3;
     o->step_scale = 0.995;
     o->precision = 1;
-    o->linear_solver = 1;
+    o->linear_solver = 0;
     o->init_cost = 2.0;
     o->rm_mu_frac = 1e-3;
     o->rm_p_frac = 1e-3;
@@ -542,6 +606,7 @@ int ot_ipm_solve(ot_ipm_t *h, ot_result *res) {
         res->iters = h->iter;
         res->cg_iters = (int32_t)h->cg_total;
         res->direct_iters = h->direct_total;
+        res->max_fill = h->max_fill;
         res->psi = h->S[h->cur].psi;
         res->seconds = ms * 1e-3;
     }
@@ -626,6 +691,7 @@ void ot_ipm_destroy(ot_ipm_t *h) {
     support_free(h->S[0]);
     support_free(h->S[1]);
     newton_free(h->W);
+    chol_free(h->chol);
     void *ptrs[] = {h->a_s, h->b_s, h->C, h->sx, h->sy, h->tx, h->ty, h->u, h->v, h->pi, h->pj, h->pd,
                     h->pcount, h->pstrong, h->rowmin, h->lbv};
     for (void *p : ptrs)

@@ -26,13 +26,18 @@ def rect_coords(w: int, h: int, x0: int = 0, y0: int = 0):
 
 
 def banded_duals(sx, sy, tx, ty, seed: int, amp: float, noise: float):
-    """Duals whose reduced costs form a band of negatives near the 'diagonal' of a smooth map:
-    u_i = g(x_i), v_j = -g(y_j) + noise, g a smooth random field (the structure of IPM duals)."""
-    def field(x, y):
-        a = synth.normal(seed, 6)
-        return amp * (a[0] * np.sin(0.11 * x + a[1]) + a[2] * np.cos(0.07 * y + a[3]) + a[4] * 0.01 * x * y / 16.0)
-    u = field(sx.astype(float), sy.astype(float))
-    v = -field(tx.astype(float), ty.astype(float)) + noise * (synth.uniform01(seed + 99, len(tx)) - 0.5)
+    """Duals with the structure of IPM iterates: u_i = phi(x_i), v_j = -phi(y_j) + noise, phi a
+    tilted smooth field of gradient about `amp`; the negative reduced costs then form a disc of
+    radius about amp/2 around each source (|d| grows away from it)."""
+    a = synth.normal(seed, 4)
+    t = a[:2] / np.linalg.norm(a[:2])
+
+    def phi(x, y):
+        x = x.astype(float)
+        y = y.astype(float)
+        return amp * (t[0] * x + t[1] * y) + 2.0 * np.sin(0.13 * x + a[2]) * np.cos(0.09 * y + a[3])
+    u = phi(sx, sy)
+    v = -phi(tx, ty) + noise * (synth.uniform01(seed + 99, len(tx)) - 0.5)
     return u, v
 
 
