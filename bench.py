@@ -1,0 +1,338 @@
+"""Benchmark: time-to-solution of the hybrid IPM / column-generation OT solver on GB300.
+
+Workload: one 64x64 image pair (m = n = 4096, 16.8M variables), seeded log-normal Gaussian
+random-field marginals, squared-Euclidean pixel cost, solved to relative gap 1e-6 with the mixed
+precision path (FP32 pricing scan + FP64 recheck, FP32 PCG + FP64 refinement, FP64 LDL^T near
+optimality).  A step = one full solve of that instance.  The plain FP64 path is timed beside it.
+
+JSON line (rank 0): metric/value/unit (seconds, lower is better), e2e through the public API
+with host buffers, pricing throughput, the roofline of the dominant instrumented kernel, the
+oracle's CPU time on a bounded sample, clocks sampled during the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--k 64]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "OT time-to-solution at rel. gap 1e-6 (learned+mixed vs plain FP64); pricing Gcols/s"
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling (every 200 ms) while the timed region runs."""
+
+    def __init__(self):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self, gpu_index: int = 0) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.f.read().splitlines():
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9 or parts[0] != str(gpu_index):
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------------------ oracle arm
+def oracle_sample(k: int, iters: int, seed: int):
+    """Time `iters` outer iterations of the CPU oracle (plain float64 rendition of the method)
+    on the bench instance; returns (seconds per iteration, iterations timed)."""
+    from oracle import costs, ipm
+    from paper_2206_11009_gb300 import synth
+    inst = synth.image_pair(k, seed)
+    c = costs.square_grid(k)
+    opt = ipm.Options(tol=1e-6, max_iter=iters)
+    prob = ipm.Problem(c, inst.a, inst.b)
+    t0 = time.perf_counter()
+    I, J = ipm.initial_support(prob, opt)
+    st = ipm.initial_point(prob, I, J)
+    tr = ipm.Tracker()
+    done = 0
+    for it in range(iters):
+        stop, res, _ = ipm.stop_test(prob, st, opt, tr)
+        if stop:
+            break
+        st, _, _, _, _ = ipm.one_iteration(prob, st, res, opt, tr, it)
+        done += 1
+    return (time.perf_counter() - t0) / max(done, 1), done
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    iters_per_step = 2
+    gpu_iters = args.scale_iters
+    times = []
+    for s in range(args.warmup + args.steps):
+        per_iter, done = oracle_sample(args.k, iters_per_step, 0)
+        if s >= args.warmup:
+            times.append(per_iter * gpu_iters)
+    v = statistics.mean(times)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(args),
+            "cpu_baseline": {"kind": "oracle", "value": v, "unit": "s", "cores": 1,
+                             "sample": f"{iters_per_step} outer iterations of the CPU oracle per step on the "
+                                       f"{args.k}x{args.k} instance, scaled to {gpu_iters} iterations"},
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_dict(args):
+    return {"workload": f"{args.k}x{args.k} image pair (m=n={args.k * args.k}, {args.k ** 4} variables), "
+                        "GRF marginals, squared-Euclidean cost, rel. gap 1e-6, mixed precision",
+            "k": args.k, "m": args.k * args.k, "n": args.k * args.k, "tol": 1e-6,
+            "l2": "flushed between steps (256 MiB write)", "seed": 0}
+
+
+# ------------------------------------------------------------------------------ GPU arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native")
+    ap.add_argument("--k", type=int, default=64)
+    ap.add_argument("--scale-iters", type=int, default=60, help="oracle extrapolation (reference arm)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_init()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import numpy as np
+    import torch
+    import __graft_entry__
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    barrier(world)
+    __graft_entry__.build()
+    from paper_2206_11009_gb300 import Solver, kernel_launches, kernel_timing, price_topk, synth
+
+    k = args.k
+    inst = synth.image_pair(k, rank)          # each rank: its own instance (replicas, weak scaling)
+    a_pin = torch.from_numpy(inst.a).pin_memory()
+    b_pin = torch.from_numpy(inst.b).pin_memory()
+    a_np, b_np = a_pin.numpy(), b_pin.numpy()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def one_solve(precision, timing=False):
+        with Solver(a_np, b_np, grid=(k, k), tol=1e-6, precision=precision) as s:
+            torch.cuda.synchronize()
+            r = s.solve(raise_on_error=False)
+            sol = s.solution()
+        return r, sol
+
+    # warm-up (untimed)
+    for _ in range(args.warmup):
+        one_solve(1)
+    # timed: device time of each solve (CUDA events around the iterations on the solver's stream)
+    clocks = Clocks()
+    dev_times, e2e_times, results = [], [], []
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = kernel_launches()
+    kernel_timing(True)
+    h2d = d2h = 0
+    for _ in range(args.steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with Solver(a_np, b_np, grid=(k, k), tol=1e-6, precision=1) as s:
+            r = s.solve(raise_on_error=False)
+            I, J, P, u, v = s.solution()
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+        dev_times.append(r.seconds)
+        results.append(r)
+        h2d = a_np.nbytes + b_np.nbytes
+        d2h = I.nbytes + J.nbytes + P.nbytes + u.nbytes + v.nbytes
+    torch.cuda.synchronize()
+    ktimes = kernel_timing()
+    kernel_timing(False)
+    launches = kernel_launches() - launches0
+    clk = clocks.stop(local)
+    barrier(world)
+    t_dev = max_over_ranks(statistics.mean(dev_times), world)
+    t_e2e = max_over_ranks(statistics.mean(e2e_times), world)
+
+    # plain FP64 GPU path on the same instance (the comparison the metric names)
+    plain = None
+    if not args.no_plain:
+        rp, _ = one_solve(0)
+        plain = {"seconds": rp.seconds, "status": rp.status, "iters": rp.iters, "rel_gap": rp.rel_gap}
+
+    # pricing throughput at this size with the final duals of a solve (realistic reduced costs)
+    with Solver(a_np, b_np, grid=(k, k), tol=1e-6, precision=1) as s:
+        s.solve(raise_on_error=False)
+        Is, Js, Ps, Ss, us, vs = s.state()
+    x, y = synth.grid_coords(k)
+    T = lambda arr, dt: torch.as_tensor(np.ascontiguousarray(arr), dtype=dt, device="cuda")
+    tx, ty = T(x, torch.int32), T(y, torch.int32)
+    tu, tv = T(us, torch.float64), T(vs, torch.float64)
+    ti, tj = T(Is, torch.int32), T(Js, torch.int32)
+    for _ in range(3):
+        price_topk(tx, ty, tx, ty, tu, tv, ti, tj, kmax=k * k, precision=1)
+    torch.cuda.synchronize()
+    kernel_timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 10
+    e0.record()
+    for _ in range(reps):
+        price_topk(tx, ty, tx, ty, tu, tv, ti, tj, kmax=k * k, precision=1)
+    e1.record()
+    torch.cuda.synchronize()
+    price_ms = e0.elapsed_time(e1) / reps
+    pk = kernel_timing()
+    kernel_timing(False)
+    pairs = (k * k) ** 2
+    gcols = pairs / (price_ms * 1e-3) / 1e9
+
+    pk_d, src = peaks()
+    # dominant instrumented kernel of the solve and its roofline
+    dom = max(ktimes.items(), key=lambda kv: kv[1][0])
+    roof = roofline(dom, ktimes, pk, pairs, pk_d, src, clk)
+
+    r0 = results[-1]
+    line = {
+        "metric": METRIC, "value": t_dev, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_dev * 1e3, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic", "config": config_dict(args),
+        "e2e": {"value": t_e2e, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "solve": {"status": r0.status, "iters": r0.iters, "direct_iters": r0.direct_iters, "cg_iters": r0.cg_iters,
+                  "rel_gap": r0.rel_gap, "r1_l1": r0.r1_l1, "obj": r0.obj, "psi": r0.psi, "max_fill_pct": r0.max_fill},
+        "plain_fp64": plain,
+        "pricing": {"gcols_per_s": gcols, "ms_per_call": price_ms, "pairs": pairs,
+                    "kernels_ms": {kk: vv[0] / reps for kk, vv in pk.items() if vv[1]}},
+        "kernels_ms_per_step": {kk: vv[0] / args.steps for kk, vv in ktimes.items() if vv[1]},
+        "roofline": roof,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        os.environ.setdefault("OMP_NUM_THREADS", "1")
+        per_iter, done = oracle_sample(k, 2, 0)
+        est = per_iter * r0.iters
+        line["cpu_baseline"] = {"value": est, "unit": "s", "cores": 1, "kind": "oracle",
+                                "sample": f"{done} outer iterations of the CPU oracle on the same instance "
+                                          f"({per_iter:.2f} s each), scaled to the GPU's {r0.iters} iterations"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def roofline(dom, ktimes, pk, pairs, pk_d, src, clk):
+    """Roofline of the dominant kernel: the pricing scan is FP32-ALU bound (4 FP32 operations
+    per pair: add, 2 FMA, compare), the PCG is bandwidth/latency bound, the LDL^T dataflow
+    kernels are latency bound (reported as 'latency')."""
+    name, (ms, cnt) = dom
+    mhz = pk_d.get("sm_max_mhz", 2070.0)
+    alu_peak_ops = SM_COUNT * FP32_LANES_PER_SM * mhz * 1e6      # FP32 lane-ops/s
+    if name == "scan_hist":
+        per = 4.0 * pairs
+        ach = per / (ms / cnt * 1e-3)
+        return {"kernel": name, "bound": "alu", "achieved": ach / 1e12, "peak": alu_peak_ops / 1e12,
+                "unit": "TFLOP/s", "frac": ach / alu_peak_ops, "traffic": None,
+                "peak_source": "152 SMs x 128 FP32 lanes x max SM clock", "ms_per_launch": ms / cnt}
+    # report the pricing scan beside the dominant kernel (the ALU-bound hot loop)
+    sh = pk.get("scan_hist", (0.0, 0))
+    out = {"kernel": name, "bound": "latency", "achieved": None, "peak": None, "unit": None, "frac": None,
+           "traffic": None, "ms_total_per_step": ms, "launches": cnt}
+    if sh[1]:
+        ach = 4.0 * pairs / (sh[0] / sh[1] * 1e-3)
+        out["scan_hist"] = {"bound": "alu", "achieved": ach / 1e12, "peak": alu_peak_ops / 1e12,
+                            "unit": "TFLOP/s", "frac": ach / alu_peak_ops, "ms_per_launch": sh[0] / sh[1],
+                            "peak_source": f"152 SMs x 128 FP32 lanes x {mhz:.0f} MHz ({src})"}
+    return out
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -192,6 +192,16 @@ int ot_price_topk(int32_t m, int32_t n, const int32_t *sx, const int32_t *sy,
 /* Number of kernels this library launched since load (for launch accounting). */
 int64_t ot_kernel_launches(void);
 
+/* Opt-in timing of the library's main kernels with CUDA events recorded on the stream each one
+ * is launched on.  enable(1) clears the totals and starts recording; read() resolves the events
+ * (synchronising on them) and writes, per kernel id, the total milliseconds and the launch count:
+ *   0 pricing scan (histogram pass)   1 pricing scan (gather pass)   2 FP64 recheck
+ *   3 PCG FP64 (persistent kernel)    4 PCG FP32                     5 LDL^T numeric
+ *   6 LDL^T forward solve             7 LDL^T backward solve         8 (reserved)
+ * cap >= 9.  Returns the number of ids written, or OT_ERR_ARG.  Not thread-safe. */
+void ot_kernel_timing_enable(int32_t on);
+int ot_kernel_timing_read(double *ms, int64_t *count, int32_t cap);
+
 /* sizeof(ot_problem), sizeof(ot_options), sizeof(ot_iter_info), sizeof(ot_result) written to
  * out[0..3] (count >= 4), so bindings can check their struct layouts.  Returns 4. */
 int ot_abi_struct_sizes(int64_t *out, int32_t count);

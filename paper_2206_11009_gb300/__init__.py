@@ -5,4 +5,4 @@ Method: Zanetti & Gondzio, arXiv:2206.11009.  The compute path is the CUDA libra
 the package does not load the library; the first call that needs it does, and fails loudly if
 it has not been built (``paper_2206_11009_gb300.build.build()``).
 """
-from .api import Result, Solver, default_options, kernel_launches, price_topk  # noqa: F401
+from .api import Result, Solver, default_options, kernel_launches, kernel_timing, price_topk  # noqa: F401

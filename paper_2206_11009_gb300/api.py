@@ -174,5 +174,17 @@ def price_topk(sx, sy, tx, ty, u, v, sup_i, sup_j, kmax: int, precision: int = 1
     return out_i[:k], out_j[:k], out_d[:k]
 
 
+def kernel_timing(enable: bool | None = None) -> dict:
+    """Enable/disable (and clear) per-kernel event timing, or read {name: (ms, launches)}."""
+    lib = _lib.load()
+    if enable is not None:
+        lib.ot_kernel_timing_enable(int(enable))
+        return {}
+    ms = np.zeros(len(_lib.KERNEL_IDS))
+    cnt = np.zeros(len(_lib.KERNEL_IDS), np.int64)
+    lib.ot_kernel_timing_read(_ptr(ms), _ptr(cnt), len(ms))
+    return {k: (float(a), int(b)) for k, a, b in zip(_lib.KERNEL_IDS, ms, cnt)}
+
+
 def kernel_launches() -> int:
     return int(_lib.load().ot_kernel_launches())

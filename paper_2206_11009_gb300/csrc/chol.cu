@@ -464,9 +464,11 @@ Error chol_numeric(Chol &C, double eps, cudaStream_t st) {
     }
     OT_CUDA(cudaMemsetAsync(C.counter, 0, sizeof(unsigned), st));
     OT_CUDA(cudaMemsetAsync(C.err, 0, sizeof(int), st));
+    ktimer_begin(KT_LDL_NUMERIC, st);
     ldl_numeric_kernel<<<dataflow_grid(n), kT, 0, st>>>(n, C.Lp, C.Li, C.Rp, C.Rj, C.Rpos, C.Lx, C.dperm, C.D,
                                                          C.done, C.counter, C.err, eps);
     OT_LAUNCHED();
+    ktimer_end(KT_LDL_NUMERIC, st);
     int errv = 0;
     OT_CUDA(cudaMemcpyAsync(&errv, C.err, sizeof(int), cudaMemcpyDeviceToHost, st));
     OT_CUDA(cudaStreamSynchronize(st));
@@ -481,14 +483,18 @@ Error chol_solve(Chol &C, const double *b, double *x, cudaStream_t st) {
     OT_LAUNCHED();
     OT_CUDA(cudaMemsetAsync(C.counter, 0, sizeof(unsigned), st));
     OT_CUDA(cudaMemsetAsync(C.err, 0, sizeof(int), st));
+    ktimer_begin(KT_LDL_FORWARD, st);
     ldl_forward_kernel<<<dataflow_grid(n), kT, 0, st>>>(n, C.Rp, C.Rj, C.Rpos, C.Lx, C.D, C.z, C.y, C.done,
                                                          C.counter, C.err);
     OT_LAUNCHED();
+    ktimer_end(KT_LDL_FORWARD, st);
     reset_flags_kernel<<<gridn(n), kT, 0, st>>>(n, C.done);
     OT_LAUNCHED();
     OT_CUDA(cudaMemsetAsync(C.counter, 0, sizeof(unsigned), st));
+    ktimer_begin(KT_LDL_BACKWARD, st);
     ldl_backward_kernel<<<dataflow_grid(n), kT, 0, st>>>(n, C.Lp, C.Li, C.Lx, C.y, C.x, C.done, C.counter, C.err);
     OT_LAUNCHED();
+    ktimer_end(KT_LDL_BACKWARD, st);
     unpermute_kernel<<<gridn(n), kT, 0, st>>>(n, C.perm, C.x, x);
     OT_LAUNCHED();
     int errv = 0;

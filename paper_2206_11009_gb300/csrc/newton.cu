@@ -443,8 +443,11 @@ Error launch_pcg(Newton &W, const Support &S, const T *th, const T *thc, const T
     PcgArgs<T> A{W.m, W.n, S.row_ptr, S.j, S.col_ptr, S.col_row, th, thc, Minv, Dinv, b, x, r, z, p, q, w,
                  W.part, W.bar, W.err, tol, maxit, W.scal};
     void *args[] = {&A};
+    const int kid = sizeof(T) == 8 ? KT_PCG64 : KT_PCG32;
+    ktimer_begin(kid, st);
     OT_CUDA(cudaLaunchCooperativeKernel((void *)pcg_kernel<T>, dim3(G), dim3(kT), args, 0, st));
     OT_LAUNCHED();
+    ktimer_end(kid, st);
     return ok();
 }
 

@@ -461,6 +461,7 @@ Error price_topk(const PriceInput &in, int32_t *out_i, int32_t *out_j, double *o
     OT_LAUNCHED();
 
     const int grid = (int)std::min<int64_t>(ntiles, 8LL * sms);
+    ktimer_begin(KT_SCAN_HIST, st);
     if (fp64)
         scan_kernel<true, false><<<grid, kPT, 0, st>>>(m, n, TI, ncb, ntiles, rows.p, cols.p, in.sx, in.sy,
                                                        in.tx, in.ty, in.u, in.v, geo.p, tmin.p, hist.p,
@@ -470,6 +471,7 @@ Error price_topk(const PriceInput &in, int32_t *out_i, int32_t *out_j, double *o
                                                         in.tx, in.ty, in.u, in.v, geo.p, tmin.p, hist.p,
                                                         nullptr, nullptr, 0, nullptr);
     OT_LAUNCHED();
+    ktimer_end(KT_SCAN_HIST, st);
     OT_CUDA(cudaMemcpyAsync(hist.p + kBins, hist.p, sizeof(unsigned long long) * kBins,
                             cudaMemcpyDeviceToDevice, st));
     if (in.psi > 0) {
@@ -494,6 +496,7 @@ Error price_topk(const PriceInput &in, int32_t *out_i, int32_t *out_j, double *o
     OT_TRY(ci.alloc((int64_t)cap, st));
     OT_TRY(cj.alloc((int64_t)cap, st));
     if (cap > 0) {
+        ktimer_begin(KT_SCAN_GATHER, st);
         if (fp64)
             scan_kernel<true, true><<<grid, kPT, 0, st>>>(m, n, TI, ncb, ntiles, rows.p, cols.p, in.sx, in.sy,
                                                           in.tx, in.ty, in.u, in.v, geo.p, tmin.p, nullptr,
@@ -503,6 +506,7 @@ Error price_topk(const PriceInput &in, int32_t *out_i, int32_t *out_j, double *o
                                                            in.tx, in.ty, in.u, in.v, geo.p, tmin.p, nullptr,
                                                            ci.p, cj.p, cap, &geo.p->ncand);
         OT_LAUNCHED();
+        ktimer_end(KT_SCAN_GATHER, st);
     }
     // support membership needs CSR rows
     DevTemp<int32_t> rp_tmp;
@@ -522,9 +526,11 @@ Error price_topk(const PriceInput &in, int32_t *out_i, int32_t *out_j, double *o
     OT_TRY(dval.alloc(cnt, st));
     if (cnt > 0) {
         const int rb = (int)std::min<int64_t>(8 * sms, ceil_div(cnt, 256));
+        ktimer_begin(KT_RECHECK, st);
         recheck_kernel<<<rb, 256, 0, st>>>(m, (unsigned long long)cnt, ci.p, cj.p, in.sx, in.sy, in.tx, in.ty,
                                            in.u, in.v, rp, in.sup_j, geo.p, key.p, val.p, dkey.p, dval.p);
         OT_LAUNCHED();
+        ktimer_end(KT_RECHECK, st);
         int jbits = 1;
         while (jbits < 64 && ((uint64_t)m * (uint64_t)n - 1) >> jbits) ++jbits;
         OT_TRY(radix_sort_pairs(key.p, val.p, cnt, jbits, st));

@@ -17,6 +17,40 @@ namespace ot {
 std::atomic<int64_t> g_launches{0};
 
 static thread_local std::string t_last_error;
+
+// ---- kernel timing registry (pairs of events per kernel id, resolved when read)
+namespace {
+struct KTimer {
+    bool on = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending[KT_COUNT];
+    std::vector<cudaEvent_t> open[KT_COUNT];
+    double ms[KT_COUNT] = {0};
+    int64_t count[KT_COUNT] = {0};
+    std::vector<cudaEvent_t> pool;
+    cudaEvent_t get() {
+        cudaEvent_t e;
+        if (!pool.empty()) { e = pool.back(); pool.pop_back(); return e; }
+        cudaEventCreate(&e);
+        return e;
+    }
+};
+KTimer g_kt;
+}  // namespace
+
+void ktimer_begin(int id, cudaStream_t st) {
+    if (!g_kt.on) return;
+    cudaEvent_t e = g_kt.get();
+    cudaEventRecord(e, st);
+    g_kt.open[id].push_back(e);
+}
+
+void ktimer_end(int id, cudaStream_t st) {
+    if (!g_kt.on || g_kt.open[id].empty()) return;
+    cudaEvent_t e = g_kt.get();
+    cudaEventRecord(e, st);
+    g_kt.pending[id].push_back({g_kt.open[id].back(), e});
+    g_kt.open[id].pop_back();
+}
 void set_thread_error(const char *msg) { t_last_error = msg ? msg : ""; }
 
 namespace {
@@ -728,6 +762,30 @@ int ot_price_topk(int32_t m, int32_t n, const int32_t *sx, const int32_t *sy, co
 }
 
 int64_t ot_kernel_launches(void) { return g_launches.load(); }
+
+void ot_kernel_timing_enable(int32_t on) {
+    g_kt.on = on != 0;
+    for (int k = 0; k < KT_COUNT; ++k) { g_kt.ms[k] = 0; g_kt.count[k] = 0; }
+}
+
+int ot_kernel_timing_read(double *ms, int64_t *count, int32_t cap) {
+    if (!ms || !count || cap < KT_COUNT) return OT_ERR_ARG;
+    for (int k = 0; k < KT_COUNT; ++k) {
+        for (auto &pr : g_kt.pending[k]) {
+            cudaEventSynchronize(pr.second);
+            float t = 0;
+            cudaEventElapsedTime(&t, pr.first, pr.second);
+            g_kt.ms[k] += t;
+            g_kt.count[k] += 1;
+            g_kt.pool.push_back(pr.first);
+            g_kt.pool.push_back(pr.second);
+        }
+        g_kt.pending[k].clear();
+        ms[k] = g_kt.ms[k];
+        count[k] = g_kt.count[k];
+    }
+    return KT_COUNT;
+}
 
 int ot_abi_struct_sizes(int64_t *out, int32_t count) {
     if (!out || count < 4) return OT_ERR_ARG;
