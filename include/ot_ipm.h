@@ -189,6 +189,28 @@ int ot_price_topk(int32_t m, int32_t n, const int32_t *sx, const int32_t *sy,
                   int32_t precision, int32_t *out_i, int32_t *out_j, double *out_d,
                   int32_t *out_count, void *stream);
 
+/* ot_price_topk without any device allocation.  The paper has no counterpart: this exists for
+ * callers that cannot allocate device memory while they run -- for example a serving process
+ * that reserved its whole memory budget at start-up, where a further cudaMalloc would fail or
+ * evict its caches, or a latency-critical loop that must not pay the implicit device-wide
+ * synchronisation an allocation or release can cause.
+ *
+ * Same arguments, outputs and selection as ot_price_topk.  All temporary buffers come from one
+ * fixed 24 MiB array in device memory, declared statically in the library, so every GPU that
+ * loads the library holds those 24 MiB until the process exits.  Limits: m, n <= 16384, and the
+ * candidate set the selection has to recheck must fit the array (about 400k pairs); beyond either
+ * limit the call returns OT_ERR_ARG or OT_ERR_BUF_TOO_SMALL with a message (ot_last_error) and
+ * changes no output.  The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  Every call on a device uses
+ * the same array and leaves its contents behind (each call clears what it needs), so calls that
+ * overlap on the GPU -- on two streams, or from two threads -- race and must be serialised by
+ * the caller.  No cudaMalloc, cudaFree or allocating library routine is called. */
+int ot_price_topk_noalloc(int32_t m, int32_t n, const int32_t *sx, const int32_t *sy,
+                          const int32_t *tx, const int32_t *ty, const double *u, const double *v,
+                          const int32_t *sup_i, const int32_t *sup_j, int64_t psi, int32_t kmax,
+                          int32_t precision, int32_t *out_i, int32_t *out_j, double *out_d,
+                          int32_t *out_count, void *stream);
+
 /* Number of kernels this library launched since load (for launch accounting). */
 int64_t ot_kernel_launches(void);
 

@@ -65,6 +65,9 @@ SIGNATURES = {
     "ot_price_topk": (c_int32, [c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                 c_void_p, c_void_p, c_int64, c_int32, c_int32, c_void_p, c_void_p, c_void_p,
                                 c_void_p, c_void_p]),
+    "ot_price_topk_noalloc": (c_int32, [c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                        c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_int32, c_void_p,
+                                        c_void_p, c_void_p, c_void_p, c_void_p]),
     "ot_kernel_launches": (c_int64, []),
     "ot_abi_struct_sizes": (c_int32, [c_void_p, c_int32]),
     "ot_kernel_timing_enable": (None, [c_int32]),

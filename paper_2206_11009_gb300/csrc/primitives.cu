@@ -4,6 +4,11 @@
 
 namespace ot {
 
+Arena *&active_arena() {
+    static thread_local Arena *a = nullptr;
+    return a;
+}
+
 // ----------------------------------------------------------------------------- scan
 namespace {
 
