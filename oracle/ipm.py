@@ -30,7 +30,8 @@ Readings where the paper is silent (each listed in the design doc as well):
     of ``oracle.pricing``) at p = s = sqrt(mu) (Section 3.2);
   * support reduction, active once mu <= rm_mu_frac * mu_0: a pair leaves when
     p < rm_p_frac * min(a_i, b_j) and theta < 1; at most m leave (smallest p first, ties by
-    jlin), and no row or column loses its last pair.
+    jlin); the edges of a maximum-weight spanning forest (weights p) never leave, so the support
+    graph stays connected (and no row or column loses its last pair).
 """
 from __future__ import annotations
 
@@ -337,15 +338,22 @@ def removal_select(prob: Problem, st: State, opt: Options, kmax: int):
     if not cand.any():
         return np.zeros(0, dtype=np.int64)
     jlin = st.I + st.J * m
-    for lab, size in ((st.I, m), (st.J, n)):
-        tot = np.bincount(lab, minlength=size)
-        cc = np.bincount(lab[cand], minlength=size)
-        full = np.nonzero((tot > 0) & (cc == tot))[0]
-        for r in full:
-            ent = np.nonzero(lab == r)[0]
-            # keep the entry with the largest p (ties: smallest jlin)
-            o = np.lexsort((jlin[ent], -st.p[ent]))
-            cand[ent[o[0]]] = False
+    # never remove an edge of the maximum-weight spanning forest of the support graph (weights p,
+    # ties: smaller jlin first, Kruskal): the support stays connected, so the restricted problem
+    # cannot split into components whose masses do not balance
+    parent = np.arange(m + n)
+
+    def find(x):
+        while parent[x] != x:
+            parent[x] = parent[parent[x]]
+            x = parent[x]
+        return x
+
+    for e in np.lexsort((jlin, -st.p)):
+        ra, rb = find(int(st.I[e])), find(m + int(st.J[e]))
+        if ra != rb:
+            parent[ra] = rb
+            cand[e] = False
     idx = np.nonzero(cand)[0]
     o = np.lexsort((jlin[idx], st.p[idx]))
     return idx[o[:kmax]]

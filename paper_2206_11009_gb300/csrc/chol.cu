@@ -8,10 +8,9 @@
 // optimality the support approaches a forest, whose S_M is chordal (Theorem 2 and its
 // corollary), so a minimum-degree order produces little or no fill.
 //
-// Numeric LDL^T and both triangular solves run as dataflow kernels: one warp per column,
-// columns dispatched in elimination order by an atomic counter, each waiting (bounded spin)
-// on the completion flags of the columns it depends on.  Only running warps ever take a column,
-// so every awaited column is in progress and the wait ends.  A pivot d <= eps * S_jj becomes
+// Numeric LDL^T and the triangular solves are level scheduled: the host groups the columns by
+// their level in the dependency DAG of L, and one cooperative launch walks the levels with a
+// bounded grid barrier between them, one warp per column.  A pivot d <= eps * S_jj becomes
 // +infinity (the modified factorisation mentioned in Section 4.2), which grounds one node per
 // connected component of the singular S_M.
 #include "chol.cuh"
@@ -35,29 +34,68 @@ inline unsigned gridn(int64_t work) {
 }
 
 // ----------------------------------------------------------------------------- assembly
-__global__ void asm_count_kernel(int m, const int32_t *__restrict__ rp, uint32_t *__restrict__ cnt) {
+// per source row: kept pairs (theta >= drop * row max), kept-only sums, pair counts
+__global__ void sp_rows_kernel(int m, const int32_t *__restrict__ rp, const double *__restrict__ th, double drop,
+                               uint8_t *__restrict__ keep, double *__restrict__ exd, double *__restrict__ Mt,
+                               uint32_t *__restrict__ cnt) {
     GS(i, m) {
-        const int d = rp[i + 1] - rp[i];
-        cnt[i] = (uint32_t)(d * (d - 1));
+        const int lo = rp[i], hi = rp[i + 1];
+        double tmax = 0;
+        for (int e = lo; e < hi; ++e) tmax = fmax(tmax, th[e]);
+        const double cut = drop * tmax;
+        int dk = 0;
+        double pre = 0;
+        for (int e = lo; e < hi; ++e) {
+            const bool k = th[e] >= cut && th[e] > 0;
+            keep[e] = k ? 1 : 0;
+            exd[e] = pre;
+            if (k) { pre += th[e]; ++dk; }
+        }
+        double suf = 0;
+        for (int e = hi - 1; e >= lo; --e) {
+            exd[e] += suf;
+            if (keep[e]) suf += th[e];
+        }
+        Mt[i] = pre;
+        cnt[i] = (uint32_t)(dk * (dk - 1));
     }
 }
 
 __global__ void asm_emit_kernel(int m, int n, const int32_t *__restrict__ rp, const int32_t *__restrict__ sj,
-                                const double *__restrict__ th, const double *__restrict__ Minv,
-                                const uint32_t *__restrict__ off, uint64_t *__restrict__ key,
-                                uint32_t *__restrict__ val, double *__restrict__ raw) {
+                                const double *__restrict__ th, const uint8_t *__restrict__ keep,
+                                const double *__restrict__ Mt, const uint32_t *__restrict__ off,
+                                uint64_t *__restrict__ key, uint32_t *__restrict__ val, double *__restrict__ raw) {
     GS(i, m) {
         const int lo = rp[i], hi = rp[i + 1];
         uint32_t o = off[i];
-        const double mi = Minv[i];
-        for (int a = lo; a < hi; ++a)
+        const double mi = Mt[i] > 0 ? 1.0 / Mt[i] : 0.0;
+        for (int a = lo; a < hi; ++a) {
+            if (!keep[a]) continue;
             for (int b = lo; b < hi; ++b) {
-                if (a == b) continue;
+                if (a == b || !keep[b]) continue;
                 key[o] = (uint64_t)sj[a] * (uint64_t)n + (uint64_t)sj[b];
                 val[o] = o;
                 raw[o] = -(th[a] * th[b]) * mi;
                 ++o;
             }
+        }
+    }
+}
+
+// diagonal of the kept graph's Schur complement: sum over kept pairs theta * (kept others) / Mt
+__global__ void sp_diag_kernel(int n, const int32_t *__restrict__ cp, const int32_t *__restrict__ perm,
+                               const int32_t *__restrict__ crow, const double *__restrict__ th,
+                               const uint8_t *__restrict__ keep, const double *__restrict__ exd,
+                               const double *__restrict__ Mt, double *__restrict__ diag) {
+    GS(j, n) {
+        double d = 0;
+        for (int k = cp[j]; k < cp[j + 1]; ++k) {
+            const int e = perm[k];
+            if (!keep[e]) continue;
+            const double mt = Mt[crow[k]];
+            if (mt > 0) d += th[e] * exd[e] / mt;
+        }
+        diag[j] = d;
     }
 }
 
@@ -132,146 +170,103 @@ __global__ void ldl_scatter_kernel(int64_t nnzA, const int64_t *__restrict__ a2l
     GS(e, nnzA) if (a2l[e] >= 0) Lx[a2l[e]] = Ax[e];
 }
 
-__device__ __forceinline__ bool wait_flag(const int *flag, int *err) {
-    unsigned spins = 0;
-    while (*(volatile const int *)flag == 0) {
-        if (++spins > kSpinLimit || *(volatile int *)err) {
-            atomicCAS(err, 0, (int)OT_ERR_TIMEOUT);
-            return false;
-        }
-        __nanosleep(32);
-    }
-    __threadfence();
-    return true;
-}
+// Level-scheduled kernels.  Columns are grouped by their level in the dependency DAG of L
+// (level(q) = 1 + max level of the columns q depends on); columns of one level are independent.
+// One cooperative launch walks the levels with a grid barrier between them (bounded waits, see
+// grid_barrier), one warp per column.
 
-__global__ void __launch_bounds__(kT)
-ldl_numeric_kernel(int n, const int32_t *__restrict__ Lp, const int32_t *__restrict__ Li,
-                   const int32_t *__restrict__ Rp, const int32_t *__restrict__ Rj,
-                   const int64_t *__restrict__ Rpos, double *Lx, const double *__restrict__ dperm, double *D,
-                   int *done, unsigned *counter, int *err, double eps) {
-    const int lane = threadIdx.x & 31;
-    for (;;) {
-        unsigned q = 0;
-        if (lane == 0) q = atomicAdd(counter, 1u);
-        q = __shfl_sync(0xffffffffu, q, 0);
-        if ((int)q >= n) return;
-        const int lo = Lp[q], hi = Lp[q + 1];
-        const double d0 = dperm[q];
-        double d = d0;
-        for (int t = Rp[q]; t < Rp[q + 1]; ++t) {
-            const int k = Rj[t];
-            int okw = 1;
-            if (lane == 0) okw = wait_flag(done + k, err) ? 1 : 0;
-            okw = __shfl_sync(0xffffffffu, okw, 0);
-            if (!okw) return;
-            const double dk = *(volatile double *)(D + k);
-            if (isinf(dk)) continue;
-            const int64_t pq = Rpos[t];
-            const double ljk = *(volatile double *)(Lx + pq);
-            d -= ljk * ljk * dk;
-            const double f = dk * ljk;
-            const int kend = Lp[k + 1];
-            for (int64_t idx = pq + 1 + lane; idx < kend; idx += 32) {
-                const int r = Li[idx];
-                const double lrk = *(volatile double *)(Lx + idx);
-                int a = lo, b = hi;
-                while (a < b) {
-                    int mid = (a + b) >> 1;
-                    if (Li[mid] < r) a = mid + 1; else b = mid;
-                }
-                if (a < hi && Li[a] == r) Lx[a] -= lrk * f;
-                else atomicExch(err, 2);
+// left-looking column: L(:,q) and D_q from the already final columns of lower levels
+__device__ __forceinline__ void ldl_column(int q, int lane, const int32_t *__restrict__ Lp,
+                                           const int32_t *__restrict__ Li, const int32_t *__restrict__ Rp,
+                                           const int32_t *__restrict__ Rj, const int64_t *__restrict__ Rpos,
+                                           double *Lx, const double *__restrict__ dperm, double *D, int *err,
+                                           double eps) {
+    const int lo = Lp[q], hi = Lp[q + 1];
+    const double d0 = dperm[q];
+    double d = d0;
+    for (int t = Rp[q]; t < Rp[q + 1]; ++t) {
+        const int k = Rj[t];
+        const double dk = D[k];
+        if (isinf(dk)) continue;
+        const int64_t pq = Rpos[t];
+        const double ljk = Lx[pq];
+        d -= ljk * ljk * dk;
+        const double f = dk * ljk;
+        const int kend = Lp[k + 1];
+        for (int64_t idx = pq + 1 + lane; idx < kend; idx += 32) {
+            const int r = Li[idx];
+            const double lrk = Lx[idx];
+            int a = lo, b = hi;
+            while (a < b) {
+                int mid = (a + b) >> 1;
+                if (Li[mid] < r) a = mid + 1; else b = mid;
             }
-            __syncwarp();
+            if (a < hi && Li[a] == r) Lx[a] -= lrk * f;
+            else atomicExch(err, 2);
         }
-        const bool inf_pivot = !(d > eps * d0);
-        for (int idx = lo + lane; idx < hi; idx += 32) Lx[idx] = inf_pivot ? 0.0 : Lx[idx] / d;
         __syncwarp();
-        if (lane == 0) {
-            D[q] = inf_pivot ? INFINITY : d;
-            __threadfence();
-            atomicExch(done + q, 1);
-        }
     }
+    const bool inf_pivot = !(d > eps * d0);
+    for (int idx = lo + lane; idx < hi; idx += 32) Lx[idx] = inf_pivot ? 0.0 : Lx[idx] / d;
+    if (lane == 0) D[q] = inf_pivot ? INFINITY : d;
 }
 
-// ----------------------------------------------------------------------------- solves
-__global__ void permute_kernel(int n, const int32_t *__restrict__ perm, const double *__restrict__ b,
-                               double *__restrict__ z, int *__restrict__ done) {
-    GS(q, n) {
-        z[q] = b[perm[q]];
-        done[q] = 0;
-    }
-}
-
-__global__ void unpermute_kernel(int n, const int32_t *__restrict__ perm, const double *__restrict__ x,
-                                 double *__restrict__ out) {
-    GS(q, n) out[perm[q]] = x[q];
-}
-
-// forward: z_q -= sum_k L(q,k) z_k over the row structure; then z_q /= D_q (0 for +inf pivots)
 __global__ void __launch_bounds__(kT)
-ldl_forward_kernel(int n, const int32_t *__restrict__ Rp, const int32_t *__restrict__ Rj,
-                   const int64_t *__restrict__ Rpos, const double *__restrict__ Lx, const double *__restrict__ D,
-                   double *z, double *y, int *done, unsigned *counter, int *err) {
+ldl_numeric_kernel(int nlev, const int32_t *__restrict__ lvl_ptr, const int32_t *__restrict__ lvl_cols,
+                   const int32_t *__restrict__ Lp, const int32_t *__restrict__ Li, const int32_t *__restrict__ Rp,
+                   const int32_t *__restrict__ Rj, const int64_t *__restrict__ Rpos, double *Lx,
+                   const double *__restrict__ dperm, double *D, unsigned *bar, int *err, double eps) {
     const int lane = threadIdx.x & 31;
-    for (;;) {
-        unsigned q = 0;
-        if (lane == 0) q = atomicAdd(counter, 1u);
-        q = __shfl_sync(0xffffffffu, q, 0);
-        if ((int)q >= n) return;
-        double acc = 0;
-        int okw = 1;
-        for (int t = Rp[q] + lane; t < Rp[q + 1]; t += 32) {
-            const int k = Rj[t];
-            if (!wait_flag(done + k, err)) { okw = 0; break; }
-            acc += Lx[Rpos[t]] * *(volatile double *)(z + k);
-        }
-        if (!__all_sync(0xffffffffu, okw)) return;
-        acc = warp_sum(acc);
-        if (lane == 0) {
-            const double zq = z[q] - acc;
-            z[q] = zq;
-            const double dq = D[q];
-            y[q] = isinf(dq) ? 0.0 : zq / dq;
-            __threadfence();
-            atomicExch(done + q, 1);
-        }
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int lv = 0; lv < nlev; ++lv) {
+        for (int c = lvl_ptr[lv] + gw; c < lvl_ptr[lv + 1]; c += nw)
+            ldl_column(lvl_cols[c], lane, Lp, Li, Rp, Rj, Rpos, Lx, dperm, D, err, eps);
+        if (!grid_barrier(bar, gridDim.x, err)) return;
     }
 }
 
-// backward (reverse order): x_q = y_q - sum_{r > q} L(r,q) x_r
+// forward (z = L^-1 P b, y = D^-1 z, levels ascending) then backward (x = L^-T y, levels
+// descending), out = P^T x; one launch per solve
 __global__ void __launch_bounds__(kT)
-ldl_backward_kernel(int n, const int32_t *__restrict__ Lp, const int32_t *__restrict__ Li,
-                    const double *__restrict__ Lx, const double *__restrict__ y, double *x, int *done,
-                    unsigned *counter, int *err) {
+ldl_solve_kernel(int nlev, const int32_t *__restrict__ lvl_ptr, const int32_t *__restrict__ lvl_cols,
+                 const int32_t *__restrict__ perm, const int32_t *__restrict__ Lp, const int32_t *__restrict__ Li,
+                 const int32_t *__restrict__ Rp, const int32_t *__restrict__ Rj,
+                 const int64_t *__restrict__ Rpos, const double *__restrict__ Lx, const double *__restrict__ D,
+                 const double *__restrict__ b, double *z, double *y, double *x, double *out, unsigned *bar,
+                 int *err) {
     const int lane = threadIdx.x & 31;
-    for (;;) {
-        unsigned c = 0;
-        if (lane == 0) c = atomicAdd(counter, 1u);
-        c = __shfl_sync(0xffffffffu, c, 0);
-        if ((int)c >= n) return;
-        const int q = n - 1 - (int)c;
-        double acc = 0;
-        int okw = 1;
-        for (int t = Lp[q] + lane; t < Lp[q + 1]; t += 32) {
-            const int r = Li[t];
-            if (!wait_flag(done + r, err)) { okw = 0; break; }
-            acc += Lx[t] * *(volatile double *)(x + r);
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int lv = 0; lv < nlev; ++lv) {
+        for (int c = lvl_ptr[lv] + gw; c < lvl_ptr[lv + 1]; c += nw) {
+            const int q = lvl_cols[c];
+            double acc = 0;
+            for (int t = Rp[q] + lane; t < Rp[q + 1]; t += 32) acc += Lx[Rpos[t]] * z[Rj[t]];
+            acc = warp_sum(acc);
+            if (lane == 0) {
+                const double zq = b[perm[q]] - acc;
+                z[q] = zq;
+                const double dq = D[q];
+                y[q] = isinf(dq) ? 0.0 : zq / dq;
+            }
         }
-        if (!__all_sync(0xffffffffu, okw)) return;
-        acc = warp_sum(acc);
-        if (lane == 0) {
-            x[q] = y[q] - acc;
-            __threadfence();
-            atomicExch(done + q, 1);
-        }
+        if (!grid_barrier(bar, gridDim.x, err)) return;
     }
-}
-
-__global__ void reset_flags_kernel(int n, int *done) {
-    GS(q, n) done[q] = 0;
+    for (int lv = nlev - 1; lv >= 0; --lv) {
+        for (int c = lvl_ptr[lv] + gw; c < lvl_ptr[lv + 1]; c += nw) {
+            const int q = lvl_cols[c];
+            double acc = 0;
+            for (int t = Lp[q] + lane; t < Lp[q + 1]; t += 32) acc += Lx[t] * x[Li[t]];
+            acc = warp_sum(acc);
+            if (lane == 0) {
+                const double xq = y[q] - acc;
+                x[q] = xq;
+                out[perm[q]] = xq;
+            }
+        }
+        if (lv > 0 && !grid_barrier(bar, gridDim.x, err)) return;
+    }
 }
 
 template <typename T>
@@ -286,9 +281,17 @@ void dfree(T *&p) {
     p = nullptr;
 }
 
-unsigned dataflow_grid(int n) {
-    // warps = columns in flight; a few per SM are plenty (dependency chains dominate)
-    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, kT / 32), 1024));
+// cooperative grid for the level-scheduled kernels: enough warps for the widest level, capped by
+// what can be co-resident
+template <typename K>
+Error coop_grid(K kernel, int width, int *grid) {
+    int dev = 0, sms = 0, per_sm = 0;
+    OT_CUDA(cudaGetDevice(&dev));
+    OT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    OT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kT, 0));
+    const int want = (int)std::max<int64_t>(1, ceil_div(width, kT / 32));
+    *grid = std::max(1, std::min(want, std::max(per_sm, 1) * sms));
+    return ok();
 }
 
 }  // namespace
@@ -308,26 +311,36 @@ Error chol_alloc(Chol &C, int32_t n) {
     OT_TRY(dalloc(&C.y, n));
     OT_TRY(dalloc(&C.done, n));
     OT_TRY(dalloc(&C.counter, 1));
+    OT_TRY(dalloc(&C.bar, 2));
+    OT_TRY(dalloc(&C.lvl_cols, n));
     OT_TRY(dalloc(&C.err, 1));
-    if (C.max_nnzL <= 0) C.max_nnzL = std::max<int64_t>(400LL * n, 1LL << 22);
+    if (C.max_nnzL <= 0) C.max_nnzL = std::max<int64_t>(48LL * n, 1LL << 20);
     return ok();
 }
 
 void chol_free(Chol &C) {
-    dfree(C.Ap); dfree(C.Aj); dfree(C.Ax); dfree(C.Adiag); dfree(C.a2l);
+    dfree(C.Ap); dfree(C.Aj); dfree(C.Ax); dfree(C.Adiag); dfree(C.a2l); dfree(C.keep); dfree(C.exd); dfree(C.Mt);
     dfree(C.perm); dfree(C.iperm); dfree(C.Lp); dfree(C.Li); dfree(C.Rp); dfree(C.Rj); dfree(C.Rpos);
-    dfree(C.Lx); dfree(C.D); dfree(C.dperm); dfree(C.z); dfree(C.x); dfree(C.y); dfree(C.done); dfree(C.counter);
+    dfree(C.Lx); dfree(C.D); dfree(C.dperm); dfree(C.z); dfree(C.x); dfree(C.y); dfree(C.done); dfree(C.counter); dfree(C.bar); dfree(C.lvl_ptr); dfree(C.lvl_cols);
     dfree(C.err);
     C = Chol();
 }
 
-Error chol_assemble(Chol &C, Newton &W, const Support &S, bool *pattern_changed, cudaStream_t st) {
+Error chol_assemble(Chol &C, Newton &W, const Support &S, double drop, bool *pattern_changed, cudaStream_t st) {
     const int m = W.m, n = W.n;
+    if (S.psi > C.capE) {
+        dfree(C.keep); dfree(C.exd);
+        C.capE = std::max<int64_t>(S.psi, (int64_t)(1.5 * C.capE));
+        OT_TRY(dalloc(&C.keep, C.capE));
+        OT_TRY(dalloc(&C.exd, C.capE));
+    }
+    if (!C.Mt) OT_TRY(dalloc(&C.Mt, m));
+    C.drop = drop;
     DevTemp<uint32_t> cnt, off, tot;
     OT_TRY(cnt.alloc(m, st));
     OT_TRY(off.alloc(m, st));
     OT_TRY(tot.alloc(1, st));
-    asm_count_kernel<<<gridn(m), kT, 0, st>>>(m, S.row_ptr, cnt.p);
+    sp_rows_kernel<<<gridn(m), kT, 0, st>>>(m, S.row_ptr, W.theta, drop, C.keep, C.exd, C.Mt, cnt.p);
     OT_LAUNCHED();
     OT_TRY(scan_exclusive_u32(cnt.p, off.p, m, tot.p, st));
     uint32_t total = 0;
@@ -340,7 +353,8 @@ Error chol_assemble(Chol &C, Newton &W, const Support &S, bool *pattern_changed,
     OT_TRY(flag.alloc(total, st)); OT_TRY(pos.alloc(total, st)); OT_TRY(start.alloc(total, st));
     uint32_t nu = 0;
     if (total > 0) {
-        asm_emit_kernel<<<gridn(m), kT, 0, st>>>(m, n, S.row_ptr, S.j, W.theta, W.Minv, off.p, key.p, val.p, raw.p);
+        asm_emit_kernel<<<gridn(m), kT, 0, st>>>(m, n, S.row_ptr, S.j, W.theta, C.keep, C.Mt, off.p, key.p, val.p,
+                                                 raw.p);
         OT_LAUNCHED();
         int bits = 1;
         while (bits < 64 && (((uint64_t)n * n - 1) >> bits)) ++bits;
@@ -368,7 +382,9 @@ Error chol_assemble(Chol &C, Newton &W, const Support &S, bool *pattern_changed,
     }
     ptr_from_sorted_kernel<<<gridn((int64_t)n + 1), kT, 0, st>>>(nu, n, arow.p, C.Ap);
     OT_LAUNCHED();
-    OT_CUDA(cudaMemcpyAsync(C.Adiag, W.Sdiag, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    sp_diag_kernel<<<gridn(n), kT, 0, st>>>(n, S.col_ptr, S.col_perm, S.col_row, W.theta, C.keep, C.exd, C.Mt,
+                                            C.Adiag);
+    OT_LAUNCHED();
     C.nnzA = nu;
     // pattern on the host (for the symbolic analysis and change detection)
     std::vector<int32_t> hp(n + 1), hj(nu);
@@ -396,14 +412,29 @@ Error chol_symbolic(Chol &C, cudaStream_t st) {
     // 1) a chordal S_M (a forest support, Theorem 2) factors with zero fill in reverse
     //    maximum-cardinality-search order; 2) otherwise minimum degree while its fill stays
     //    small; 3) otherwise nested dissection by level structures.
-    const int64_t lower = (int64_t)g.adj.size() / 2;
+    const int64_t nnzA = (int64_t)g.adj.size();
+    const int64_t lower = nnzA / 2;
     std::vector<int32_t> perm, Lp, Li;
-    ordering::mcs_order(g, perm);
-    bool ok_sym = ordering::symbolic_factor(g, perm, lower, Lp, Li);
+    bool ok_sym = false;
+    // reuse the last ordering while the pattern has not grown much and its fill stays moderate
+    if ((int)C.hperm.size() == n && nnzA <= (C.perm_nnzA * 5) / 4) {
+        perm = C.hperm;
+        ok_sym = ordering::symbolic_factor(g, perm, std::min<int64_t>(C.max_nnzL, 2 * C.perm_nnzL + lower + n), Lp, Li);
+    }
     if (!ok_sym) {
-        if (!ordering::minimum_degree(g, std::min<int64_t>(128LL * n + 4096, 1LL << 22), perm))
-            ordering::nested_dissection(g, perm);
-        ok_sym = ordering::symbolic_factor(g, perm, C.max_nnzL, Lp, Li);
+        ordering::mcs_order(g, perm);
+        ok_sym = ordering::symbolic_factor(g, perm, lower, Lp, Li);
+        if (!ok_sym) {
+            const bool sparse = nnzA <= 16LL * n;
+            if (!sparse || !ordering::minimum_degree(g, std::min<int64_t>(64LL * n + 4096, 1LL << 22), perm))
+                ordering::nested_dissection(g, perm);
+            ok_sym = ordering::symbolic_factor(g, perm, C.max_nnzL, Lp, Li);
+        }
+        if (ok_sym) {
+            C.hperm = perm;
+            C.perm_nnzA = nnzA;
+            C.perm_nnzL = (int64_t)Li.size();
+        }
     }
     if (!ok_sym) return fail(OT_ERR_UNSUPPORTED, "symbolic: fill above the direct-solver limit");
     const int64_t nnzL = (int64_t)Li.size();
@@ -440,6 +471,31 @@ Error chol_symbolic(Chol &C, cudaStream_t st) {
     }
     C.nnzL = nnzL;
     C.fill_pct = 100.0 * (double)nnzL / ((double)n * n);
+    // levels of the dependency DAG of L: level(r) >= level(q) + 1 for every L(r, q) != 0
+    {
+        std::vector<int32_t> level(n, 0);
+        int nlev = 0;
+        for (int q = 0; q < n; ++q) {
+            nlev = std::max(nlev, level[q] + 1);
+            for (int t = Lp[q]; t < Lp[q + 1]; ++t) level[Li[t]] = std::max(level[Li[t]], level[q] + 1);
+        }
+        std::vector<int32_t> lptr(nlev + 1, 0), lcols(n);
+        for (int q = 0; q < n; ++q) lptr[level[q] + 1]++;
+        int width = 0;
+        for (int l = 0; l < nlev; ++l) { width = std::max(width, lptr[l + 1]); lptr[l + 1] += lptr[l]; }
+        std::vector<int32_t> fillp(lptr.begin(), lptr.end() - 1);
+        for (int q = 0; q < n; ++q) lcols[fillp[level[q]]++] = q;
+        if (nlev + 1 > C.cap_lev) {
+            dfree(C.lvl_ptr);
+            C.cap_lev = std::max(nlev + 1, 2 * C.cap_lev);
+            OT_TRY(dalloc(&C.lvl_ptr, C.cap_lev));
+        }
+        OT_CUDA(cudaMemcpyAsync(C.lvl_ptr, lptr.data(), sizeof(int32_t) * (nlev + 1), cudaMemcpyHostToDevice, st));
+        OT_CUDA(cudaMemcpyAsync(C.lvl_cols, lcols.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
+        OT_CUDA(cudaStreamSynchronize(st));
+        C.nlev = nlev;
+        C.max_width = width;
+    }
     OT_CUDA(cudaMemsetAsync(C.err, 0, sizeof(int), st));
     if (C.nnzA > 0) {
         a2l_kernel<<<gridn(n), kT, 0, st>>>(n, C.Ap, C.Aj, C.iperm, C.Lp, C.Li, C.a2l, C.err);
@@ -462,45 +518,46 @@ Error chol_numeric(Chol &C, double eps, cudaStream_t st) {
         ldl_scatter_kernel<<<gridn(C.nnzA), kT, 0, st>>>(C.nnzA, C.a2l, C.Ax, C.Lx);
         OT_LAUNCHED();
     }
-    OT_CUDA(cudaMemsetAsync(C.counter, 0, sizeof(unsigned), st));
+    OT_CUDA(cudaMemsetAsync(C.bar, 0, 2 * sizeof(unsigned), st));
     OT_CUDA(cudaMemsetAsync(C.err, 0, sizeof(int), st));
+    int grid = 1;
+    OT_TRY(coop_grid(ldl_numeric_kernel, C.max_width, &grid));
+    int nlev = C.nlev;
+    const int32_t *lp = C.lvl_ptr, *lc = C.lvl_cols, *Lp = C.Lp, *Li = C.Li, *Rp = C.Rp, *Rj = C.Rj;
+    const int64_t *Rpos = C.Rpos;
+    double *Lx = C.Lx, *D = C.D;
+    const double *dp = C.dperm;
+    unsigned *bar = C.bar;
+    int *err = C.err;
+    void *args[] = {&nlev, &lp, &lc, &Lp, &Li, &Rp, &Rj, &Rpos, &Lx, &dp, &D, &bar, &err, &eps};
     ktimer_begin(KT_LDL_NUMERIC, st);
-    ldl_numeric_kernel<<<dataflow_grid(n), kT, 0, st>>>(n, C.Lp, C.Li, C.Rp, C.Rj, C.Rpos, C.Lx, C.dperm, C.D,
-                                                         C.done, C.counter, C.err, eps);
+    OT_CUDA(cudaLaunchCooperativeKernel((void *)ldl_numeric_kernel, dim3(grid), dim3(kT), args, 0, st));
     OT_LAUNCHED();
     ktimer_end(KT_LDL_NUMERIC, st);
     int errv = 0;
     OT_CUDA(cudaMemcpyAsync(&errv, C.err, sizeof(int), cudaMemcpyDeviceToHost, st));
     OT_CUDA(cudaStreamSynchronize(st));
-    if (errv == OT_ERR_TIMEOUT) return fail(OT_ERR_TIMEOUT, "ldl: dependency wait limit reached");
+    if (errv == OT_ERR_TIMEOUT) return fail(OT_ERR_TIMEOUT, "ldl: grid barrier wait limit reached");
     if (errv) return fail(OT_ERR_NUMERIC, "ldl: update outside the pattern of L");
     return ok();
 }
 
 Error chol_solve(Chol &C, const double *b, double *x, cudaStream_t st) {
-    const int n = C.n;
-    permute_kernel<<<gridn(n), kT, 0, st>>>(n, C.perm, b, C.z, C.done);
-    OT_LAUNCHED();
-    OT_CUDA(cudaMemsetAsync(C.counter, 0, sizeof(unsigned), st));
-    OT_CUDA(cudaMemsetAsync(C.err, 0, sizeof(int), st));
+    OT_CUDA(cudaMemsetAsync(C.bar, 0, 2 * sizeof(unsigned), st));
+    int grid = 1;
+    OT_TRY(coop_grid(ldl_solve_kernel, C.max_width, &grid));
+    int nlev = C.nlev;
+    const int32_t *lp = C.lvl_ptr, *lc = C.lvl_cols, *pm = C.perm, *Lp = C.Lp, *Li = C.Li, *Rp = C.Rp, *Rj = C.Rj;
+    const int64_t *Rpos = C.Rpos;
+    const double *Lx = C.Lx, *D = C.D;
+    double *z = C.z, *y = C.y, *xx = C.x;
+    unsigned *bar = C.bar;
+    int *err = C.err;
+    void *args[] = {&nlev, &lp, &lc, &pm, &Lp, &Li, &Rp, &Rj, &Rpos, &Lx, &D, &b, &z, &y, &xx, &x, &bar, &err};
     ktimer_begin(KT_LDL_FORWARD, st);
-    ldl_forward_kernel<<<dataflow_grid(n), kT, 0, st>>>(n, C.Rp, C.Rj, C.Rpos, C.Lx, C.D, C.z, C.y, C.done,
-                                                         C.counter, C.err);
+    OT_CUDA(cudaLaunchCooperativeKernel((void *)ldl_solve_kernel, dim3(grid), dim3(kT), args, 0, st));
     OT_LAUNCHED();
     ktimer_end(KT_LDL_FORWARD, st);
-    reset_flags_kernel<<<gridn(n), kT, 0, st>>>(n, C.done);
-    OT_LAUNCHED();
-    OT_CUDA(cudaMemsetAsync(C.counter, 0, sizeof(unsigned), st));
-    ktimer_begin(KT_LDL_BACKWARD, st);
-    ldl_backward_kernel<<<dataflow_grid(n), kT, 0, st>>>(n, C.Lp, C.Li, C.Lx, C.y, C.x, C.done, C.counter, C.err);
-    OT_LAUNCHED();
-    ktimer_end(KT_LDL_BACKWARD, st);
-    unpermute_kernel<<<gridn(n), kT, 0, st>>>(n, C.perm, C.x, x);
-    OT_LAUNCHED();
-    int errv = 0;
-    OT_CUDA(cudaMemcpyAsync(&errv, C.err, sizeof(int), cudaMemcpyDeviceToHost, st));
-    OT_CUDA(cudaStreamSynchronize(st));
-    if (errv) return fail(OT_ERR_TIMEOUT, "ldl solve: dependency wait limit reached");
     return ok();
 }
 

@@ -17,6 +17,12 @@ struct Chol {
     int32_t *Ap = nullptr, *Aj = nullptr;
     double *Ax = nullptr;
     double *Adiag = nullptr;            // S_jj (cancellation-free form)
+    // sparsification (drop tolerance): kept flags and kept-only row sums
+    int64_t capE = 0;
+    uint8_t *keep = nullptr;
+    double *exd = nullptr;              // per entry: sum of the OTHER kept theta of its row
+    double *Mt = nullptr;               // per row: sum of kept theta
+    double drop = 0.0;                  // drop tolerance used by the current assembly
     int64_t *a2l = nullptr;             // per A entry: position in Lx (lower part) or -1
     // symbolic (device)
     int64_t nnzL = 0, capL = 0;
@@ -28,20 +34,28 @@ struct Chol {
     double *z = nullptr, *x = nullptr, *y = nullptr;
     int *done = nullptr;
     unsigned *counter = nullptr;
+    unsigned *bar = nullptr;             // grid barrier of the level-scheduled kernels
+    int32_t *lvl_ptr = nullptr, *lvl_cols = nullptr;
+    int nlev = 0, cap_lev = 0, max_width = 0;
     int *err = nullptr;
     bool have_symbolic = false;
     double fill_pct = 0.0;              // nnz(L) / n^2 * 100
     int64_t max_nnzL = 0;               // symbolic gives up beyond this (too much fill)
     // host copy of the pattern used by the current symbolic analysis
     std::vector<int32_t> hAp, hAj;
+    // ordering reused while the pattern does not grow much
+    std::vector<int32_t> hperm;
+    int64_t perm_nnzA = 0, perm_nnzL = 0;
 };
 
 Error chol_alloc(Chol &C, int32_t n);
 void chol_free(Chol &C);
 
-// Assemble S_M = N - V^T M^-1 V (off-diagonal part by rows of V, diagonal from the
-// cancellation-free form) for the current theta.  Sets *pattern_changed.
-Error chol_assemble(Chol &C, Newton &W, const Support &S, bool *pattern_changed, cudaStream_t st);
+// Assemble the Schur complement of the support graph with its negligible pairs dropped: a pair
+// whose theta is below drop x (largest theta of its source row) is left out (drop = 0: the exact
+// S_M = N - V^T M^-1 V).  Off-diagonal part by rows of V; diagonal by the cancellation-free form
+// over the kept pairs, so every connected component still has S e = 0.  Sets *pattern_changed.
+Error chol_assemble(Chol &C, Newton &W, const Support &S, double drop, bool *pattern_changed, cudaStream_t st);
 
 // Minimum-degree ordering and the pattern of L (host), uploaded to the device.  Returns
 // OT_ERR_UNSUPPORTED when nnz(L) would exceed C.max_nnzL (the caller keeps using PCG).
@@ -51,7 +65,8 @@ Error chol_symbolic(Chol &C, cudaStream_t st);
 Error chol_numeric(Chol &C, double eps, cudaStream_t st);
 
 // x = S_M^+ b through L D L^T (+inf pivots ground one node per component), b and x device
-// vectors of length n (natural order).  x may alias nothing.
+// vectors of length n (natural order), one cooperative launch.  Errors of the launch's bounded
+// barrier are reported by the next chol_numeric / by the caller reading C.err.
 Error chol_solve(Chol &C, const double *b, double *x, cudaStream_t st);
 
 }  // namespace ot

@@ -582,6 +582,50 @@ __global__ void axpy_kernel(int64_t count, double a, const double *__restrict__ 
     GRID_STRIDE(k, count) x[k] += a * y[k];
 }
 
+
+// y = S_M x ; partial x.y  (host-driven PCG with the LDL^T preconditioner)
+__global__ void mv_cols_kernel(int n, const int32_t *__restrict__ cp, const int32_t *__restrict__ crow,
+                               const double *__restrict__ thc, const double *__restrict__ w,
+                               const double *__restrict__ x, double *__restrict__ y, double *part) {
+    __shared__ double sh[kT / 32];
+    double acc2 = 0;
+    GRID_STRIDE(j, n) {
+        const double xj = x[j];
+        double acc = 0;
+        for (int k = cp[j]; k < cp[j + 1]; ++k) acc += thc[k] * (xj - w[crow[k]]);
+        y[j] = acc;
+        acc2 += xj * acc;
+    }
+    put_sum(acc2, part, SC_SUM_A, sh);
+}
+
+// x += a p ; r -= a q ; partial r.r
+__global__ void pcg_step_kernel(int n, double a, const double *__restrict__ p, const double *__restrict__ q,
+                                double *__restrict__ x, double *__restrict__ r, double *part) {
+    __shared__ double sh[kT / 32];
+    double rr = 0;
+    GRID_STRIDE(j, n) {
+        x[j] += a * p[j];
+        const double rj = r[j] - a * q[j];
+        r[j] = rj;
+        rr += rj * rj;
+    }
+    put_sum(rr, part, SC_NORM_A, sh);
+}
+
+__global__ void dot_kernel(int n, const double *__restrict__ a, const double *__restrict__ b, double *part,
+                           int slot) {
+    __shared__ double sh[kT / 32];
+    double t = 0;
+    GRID_STRIDE(j, n) t += a[j] * b[j];
+    put_sum(t, part, slot, sh);
+}
+
+// p = z + b p   (b = 0 starts the recurrence)
+__global__ void pcg_dir_kernel(int n, double b, const double *__restrict__ z, double *__restrict__ p) {
+    GRID_STRIDE(j, n) p[j] = z[j] + b * p[j];
+}
+
 template <typename T>
 Error dev_alloc(T **p, int64_t count) {
     OT_CUDA(cudaMalloc((void **)p, sizeof(T) * (size_t)std::max<int64_t>(count, 1)));
@@ -671,32 +715,82 @@ static Error solve_mixed(Newton &W, const Support &S, double tol, int max_cg, do
     return ok();
 }
 
-// LDL^T solve with FP64 iterative refinement (the factorisation may have +inf pivots)
-static Error solve_direct(Newton &W, const Support &S, double tol, double *dv, SolveStats *ss, cudaStream_t st) {
-    const unsigned gn = grid_of(W.n, W.num_sms);
+// PCG (FP64) on S_M preconditioned by the LDL^T factorisation of the sparsified Schur complement
+// (chol.cuh).  With no pair dropped the factorisation is exact and one iteration suffices; the
+// dropped pairs (negligible theta in their row) only perturb the spectrum slightly.
+static Error solve_direct(Newton &W, const Support &S, double tol, int max_cg, double *dv, SolveStats *ss,
+                          cudaStream_t st) {
+    const unsigned gm = grid_of(W.m, W.num_sms), gn = grid_of(W.n, W.num_sms);
     Chol &C = *W.direct;
-    double nrm0;
-    OT_TRY(rhs_norm(W, &nrm0, st));
-    OT_TRY(chol_solve(C, W.rhs, dv, st));
-    double nrm;
-    OT_TRY(residual_norm(W, S, dv, W.res64, &nrm, st));
+    // near optimality the primal-infeasibility part of the right-hand side is tiny next to the
+    // complementarity part, so the direct branch solves far below the PCG tolerance
     const double target = std::min(tol, 1e-10);
-    for (int ref = 0; ref < 3 && nrm > target * nrm0; ++ref) {
-        OT_TRY(chol_solve(C, W.res64, W.x64, st));
-        add_kernel<<<gn, kT, 0, st>>>(W.n, dv, W.x64);
-        OT_LAUNCHED();
-        const double prev = nrm;
-        OT_TRY(residual_norm(W, S, dv, W.res64, &nrm, st));
-        ss->refinements = ref + 1;
-        if (!(nrm < 0.5 * prev)) break;
+    double *x = W.x64, *r = W.r64, *z = W.z64, *p = W.p64, *q = W.q64;
+    double hs[SC_COUNT];
+    OT_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * W.n, st));
+    copy_kernel<<<gn, kT, 0, st>>>(W.n, W.rhs, r);
+    OT_LAUNCHED();
+    OT_TRY(chol_solve(C, r, z, st));
+    pcg_dir_kernel<<<gn, kT, 0, st>>>(W.n, 0.0, z, p);
+    OT_LAUNCHED();
+    dot_kernel<<<gn, kT, 0, st>>>(W.n, r, z, W.part, SC_SUM_B);
+    OT_LAUNCHED();
+    dot_kernel<<<gn, kT, 0, st>>>(W.n, r, r, W.part, SC_NORM_B);
+    OT_LAUNCHED();
+    {
+        Finish f{2, {SC_SUM_B, SC_NORM_B}, {(int)gn, (int)gn}, {0, 0}};
+        OT_TRY(finish(f, W, st));
     }
+    OT_TRY(read_scalars(W, hs, st));
+    double rz = hs[SC_SUM_B];
+    const double bb = hs[SC_NORM_B];
+    double rr = bb;
+    int it = 0;
+    if (bb > 0 && rz > 0) {
+        for (it = 0; it < max_cg;) {
+            mv_rows_kernel<<<gm, kT, 0, st>>>(W.m, S.row_ptr, S.j, W.theta, W.Minv, p, W.w64);
+            OT_LAUNCHED();
+            mv_cols_kernel<<<gn, kT, 0, st>>>(W.n, S.col_ptr, S.col_row, W.theta_col, W.w64, p, q, W.part);
+            OT_LAUNCHED();
+            Finish f1{1, {SC_SUM_A}, {(int)gn}, {0}};
+            OT_TRY(finish(f1, W, st));
+            OT_TRY(read_scalars(W, hs, st));
+            const double pq = hs[SC_SUM_A];
+            if (!(pq > 0)) break;
+            const double alpha = rz / pq;
+            pcg_step_kernel<<<gn, kT, 0, st>>>(W.n, alpha, p, q, x, r, W.part);
+            OT_LAUNCHED();
+            Finish f2{1, {SC_NORM_A}, {(int)gn}, {0}};
+            OT_TRY(finish(f2, W, st));
+            OT_TRY(read_scalars(W, hs, st));
+            rr = hs[SC_NORM_A];
+            ++it;
+            if (rr <= target * target * bb) break;
+            OT_TRY(chol_solve(C, r, z, st));
+            dot_kernel<<<gn, kT, 0, st>>>(W.n, r, z, W.part, SC_SUM_B);
+            OT_LAUNCHED();
+            Finish f3{1, {SC_SUM_B}, {(int)gn}, {0}};
+            OT_TRY(finish(f3, W, st));
+            OT_TRY(read_scalars(W, hs, st));
+            const double rzn = hs[SC_SUM_B];
+            if (!(rzn > 0)) break;
+            pcg_dir_kernel<<<gn, kT, 0, st>>>(W.n, rzn / rz, z, p);
+            OT_LAUNCHED();
+            rz = rzn;
+        }
+    }
+    copy_kernel<<<gn, kT, 0, st>>>(W.n, x, dv);
+    OT_LAUNCHED();
+    int errv = 0;
+    OT_CUDA(cudaMemcpyAsync(&errv, C.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    OT_CUDA(cudaStreamSynchronize(st));
+    if (errv) return fail(OT_ERR_TIMEOUT, "ldl solve: grid barrier wait limit reached");
+    ss->cg_iters = it;
     ss->direct = 1;
-    ss->relres = nrm0 > 0 ? nrm / nrm0 : 0.0;
+    ss->relres = bb > 0 ? std::sqrt(rr / bb) : 0.0;
     return ok();
 }
 
-
-// =====================================================================================
 Error newton_alloc(Newton &W, int32_t m, int32_t n, int64_t cap, int num_sms) {
     W.m = m;
     W.n = n;
@@ -832,7 +926,7 @@ Error newton_solve(Newton &W, const Support &S, const Rhs &R, double cg_tol, int
 
     SolveStats ss;
     if (W.direct) {
-        OT_TRY(solve_direct(W, S, cg_tol, dv, &ss, st));
+        OT_TRY(solve_direct(W, S, cg_tol, max_cg, dv, &ss, st));
     } else if (precision == 0) {
         OT_TRY(solve_pcg64(W, S, cg_tol, max_cg, dv, &ss, st));
     } else {

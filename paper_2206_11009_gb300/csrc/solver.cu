@@ -63,6 +63,8 @@ constexpr double kSwitchDrop = 0.1, kSwitchBack = 1.05;
 constexpr double kPivotEps = 1e-12;
 // a PCG result with relative residual above kPcgFail x tolerance counts as a failed solve
 constexpr double kPcgFail = 10.0;
+// preconditioned-CG iterations above which the next factorisation drops less
+constexpr int kDirectCgMany = 25;
 
 // c-transform lower bound (weak duality): ubar_i = min_j (c_ij - v_j); LB = a^T ubar + b^T v.
 __global__ void ctrans_kernel(CostDev cd, const double *__restrict__ v, unsigned long long *__restrict__ rowmin) {
@@ -136,6 +138,8 @@ struct ot_ipm {
     bool direct_mode = false;
     int64_t psi_min = 0;
     double max_fill = 0.0;
+    double drop = 1e-8;            // drop tolerance of the LDL^T preconditioner (adapted)
+    int direct_cg_last = 0;
     int32_t *pi = nullptr, *pj = nullptr, *pcount = nullptr;
     double *pd = nullptr;
     int *pstrong = nullptr;
@@ -305,12 +309,23 @@ Error do_step(ot_ipm *h, ot_iter_info *info) {
         use_direct = h->direct_mode;
     }
     W.direct = nullptr;
+    const int direct_cg_prev = h->direct_cg_last;
+    h->direct_cg_last = 0;
     // factor S_M once for every solve of this iteration; false when the fill is over budget
     auto enable_direct = [&]() -> Error {
-        bool changed = false;
-        OT_TRY(chol_assemble(h->chol, W, S, &changed, st));
+        // Section 4.2: the drop tolerance is lowered when the preconditioned CG needed too many
+        // iterations, and raised here while the factor's fill is over budget
+        if (direct_cg_prev > kDirectCgMany) h->drop = std::max(h->drop * 1e-2, 0.0);
+        if (h->drop < 1e-14) h->drop = 0.0;
         Error e = ok();
-        if (changed || !h->chol.have_symbolic) e = chol_symbolic(h->chol, st);
+        for (int attempt = 0; attempt < 4; ++attempt) {
+            bool changed = false;
+            OT_TRY(chol_assemble(h->chol, W, S, h->drop, &changed, st));
+            e = ok();
+            if (changed || !h->chol.have_symbolic) e = chol_symbolic(h->chol, st);
+            if (e.code != OT_ERR_UNSUPPORTED) break;
+            h->drop = h->drop > 0 ? std::min(h->drop * 1e2, 1e-2) : 1e-10;
+        }
         if (e.code == OT_OK) {
             OT_TRY(chol_numeric(h->chol, kPivotEps, st));
             W.direct = &h->chol;
@@ -330,6 +345,7 @@ Error do_step(ot_ipm *h, ot_iter_info *info) {
         W.fp64_fallback = o.linear_solver != 0;  // in auto mode a failed solve escalates to LDL^T
         OT_TRY(newton_solve(W, S, R, tol, o.max_cg, o.precision, du, dv, ds, dp, &ss, st));
         cg += ss.cg_iters;
+        if (ss.direct) h->direct_cg_last = std::max(h->direct_cg_last, ss.cg_iters);
         if (!W.direct && o.linear_solver == 0 && !(ss.relres <= kPcgFail * tol)) {
             OT_TRY(enable_direct());
             if (W.direct) {

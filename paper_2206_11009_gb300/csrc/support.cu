@@ -3,6 +3,9 @@
 #include "pricing.cuh"
 #include "primitives.cuh"
 
+#include <algorithm>
+#include <vector>
+
 namespace ot {
 namespace {
 
@@ -126,26 +129,6 @@ __global__ void removal_cand_kernel(int64_t psi, const int32_t *__restrict__ si,
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < psi; e += (int64_t)gridDim.x * blockDim.x) {
         const double thr = frac * fmin(a[si[e]], b[sj[e]]);
         flag[e] = (p[e] < thr && p[e] / s[e] < 1.0) ? 1 : 0;
-    }
-}
-
-// A row (or column, through the CSC permutation) whose every pair is flagged keeps the pair
-// with the largest p; equal p: the smaller jlin (within a row: smaller j; within a column:
-// smaller i -- both are the first in storage order).
-__global__ void removal_guard_kernel(int nseg, const int32_t *__restrict__ ptr, const int32_t *__restrict__ perm,
-                                     const double *__restrict__ p, uint8_t *__restrict__ flag) {
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nseg; q += (int64_t)gridDim.x * blockDim.x) {
-        const int lo = ptr[q], hi = ptr[q + 1];
-        if (lo >= hi) continue;
-        bool all = true;
-        int best = -1;
-        double bp = -1.0;
-        for (int k = lo; k < hi; ++k) {
-            const int e = perm ? perm[k] : k;
-            if (!flag[e]) { all = false; break; }
-            if (p[e] > bp) { bp = p[e]; best = e; }
-        }
-        if (all && best >= 0) flag[best] = 0;
     }
 }
 
@@ -331,10 +314,45 @@ Error removal_flags(const Support &S, int32_t m, int32_t n, const double *a_s, c
     if (psi == 0) return ok();
     removal_cand_kernel<<<grid_for(psi), 256, 0, st>>>(psi, S.i, S.j, S.p, S.s, a_s, b_s, rm_p_frac, flag);
     OT_LAUNCHED();
-    removal_guard_kernel<<<grid_for(m), 256, 0, st>>>(m, S.row_ptr, nullptr, S.p, flag);
-    OT_LAUNCHED();
-    removal_guard_kernel<<<grid_for(n), 256, 0, st>>>(n, S.col_ptr, S.col_perm, S.p, flag);
-    OT_LAUNCHED();
+    // Keep a maximum-weight spanning forest of the support graph (weights p, ties: smaller jlin
+    // first; Kruskal on the host): the support stays connected, so the restricted problem cannot
+    // split into components whose masses do not balance (and no row or column empties).
+    {
+        std::vector<int32_t> hi(psi), hj(psi);
+        std::vector<double> hp(psi);
+        std::vector<uint8_t> hf(psi);
+        OT_CUDA(cudaMemcpyAsync(hi.data(), S.i, sizeof(int32_t) * psi, cudaMemcpyDeviceToHost, st));
+        OT_CUDA(cudaMemcpyAsync(hj.data(), S.j, sizeof(int32_t) * psi, cudaMemcpyDeviceToHost, st));
+        OT_CUDA(cudaMemcpyAsync(hp.data(), S.p, sizeof(double) * psi, cudaMemcpyDeviceToHost, st));
+        OT_CUDA(cudaMemcpyAsync(hf.data(), flag, psi, cudaMemcpyDeviceToHost, st));
+        OT_CUDA(cudaStreamSynchronize(st));
+        bool any = false;
+        for (int64_t e = 0; e < psi && !any; ++e) any = hf[e] != 0;
+        if (any) {
+            std::vector<int64_t> order(psi);
+            for (int64_t e = 0; e < psi; ++e) order[e] = e;
+            std::sort(order.begin(), order.end(), [&](int64_t x, int64_t y) {
+                if (hp[x] != hp[y]) return hp[x] > hp[y];
+                const uint64_t jx = (uint64_t)hi[x] + (uint64_t)hj[x] * m, jy = (uint64_t)hi[y] + (uint64_t)hj[y] * m;
+                return jx < jy;
+            });
+            std::vector<int32_t> parent(m + n);
+            for (int v = 0; v < m + n; ++v) parent[v] = v;
+            auto find = [&](int x) {
+                while (parent[x] != x) { parent[x] = parent[parent[x]]; x = parent[x]; }
+                return x;
+            };
+            for (int64_t e : order) {
+                const int ra = find(hi[e]), rb = find(m + hj[e]);
+                if (ra != rb) {
+                    parent[ra] = rb;
+                    hf[e] = 0;
+                }
+            }
+            OT_CUDA(cudaMemcpyAsync(flag, hf.data(), psi, cudaMemcpyHostToDevice, st));
+            OT_CUDA(cudaStreamSynchronize(st));
+        }
+    }
     DevTemp<uint32_t> f32, pos, tot;
     OT_TRY(f32.alloc(psi, st)); OT_TRY(pos.alloc(psi, st)); OT_TRY(tot.alloc(1, st));
     count_flags_kernel<<<grid_for(psi), 256, 0, st>>>(psi, flag, f32.p);

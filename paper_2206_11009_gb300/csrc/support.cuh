@@ -46,9 +46,9 @@ Error initial_support(const CostDev &c, double thr, int32_t **out_i, int32_t **o
 Error rebuild_views(Support &S, int32_t m, int32_t n, cudaStream_t st);
 
 // Removal (reading of Section 3.2): flag[e] = 1 for the pairs that leave -- candidates
-// p < rm_p_frac*min(a_i, b_j) with theta < 1; no row or column loses its last pair (the entry
-// with the largest p, then the smallest jlin, is kept); at most kmax leave, smallest (p, jlin)
-// first.  *count (host) receives the number flagged.
+// p < rm_p_frac*min(a_i, b_j) with theta < 1, except the edges of a maximum-weight spanning
+// forest of the support graph (weights p, ties by jlin), so the support stays connected; at most
+// kmax leave, smallest (p, jlin) first.  *count (host) receives the number flagged.
 Error removal_flags(const Support &S, int32_t m, int32_t n, const double *a_s, const double *b_s,
                     double rm_p_frac, int32_t kmax, uint8_t *flag, int64_t *count, cudaStream_t st);
 
