@@ -48,6 +48,23 @@ struct Chol {
     int64_t perm_nnzA = 0, perm_nnzL = 0;
 };
 
+// Dense LDL^T of the assembled S_M (moderate n, a sizeable fraction of the factor dense).
+struct DenseLDL {
+    int32_t n = 0;
+    double *A = nullptr;      // n x n column-major; strictly lower part holds L after dense_factor
+    double *LD = nullptr;     // n x 64 panel scratch (L21 D1)
+    double *D = nullptr, *d0 = nullptr, *z = nullptr, *part = nullptr;
+    unsigned *bar = nullptr;
+    int *err = nullptr;
+};
+
+Error dense_alloc(DenseLDL &M, int32_t n);
+void dense_free(DenseLDL &M);
+// factor the matrix assembled in C (chol_assemble with drop = 0); +inf pivots as in chol_numeric
+Error dense_factor(DenseLDL &M, const Chol &C, double eps, cudaStream_t st);
+// x = S^+ b (one cooperative launch); b and x distinct device vectors of length n
+Error dense_solve(DenseLDL &M, const double *b, double *x, cudaStream_t st);
+
 Error chol_alloc(Chol &C, int32_t n);
 void chol_free(Chol &C);
 

@@ -730,7 +730,10 @@ static Error solve_direct(Newton &W, const Support &S, double tol, int max_cg, d
     OT_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * W.n, st));
     copy_kernel<<<gn, kT, 0, st>>>(W.n, W.rhs, r);
     OT_LAUNCHED();
-    OT_TRY(chol_solve(C, r, z, st));
+    auto precond = [&](const double *in, double *out) -> Error {
+        return W.dense ? dense_solve(*W.dense, in, out, st) : chol_solve(C, in, out, st);
+    };
+    OT_TRY(precond(r, z));
     pcg_dir_kernel<<<gn, kT, 0, st>>>(W.n, 0.0, z, p);
     OT_LAUNCHED();
     dot_kernel<<<gn, kT, 0, st>>>(W.n, r, z, W.part, SC_SUM_B);
@@ -766,7 +769,7 @@ static Error solve_direct(Newton &W, const Support &S, double tol, int max_cg, d
             rr = hs[SC_NORM_A];
             ++it;
             if (rr <= target * target * bb) break;
-            OT_TRY(chol_solve(C, r, z, st));
+            OT_TRY(precond(r, z));
             dot_kernel<<<gn, kT, 0, st>>>(W.n, r, z, W.part, SC_SUM_B);
             OT_LAUNCHED();
             Finish f3{1, {SC_SUM_B}, {(int)gn}, {0}};
@@ -782,7 +785,7 @@ static Error solve_direct(Newton &W, const Support &S, double tol, int max_cg, d
     copy_kernel<<<gn, kT, 0, st>>>(W.n, x, dv);
     OT_LAUNCHED();
     int errv = 0;
-    OT_CUDA(cudaMemcpyAsync(&errv, C.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    OT_CUDA(cudaMemcpyAsync(&errv, W.dense ? W.dense->err : C.err, sizeof(int), cudaMemcpyDeviceToHost, st));
     OT_CUDA(cudaStreamSynchronize(st));
     if (errv) return fail(OT_ERR_TIMEOUT, "ldl solve: grid barrier wait limit reached");
     ss->cg_iters = it;

@@ -48,6 +48,7 @@ struct Newton {
     int pcg_grid = 0;
     // direct branch: when set, S_M x = rhs is solved by its LDL^T factorisation (chol.cuh)
     struct Chol *direct = nullptr;
+    struct DenseLDL *dense = nullptr;   // when set (with direct), solve with the dense factor
     int fallbacks = 0;        // mixed-precision solves redone in FP64
     bool fp64_fallback = true;  // redo a failed mixed-precision solve with FP64 PCG
 };

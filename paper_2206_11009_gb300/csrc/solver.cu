@@ -65,6 +65,8 @@ constexpr double kPivotEps = 1e-12;
 constexpr double kPcgFail = 10.0;
 // preconditioned-CG iterations above which the next factorisation drops less
 constexpr int kDirectCgMany = 25;
+// up to this many targets the direct branch factors S_M densely
+constexpr int kDenseMaxN = 8192;
 
 // c-transform lower bound (weak duality): ubar_i = min_j (c_ij - v_j); LB = a^T ubar + b^T v.
 __global__ void ctrans_kernel(CostDev cd, const double *__restrict__ v, unsigned long long *__restrict__ rowmin) {
@@ -134,6 +136,7 @@ struct ot_ipm {
     int cur = 0;
     Newton W;
     Chol chol;
+    DenseLDL dense;
     std::vector<int64_t> psi_hist;
     bool direct_mode = false;
     int64_t psi_min = 0;
@@ -309,10 +312,25 @@ Error do_step(ot_ipm *h, ot_iter_info *info) {
         use_direct = h->direct_mode;
     }
     W.direct = nullptr;
+    W.dense = nullptr;
     const int direct_cg_prev = h->direct_cg_last;
     h->direct_cg_last = 0;
     // factor S_M once for every solve of this iteration; false when the fill is over budget
     auto enable_direct = [&]() -> Error {
+        if (n <= kDenseMaxN) {
+            // moderate n: exact assembly and a dense blocked LDL^T (the exact factor is dense-ish)
+            if (!h->dense.A) OT_TRY(dense_alloc(h->dense, n));
+            bool changed = false;
+            OT_TRY(chol_assemble(h->chol, W, S, 0.0, &changed, st));
+            OT_CUDA(cudaMemsetAsync(h->dense.err, 0, sizeof(int), st));
+            OT_TRY(dense_factor(h->dense, h->chol, kPivotEps, st));
+            W.direct = &h->chol;
+            W.dense = &h->dense;
+            h->max_fill = 100.0;
+            h->direct_total++;
+            inf.direct = 1;
+            return ok();
+        }
         // Section 4.2: the drop tolerance is lowered when the preconditioned CG needed too many
         // iterations, and raised here while the factor's fill is over budget
         if (direct_cg_prev > kDirectCgMany) h->drop = std::max(h->drop * 1e-2, 0.0);
@@ -742,6 +760,7 @@ void ot_ipm_destroy(ot_ipm_t *h) {
     support_free(h->S[1]);
     newton_free(h->W);
     chol_free(h->chol);
+    dense_free(h->dense);
     void *ptrs[] = {h->a_s, h->b_s, h->C, h->sx, h->sy, h->tx, h->ty, h->u, h->v, h->pi, h->pj, h->pd,
                     h->pcount, h->pstrong, h->rowmin, h->lbv};
     for (void *p : ptrs)
