@@ -274,9 +274,10 @@ def main():
     gcols = pairs / (price_ms * 1e-3) / 1e9
 
     pk_d, src = peaks()
-    # dominant instrumented kernel of the solve and its roofline
-    dom = max(ktimes.items(), key=lambda kv: kv[1][0])
-    roof = roofline(dom, ktimes, pk, pairs, pk_d, src, clk)
+    table = kernel_table(ktimes, pk_d, src)
+    roof = roofline(table)
+    # the pricing scan beside it (ALU-bound hot loop of the pricing)
+    ptable = kernel_table(pk, pk_d, src)
 
     r0 = results[-1]
     line = {
@@ -288,9 +289,8 @@ def main():
         "solve": {"status": r0.status, "iters": r0.iters, "direct_iters": r0.direct_iters, "cg_iters": r0.cg_iters,
                   "rel_gap": r0.rel_gap, "r1_l1": r0.r1_l1, "obj": r0.obj, "psi": r0.psi, "max_fill_pct": r0.max_fill},
         "plain_fp64": plain,
-        "pricing": {"gcols_per_s": gcols, "ms_per_call": price_ms, "pairs": pairs,
-                    "kernels_ms": {kk: vv[0] / reps for kk, vv in pk.items() if vv[1]}},
-        "kernels_ms_per_step": {kk: vv[0] / args.steps for kk, vv in ktimes.items() if vv[1]},
+        "pricing": {"gcols_per_s": gcols, "ms_per_call": price_ms, "pairs": pairs, "kernels": ptable},
+        "kernels": table,
         "roofline": roof,
         "clocks": clk,
     }
@@ -309,29 +309,41 @@ def main():
     return 0
 
 
-def roofline(dom, ktimes, pk, pairs, pk_d, src, clk):
-    """Roofline of the dominant kernel: the pricing scan is FP32-ALU bound (4 FP32 operations
-    per pair: add, 2 FMA, compare), the PCG is bandwidth/latency bound, the LDL^T dataflow
-    kernels are latency bound (reported as 'latency')."""
-    name, (ms, cnt) = dom
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 rate (nominal; no measured FP64 peak is available)
+
+
+def kernel_table(ktimes, pk_d, src):
+    """Per instrumented kernel: total ms, launches and achieved rate against its bound."""
     mhz = pk_d.get("sm_max_mhz", 2070.0)
-    alu_peak_ops = SM_COUNT * FP32_LANES_PER_SM * mhz * 1e6      # FP32 lane-ops/s
-    if name == "scan_hist":
-        per = 4.0 * pairs
-        ach = per / (ms / cnt * 1e-3)
-        return {"kernel": name, "bound": "alu", "achieved": ach / 1e12, "peak": alu_peak_ops / 1e12,
-                "unit": "TFLOP/s", "frac": ach / alu_peak_ops, "traffic": None,
-                "peak_source": "152 SMs x 128 FP32 lanes x max SM clock", "ms_per_launch": ms / cnt}
-    # report the pricing scan beside the dominant kernel (the ALU-bound hot loop)
-    sh = pk.get("scan_hist", (0.0, 0))
-    out = {"kernel": name, "bound": "latency", "achieved": None, "peak": None, "unit": None, "frac": None,
-           "traffic": None, "ms_total_per_step": ms, "launches": cnt}
-    if sh[1]:
-        ach = 4.0 * pairs / (sh[0] / sh[1] * 1e-3)
-        out["scan_hist"] = {"bound": "alu", "achieved": ach / 1e12, "peak": alu_peak_ops / 1e12,
-                            "unit": "TFLOP/s", "frac": ach / alu_peak_ops, "ms_per_launch": sh[0] / sh[1],
-                            "peak_source": f"152 SMs x 128 FP32 lanes x {mhz:.0f} MHz ({src})"}
+    alu_peak = SM_COUNT * FP32_LANES_PER_SM * mhz * 1e6            # FP32 lane-ops/s
+    hbm_peak = pk_d.get("hbm_gbs", 6800.0)                          # GB/s
+    out = {}
+    for name, (ms, cnt, work) in ktimes.items():
+        if not cnt:
+            continue
+        row = {"ms": ms, "launches": cnt, "ms_per_launch": ms / cnt}
+        sec = ms * 1e-3
+        if name in ("scan_hist", "scan_gather") and work:
+            row.update(bound="alu", achieved=work / sec / 1e12, peak=alu_peak / 1e12, unit="TFLOP/s",
+                       frac=work / sec / alu_peak,
+                       peak_source=f"152 SMs x 128 FP32 lanes x {mhz:.0f} MHz (unit counts)")
+        elif name in ("pcg32", "pcg64", "ldl_forward") and work:
+            row.update(bound="hbm", achieved=work / sec / 1e9, peak=hbm_peak, unit="GB/s",
+                       frac=work / sec / 1e9 / hbm_peak, peak_source=f"MEASURED_PEAKS.json hbm_gbs ({src})")
+        elif name == "ldl_numeric" and work:
+            row.update(bound="alu", achieved=work / sec / 1e12, peak=FP64_NOMINAL_TFLOPS, unit="TFLOP/s",
+                       frac=work / sec / 1e12 / FP64_NOMINAL_TFLOPS, peak_source="nominal GB300 FP64 rate")
+        out[name] = row
     return out
+
+
+def roofline(table):
+    """Roofline object of the dominant instrumented kernel (largest total device time)."""
+    name, row = max(table.items(), key=lambda kv: kv[1]["ms"])
+    return {"kernel": name, "bound": row.get("bound"), "achieved": row.get("achieved"), "peak": row.get("peak"),
+            "unit": row.get("unit"), "frac": row.get("frac"), "traffic": None,
+            "ms_per_launch": row["ms_per_launch"], "launches": row["launches"],
+            "peak_source": row.get("peak_source")}
 
 
 if __name__ == "__main__":

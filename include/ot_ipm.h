@@ -216,13 +216,17 @@ int64_t ot_kernel_launches(void);
 
 /* Opt-in timing of the library's main kernels with CUDA events recorded on the stream each one
  * is launched on.  enable(1) clears the totals and starts recording; read() resolves the events
- * (synchronising on them) and writes, per kernel id, the total milliseconds and the launch count:
+ * (synchronising on them) and writes, per kernel id, the total milliseconds, the launch count and
+ * (work != NULL) the algorithmic work of those launches: FP32 operations for the pricing scan
+ * (4 per pair), bytes for the PCG (per CG iteration: theta, index and gathered vector entry per
+ * support pair in both passes, plus the row/column vectors), FP64 flops for the LDL^T numeric
+ * factorisation (2n^3/3 when dense), bytes for the dense solves (L read twice):
  *   0 pricing scan (histogram pass)   1 pricing scan (gather pass)   2 FP64 recheck
  *   3 PCG FP64 (persistent kernel)    4 PCG FP32                     5 LDL^T numeric
  *   6 LDL^T forward solve             7 LDL^T backward solve         8 (reserved)
  * cap >= 9.  Returns the number of ids written, or OT_ERR_ARG.  Not thread-safe. */
 void ot_kernel_timing_enable(int32_t on);
-int ot_kernel_timing_read(double *ms, int64_t *count, int32_t cap);
+int ot_kernel_timing_read(double *ms, int64_t *count, double *work, int32_t cap);
 
 /* sizeof(ot_problem), sizeof(ot_options), sizeof(ot_iter_info), sizeof(ot_result) written to
  * out[0..3] (count >= 4), so bindings can check their struct layouts.  Returns 4. */

@@ -71,7 +71,7 @@ SIGNATURES = {
     "ot_kernel_launches": (c_int64, []),
     "ot_abi_struct_sizes": (c_int32, [c_void_p, c_int32]),
     "ot_kernel_timing_enable": (None, [c_int32]),
-    "ot_kernel_timing_read": (c_int32, [c_void_p, c_void_p, c_int32]),
+    "ot_kernel_timing_read": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32]),
 }
 
 KERNEL_IDS = ["scan_hist", "scan_gather", "recheck", "pcg64", "pcg32", "ldl_numeric", "ldl_forward",

@@ -175,15 +175,16 @@ def price_topk(sx, sy, tx, ty, u, v, sup_i, sup_j, kmax: int, precision: int = 1
 
 
 def kernel_timing(enable: bool | None = None) -> dict:
-    """Enable/disable (and clear) per-kernel event timing, or read {name: (ms, launches)}."""
+    """Enable/disable (and clear) per-kernel event timing, or read {name: (ms, launches, work)}."""
     lib = _lib.load()
     if enable is not None:
         lib.ot_kernel_timing_enable(int(enable))
         return {}
     ms = np.zeros(len(_lib.KERNEL_IDS))
     cnt = np.zeros(len(_lib.KERNEL_IDS), np.int64)
-    lib.ot_kernel_timing_read(_ptr(ms), _ptr(cnt), len(ms))
-    return {k: (float(a), int(b)) for k, a, b in zip(_lib.KERNEL_IDS, ms, cnt)}
+    work = np.zeros(len(_lib.KERNEL_IDS))
+    lib.ot_kernel_timing_read(_ptr(ms), _ptr(cnt), _ptr(work), len(ms))
+    return {k: (float(a), int(b), float(c)) for k, a, b, c in zip(_lib.KERNEL_IDS, ms, cnt, work)}
 
 
 def kernel_launches() -> int:

@@ -53,6 +53,7 @@ struct DenseLDL {
     int32_t n = 0;
     double *A = nullptr;      // n x n column-major; strictly lower part holds L after dense_factor
     double *LD = nullptr;     // n x 64 panel scratch (L21 D1)
+    double *Linv = nullptr;   // n x 64: inverses of the unit lower diagonal blocks
     double *D = nullptr, *d0 = nullptr, *z = nullptr, *part = nullptr;
     unsigned *bar = nullptr;
     int *err = nullptr;

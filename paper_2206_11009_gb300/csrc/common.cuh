@@ -56,6 +56,8 @@ enum KernelId : int {
 };
 void ktimer_begin(int id, cudaStream_t st);
 void ktimer_end(int id, cudaStream_t st);
+// algorithmic work (bytes or flops, per kernel id) accumulated while timing is on
+void ktimer_add_work(int id, double work);
 inline Error fail(int code, const std::string &m) { return Error{code, m}; }
 
 // ------------------------------------------------------------------------ small utilities

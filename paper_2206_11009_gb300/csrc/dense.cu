@@ -41,7 +41,7 @@ __global__ void dense_scatter_kernel(int n, const int32_t *__restrict__ Ap, cons
 // (1) diagonal block [k, k+bs) in shared memory
 __global__ void __launch_bounds__(kT)
 dense_diag_kernel(int n, int k, int bs, double *__restrict__ A, double *__restrict__ D,
-                  const double *__restrict__ d0, double eps) {
+                  const double *__restrict__ d0, double eps, double *__restrict__ Linv) {
     __shared__ double S[kB][kB + 1];
     __shared__ double s_d;
     __shared__ int s_inf;
@@ -75,6 +75,18 @@ dense_diag_kernel(int n, int k, int bs, double *__restrict__ A, double *__restri
     for (int t = threadIdx.x; t < bs * bs; t += blockDim.x) {
         const int i = t % bs, j = t / bs;
         if (i > j) A[(int64_t)(k + j) * n + (k + i)] = S[i][j];
+    }
+    // inverse of the unit lower block, column by column: X[:,c] solves L X[:,c] = e_c, written
+    // to Linv (row k+i, column c) so that the solves need no serial substitution
+    __syncthreads();
+    for (int c = threadIdx.x; c < bs; c += blockDim.x) {
+        double x[kB];
+        for (int i = 0; i < bs; ++i) {
+            double t = (i == c) ? 1.0 : 0.0;
+            for (int l = c; l < i; ++l) t -= S[i][l] * x[l];
+            x[i] = (i < c) ? 0.0 : t;
+        }
+        for (int i = 0; i < bs; ++i) Linv[(int64_t)c * n + (k + i)] = x[i];
     }
 }
 
@@ -154,10 +166,16 @@ dense_update_kernel(int n, int k, int bs, double *__restrict__ A, const double *
         }
 }
 
-// forward L z = b, y = D^-1 z, backward L^T x = y; one cooperative launch
+// forward L z = b, y = D^-1 z, backward L^T x = y; one cooperative launch.  The diagonal blocks
+// are applied through their stored inverses (small GEMVs by block 0), the off-diagonal panels by
+// all blocks; one grid barrier after each step.
 __global__ void __launch_bounds__(kT)
-dense_solve_kernel(int n, const double *__restrict__ A, const double *__restrict__ D, const double *__restrict__ b,
-                   double *z, double *x, double *part /* gridDim x kB */, unsigned *bar, int *err) {
+dense_solve_kernel(int n, const double *__restrict__ A, const double *__restrict__ Linv,
+                   const double *__restrict__ D, const double *__restrict__ b, double *z, double *x,
+                   double *part /* gridDim x kB */, unsigned *bar, int *err) {
+    __shared__ double vb[kB];
+    __shared__ double red[kT / 32][32];
+    __shared__ double Ls[kB][kB + 1];      // inverse diagonal block (block 0 only)
     const int lane = threadIdx.x & 31;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -166,35 +184,48 @@ dense_solve_kernel(int n, const double *__restrict__ A, const double *__restrict
     // ---- forward
     for (int k = 0; k < n; k += kB) {
         const int bs = min(kB, n - k);
-        if (blockIdx.x == 0 && threadIdx.x < 32) {
-            // unit lower diagonal block, one warp: z_j -= sum_{l<j} L(j,l) z_l
-            for (int j = 1; j < bs; ++j) {
-                double acc = 0;
-                for (int l = lane; l < j; l += 32) acc += A[(int64_t)(k + l) * n + (k + j)] * z[k + l];
-                acc = warp_sum(acc);
-                if (lane == 0) z[k + j] -= acc;
-                __syncwarp();
+        if (blockIdx.x == 0) {
+            // z_blk = L11^-1 z_blk, the inverse block staged in shared memory
+            for (int q = threadIdx.x; q < kB * kB; q += blockDim.x) {
+                const int i = q % kB, c = q / kB;
+                Ls[c][i] = (i < bs && c < bs) ? Linv[(int64_t)c * n + (k + i)] : 0.0;
             }
+            if (threadIdx.x < kB) vb[threadIdx.x] = threadIdx.x < bs ? z[k + threadIdx.x] : 0.0;
+            __syncthreads();
+            if (threadIdx.x < bs) {
+                const int i = threadIdx.x;
+                double t = 0;
+#pragma unroll 16
+                for (int c = 0; c < kB; ++c) t += Ls[c][i] * vb[c];
+                z[k + i] = t;
+            }
+            __syncthreads();
         }
         if (!grid_barrier(bar, gridDim.x, err)) return;
         if (k + bs < n) {
+            if (threadIdx.x < kB) vb[threadIdx.x] = threadIdx.x < bs ? z[k + threadIdx.x] : 0.0;
+            __syncthreads();
             for (int64_t r = k + bs + tid; r < n; r += stride) {
                 double acc = 0;
-                for (int l = 0; l < bs; ++l) acc += A[(int64_t)(k + l) * n + r] * z[k + l];
+                if (bs == kB) {
+#pragma unroll 16
+                    for (int l = 0; l < kB; ++l) acc += A[(int64_t)(k + l) * n + r] * vb[l];
+                } else {
+                    for (int l = 0; l < bs; ++l) acc += A[(int64_t)(k + l) * n + r] * vb[l];
+                }
                 z[r] -= acc;
             }
+            __syncthreads();
             if (!grid_barrier(bar, gridDim.x, err)) return;
         }
     }
     // ---- diagonal
     for (int64_t r = tid; r < n; r += stride) x[r] = isinf(D[r]) ? 0.0 : z[r] / D[r];
     if (!grid_barrier(bar, gridDim.x, err)) return;
-    // ---- backward: x_k-block -= L21^T x_rest, then the transposed diagonal block
-    __shared__ double red[kT / 32][32];
+    // ---- backward: t = y_blk - L21^T x_rest, then x_blk = L11^-T t
     for (int k = ((n - 1) / kB) * kB; k >= 0; k -= kB) {
         const int bs = min(kB, n - k);
         if (k + bs < n) {
-            // partial dot products L21(:, j)^T x over this block's rows, 32 panel columns per pass
             for (int h = 0; h < bs; h += 32) {
                 const int hb = min(32, bs - h);
                 double acc[32];
@@ -221,22 +252,29 @@ dense_solve_kernel(int n, const double *__restrict__ A, const double *__restrict
             }
             if (!grid_barrier(bar, gridDim.x, err)) return;
         }
-        if (blockIdx.x == 0 && threadIdx.x < 32) {
-            if (k + bs < n) {
-                for (int j = lane; j < bs; j += 32) {
-                    double s = 0;
-                    for (unsigned g = 0; g < gridDim.x; ++g) s += part[(int64_t)g * kB + j];
-                    x[k + j] -= s;
+        if (blockIdx.x == 0) {
+            for (int q = threadIdx.x; q < kB * kB; q += blockDim.x) {
+                const int i = q % kB, c = q / kB;
+                Ls[c][i] = (i < bs && c < bs) ? Linv[(int64_t)c * n + (k + i)] : 0.0;
+            }
+            if (threadIdx.x < kB) {
+                double t = 0.0;
+                if (threadIdx.x < bs) {
+                    t = x[k + threadIdx.x];
+                    if (k + bs < n)
+                        for (unsigned g = 0; g < gridDim.x; ++g) t -= part[(int64_t)g * kB + threadIdx.x];
                 }
-                __syncwarp();
+                vb[threadIdx.x] = t;
             }
-            for (int j = bs - 2; j >= 0; --j) {
-                double acc = 0;
-                for (int l = j + 1 + lane; l < bs; l += 32) acc += A[(int64_t)(k + j) * n + (k + l)] * x[k + l];
-                acc = warp_sum(acc);
-                if (lane == 0) x[k + j] -= acc;
-                __syncwarp();
+            __syncthreads();
+            if (threadIdx.x < bs) {
+                const int c = threadIdx.x;  // x_c = sum_i Linv(i, c) t_i   (L11^-T t)
+                double v = 0;
+#pragma unroll 16
+                for (int i = 0; i < kB; ++i) v += Ls[c][i] * vb[i];
+                x[k + c] = v;
             }
+            __syncthreads();
         }
         if (!grid_barrier(bar, gridDim.x, err)) return;
     }
@@ -248,6 +286,7 @@ Error dense_alloc(DenseLDL &M, int32_t n) {
     M.n = n;
     OT_CUDA(cudaMalloc((void **)&M.A, sizeof(double) * (size_t)n * n));
     OT_CUDA(cudaMalloc((void **)&M.LD, sizeof(double) * (size_t)n * kB));
+    OT_CUDA(cudaMalloc((void **)&M.Linv, sizeof(double) * (size_t)n * kB));
     OT_CUDA(cudaMalloc((void **)&M.D, sizeof(double) * n));
     OT_CUDA(cudaMalloc((void **)&M.d0, sizeof(double) * n));
     OT_CUDA(cudaMalloc((void **)&M.z, sizeof(double) * n));
@@ -258,7 +297,7 @@ Error dense_alloc(DenseLDL &M, int32_t n) {
 }
 
 void dense_free(DenseLDL &M) {
-    for (void *p : {(void *)M.A, (void *)M.LD, (void *)M.D, (void *)M.d0, (void *)M.z, (void *)M.part,
+    for (void *p : {(void *)M.A, (void *)M.LD, (void *)M.Linv, (void *)M.D, (void *)M.d0, (void *)M.z, (void *)M.part,
                     (void *)M.bar, (void *)M.err})
         if (p) cudaFree(p);
     M = DenseLDL();
@@ -272,7 +311,7 @@ Error dense_factor(DenseLDL &M, const Chol &C, double eps, cudaStream_t st) {
     ktimer_begin(KT_LDL_NUMERIC, st);
     for (int k = 0; k < n; k += kB) {
         const int bs = std::min(kB, n - k);
-        dense_diag_kernel<<<1, kT, 0, st>>>(n, k, bs, M.A, M.D, M.d0, eps);
+        dense_diag_kernel<<<1, kT, 0, st>>>(n, k, bs, M.A, M.D, M.d0, eps, M.Linv);
         OT_LAUNCHED();
         if (k + bs < n) {
             dense_panel_kernel<<<(unsigned)ceil_div(n - k - bs, kT), kT, 0, st>>>(n, k, bs, M.A, M.D, M.LD);
@@ -283,6 +322,7 @@ Error dense_factor(DenseLDL &M, const Chol &C, double eps, cudaStream_t st) {
         }
     }
     ktimer_end(KT_LDL_NUMERIC, st);
+    ktimer_add_work(KT_LDL_NUMERIC, 2.0 * (double)n * n * n / 3.0);
     return ok();
 }
 
@@ -291,19 +331,20 @@ Error dense_solve(DenseLDL &M, const double *b, double *x, cudaStream_t st) {
     OT_CUDA(cudaGetDevice(&dev));
     OT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     OT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dense_solve_kernel, kT, 0));
-    int grid = std::max(1, std::min<int>(std::min(per_sm, 1) * sms, (int)ceil_div(M.n, kT)));
+    int grid = std::max(1, std::min<int>(std::min(per_sm, 2) * sms, (int)ceil_div(M.n, kT)));
     grid = std::min(grid, 4096);
     OT_CUDA(cudaMemsetAsync(M.bar, 0, 2 * sizeof(unsigned), st));
     int n = M.n;
-    const double *A = M.A, *D = M.D;
+    const double *A = M.A, *Li = M.Linv, *D = M.D;
     double *z = M.z, *part = M.part;
     unsigned *bar = M.bar;
     int *err = M.err;
-    void *args[] = {&n, &A, &D, &b, &z, &x, &part, &bar, &err};
+    void *args[] = {&n, &A, &Li, &D, &b, &z, &x, &part, &bar, &err};
     ktimer_begin(KT_LDL_FORWARD, st);
     OT_CUDA(cudaLaunchCooperativeKernel((void *)dense_solve_kernel, dim3(grid), dim3(kT), args, 0, st));
     OT_LAUNCHED();
     ktimer_end(KT_LDL_FORWARD, st);
+    ktimer_add_work(KT_LDL_FORWARD, 8.0 * (double)n * n);  // reads L twice
     return ok();
 }
 

@@ -306,7 +306,7 @@ struct PcgArgs {
     const int32_t *rp, *sj, *cp, *crow;
     const T *th, *thc, *Minv, *Dinv;
     const T *b;
-    T *x, *r, *z, *p, *q, *w;
+    T *x, *r, *z, *pa, *pb, *q, *w;   // pa / pb: double-buffered search direction
     double *part;  // 3 slots x gridDim
     unsigned *bar;
     int *err;
@@ -315,20 +315,47 @@ struct PcgArgs {
     double *scal;  // SC_PCG_ITERS, SC_PCG_RELRES
 };
 
-// Jacobi-preconditioned CG, persistent cooperative kernel.  One iteration:
-//   w = M^-1 V p          (rows)      | barrier
-//   q = S_M p = sum_i theta_ij (p_j - w_i)  and  p.q  (columns)  | barrier
-//   x += a p, r -= a q, z = D^-1 r, r.z, r.r          | barrier
-//   p = z + b p                                         | barrier
+constexpr int kPcgT = 512;   // threads per PCG block
+
+// sum of `x` over the g lanes of an aligned lane group (g a power of two <= 32)
+template <typename T>
+__device__ __forceinline__ T group_sum(T x, int g) {
+    for (int o = g >> 1; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// every block sums the gridDim partials of `slots` (fixed order: deterministic, identical in
+// all blocks); warp 0 does it, lanes taking strided partials
+__device__ __forceinline__ void sum_partials(const double *part, unsigned G, int nslots, double *out_sh) {
+    if (threadIdx.x < 32) {
+        for (int s = 0; s < nslots; ++s) {
+            double a = 0;
+            for (unsigned k = threadIdx.x; k < G; k += 32) a += part[(int64_t)s * G + k];
+            a = warp_sum(a);
+            if (threadIdx.x == 0) out_sh[s] = a;
+        }
+    }
+    __syncthreads();
+}
+
+// Jacobi-preconditioned CG on S_M, persistent cooperative kernel.  Rows and columns are handled
+// by lane groups of g threads (g ~ the average row/column length).  With p_k = z_k + beta_k p_{k-1}
+// formed on the fly from z and the previous direction (double buffer), one iteration is
+//   row pass:    w_i = M_i^-1 sum_j theta_ij p_j                                   | barrier
+//   column pass: p_j stored; q_j = sum_i theta_ij (p_j - w_i); partial p.q           | barrier
+//   update:      alpha = rz/pq; x += alpha p; r -= alpha q; z = D^-1 r; partial r.z, r.r | barrier
 // Dot products are accumulated in double in every precision.
 template <typename T>
-__global__ void __launch_bounds__(kT) pcg_kernel(PcgArgs<T> A) {
-    __shared__ double sh[kT / 32];
+__global__ void __launch_bounds__(kPcgT) pcg_kernel(PcgArgs<T> A, int g) {
+    __shared__ double sh[kPcgT / 32];
     __shared__ double s_val[3];
     const unsigned G = gridDim.x;
     const int n = A.n, m = A.m;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)G * blockDim.x;
+    const int lg = threadIdx.x & (g - 1);                 // lane within its group
+    const int64_t grp = tid / g, ngrp = stride / g;
+    const int64_t wgrp0 = (tid & ~(int64_t)31) / g;          // first group of this warp
     double *P0 = A.part, *P1 = A.part + G, *P2 = A.part + 2 * G;
 
     double bb = 0, rz = 0;
@@ -338,7 +365,7 @@ __global__ void __launch_bounds__(kT) pcg_kernel(PcgArgs<T> A) {
         A.r[j] = bj;
         const T zj = A.Dinv[j] * bj;
         A.z[j] = zj;
-        A.p[j] = zj;
+        A.pa[j] = (T)0;
         bb += (double)bj * (double)bj;
         rz += (double)bj * (double)zj;
     }
@@ -347,54 +374,64 @@ __global__ void __launch_bounds__(kT) pcg_kernel(PcgArgs<T> A) {
         if (threadIdx.x == 0) { P0[blockIdx.x] = s0; P1[blockIdx.x] = s1; }
     }
     if (!grid_barrier(A.bar, G, A.err)) return;
-    if (threadIdx.x == 0) {
-        double a0 = 0, a1 = 0;
-        for (unsigned k = 0; k < G; ++k) { a0 += P0[k]; a1 += P1[k]; }
-        s_val[0] = a0; s_val[1] = a1;
-    }
-    __syncthreads();
+    sum_partials(A.part, G, 2, s_val);
     bb = s_val[0];
     rz = s_val[1];
     const double tol2 = A.tol * A.tol * bb;
     int it = 0;
     double rr = bb;
+    T beta = (T)0;
+    T *pprev = A.pa, *pcur = A.pb;
     if (bb > 0.0 && rz > 0.0) {
         for (it = 0; it < A.maxit;) {
-            // w = M^-1 V p
-            for (int64_t i = tid; i < m; i += stride) {
+            // row pass with p = z + beta pprev (the trip count is uniform across a warp: groups
+            // past the end contribute zero but still take part in the shuffles)
+            for (int64_t i0 = wgrp0; i0 < m; i0 += ngrp) {
+                const int64_t i = i0 + (grp - wgrp0);
                 T acc = (T)0;
-                for (int e = A.rp[i]; e < A.rp[i + 1]; ++e) acc += A.th[e] * A.p[A.sj[e]];
-                A.w[i] = A.Minv[i] * acc;
+                if (i < m) {
+                    const int lo = A.rp[i], hi = A.rp[i + 1];
+                    for (int e = lo + lg; e < hi; e += g) {
+                        const int j = A.sj[e];
+                        acc += A.th[e] * (A.z[j] + beta * pprev[j]);
+                    }
+                }
+                acc = group_sum(acc, g);
+                if (lg == 0 && i < m) A.w[i] = A.Minv[i] * acc;
             }
             if (!grid_barrier(A.bar, G, A.err)) return;
+            // column pass
             double pq = 0;
-            for (int64_t j = tid; j < n; j += stride) {
-                const T pj = A.p[j];
-                T acc = (T)0;
-                for (int k = A.cp[j]; k < A.cp[j + 1]; ++k) acc += A.thc[k] * (pj - A.w[A.crow[k]]);
-                A.q[j] = acc;
-                pq += (double)pj * (double)acc;
+            for (int64_t j0 = wgrp0; j0 < n; j0 += ngrp) {
+                const int64_t j = j0 + (grp - wgrp0);
+                T pj = (T)0, acc = (T)0;
+                if (j < n) {
+                    pj = A.z[j] + beta * pprev[j];
+                    const int lo = A.cp[j], hi = A.cp[j + 1];
+                    for (int k = lo + lg; k < hi; k += g) acc += A.thc[k] * (pj - A.w[A.crow[k]]);
+                }
+                acc = group_sum(acc, g);
+                if (lg == 0 && j < n) {
+                    A.q[j] = acc;
+                    pcur[j] = pj;
+                    pq += (double)pj * (double)acc;
+                }
             }
             {
                 double s0 = block_sum(pq, sh);
                 if (threadIdx.x == 0) P0[blockIdx.x] = s0;
             }
             if (!grid_barrier(A.bar, G, A.err)) return;
-            if (threadIdx.x == 0) {
-                double a0 = 0;
-                for (unsigned k = 0; k < G; ++k) a0 += P0[k];
-                s_val[0] = a0;
-            }
-            __syncthreads();
+            sum_partials(A.part, G, 1, s_val);
             pq = s_val[0];
             if (!(pq > 0.0)) break;  // breakdown (exact zero direction or loss of definiteness)
             const double alpha = rz / pq;
             double rzn = 0, rrn = 0;
             for (int64_t j = tid; j < n; j += stride) {
-                const T xj = A.x[j] + (T)alpha * A.p[j];
+                const T pj = pcur[j];
                 const T rj = A.r[j] - (T)alpha * A.q[j];
                 const T zj = A.Dinv[j] * rj;
-                A.x[j] = xj;
+                A.x[j] += (T)alpha * pj;
                 A.r[j] = rj;
                 A.z[j] = zj;
                 rzn += (double)rj * (double)zj;
@@ -405,20 +442,14 @@ __global__ void __launch_bounds__(kT) pcg_kernel(PcgArgs<T> A) {
                 if (threadIdx.x == 0) { P1[blockIdx.x] = s1; P2[blockIdx.x] = s2; }
             }
             if (!grid_barrier(A.bar, G, A.err)) return;
-            if (threadIdx.x == 0) {
-                double a1 = 0, a2 = 0;
-                for (unsigned k = 0; k < G; ++k) { a1 += P1[k]; a2 += P2[k]; }
-                s_val[1] = a1; s_val[2] = a2;
-            }
-            __syncthreads();
+            sum_partials(A.part + G, G, 2, s_val + 1);
             rzn = s_val[1];
             rr = s_val[2];
             ++it;
             if (rr <= tol2 || !(rzn > 0.0)) break;
-            const double beta = rzn / rz;
+            beta = (T)(rzn / rz);
             rz = rzn;
-            for (int64_t j = tid; j < n; j += stride) A.p[j] = A.z[j] + (T)beta * A.p[j];
-            if (!grid_barrier(A.bar, G, A.err)) return;
+            T *t = pprev; pprev = pcur; pcur = t;
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -430,24 +461,32 @@ __global__ void __launch_bounds__(kT) pcg_kernel(PcgArgs<T> A) {
 template <typename T>
 Error launch_pcg(Newton &W, const Support &S, const T *th, const T *thc, const T *Minv, const T *Dinv,
                  const T *b, T *x, T *r, T *z, T *p, T *q, T *w, double tol, int maxit, cudaStream_t st) {
-    int dev;
-    OT_CUDA(cudaGetDevice(&dev));
     int per_sm = 0;
-    OT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg_kernel<T>, kT, 0));
-    int maxg = std::max(1, per_sm) * W.num_sms;
-    int G = W.pcg_grid > 0 ? W.pcg_grid
-                           : (int)std::max<int64_t>(1, ceil_div(std::max<int64_t>(W.m, W.n), 512));
+    OT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg_kernel<T>, kPcgT, 0));
+    // lane-group size ~ half the average row length (power of two, <= 32)
+    const double avg = (double)std::max<int64_t>(S.psi, 1) / (double)std::max(W.m, 1);
+    int g = 1;
+    while (g < 32 && 2 * g <= avg) g <<= 1;
+    const int64_t threads = (int64_t)std::max(W.m, W.n) * g;
+    const int maxg = std::max(1, per_sm) * W.num_sms;
+    int G = W.pcg_grid > 0 ? W.pcg_grid : (int)std::max<int64_t>(1, ceil_div(threads, kPcgT));
     G = std::min(G, std::min(maxg, kMaxPartBlocks / 3));
     OT_CUDA(cudaMemsetAsync(W.bar, 0, 2 * sizeof(unsigned), st));
     OT_CUDA(cudaMemsetAsync(W.err, 0, sizeof(int), st));
-    PcgArgs<T> A{W.m, W.n, S.row_ptr, S.j, S.col_ptr, S.col_row, th, thc, Minv, Dinv, b, x, r, z, p, q, w,
+    T *pb = (T *)W.pcg_pb;
+    if (sizeof(T) == 4) pb = (T *)W.pcg_pb32;
+    PcgArgs<T> A{W.m, W.n, S.row_ptr, S.j, S.col_ptr, S.col_row, th, thc, Minv, Dinv, b, x, r, z, p, pb, q, w,
                  W.part, W.bar, W.err, tol, maxit, W.scal};
-    void *args[] = {&A};
+    void *args[] = {&A, &g};
     const int kid = sizeof(T) == 8 ? KT_PCG64 : KT_PCG32;
     ktimer_begin(kid, st);
-    OT_CUDA(cudaLaunchCooperativeKernel((void *)pcg_kernel<T>, dim3(G), dim3(kT), args, 0, st));
+    OT_CUDA(cudaLaunchCooperativeKernel((void *)pcg_kernel<T>, dim3(G), dim3(kPcgT), args, 0, st));
     OT_LAUNCHED();
     ktimer_end(kid, st);
+    // algorithmic bytes of one CG iteration: both passes read theta, an index and a gathered
+    // vector entry per support pair, plus the per-row / per-column vectors
+    W.pcg_bytes_per_iter = (double)S.psi * 2.0 * (2.0 * sizeof(T) + 4.0) + (double)W.m * (3.0 * 4.0 + 2.0 * sizeof(T)) +
+                           (double)W.n * (2.0 * 4.0 + 12.0 * sizeof(T));
     return ok();
 }
 
@@ -673,6 +712,7 @@ static Error solve_pcg64(Newton &W, const Support &S, double tol, int max_cg, do
     if (errv) return fail(OT_ERR_TIMEOUT, "pcg: grid barrier wait limit reached");
     ss->cg_iters = (int)hs[SC_PCG_ITERS];
     ss->relres = hs[SC_PCG_RELRES];
+    ktimer_add_work(KT_PCG64, ss->cg_iters * W.pcg_bytes_per_iter);
     copy_kernel<<<gn, kT, 0, st>>>(W.n, W.x64, dv);
     OT_LAUNCHED();
     return ok();
@@ -706,6 +746,7 @@ static Error solve_mixed(Newton &W, const Support &S, double tol, int max_cg, do
         OT_CUDA(cudaMemcpy(&errv, W.err, sizeof(int), cudaMemcpyDeviceToHost));
         if (errv) return fail(OT_ERR_TIMEOUT, "pcg: grid barrier wait limit reached");
         const int its = (int)hs[SC_PCG_ITERS];
+        ktimer_add_work(KT_PCG32, its * W.pcg_bytes_per_iter);
         ss->cg_iters += its;
         budget -= std::max(its, 1);
         ss->refinements = ref + 1;
@@ -804,7 +845,8 @@ Error newton_alloc(Newton &W, int32_t m, int32_t n, int64_t cap, int num_sms) {
     for (double **p : {&W.r1b, &W.beta2, &W.N, &W.Dinv, &W.Sdiag, &W.rhs, &W.dv, &W.dv2, &W.dv3, &W.res64, &W.y64, &W.x64,
                        &W.r64, &W.z64, &W.p64, &W.q64})
         OT_TRY(dev_alloc(p, n));
-    for (float **p : {&W.Dinv32, &W.b32, &W.x32, &W.r32, &W.z32, &W.p32, &W.q32}) OT_TRY(dev_alloc(p, n));
+    for (float **p : {&W.Dinv32, &W.b32, &W.x32, &W.r32, &W.z32, &W.p32, &W.q32, &W.pcg_pb32}) OT_TRY(dev_alloc(p, n));
+    OT_TRY(dev_alloc(&W.pcg_pb, n));
     OT_TRY(dev_alloc(&W.parent, (int64_t)m + n));
     OT_TRY(dev_alloc(&W.comp_sum, (int64_t)m + n));
     OT_TRY(dev_alloc(&W.comp_cnt, (int64_t)m + n));
@@ -832,7 +874,7 @@ void newton_free(Newton &W) {
     void *ptrs[] = {W.c, W.theta, W.excl, W.r2, W.r3, W.g, W.dp, W.ds, W.dp2, W.ds2, W.dp3, W.ds3, W.theta32,
                     W.theta_col, W.theta32_col, W.flag, W.r1a, W.beta1, W.M, W.Minv, W.du, W.du2, W.du3, W.w64,
                     W.Minv32, W.w32, W.r1b, W.beta2, W.N, W.Dinv, W.Sdiag, W.rhs, W.dv, W.dv2, W.dv3, W.res64, W.y64,
-                    W.x64, W.r64, W.z64, W.p64, W.q64, W.Dinv32, W.b32, W.x32, W.r32, W.z32, W.p32, W.q32,
+                    W.x64, W.r64, W.z64, W.p64, W.q64, W.Dinv32, W.b32, W.x32, W.r32, W.z32, W.p32, W.q32, W.pcg_pb, W.pcg_pb32,
                     W.parent, W.comp_sum, W.comp_cnt, W.part, W.scal, W.bar, W.err};
     for (void *p : ptrs)
         if (p) cudaFree(p);

@@ -46,6 +46,9 @@ struct Newton {
     unsigned *bar = nullptr;
     int *err = nullptr;
     int pcg_grid = 0;
+    double *pcg_pb = nullptr;     // second direction buffer of the PCG (fp64 / fp32)
+    float *pcg_pb32 = nullptr;
+    double pcg_bytes_per_iter = 0.0;
     // direct branch: when set, S_M x = rhs is solved by its LDL^T factorisation (chol.cuh)
     struct Chol *direct = nullptr;
     struct DenseLDL *dense = nullptr;   // when set (with direct), solve with the dense factor

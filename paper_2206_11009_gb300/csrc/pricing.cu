@@ -472,6 +472,7 @@ Error price_topk(const PriceInput &in, int32_t *out_i, int32_t *out_j, double *o
                                                         nullptr, nullptr, 0, nullptr);
     OT_LAUNCHED();
     ktimer_end(KT_SCAN_HIST, st);
+    ktimer_add_work(KT_SCAN_HIST, 4.0 * (double)m * (double)n);
     OT_CUDA(cudaMemcpyAsync(hist.p + kBins, hist.p, sizeof(unsigned long long) * kBins,
                             cudaMemcpyDeviceToDevice, st));
     if (in.psi > 0) {

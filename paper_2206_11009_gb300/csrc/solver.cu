@@ -26,6 +26,7 @@ struct KTimer {
     std::vector<cudaEvent_t> open[KT_COUNT];
     double ms[KT_COUNT] = {0};
     int64_t count[KT_COUNT] = {0};
+    double work[KT_COUNT] = {0};
     std::vector<cudaEvent_t> pool;
     cudaEvent_t get() {
         cudaEvent_t e;
@@ -42,6 +43,10 @@ void ktimer_begin(int id, cudaStream_t st) {
     cudaEvent_t e = g_kt.get();
     cudaEventRecord(e, st);
     g_kt.open[id].push_back(e);
+}
+
+void ktimer_add_work(int id, double w) {
+    if (g_kt.on) g_kt.work[id] += w;
 }
 
 void ktimer_end(int id, cudaStream_t st) {
@@ -800,10 +805,10 @@ int64_t ot_kernel_launches(void) { return g_launches.load(); }
 
 void ot_kernel_timing_enable(int32_t on) {
     g_kt.on = on != 0;
-    for (int k = 0; k < KT_COUNT; ++k) { g_kt.ms[k] = 0; g_kt.count[k] = 0; }
+    for (int k = 0; k < KT_COUNT; ++k) { g_kt.ms[k] = 0; g_kt.count[k] = 0; g_kt.work[k] = 0; }
 }
 
-int ot_kernel_timing_read(double *ms, int64_t *count, int32_t cap) {
+int ot_kernel_timing_read(double *ms, int64_t *count, double *work, int32_t cap) {
     if (!ms || !count || cap < KT_COUNT) return OT_ERR_ARG;
     for (int k = 0; k < KT_COUNT; ++k) {
         for (auto &pr : g_kt.pending[k]) {
@@ -818,6 +823,7 @@ int ot_kernel_timing_read(double *ms, int64_t *count, int32_t cap) {
         g_kt.pending[k].clear();
         ms[k] = g_kt.ms[k];
         count[k] = g_kt.count[k];
+        if (work) work[k] = g_kt.work[k];
     }
     return KT_COUNT;
 }
