@@ -6,6 +6,7 @@
 #include "primitives.cuh"
 
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 namespace ot {
@@ -458,6 +459,262 @@ __global__ void __launch_bounds__(kPcgT) pcg_kernel(PcgArgs<T> A, int g) {
     }
 }
 
+// ---- cluster variant (FP32).  One thread-block cluster of R CTAs (16 where the GPC allows it)
+// runs the whole CG.  CTA r owns a contiguous slice of the rows and one of the columns of S_M
+// (balanced on pairs + rows / columns, never more than 2*ceil(m/R)+1 rows or 2*ceil(n/R)+1
+// columns), keeps its slices of theta and of the indices in shared memory (a tail that does not
+// fit is read from global memory), and every CTA keeps full copies of the direction p, the
+// preconditioned residual z and w = M^{-1} V p in shared memory.  A CTA pushes the w / z entries
+// it computes into every CTA's copy with distributed-shared-memory stores, and the hardware
+// cluster barrier (release / acquire at cluster scope) publishes them together with the partial
+// dot products.  Three barriers per iteration, no spin loop: the CTAs of a cluster are
+// co-scheduled, and every CTA takes the same branch decisions because it sums the same partials
+// in the same order.
+constexpr int kClT = 1024;
+constexpr int kClMaxR = 16;
+
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_addr(const void *local, unsigned rank) {
+    uint32_t ra;
+    const uint32_t la = (uint32_t)__cvta_generic_to_shared(local);
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(la), "r"(rank));
+    return ra;
+}
+
+__device__ __forceinline__ void st_cluster(uint32_t addr, float v) {
+    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+}
+
+__device__ __forceinline__ float ld_cluster(uint32_t addr) {
+    float v;
+    asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
+    return v;
+}
+
+// Sums shared slots [0, ns) over the R CTAs (R <= 32): lane q of warp 0 reads CTA q's slots, a
+// fixed xor-shuffle tree adds them (the same order in every CTA, so every CTA gets the same bits),
+// and the sums land in out[0, ns) for the whole block.
+__device__ __forceinline__ void cluster_reduce(const float *slots, int ns, unsigned R, float *out) {
+    if (threadIdx.x < 32) {
+        const unsigned lane = threadIdx.x;
+        float v[3];
+#pragma unroll
+        for (int s = 0; s < 3; ++s)
+            v[s] = (s < ns && lane < R) ? ld_cluster(cluster_addr(&slots[s], lane)) : 0.f;
+#pragma unroll
+        for (int s = 0; s < 3; ++s) {
+            float x = v[s];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            if (lane == 0 && s < ns) out[s] = x;
+        }
+    }
+    __syncthreads();
+}
+
+// Slice boundary r of R over [0, cnt]: the first index whose weight ptr[i] + i reaches
+// r*(ptr[cnt] + cnt)/R, clamped to within ceil(cnt/(2R)) of r*cnt/R.  Monotone in r, so the
+// slices tile [0, cnt) and none is longer than 2*ceil(cnt/R) + 1.  Block-wide (every thread gets
+// the result); `sh` holds kClT/32 ints.
+__device__ __forceinline__ int slice_bound(const int32_t *ptr, int cnt, int r, int R, int *sh) {
+    if (r <= 0) return 0;
+    if (r >= R) return cnt;
+    const int64_t total = (int64_t)ptr[cnt] + cnt;
+    const int64_t target = total * r / R;
+    int c = 0;  // number of i in [0, cnt] with weight below target (weights strictly increase)
+    for (int i = threadIdx.x; i <= cnt; i += blockDim.x) c += ((int64_t)ptr[i] + i < target) ? 1 : 0;
+    c = block_sum(c, sh);
+    if (threadIdx.x == 0) sh[0] = c;
+    __syncthreads();
+    c = sh[0];
+    __syncthreads();
+    const int mid = (int)((int64_t)cnt * r / R), h = (cnt + 2 * R - 1) / (2 * R);
+    return max(0, min(cnt, min(mid + h, max(mid - h, c))));
+}
+
+struct ClLayout {
+    int64_t bytes;              // fixed part (vectors, slice pointers)
+    int ncap, mcap;             // own columns / rows at most
+};
+
+__host__ __device__ inline ClLayout cl_layout(int m, int n, int R) {
+    ClLayout L;
+    L.ncap = 2 * ((n + R - 1) / R) + 2;
+    L.mcap = 2 * ((m + R - 1) / R) + 2;
+    // p, z (n each), w (m), own x, r, q, Dinv (ncap each), own Minv (mcap), slice pointers
+    L.bytes = 4 * ((int64_t)2 * n + m + 4 * (int64_t)L.ncap + L.mcap) + 4 * ((int64_t)L.ncap + L.mcap + 2);
+    L.bytes = (L.bytes + 15) & ~(int64_t)15;
+    return L;
+}
+
+__global__ void __launch_bounds__(kClT, 1) pcg_cluster_kernel(PcgArgs<float> A, int g, int smem_bytes) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    __shared__ float sh[kClT / 32];
+    __shared__ int shi[kClT / 32];
+    __shared__ float s_part[6];  // 0: p.q  1: r.z  2: r.r  3, 4: b.b, b.z at the start
+    __shared__ float s_sum[3];
+    const int R = (int)gridDim.x;  // the grid is exactly one cluster
+    const int m = A.m, n = A.n;
+    const ClLayout L = cl_layout(m, n, R);
+    float *p_full = (float *)dsm, *z_full = p_full + n, *w_full = z_full + n;
+    float *x_o = w_full + m, *r_o = x_o + L.ncap, *q_o = r_o + L.ncap, *d_o = q_o + L.ncap;
+    float *minv_o = d_o + L.ncap;
+    int32_t *rp_o = (int32_t *)(minv_o + L.mcap), *cp_o = rp_o + L.mcap + 1;
+    unsigned char *ent = dsm + L.bytes;
+
+    const int rank = (int)blockIdx.x;
+    const int r0 = slice_bound(A.rp, m, rank, R, shi), r1 = slice_bound(A.rp, m, rank + 1, R, shi);
+    const int c0 = slice_bound(A.cp, n, rank, R, shi), c1 = slice_bound(A.cp, n, rank + 1, R, shi);
+    const int nr = r1 - r0, nc = c1 - c0;
+    const int e0 = A.rp[r0], ne_r = A.rp[r1] - e0;
+    const int k0 = A.cp[c0], ne_c = A.cp[c1] - k0;
+    // entries kept in shared memory: all when they fit, else the same share of each slice
+    const int64_t room = ((int64_t)smem_bytes - L.bytes) / 8;  // theta (4 B) + index (4 B)
+    int cap_r = ne_r, cap_c = ne_c;
+    if ((int64_t)ne_r + ne_c > room) {
+        cap_r = (int)(room * ne_r / max(1, ne_r + ne_c));
+        cap_c = (int)(room - cap_r);
+        cap_c = min(cap_c, ne_c);
+    }
+    float *th_s = (float *)ent, *thc_s = th_s + cap_r;
+    int32_t *sj_s = (int32_t *)(thc_s + cap_c), *crow_s = sj_s + cap_r;
+    const float *__restrict__ th_g = A.th + e0;
+    const float *__restrict__ thc_g = A.thc + k0;
+    const int32_t *__restrict__ sj_g = A.sj + e0;
+    const int32_t *__restrict__ crow_g = A.crow + k0;
+
+    // every CTA of the cluster must be running before any distributed-shared-memory access
+    cluster_sync();
+    for (int t = threadIdx.x; t <= nr; t += blockDim.x) rp_o[t] = A.rp[r0 + t] - e0;
+    for (int t = threadIdx.x; t <= nc; t += blockDim.x) cp_o[t] = A.cp[c0 + t] - k0;
+    for (int t = threadIdx.x; t < nr; t += blockDim.x) minv_o[t] = A.Minv[r0 + t];
+    for (int t = threadIdx.x; t < cap_r; t += blockDim.x) {
+        th_s[t] = th_g[t];
+        sj_s[t] = sj_g[t];
+    }
+    for (int t = threadIdx.x; t < cap_c; t += blockDim.x) {
+        thc_s[t] = thc_g[t];
+        crow_s[t] = crow_g[t];
+    }
+    float bb = 0.f, bz = 0.f;
+    for (int t = threadIdx.x; t < nc; t += blockDim.x) {
+        const int j = c0 + t;
+        const float bj = A.b[j], dj = A.Dinv[j], zj = dj * bj;
+        x_o[t] = 0.f;
+        r_o[t] = bj;
+        d_o[t] = dj;
+        for (int q = 0; q < R; ++q) st_cluster(cluster_addr(&z_full[j], q), zj);
+        bb += bj * bj;
+        bz += bj * zj;
+    }
+    {
+        const float s3 = block_sum(bb, sh), s4 = block_sum(bz, sh);
+        if (threadIdx.x == 0) { s_part[3] = s3; s_part[4] = s4; }
+    }
+    cluster_sync();
+    cluster_reduce(&s_part[3], 2, R, s_sum);
+    bb = s_sum[0];
+    float rz = s_sum[1];
+    for (int j = threadIdx.x; j < n; j += blockDim.x) p_full[j] = z_full[j];
+    __syncthreads();
+
+    const double tol2 = A.tol * A.tol * (double)bb;
+    const int lg = threadIdx.x & (g - 1);
+    const int grp = threadIdx.x / g, ngrp = blockDim.x / g;
+    const int wgrp0 = (threadIdx.x & ~31) / g;
+    int it = 0;
+    double rr = (double)bb;
+    if (bb > 0.f && rz > 0.f) {
+        for (it = 0; it < A.maxit;) {
+            // w_i = M_i^{-1} sum_j theta_ij p_j over the own rows; pushed to every CTA
+            for (int i0 = wgrp0; i0 < nr; i0 += ngrp) {
+                const int il = i0 + (grp - wgrp0);
+                float acc = 0.f;
+                if (il < nr) {
+                    const int lo = rp_o[il], hi = rp_o[il + 1];
+                    for (int e = lo + lg; e < hi; e += g) {
+                        const bool in = e < cap_r;
+                        const int j = in ? sj_s[e] : sj_g[e];
+                        const float t = in ? th_s[e] : th_g[e];
+                        acc += t * p_full[j];
+                    }
+                }
+                acc = group_sum(acc, g);
+                if (il < nr) {
+                    const float wi = minv_o[il] * acc;
+                    for (int q = lg; q < R; q += g) st_cluster(cluster_addr(&w_full[r0 + il], q), wi);
+                }
+            }
+            cluster_sync();
+            // q_j = sum_i theta_ij (p_j - w_i) over the own columns
+            float pq = 0.f;
+            for (int j0 = wgrp0; j0 < nc; j0 += ngrp) {
+                const int jl = j0 + (grp - wgrp0);
+                float acc = 0.f, pj = 0.f;
+                if (jl < nc) {
+                    pj = p_full[c0 + jl];
+                    const int lo = cp_o[jl], hi = cp_o[jl + 1];
+                    for (int k = lo + lg; k < hi; k += g) {
+                        const bool in = k < cap_c;
+                        const int i = in ? crow_s[k] : crow_g[k];
+                        const float t = in ? thc_s[k] : thc_g[k];
+                        acc += t * (pj - w_full[i]);
+                    }
+                }
+                acc = group_sum(acc, g);
+                if (lg == 0 && jl < nc) {
+                    q_o[jl] = acc;
+                    pq += pj * acc;
+                }
+            }
+            {
+                const float s0 = block_sum(pq, sh);
+                if (threadIdx.x == 0) s_part[0] = s0;
+            }
+            cluster_sync();
+            cluster_reduce(&s_part[0], 1, R, s_sum);
+            pq = s_sum[0];
+            if (!(pq > 0.f)) break;
+            const float alpha = rz / pq;
+            float rzn = 0.f, rrn = 0.f;
+            for (int t = threadIdx.x; t < nc; t += blockDim.x) {
+                const int j = c0 + t;
+                const float rj = r_o[t] - alpha * q_o[t];
+                const float zj = d_o[t] * rj;
+                x_o[t] += alpha * p_full[j];
+                r_o[t] = rj;
+                for (int q = 0; q < R; ++q) st_cluster(cluster_addr(&z_full[j], q), zj);
+                rzn += rj * zj;
+                rrn += rj * rj;
+            }
+            {
+                const float s1 = block_sum(rzn, sh), s2 = block_sum(rrn, sh);
+                if (threadIdx.x == 0) { s_part[1] = s1; s_part[2] = s2; }
+            }
+            cluster_sync();
+            cluster_reduce(&s_part[1], 2, R, s_sum);
+            rzn = s_sum[0];
+            rr = (double)s_sum[1];
+            ++it;
+            if (rr <= tol2 || !(rzn > 0.f)) break;
+            const float beta = rzn / rz;
+            rz = rzn;
+            for (int j = threadIdx.x; j < n; j += blockDim.x) p_full[j] = z_full[j] + beta * p_full[j];
+            __syncthreads();
+        }
+    }
+    for (int t = threadIdx.x; t < nc; t += blockDim.x) A.x[c0 + t] = x_o[t];
+    // no CTA may exit while another can still read its shared memory
+    cluster_sync();
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        A.scal[SC_PCG_ITERS] = (double)it;
+        A.scal[SC_PCG_RELRES] = bb > 0.f ? sqrt(rr / (double)bb) : 0.0;
+    }
+}
+
 template <typename T>
 Error launch_pcg(Newton &W, const Support &S, const T *th, const T *thc, const T *Minv, const T *Dinv,
                  const T *b, T *x, T *r, T *z, T *p, T *q, T *w, double tol, int maxit, cudaStream_t st) {
@@ -477,12 +734,57 @@ Error launch_pcg(Newton &W, const Support &S, const T *th, const T *thc, const T
     if (sizeof(T) == 4) pb = (T *)W.pcg_pb32;
     PcgArgs<T> A{W.m, W.n, S.row_ptr, S.j, S.col_ptr, S.col_row, th, thc, Minv, Dinv, b, x, r, z, p, pb, q, w,
                  W.part, W.bar, W.err, tol, maxit, W.scal};
-    void *args[] = {&A, &g};
     const int kid = sizeof(T) == 8 ? KT_PCG64 : KT_PCG32;
-    ktimer_begin(kid, st);
-    OT_CUDA(cudaLaunchCooperativeKernel((void *)pcg_kernel<T>, dim3(G), dim3(kPcgT), args, 0, st));
-    OT_LAUNCHED();
-    ktimer_end(kid, st);
+    const int R = W.pcg_cluster;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    if (W.verbose >= 3) {
+        OT_CUDA(cudaEventCreate(&ev[0]));
+        OT_CUDA(cudaEventCreate(&ev[1]));
+        OT_CUDA(cudaEventRecord(ev[0], st));
+    }
+    const ClLayout L = cl_layout(W.m, W.n, std::max(R, 1));
+    bool clustered = false;
+    if constexpr (sizeof(T) == 4) {
+      if (R > 1 && 2 * L.bytes <= W.pcg_cluster_smem) {
+        clustered = true;
+        // one thread-block cluster with the operator slices in shared memory
+        int gc = 1;
+        while (gc < 32 && 2 * gc <= avg) gc <<= 1;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(R);
+        cfg.blockDim = dim3(kClT);
+        cfg.dynamicSmemBytes = (size_t)W.pcg_cluster_smem;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = R;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        const int sb = W.pcg_cluster_smem;
+        ktimer_begin(kid, st);
+        OT_CUDA(cudaLaunchKernelEx(&cfg, pcg_cluster_kernel, A, gc, sb));
+        OT_LAUNCHED();
+        ktimer_end(kid, st);
+      }
+    }
+    if (!clustered) {
+        void *args[] = {&A, &g};
+        ktimer_begin(kid, st);
+        OT_CUDA(cudaLaunchCooperativeKernel((void *)pcg_kernel<T>, dim3(G), dim3(kPcgT), args, 0, st));
+        OT_LAUNCHED();
+        ktimer_end(kid, st);
+    }
+    if (W.verbose >= 3) {
+        float ms = 0.f;
+        OT_CUDA(cudaEventRecord(ev[1], st));
+        OT_CUDA(cudaEventSynchronize(ev[1]));
+        OT_CUDA(cudaEventElapsedTime(&ms, ev[0], ev[1]));
+        W.last_pcg_ms = ms;
+        cudaEventDestroy(ev[0]);
+        cudaEventDestroy(ev[1]);
+    }
     // algorithmic bytes of one CG iteration: both passes read theta, an index and a gathered
     // vector entry per support pair, plus the per-row / per-column vectors
     W.pcg_bytes_per_iter = (double)S.psi * 2.0 * (2.0 * sizeof(T) + 4.0) + (double)W.m * (3.0 * 4.0 + 2.0 * sizeof(T)) +
@@ -713,6 +1015,9 @@ static Error solve_pcg64(Newton &W, const Support &S, double tol, int max_cg, do
     ss->cg_iters = (int)hs[SC_PCG_ITERS];
     ss->relres = hs[SC_PCG_RELRES];
     ktimer_add_work(KT_PCG64, ss->cg_iters * W.pcg_bytes_per_iter);
+    if (W.verbose >= 3)
+        fprintf(stderr, "      pcg64 psi %lld its %d relres %.2e ms %.3f\n", (long long)S.psi, ss->cg_iters,
+                ss->relres, W.last_pcg_ms);
     copy_kernel<<<gn, kT, 0, st>>>(W.n, W.x64, dv);
     OT_LAUNCHED();
     return ok();
@@ -747,6 +1052,9 @@ static Error solve_mixed(Newton &W, const Support &S, double tol, int max_cg, do
         if (errv) return fail(OT_ERR_TIMEOUT, "pcg: grid barrier wait limit reached");
         const int its = (int)hs[SC_PCG_ITERS];
         ktimer_add_work(KT_PCG32, its * W.pcg_bytes_per_iter);
+        if (W.verbose >= 3)
+            fprintf(stderr, "      pcg32 psi %lld its %d relres %.2e ms %.3f\n", (long long)S.psi, its,
+                    hs[SC_PCG_RELRES], W.last_pcg_ms);
         ss->cg_iters += its;
         budget -= std::max(its, 1);
         ss->refinements = ref + 1;
@@ -839,6 +1147,42 @@ Error newton_alloc(Newton &W, int32_t m, int32_t n, int64_t cap, int num_sms) {
     W.m = m;
     W.n = n;
     W.num_sms = num_sms;
+    // largest cluster (16, else 8, else none) of full-shared-memory CTAs the device schedules
+    W.pcg_cluster = 0;
+    W.pcg_cluster_smem = 0;
+    {
+        int dev = 0, optin = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess) {
+            const int sb = optin - 1024;  // room for the kernel's static shared memory
+            if (sb > 0 &&
+                cudaFuncSetAttribute(pcg_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sb) == cudaSuccess &&
+                cudaFuncSetAttribute(pcg_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+                    cudaSuccess) {
+                for (int c : {kClMaxR, 8}) {
+                    cudaLaunchConfig_t cfg = {};
+                    cfg.gridDim = dim3(c);
+                    cfg.blockDim = dim3(kClT);
+                    cfg.dynamicSmemBytes = (size_t)sb;
+                    cudaLaunchAttribute attr[1];
+                    attr[0].id = cudaLaunchAttributeClusterDimension;
+                    attr[0].val.clusterDim.x = c;
+                    attr[0].val.clusterDim.y = 1;
+                    attr[0].val.clusterDim.z = 1;
+                    cfg.attrs = attr;
+                    cfg.numAttrs = 1;
+                    int nclusters = 0;
+                    if (cudaOccupancyMaxActiveClusters(&nclusters, pcg_cluster_kernel, &cfg) == cudaSuccess &&
+                        nclusters >= 1) {
+                        W.pcg_cluster = c;
+                        W.pcg_cluster_smem = sb;
+                        break;
+                    }
+                }
+            }
+        }
+        cudaGetLastError();  // a refused attribute or query only disables the cluster variant
+    }
     OT_TRY(newton_grow(W, cap));
     for (double **p : {&W.r1a, &W.beta1, &W.M, &W.Minv, &W.du, &W.du2, &W.du3, &W.w64}) OT_TRY(dev_alloc(p, m));
     for (float **p : {&W.Minv32, &W.w32}) OT_TRY(dev_alloc(p, m));

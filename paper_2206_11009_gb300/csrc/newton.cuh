@@ -46,9 +46,13 @@ struct Newton {
     unsigned *bar = nullptr;
     int *err = nullptr;
     int pcg_grid = 0;
+    int verbose = 0;
+    double last_pcg_ms = 0.0;  // >= 3: one line per PCG launch (support size, iterations, device ms)
     double *pcg_pb = nullptr;     // second direction buffer of the PCG (fp64 / fp32)
     float *pcg_pb32 = nullptr;
     double pcg_bytes_per_iter = 0.0;
+    int pcg_cluster = 0;       // CTAs of the FP32 cluster PCG (0: not available on this device)
+    int pcg_cluster_smem = 0;  // dynamic shared memory of one of its CTAs
     // direct branch: when set, S_M x = rhs is solved by its LDL^T factorisation (chol.cuh)
     struct Chol *direct = nullptr;
     struct DenseLDL *dense = nullptr;   // when set (with direct), solve with the dense factor

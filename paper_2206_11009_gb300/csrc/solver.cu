@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <chrono>
 #include <cstdarg>
 #include <vector>
 
@@ -255,6 +256,26 @@ Error price_support(ot_ipm *h, const Support &S, int32_t kmax, int32_t *count, P
 
 double step_of(double ratio, double scale) { return std::min(1.0, scale * ratio); }
 
+// wall-clock phase breakdown of one iteration (verbose >= 2): synchronises at each mark
+struct PhaseClock {
+    bool on;
+    cudaStream_t st;
+    std::chrono::steady_clock::time_point t;
+    std::string line;
+    PhaseClock(bool on_, cudaStream_t s) : on(on_), st(s) {
+        if (on) { cudaStreamSynchronize(st); t = std::chrono::steady_clock::now(); }
+    }
+    void mark(const char *name) {
+        if (!on) return;
+        cudaStreamSynchronize(st);
+        auto now = std::chrono::steady_clock::now();
+        char buf[64];
+        snprintf(buf, sizeof(buf), " %s %.2f", name, std::chrono::duration<double, std::milli>(now - t).count());
+        line += buf;
+        t = now;
+    }
+};
+
 Error do_step(ot_ipm *h, ot_iter_info *info) {
     const ot_options &o = h->opt;
     cudaStream_t st = h->st;
@@ -266,8 +287,10 @@ Error do_step(ot_ipm *h, ot_iter_info *info) {
     inf.psi = S.psi;
     double hs[SC_COUNT];
 
+    PhaseClock pc(o.verbose >= 2, st);
     OT_TRY(residuals(W, S, h->a_s, h->b_s, h->u, h->v, st));
     OT_TRY(read_scalars(W, hs, st));
+    pc.mark("res");
     const double psi = (double)S.psi;
     const double mu = hs[SC_PS] / psi;
     const double ctp = hs[SC_CP];
@@ -301,6 +324,7 @@ Error do_step(ot_ipm *h, ot_iter_info *info) {
 
     // ---- Newton direction: Mehrotra predictor-corrector + centrality correctors
     OT_TRY(schur_setup(W, S, st));
+    pc.mark("schur");
     // iterative (PCG) or direct (LDL^T) solves of S_M, Section 4.3
     h->psi_hist.push_back(S.psi);
     bool use_direct = o.linear_solver == 2;
@@ -360,6 +384,7 @@ Error do_step(ot_ipm *h, ot_iter_info *info) {
         return e.code == OT_ERR_UNSUPPORTED ? ok() : e;
     };
     if (use_direct) OT_TRY(enable_direct());
+    pc.mark("factor");
     int cg = 0;
     SolveStats ss;
     // a PCG solve that misses its tolerance by more than kPcgFail switches this iteration (and,
@@ -419,6 +444,7 @@ Error do_step(ot_ipm *h, ot_iter_info *info) {
             break;
         }
     }
+    pc.mark("newton");
     OT_TRY(take_step(W, S, h->u, h->v, d_dp, d_ds, d_du, d_dv, ap, as, st));
     OT_TRY(read_scalars(W, hs, st));
     const double mu_new = hs[SC_PSNEW] / psi;
@@ -428,7 +454,9 @@ Error do_step(ot_ipm *h, ot_iter_info *info) {
     const int32_t kadd = o.add_max > 0 ? o.add_max : m;
     int32_t added = 0;
     PriceStats ps;
+    pc.mark("step");
     OT_TRY(price_support(h, S, kadd, &added, &ps));
+    pc.mark("price");
     {
         count_below_kernel<<<1, 256, 0, st>>>(h->pcount, h->pd, -o.tol * (1.0 + cmax_red), h->pstrong);
         OT_LAUNCHED();
@@ -441,10 +469,12 @@ Error do_step(ot_ipm *h, ot_iter_info *info) {
     if (removing) OT_TRY(removal_flags(S, m, n, h->a_s, h->b_s, o.rm_p_frac, m, W.flag, &removed, st));
     Support &S0 = h->S[h->cur];
     Support &T = h->S[1 - h->cur];
+    pc.mark("remove");
     OT_TRY(merge_support(S0, removing ? W.flag : nullptr, h->pi, h->pj, added, std::sqrt(mu_new), m, n, T, st));
     h->cur = 1 - h->cur;
     OT_TRY(support_costs(W, h->cd, T, st));
     OT_CUDA(cudaStreamSynchronize(st));
+    pc.mark("merge");
 
     h->iter++;
     h->cg_total += cg;
@@ -455,6 +485,7 @@ Error do_step(ot_ipm *h, ot_iter_info *info) {
     inf.cg_iters = cg;
     inf.added = added;
     inf.removed = removed;
+    if (o.verbose >= 2) fprintf(stderr, "   phases(ms):%s\n", pc.line.c_str());
     if (o.verbose)
         fprintf(stderr, "it %3d psi %8lld mu %.3e crit %.3e ap %.3f as %.3f sig %.2e corr %d cg %d %s +%d -%lld\n",
                 inf.iter, (long long)inf.psi, mu, crit, ap, as, sigma, ncorr, cg, inf.direct ? "LDL" : "PCG", added,
@@ -576,6 +607,7 @@ Error create_impl(const ot_problem *P, const ot_options *O, ot_ipm *h) {
     h->S[0].psi = psi0;
     OT_TRY(rebuild_views(h->S[0], m, n, st));
     OT_TRY(newton_alloc(h->W, m, n, cap, h->num_sms));
+    h->W.verbose = h->opt.verbose;
     OT_TRY(chol_alloc(h->chol, n));
     OT_TRY(support_costs(h->W, h->cd, h->S[0], st));
     int cgs = 0;
