@@ -74,8 +74,8 @@ SIGNATURES = {
     "ot_kernel_timing_read": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32]),
 }
 
-KERNEL_IDS = ["scan_hist", "scan_gather", "recheck", "pcg64", "pcg32", "ldl_numeric", "ldl_forward",
-              "ldl_backward", "reserved"]
+KERNEL_IDS = ["scan_hist", "scan_gather", "recheck", "pcg64", "pcg32", "ldl_numeric", "ldl_solve",
+              "d32_factor", "d32_apply"]
 
 _lib = None
 

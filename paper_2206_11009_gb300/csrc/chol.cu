@@ -554,10 +554,10 @@ Error chol_solve(Chol &C, const double *b, double *x, cudaStream_t st) {
     unsigned *bar = C.bar;
     int *err = C.err;
     void *args[] = {&nlev, &lp, &lc, &pm, &Lp, &Li, &Rp, &Rj, &Rpos, &Lx, &D, &b, &z, &y, &xx, &x, &bar, &err};
-    ktimer_begin(KT_LDL_FORWARD, st);
+    ktimer_begin(KT_LDL_SOLVE, st);
     OT_CUDA(cudaLaunchCooperativeKernel((void *)ldl_solve_kernel, dim3(grid), dim3(kT), args, 0, st));
     OT_LAUNCHED();
-    ktimer_end(KT_LDL_FORWARD, st);
+    ktimer_end(KT_LDL_SOLVE, st);
     return ok();
 }
 

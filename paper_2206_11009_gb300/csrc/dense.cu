@@ -340,11 +340,11 @@ Error dense_solve(DenseLDL &M, const double *b, double *x, cudaStream_t st) {
     unsigned *bar = M.bar;
     int *err = M.err;
     void *args[] = {&n, &A, &Li, &D, &b, &z, &x, &part, &bar, &err};
-    ktimer_begin(KT_LDL_FORWARD, st);
+    ktimer_begin(KT_LDL_SOLVE, st);
     OT_CUDA(cudaLaunchCooperativeKernel((void *)dense_solve_kernel, dim3(grid), dim3(kT), args, 0, st));
     OT_LAUNCHED();
-    ktimer_end(KT_LDL_FORWARD, st);
-    ktimer_add_work(KT_LDL_FORWARD, 8.0 * (double)n * n);  // reads L twice
+    ktimer_end(KT_LDL_SOLVE, st);
+    ktimer_add_work(KT_LDL_SOLVE, 8.0 * (double)n * n);  // reads L twice
     return ok();
 }
 

@@ -1,0 +1,578 @@
+// FP32 dense LDL^T of S_M with the explicit inverse of its unit lower factor (dense32.cuh).
+//
+// Per 64-column panel k (column-major, leading dimension ld):
+//   colsum  sums of the panel's columns below its diagonal block (the rows not yet eliminated);
+//   diag    one CTA factors the 64x64 diagonal block in shared memory, each pivot being minus the
+//           sum of its column's remaining off-diagonal entries (in the block, plus the below-block
+//           sum updated as columns are eliminated), and writes the inverse of the unit block;
+//   panel   L21 = A21 L11^-T D1^-1 through the inverse block (a product of non-positive entries
+//           with non-negative ones: no cancellation), LD = L21 D1;
+//   invrow  block row k of X = L^-1: X_kj = L11^-1 B_kj (B: the updates accumulated in X);
+//   update  one launch over 128x128 tiles of both rank-64 updates: the trailing lower triangle
+//           A22 -= LD L21^T and the rows of X below the panel, B -= L21 X_k.
+// The sequence depends on n only, so it is captured once into a CUDA graph.
+#include "dense32.cuh"
+
+#include <cmath>
+#include <vector>
+
+namespace ot {
+namespace {
+
+constexpr int kP = 64;       // panel width
+constexpr int kTT = 256;     // threads per CTA
+constexpr int kTile = 128;   // update tile (rows and columns)
+constexpr int kKc = 16;      // depth of one staged slice of the update tiles
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// One CTA per column j: S_jj' = -sum_i theta_ij theta_ij' / M_i over the sources i shared by j and
+// j', accumulated in fixed point (2^62 / N_j per unit: each |S_jj'| <= N_j, and so is their sum).
+__global__ void __launch_bounds__(kTT)
+d32_assemble_kernel(int n, int ld, const int32_t *__restrict__ col_ptr, const int32_t *__restrict__ col_row,
+                    const double *__restrict__ theta_col, const int32_t *__restrict__ row_ptr,
+                    const int32_t *__restrict__ sj, const double *__restrict__ theta,
+                    const double *__restrict__ Minv, const double *__restrict__ Nc, float *__restrict__ A,
+                    float *__restrict__ d0) {
+    extern __shared__ unsigned long long acc[];
+    __shared__ unsigned long long red[kTT / 32];
+    const int j = blockIdx.x;
+    for (int t = threadIdx.x; t < n; t += blockDim.x) acc[t] = 0ull;
+    __syncthreads();
+    const double Nj = Nc[j];
+    const double scale = Nj > 0 ? 4611686018427387904.0 / Nj : 0.0;  // 2^62 / N_j
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    if (scale > 0) {
+        for (int k = col_ptr[j] + warp; k < col_ptr[j + 1]; k += nw) {
+            const int i = col_row[k];
+            const double f = theta_col[k] * Minv[i] * scale;
+            for (int e = row_ptr[i] + lane; e < row_ptr[i + 1]; e += 32) {
+                const int jp = sj[e];
+                if (jp != j) atomicAdd(&acc[jp], (unsigned long long)__double2ull_rn(f * theta[e]));
+            }
+        }
+    }
+    __syncthreads();
+    unsigned long long s = 0;
+    for (int t = threadIdx.x; t < n; t += blockDim.x) s += acc[t];
+    s = warp_sum_u64(s);
+    if (lane == 0) red[warp] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long tot = 0;
+        for (int w = 0; w < nw; ++w) tot += red[w];
+        d0[j] = scale > 0 ? (float)((double)tot / scale) : 0.f;
+    }
+    const double inv = scale > 0 ? 1.0 / scale : 0.0;
+    for (int r = j + 1 + threadIdx.x; r < n; r += blockDim.x) A[(size_t)j * ld + r] = -(float)((double)acc[r] * inv);
+}
+
+// csum[l] = sum of column l over the rows [bs, n) (first panel; later panels receive these sums
+// from the previous update's epilogue)
+__global__ void __launch_bounds__(kTT)
+d32_colsum_kernel(int n, int ld, int bs, const float *__restrict__ A, float *__restrict__ csum) {
+    __shared__ double sh[kTT / 32];
+    const int l = blockIdx.x;
+    const float *col = A + (size_t)l * ld;
+    double s = 0.0;
+    for (int r = bs + threadIdx.x; r < n; r += blockDim.x) s += (double)col[r];
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) csum[l] = (float)s;
+}
+
+// One CTA factors the diagonal block in shared memory with one barrier per column: every warp
+// forms the pivot itself (minus the sum of the column's remaining entries and of its below-block
+// sum, np fixed-order partials in csum[p * kP + l]; the same reduction in every warp), the column
+// stays unscaled until the end (l_ij = S_ij / d_j is formed where it is used), and the same row
+// operations applied to the identity build the inverse of the unit block.
+__global__ void __launch_bounds__(kTT)
+d32_diag_kernel(int ld, int k, int bs, float *__restrict__ A, float *__restrict__ D, const float *__restrict__ d0,
+                const float *__restrict__ csum, int np, float eps, float *__restrict__ Linv) {
+    __shared__ float S[kP][kP + 1];
+    __shared__ float Xs[kP][kP + 1];
+    __shared__ float g[kP], thr[kP], ids[kP];
+    for (int t = threadIdx.x; t < kP * kP; t += blockDim.x) {
+        const int i = t % kP, j = t / kP;
+        S[i][j] = (i > j && i < bs) ? A[(size_t)(k + j) * ld + (k + i)] : 0.f;
+        Xs[i][j] = (i == j && i < bs) ? 1.f : 0.f;
+    }
+    for (int l = threadIdx.x; l < kP; l += blockDim.x) {
+        float gs = 0.f;
+        if (l < bs)
+            for (int q = 0; q < np; ++q) gs += csum[q * kP + l];
+        g[l] = gs;
+        thr[l] = l < bs ? eps * d0[k + l] : 0.f;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    for (int j = 0; j < bs; ++j) {
+        float sum = (lane > j ? S[lane][j] : 0.f) + (lane + 32 > j ? S[lane + 32][j] : 0.f);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        const float d = -(sum + g[j]);
+        const bool inf = !(d > thr[j]);
+        const float id = inf ? 0.f : 1.f / d;
+        if (threadIdx.x == 0) {
+            D[k + j] = inf ? INFINITY : d;
+            ids[j] = id;
+        }
+        if (!inf) {
+            const float gj = g[j];
+            for (int i = j + 1 + ty; i < bs; i += 16) {
+                const float lij = S[i][j] * id;
+                for (int l = j + 1 + tx; l < i; l += 16) S[i][l] -= lij * S[l][j];
+                for (int c = tx; c <= j; c += 16) Xs[i][c] -= lij * Xs[j][c];
+                if (tx == 0) g[i] -= lij * gj;
+            }
+        }
+        __syncthreads();
+    }
+    for (int t = threadIdx.x; t < bs * bs; t += blockDim.x) {
+        const int i = t % bs, j = t / bs;
+        if (i > j) A[(size_t)(k + j) * ld + (k + i)] = S[i][j] * ids[j];
+        Linv[(size_t)j * ld + (k + i)] = Xs[i][j];
+    }
+}
+
+// rows r in [k+64, n) of the panel (bs = 64 whenever rows remain below the block): 64 rows per
+// CTA, 4 rows x 4 columns per thread, T = A21 L11^-T staged through shared memory
+__global__ void __launch_bounds__(kTT)
+d32_panel_kernel(int n, int ld, int k, float *__restrict__ A, const float *__restrict__ D,
+                 const float *__restrict__ Linv, float *__restrict__ LD) {
+    __shared__ __align__(16) float As[kP][kP];   // As[l][r] = A(r0 + r, k + l)
+    __shared__ __align__(16) float Lt[kP][kP];   // Lt[l][j] = (L11^-1)_jl
+    const int r0 = k + kP + blockIdx.x * kP;
+    for (int t = threadIdx.x; t < kP * kP; t += blockDim.x) {
+        const int j = t % kP, l = t / kP;
+        Lt[l][j] = Linv[(size_t)l * ld + (k + j)];
+        As[l][j] = r0 + j < n ? A[(size_t)(k + l) * ld + r0 + j] : 0.f;
+    }
+    __syncthreads();
+    const int tr = threadIdx.x & 15, tc = threadIdx.x >> 4;  // rows tr*4.., columns tc*4..
+    float acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int w = 0; w < 4; ++w) acc[u][w] = 0.f;
+#pragma unroll 16
+    for (int l = 0; l < kP; ++l) {
+        const float4 a = *(const float4 *)&As[l][tr * 4];
+        const float4 b = *(const float4 *)&Lt[l][tc * 4];
+        const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int w = 0; w < 4; ++w) acc[u][w] += av[u] * bv[w];
+    }
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        const int j = tc * 4 + w;
+        const float dj = D[k + j];
+        const bool inf = isinf(dj);
+        const float id = inf ? 0.f : 1.f / dj;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int r = r0 + tr * 4 + u;
+            if (r < n) {
+                LD[(size_t)j * ld + r] = inf ? 0.f : acc[u][w];
+                A[(size_t)(k + j) * ld + r] = acc[u][w] * id;
+            }
+        }
+    }
+}
+
+// block row k of X = L^-1 for the columns [c0, c0+64) of [0, k+bs); 4 rows x 4 columns per thread
+__global__ void __launch_bounds__(kTT)
+d32_invrow_kernel(int ld, int k, int bs, float *__restrict__ X, const float *__restrict__ Linv) {
+    __shared__ __align__(16) float Lt[kP][kP];   // Lt[l][i] = (L11^-1)_il
+    __shared__ __align__(16) float B[kP][kP];    // B[l][c] = X(k + l, c0 + c)
+    const int c0 = blockIdx.x * kP;
+    const int base = k + bs;
+    for (int t = threadIdx.x; t < kP * kP; t += blockDim.x) {
+        const int i = t % kP, l = t / kP;
+        Lt[l][i] = (i < bs && l < bs) ? Linv[(size_t)l * ld + (k + i)] : 0.f;
+    }
+    for (int t = threadIdx.x; t < kP * kP; t += blockDim.x) {
+        const int l = t % kP, c = t / kP;
+        B[l][c] = (l < bs && c0 + c < k) ? X[(size_t)(c0 + c) * ld + (k + l)] : 0.f;
+    }
+    __syncthreads();
+    const int ti = threadIdx.x & 15, tcc = threadIdx.x >> 4;  // rows ti*4.., columns tcc*4..
+    float acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int w = 0; w < 4; ++w) acc[u][w] = 0.f;
+    if (c0 < k) {
+#pragma unroll 16
+        for (int l = 0; l < kP; ++l) {
+            const float4 a = *(const float4 *)&Lt[l][ti * 4];
+            const float4 b = *(const float4 *)&B[l][tcc * 4];
+            const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int w = 0; w < 4; ++w) acc[u][w] += av[u] * bv[w];
+        }
+    }
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        const int c = c0 + tcc * 4 + w;
+        if (c >= base) continue;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = ti * 4 + u;
+            if (i >= bs) continue;
+            X[(size_t)c * ld + (k + i)] = c < k ? acc[u][w] : Lt[c - k][i];
+        }
+    }
+}
+
+// the two rank-64 updates of panel k, 128x128 tiles, 8x8 per thread
+__global__ void __launch_bounds__(kTT, 2)
+d32_update_kernel(int n, int ld, int k, int ttri, float *__restrict__ A, float *__restrict__ X,
+                  const float *__restrict__ LD, float *__restrict__ csum) {
+    __shared__ __align__(16) float As[kKc][kTile];
+    __shared__ __align__(16) float Bs[kKc][kTile];
+    const int base = k + kP;
+    int idx = blockIdx.x;
+    const bool tri = idx < ttri;
+    int r0, c0, climit, tile_i = 0, tile_j = 0;
+    if (tri) {
+        int ti = (int)((sqrt(8.0 * idx + 1.0) - 1.0) * 0.5);
+        while ((ti + 1) * (ti + 2) / 2 <= idx) ++ti;
+        while (ti * (ti + 1) / 2 > idx) --ti;
+        const int tj = idx - ti * (ti + 1) / 2;
+        r0 = base + ti * kTile;
+        c0 = base + tj * kTile;
+        climit = n;
+        tile_i = ti;
+        tile_j = tj;
+    } else {
+        idx -= ttri;
+        const int tcn = (base + kTile - 1) / kTile;
+        r0 = base + (idx / tcn) * kTile;
+        c0 = (idx % tcn) * kTile;
+        climit = base;
+    }
+    // A operand (l, r) = Pa[l * ld + r]; B operand (l, c) = Pb[l * ld + c] (trailing) or
+    // X[c * ld + k + l] (inverse)
+    const float *Pa = tri ? LD : A + (size_t)k * ld;
+    const float *Pb = A + (size_t)k * ld;
+    const int tr = threadIdx.x & 15, tc = threadIdx.x >> 4;
+    float acc[8][8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+        for (int w = 0; w < 8; ++w) acc[u][w] = 0.f;
+    for (int l0 = 0; l0 < kP; l0 += kKc) {
+        __syncthreads();
+        {
+            const int l = threadIdx.x >> 4, q = (threadIdx.x & 15) * 8;
+            const float *src = Pa + (size_t)(l0 + l) * ld + r0 + q;
+            if (r0 + q + 8 <= n) {
+                *(float4 *)&As[l][q] = *(const float4 *)src;
+                *(float4 *)&As[l][q + 4] = *(const float4 *)(src + 4);
+            } else {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) As[l][q + u] = (r0 + q + u < n) ? src[u] : 0.f;
+            }
+            if (tri) {
+                const float *sb = Pb + (size_t)(l0 + l) * ld + c0 + q;
+                if (c0 + q + 8 <= climit) {
+                    *(float4 *)&Bs[l][q] = *(const float4 *)sb;
+                    *(float4 *)&Bs[l][q + 4] = *(const float4 *)(sb + 4);
+                } else {
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) Bs[l][q + u] = (c0 + q + u < climit) ? sb[u] : 0.f;
+                }
+            } else {
+                const int c = threadIdx.x & (kTile - 1), h = threadIdx.x >> 7;
+                if (c0 + c < climit) {
+                    const float *sx = X + (size_t)(c0 + c) * ld + k + l0 + h * 8;
+                    const float4 v0 = *(const float4 *)sx, v1 = *(const float4 *)(sx + 4);
+                    Bs[h * 8 + 0][c] = v0.x; Bs[h * 8 + 1][c] = v0.y; Bs[h * 8 + 2][c] = v0.z; Bs[h * 8 + 3][c] = v0.w;
+                    Bs[h * 8 + 4][c] = v1.x; Bs[h * 8 + 5][c] = v1.y; Bs[h * 8 + 6][c] = v1.z; Bs[h * 8 + 7][c] = v1.w;
+                } else {
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) Bs[h * 8 + u][c] = 0.f;
+                }
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int l = 0; l < kKc; ++l) {
+            const float4 a0 = *(const float4 *)&As[l][tr * 8], a1 = *(const float4 *)&As[l][tr * 8 + 4];
+            const float4 b0 = *(const float4 *)&Bs[l][tc * 8], b1 = *(const float4 *)&Bs[l][tc * 8 + 4];
+            const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+#pragma unroll
+                for (int w = 0; w < 8; ++w) acc[u][w] += a[u] * b[w];
+        }
+    }
+    float *C = tri ? A : X;
+    // the first column tile of the trailing part holds the next panel's columns: their sums below
+    // the next diagonal block (rows >= base + 64) go to csum[tile_i][.] (fixed-order partials)
+    const bool sums = tri && tile_j == 0 && tc < kP / 8;
+    float cs[8];
+#pragma unroll
+    for (int w = 0; w < 8; ++w) cs[w] = 0.f;
+    const bool full = r0 + kTile <= n && c0 + kTile <= climit && (!tri || r0 > c0);
+    if (full) {
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+            float *dst = C + (size_t)(c0 + tc * 8 + w) * ld + r0 + tr * 8;
+            float4 v0 = *(float4 *)dst, v1 = *(float4 *)(dst + 4);
+            v0.x -= acc[0][w]; v0.y -= acc[1][w]; v0.z -= acc[2][w]; v0.w -= acc[3][w];
+            v1.x -= acc[4][w]; v1.y -= acc[5][w]; v1.z -= acc[6][w]; v1.w -= acc[7][w];
+            *(float4 *)dst = v0;
+            *(float4 *)(dst + 4) = v1;
+            cs[w] = ((v0.x + v0.y) + (v0.z + v0.w)) + ((v1.x + v1.y) + (v1.z + v1.w));
+        }
+    } else {
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+            const int c = c0 + tc * 8 + w;
+            if (c >= climit) continue;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int r = r0 + tr * 8 + u;
+                if (r < n && (!tri || r > c)) {
+                    const float v = C[(size_t)c * ld + r] - acc[u][w];
+                    C[(size_t)c * ld + r] = v;
+                    if (r >= base + kP) cs[w] += v;
+                }
+            }
+        }
+    }
+    if (tri && tile_j == 0) {
+        // rows of the next diagonal block (tile 0, rows < base + 64) are not part of the sums; a
+        // full tile 0 starts at base, so its first 64 rows are dropped here
+        const bool drop = full && tile_i == 0 && tr * 8 < kP;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+            float v = (sums && !drop) ? cs[w] : 0.f;
+            // the 16 threads with this tc are lanes tr = 0..15 of one half-warp
+#pragma unroll
+            for (int o = 1; o < 16; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (sums && tr == 0) csum[tile_i * kP + tc * 8 + w] = v;
+        }
+    }
+}
+
+// partial sums of y = X r: CTA (rb, cb) covers rows [rb*512, +512) (four per thread, float4 loads)
+// and columns [cb*64, +64) for the lower-triangle tiles only (rows beyond n read the zero padding)
+constexpr int kFr = 512, kFc = 64;
+__global__ void __launch_bounds__(kFr / 4)
+d32_fwd_kernel(int n, int ld, int ncb, const float *__restrict__ X, const double *__restrict__ r,
+               float *__restrict__ part) {
+    __shared__ float rs[kFc];
+    // tile index -> (rb, cb) with cb*kFc < (rb+1)*kFr
+    const int per = kFr / kFc;
+    int idx = blockIdx.x, rb = 0;
+    while (idx >= min(ncb, (rb + 1) * per)) { idx -= min(ncb, (rb + 1) * per); ++rb; }
+    const int cb = idx;
+    const int c0 = cb * kFc, i = rb * kFr + threadIdx.x * 4;
+    if (threadIdx.x < kFc) rs[threadIdx.x] = c0 + (int)threadIdx.x < n ? (float)r[c0 + threadIdx.x] : 0.f;
+    __syncthreads();
+    if (i >= n || i + 3 < c0) return;
+    const int jn = min(kFc, n - c0);
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float *col = X + (size_t)c0 * ld + i;
+    if (i >= c0 + kFc - 1) {
+#pragma unroll 16
+        for (int jj = 0; jj < jn; ++jj) {
+            const float4 v = *(const float4 *)(col + (size_t)jj * ld);
+            const float rj = rs[jj];
+            acc.x += v.x * rj; acc.y += v.y * rj; acc.z += v.z * rj; acc.w += v.w * rj;
+        }
+    } else {
+        for (int jj = 0; jj < jn; ++jj) {
+            const int j = c0 + jj;
+            const float4 v = *(const float4 *)(col + (size_t)jj * ld);
+            const float rj = rs[jj];
+            if (j <= i) acc.x += v.x * rj;
+            if (j <= i + 1) acc.y += v.y * rj;
+            if (j <= i + 2) acc.z += v.z * rj;
+            if (j <= i + 3) acc.w += v.w * rj;
+        }
+    }
+    *(float4 *)(part + (size_t)cb * ld + i) = acc;
+}
+
+// w = D^+ y, y_i = sum of the partials of row i (fixed order)
+__global__ void d32_mid_kernel(int n, int ld, const float *__restrict__ part, const float *__restrict__ D,
+                               float *__restrict__ w) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int last = i / kFc;
+    float y = 0.f;
+    for (int cb = 0; cb <= last; ++cb) y += part[(size_t)cb * ld + i];
+    const float d = D[i];
+    w[i] = isinf(d) ? 0.f : y / d;
+}
+
+// z_j = sum_{i >= j} X_ij w_i, one warp per column, float4 per lane
+__global__ void __launch_bounds__(kTT)
+d32_bwd_kernel(int n, int ld, const float *__restrict__ X, const float *__restrict__ w, double *__restrict__ z) {
+    const int j = blockIdx.x * (kTT / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (j >= n) return;
+    const float *col = X + (size_t)j * ld;
+    float acc = 0.f;
+    const int i0 = j & ~3;
+#pragma unroll 4
+    for (int i = i0 + lane * 4; i < n; i += 128) {
+        const float4 v = *(const float4 *)(col + i);
+        if (i >= j && i + 3 < n) {
+            acc += v.x * w[i] + v.y * w[i + 1] + v.z * w[i + 2] + v.w * w[i + 3];
+        } else {
+            if (i >= j && i < n) acc += v.x * w[i];
+            if (i + 1 >= j && i + 1 < n) acc += v.y * w[i + 1];
+            if (i + 2 >= j && i + 2 < n) acc += v.z * w[i + 2];
+            if (i + 3 >= j && i + 3 < n) acc += v.w * w[i + 3];
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) z[j] = (double)acc;
+}
+
+}  // namespace
+
+Error d32_alloc(Dense32 &F, int32_t n) {
+    F.n = n;
+    F.ld = (n + 31) / 32 * 32;
+    const size_t big = sizeof(float) * (size_t)F.ld * n;
+    OT_CUDA(cudaMalloc((void **)&F.A, big));
+    OT_CUDA(cudaMalloc((void **)&F.X, big));
+    OT_CUDA(cudaMalloc((void **)&F.LD, sizeof(float) * (size_t)F.ld * kP));
+    OT_CUDA(cudaMalloc((void **)&F.Linv, sizeof(float) * (size_t)F.ld * kP));
+    OT_CUDA(cudaMalloc((void **)&F.D, sizeof(float) * n));
+    OT_CUDA(cudaMalloc((void **)&F.d0, sizeof(float) * n));
+    OT_CUDA(cudaMalloc((void **)&F.csum, sizeof(float) * kP * (size_t)ceil_div(n, kTile)));
+    OT_CUDA(cudaMalloc((void **)&F.w, sizeof(float) * n));
+    OT_CUDA(cudaMalloc((void **)&F.part, sizeof(float) * (size_t)F.ld * (size_t)ceil_div(n, kFc)));
+    // lower bound of the unwritten upper parts, so that nothing uninitialised is ever read
+    OT_CUDA(cudaMemset(F.A, 0, big));
+    OT_CUDA(cudaMemset(F.LD, 0, sizeof(float) * (size_t)F.ld * kP));
+    OT_CUDA(cudaMemset(F.Linv, 0, sizeof(float) * (size_t)F.ld * kP));
+    const int smem = (int)(sizeof(unsigned long long) * n);
+    if (smem > 48 * 1024)
+        OT_CUDA(cudaFuncSetAttribute(d32_assemble_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    return ok();
+}
+
+void d32_free(Dense32 &F) {
+    if (F.graph) cudaGraphExecDestroy(F.graph);
+    for (void *p : {(void *)F.A, (void *)F.X, (void *)F.LD, (void *)F.Linv, (void *)F.D, (void *)F.d0, (void *)F.csum,
+                    (void *)F.w, (void *)F.part})
+        if (p) cudaFree(p);
+    F = Dense32();
+}
+
+Error d32_assemble(Dense32 &F, const Newton &W, const Support &S, cudaStream_t st) {
+    const int n = F.n;
+    const size_t smem = sizeof(unsigned long long) * n;
+    d32_assemble_kernel<<<n, kTT, smem, st>>>(n, F.ld, S.col_ptr, S.col_row, W.theta_col, S.row_ptr, S.j, W.theta,
+                                               W.Minv, W.N, F.A, F.d0);
+    OT_LAUNCHED();
+    return ok();
+}
+
+// the factorisation's launches for this n on stream `cs` (captured into the graph)
+static Error d32_enqueue(Dense32 &F, float eps, cudaStream_t cs, int64_t *nodes) {
+    const int n = F.n, ld = F.ld;
+    int64_t cnt = 0;
+    OT_CUDA(cudaMemsetAsync(F.X, 0, sizeof(float) * (size_t)ld * n, cs));
+    ++cnt;
+    int np = 1;  // partial column sums feeding the next diagonal block
+    for (int k = 0; k < n; k += kP) {
+        const int bs = std::min(kP, n - k), base = k + bs;
+        if (k == 0) {
+            d32_colsum_kernel<<<bs, kTT, 0, cs>>>(n, ld, bs, F.A, F.csum);
+            ++cnt;
+        }
+        d32_diag_kernel<<<1, kTT, 0, cs>>>(ld, k, bs, F.A, F.D, F.d0, F.csum, np, eps, F.Linv);
+        ++cnt;
+        if (base < n) {
+            d32_panel_kernel<<<(unsigned)ceil_div(n - base, kP), kTT, 0, cs>>>(n, ld, k, F.A, F.D, F.Linv, F.LD);
+            ++cnt;
+        }
+        d32_invrow_kernel<<<(unsigned)ceil_div(base, kP), kTT, 0, cs>>>(ld, k, bs, F.X, F.Linv);
+        ++cnt;
+        if (base < n) {
+            const int t = (int)ceil_div(n - base, kTile);
+            const int ttri = t * (t + 1) / 2, tinv = t * (int)ceil_div(base, kTile);
+            d32_update_kernel<<<(unsigned)(ttri + tinv), kTT, 0, cs>>>(n, ld, k, ttri, F.A, F.X, F.LD, F.csum);
+            ++cnt;
+            np = t;
+        }
+    }
+    OT_CUDA(cudaGetLastError());
+    *nodes = cnt;
+    return ok();
+}
+
+Error d32_factor(Dense32 &F, float eps, cudaStream_t st) {
+    if (!F.graph || F.eps != eps) {
+        if (F.graph) {
+            cudaGraphExecDestroy(F.graph);
+            F.graph = nullptr;
+        }
+        cudaStream_t cs;
+        OT_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t g = nullptr;
+        Error e = ok();
+        if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            e = fail(OT_ERR_CUDA, "dense32: stream capture refused");
+        } else {
+            int64_t nodes = 0;
+            e = d32_enqueue(F, eps, cs, &nodes);
+            const cudaError_t ce = cudaStreamEndCapture(cs, &g);
+            if (e.code == OT_OK && ce != cudaSuccess) e = fail(OT_ERR_CUDA, cudaGetErrorString(ce));
+            if (e.code == OT_OK && cudaGraphInstantiate(&F.graph, g, 0) != cudaSuccess) {
+                F.graph = nullptr;
+                e = fail(OT_ERR_CUDA, "dense32: graph instantiation failed");
+            }
+            F.graph_nodes = nodes;
+        }
+        if (g) cudaGraphDestroy(g);
+        cudaStreamDestroy(cs);
+        cudaGetLastError();
+        OT_TRY(e);
+        F.eps = eps;
+    }
+    ktimer_begin(KT_D32_FACTOR, st);
+    OT_CUDA(cudaGraphLaunch(F.graph, st));
+    g_launches.fetch_add(F.graph_nodes, std::memory_order_relaxed);
+    ktimer_end(KT_D32_FACTOR, st);
+    // FP32 flops: 2n^3/3 for L D L^T and n^3/3 for L^-1
+    ktimer_add_work(KT_D32_FACTOR, (double)F.n * F.n * F.n);
+    return ok();
+}
+
+Error d32_apply(Dense32 &F, const double *r, double *z, cudaStream_t st) {
+    const int n = F.n, ld = F.ld;
+    const int ncb = (int)ceil_div(n, kFc), nrb = (int)ceil_div(n, kFr);
+    int tiles = 0;
+    for (int rb = 0; rb < nrb; ++rb) tiles += std::min(ncb, (rb + 1) * (kFr / kFc));
+    ktimer_begin(KT_D32_APPLY, st);
+    d32_fwd_kernel<<<(unsigned)tiles, kFr / 4, 0, st>>>(n, ld, ncb, F.X, r, F.part);
+    OT_LAUNCHED();
+    d32_mid_kernel<<<(unsigned)ceil_div(n, kTT), kTT, 0, st>>>(n, ld, F.part, F.D, F.w);
+    OT_LAUNCHED();
+    d32_bwd_kernel<<<(unsigned)ceil_div(n, kTT / 32), kTT, 0, st>>>(n, ld, F.X, F.w, z);
+    OT_LAUNCHED();
+    ktimer_end(KT_D32_APPLY, st);
+    // bytes: the lower triangle of L^-1 read twice
+    ktimer_add_work(KT_D32_APPLY, 4.0 * (double)n * n);
+    return ok();
+}
+
+}  // namespace ot

@@ -2,10 +2,12 @@
 // (eq. normalequationsipm) and the Schur complement S_M = N - V^T M^-1 V (Section 4), solved
 // matrix-free by PCG.  All reductions are deterministic (fixed-order two-stage sums).
 #include "newton.cuh"
+#include "dense32.cuh"
 #include "chol.cuh"
 #include "primitives.cuh"
 
 #include <cmath>
+#include <cstring>
 #include <type_traits>
 #include <vector>
 
@@ -967,6 +969,129 @@ __global__ void pcg_dir_kernel(int n, double b, const double *__restrict__ z, do
     GRID_STRIDE(j, n) p[j] = z[j] + b * p[j];
 }
 
+// the same two steps with alpha = r.z / p.q and beta = r.z(new) / r.z(old) read from the device
+// scalars (no host round trip; a non-positive denominator makes the step a no-op)
+__global__ void dcg_step_kernel(int n, const double *__restrict__ scal, int rz_slot, const double *__restrict__ p,
+                                const double *__restrict__ q, double *__restrict__ x, double *__restrict__ r,
+                                double *part) {
+    __shared__ double sh[kT / 32];
+    const double pq = scal[SC_SUM_A], rz = scal[rz_slot];
+    const double a = (pq > 0 && rz > 0) ? rz / pq : 0.0;
+    double rr = 0;
+    GRID_STRIDE(j, n) {
+        x[j] += a * p[j];
+        const double rj = r[j] - a * q[j];
+        r[j] = rj;
+        rr += rj * rj;
+    }
+    put_sum(rr, part, SC_NORM_A, sh);
+}
+
+__global__ void dcg_dir_kernel(int n, const double *__restrict__ scal, int old_slot, int new_slot,
+                               const double *__restrict__ z, double *__restrict__ p) {
+    const double rzo = scal[old_slot], rzn = scal[new_slot];
+    const double b = (rzo > 0 && rzn > 0) ? rzn / rzo : 0.0;
+    GRID_STRIDE(j, n) p[j] = z[j] + b * p[j];
+}
+
+// sum of the nb stage-1 partials of `slot`, in the same order in every block; all threads get it
+__device__ __forceinline__ double sum_slot(const double *part, int slot, int nb, double *sh, double *bc) {
+    double a = 0;
+    for (int k = threadIdx.x; k < nb; k += blockDim.x) a += part[(int64_t)slot * kMaxPartBlocks + k];
+    a = block_sum(a, sh);
+    if (threadIdx.x == 0) *bc = a;
+    __syncthreads();
+    const double r = *bc;
+    __syncthreads();
+    return r;
+}
+
+// S_M x in FP64 with G lanes per row / column (coalesced entry reads); warps take row groups with
+// a uniform trip count so the shuffles always see full warps
+template <int G>
+__global__ void mvg_rows_kernel(int m, const int32_t *__restrict__ rp, const int32_t *__restrict__ sj,
+                                const double *__restrict__ th, const double *__restrict__ Minv,
+                                const double *__restrict__ x, double *__restrict__ w) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lg = threadIdx.x & (G - 1);
+    const int64_t grp = t / G, ngrp = (int64_t)gridDim.x * blockDim.x / G, g0 = (t & ~(int64_t)31) / G;
+    for (int64_t i0 = g0; i0 < m; i0 += ngrp) {
+        const int64_t i = i0 + (grp - g0);
+        double acc = 0;
+        if (i < m)
+            for (int e = rp[i] + lg; e < rp[i + 1]; e += G) acc += th[e] * x[sj[e]];
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lg == 0 && i < m) w[i] = Minv[i] * acc;
+    }
+}
+
+template <int G>
+__global__ void mvg_cols_kernel(int n, const int32_t *__restrict__ cp, const int32_t *__restrict__ crow,
+                                const double *__restrict__ thc, const double *__restrict__ w,
+                                const double *__restrict__ x, double *__restrict__ y, double *part) {
+    __shared__ double sh[kT / 32];
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lg = threadIdx.x & (G - 1);
+    const int64_t grp = t / G, ngrp = (int64_t)gridDim.x * blockDim.x / G, g0 = (t & ~(int64_t)31) / G;
+    double xy = 0;
+    for (int64_t j0 = g0; j0 < n; j0 += ngrp) {
+        const int64_t j = j0 + (grp - g0);
+        double acc = 0, xj = 0;
+        if (j < n) {
+            xj = x[j];
+            for (int k = cp[j] + lg; k < cp[j + 1]; k += G) acc += thc[k] * (xj - w[crow[k]]);
+        }
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lg == 0 && j < n) {
+            y[j] = acc;
+            xy += xj * acc;
+        }
+    }
+    put_sum(xy, part, SC_SUM_A, sh);
+}
+
+// x += a p, r -= a q with a = r.z / p.q: p.q reduced here from its partials (nbq of them), r.z
+// read from its scalar slot; block 0 records p.q; partial r.r
+__global__ void dcg_step2_kernel(int n, int nbq, double *__restrict__ scal, int rz_slot, const double *__restrict__ p,
+                                 const double *__restrict__ q, double *__restrict__ x, double *__restrict__ r,
+                                 double *part) {
+    __shared__ double sh[kT / 32];
+    __shared__ double bc;
+    const double pq = sum_slot(part, SC_SUM_A, nbq, sh, &bc);
+    const double rz = scal[rz_slot];
+    if (blockIdx.x == 0 && threadIdx.x == 0) scal[SC_SUM_A] = pq;
+    const double a = (pq > 0 && rz > 0) ? rz / pq : 0.0;
+    double rr = 0;
+    GRID_STRIDE(j, n) {
+        x[j] += a * p[j];
+        const double rj = r[j] - a * q[j];
+        r[j] = rj;
+        rr += rj * rj;
+    }
+    put_sum(rr, part, SC_NORM_A, sh);
+}
+
+// p = z + b p with b = r.z(new) / r.z(old): r.z(new) reduced here (nbz partials of new_slot) and
+// recorded by block 0, which also records r.r (nbr partials)
+__global__ void dcg_dir2_kernel(int n, int nbz, int nbr, double *__restrict__ scal, int old_slot, int new_slot,
+                                const double *__restrict__ z, double *__restrict__ p, const double *__restrict__ part) {
+    __shared__ double sh[kT / 32];
+    __shared__ double bc;
+    const double rzn = sum_slot(part, new_slot, nbz, sh, &bc);
+    const double rzo = scal[old_slot];
+    const double b = (rzo > 0 && rzn > 0) ? rzn / rzo : 0.0;
+    GRID_STRIDE(j, n) p[j] = z[j] + b * p[j];
+    if (blockIdx.x == 0) {
+        const double rr = sum_slot(part, SC_NORM_A, nbr, sh, &bc);
+        if (threadIdx.x == 0) {
+            scal[new_slot] = rzn;
+            scal[SC_NORM_A] = rr;
+        }
+    }
+}
+
 template <typename T>
 Error dev_alloc(T **p, int64_t count) {
     OT_CUDA(cudaMalloc((void **)p, sizeof(T) * (size_t)std::max<int64_t>(count, 1)));
@@ -1065,12 +1190,16 @@ static Error solve_mixed(Newton &W, const Support &S, double tol, int max_cg, do
 }
 
 // PCG (FP64) on S_M preconditioned by the LDL^T factorisation of the sparsified Schur complement
-// (chol.cuh).  With no pair dropped the factorisation is exact and one iteration suffices; the
-// dropped pairs (negligible theta in their row) only perturb the spectrum slightly.
+// (chol.cuh), or by the FP32 dense factorisation (dense32.cuh).  With no pair dropped the FP64
+// factorisation is exact and one iteration suffices; the dropped pairs (negligible theta in their
+// row) only perturb the spectrum slightly, and the FP32 factors are accurate entry by entry, so a
+// few iterations recover FP64 accuracy (iterative refinement in conjugate-gradient form).
+constexpr int kD32MaxCg = 60;
+
 static Error solve_direct(Newton &W, const Support &S, double tol, int max_cg, double *dv, SolveStats *ss,
                           cudaStream_t st) {
     const unsigned gm = grid_of(W.m, W.num_sms), gn = grid_of(W.n, W.num_sms);
-    Chol &C = *W.direct;
+    Chol *C = W.direct;
     // near optimality the primal-infeasibility part of the right-hand side is tiny next to the
     // complementarity part, so the direct branch solves far below the PCG tolerance
     const double target = std::min(tol, 1e-10);
@@ -1080,65 +1209,96 @@ static Error solve_direct(Newton &W, const Support &S, double tol, int max_cg, d
     copy_kernel<<<gn, kT, 0, st>>>(W.n, W.rhs, r);
     OT_LAUNCHED();
     auto precond = [&](const double *in, double *out) -> Error {
-        return W.dense ? dense_solve(*W.dense, in, out, st) : chol_solve(C, in, out, st);
+        if (!C) return d32_apply(*W.d32, in, out, st);
+        return W.dense ? dense_solve(*W.dense, in, out, st) : chol_solve(*C, in, out, st);
     };
     OT_TRY(precond(r, z));
     pcg_dir_kernel<<<gn, kT, 0, st>>>(W.n, 0.0, z, p);
     OT_LAUNCHED();
-    dot_kernel<<<gn, kT, 0, st>>>(W.n, r, z, W.part, SC_SUM_B);
+    dot_kernel<<<gn, kT, 0, st>>>(W.n, r, z, W.part, SC_RZ0);
     OT_LAUNCHED();
     dot_kernel<<<gn, kT, 0, st>>>(W.n, r, r, W.part, SC_NORM_B);
     OT_LAUNCHED();
     {
-        Finish f{2, {SC_SUM_B, SC_NORM_B}, {(int)gn, (int)gn}, {0, 0}};
+        Finish f{2, {SC_RZ0, SC_NORM_B}, {(int)gn, (int)gn}, {0, 0}};
         OT_TRY(finish(f, W, st));
     }
     OT_TRY(read_scalars(W, hs, st));
-    double rz = hs[SC_SUM_B];
     const double bb = hs[SC_NORM_B];
     double rr = bb;
     int it = 0;
-    if (bb > 0 && rz > 0) {
-        for (it = 0; it < max_cg;) {
-            mv_rows_kernel<<<gm, kT, 0, st>>>(W.m, S.row_ptr, S.j, W.theta, W.Minv, p, W.w64);
+    // an accurate FP32 factor gains several digits per iteration; one that needs many more has
+    // met a matrix beyond FP32 and hands the system to the FP64 factorisation
+    const int cap = C ? max_cg : std::min(max_cg, kD32MaxCg);
+    // alpha and beta stay on the device; the host reads p.q and r.r of each iteration while the
+    // GPU already applies the preconditioner for the next one (wasted only at the last iteration)
+    if (bb > 0 && hs[SC_RZ0] > 0) {
+        // lanes per row / column for the FP64 products: about the average row length, <= 16
+        const double avg = (double)S.psi / (double)std::max(1, std::min(W.m, W.n));
+        const int G = avg >= 12 ? 16 : (avg >= 6 ? 8 : 4);
+        const unsigned gmr = (unsigned)std::min<int64_t>(ceil_div((int64_t)W.m * G, kT), 8LL * W.num_sms);
+        const unsigned gnc = (unsigned)std::min<int64_t>(ceil_div((int64_t)W.n * G, kT), kMaxPartBlocks);
+        auto issue = [&](int k) -> Error {
+            const int cur = (k & 1) ? SC_RZ1 : SC_RZ0, nxt = (k & 1) ? SC_RZ0 : SC_RZ1;
+            if (G == 16) {
+                mvg_rows_kernel<16><<<gmr, kT, 0, st>>>(W.m, S.row_ptr, S.j, W.theta, W.Minv, p, W.w64);
+                OT_LAUNCHED();
+                mvg_cols_kernel<16><<<gnc, kT, 0, st>>>(W.n, S.col_ptr, S.col_row, W.theta_col, W.w64, p, q, W.part);
+            } else if (G == 8) {
+                mvg_rows_kernel<8><<<gmr, kT, 0, st>>>(W.m, S.row_ptr, S.j, W.theta, W.Minv, p, W.w64);
+                OT_LAUNCHED();
+                mvg_cols_kernel<8><<<gnc, kT, 0, st>>>(W.n, S.col_ptr, S.col_row, W.theta_col, W.w64, p, q, W.part);
+            } else {
+                mvg_rows_kernel<4><<<gmr, kT, 0, st>>>(W.m, S.row_ptr, S.j, W.theta, W.Minv, p, W.w64);
+                OT_LAUNCHED();
+                mvg_cols_kernel<4><<<gnc, kT, 0, st>>>(W.n, S.col_ptr, S.col_row, W.theta_col, W.w64, p, q, W.part);
+            }
             OT_LAUNCHED();
-            mv_cols_kernel<<<gn, kT, 0, st>>>(W.n, S.col_ptr, S.col_row, W.theta_col, W.w64, p, q, W.part);
+            dcg_step2_kernel<<<gn, kT, 0, st>>>(W.n, (int)gnc, W.scal, cur, p, q, x, r, W.part);
             OT_LAUNCHED();
-            Finish f1{1, {SC_SUM_A}, {(int)gn}, {0}};
-            OT_TRY(finish(f1, W, st));
-            OT_TRY(read_scalars(W, hs, st));
-            const double pq = hs[SC_SUM_A];
-            if (!(pq > 0)) break;
-            const double alpha = rz / pq;
-            pcg_step_kernel<<<gn, kT, 0, st>>>(W.n, alpha, p, q, x, r, W.part);
+            OT_TRY(precond(r, z));
+            dot_kernel<<<gn, kT, 0, st>>>(W.n, r, z, W.part, nxt);
             OT_LAUNCHED();
-            Finish f2{1, {SC_NORM_A}, {(int)gn}, {0}};
-            OT_TRY(finish(f2, W, st));
-            OT_TRY(read_scalars(W, hs, st));
-            rr = hs[SC_NORM_A];
+            dcg_dir2_kernel<<<gn, kT, 0, st>>>(W.n, (int)gn, (int)gn, W.scal, cur, nxt, z, p, W.part);
+            OT_LAUNCHED();
+            OT_CUDA(cudaMemcpyAsync(W.hscal + (k & 1) * SC_COUNT, W.scal, sizeof(double) * SC_COUNT,
+                                    cudaMemcpyDeviceToHost, st));
+            OT_CUDA(cudaEventRecord(W.ev_scal2[k & 1], st));
+            return ok();
+        };
+        // with the FP32 factor, one iteration is queued ahead of the one being checked: alpha and
+        // beta live on the device, so an iteration issued past convergence only refines x further
+        int issued = 0;
+        if (cap > 0) {
+            OT_TRY(issue(0));
+            issued = 1;
+        }
+        const bool ahead = C == nullptr;  // only where the preconditioner is cheap
+        while (it < issued) {
+            if (issued < cap && (ahead || issued == it)) {
+                OT_TRY(issue(issued));
+                ++issued;
+            }
+            OT_CUDA(cudaEventSynchronize(W.ev_scal2[it & 1]));
+            const double *h = W.hscal + (it & 1) * SC_COUNT;
+            const double pq = h[SC_SUM_A];
+            if (!(pq > 0)) break;  // breakdown: this step was a no-op
+            rr = h[SC_NORM_A];
             ++it;
             if (rr <= target * target * bb) break;
-            OT_TRY(precond(r, z));
-            dot_kernel<<<gn, kT, 0, st>>>(W.n, r, z, W.part, SC_SUM_B);
-            OT_LAUNCHED();
-            Finish f3{1, {SC_SUM_B}, {(int)gn}, {0}};
-            OT_TRY(finish(f3, W, st));
-            OT_TRY(read_scalars(W, hs, st));
-            const double rzn = hs[SC_SUM_B];
-            if (!(rzn > 0)) break;
-            pcg_dir_kernel<<<gn, kT, 0, st>>>(W.n, rzn / rz, z, p);
-            OT_LAUNCHED();
-            rz = rzn;
         }
+        // an iteration still queued ahead completes before the copy below (stream order)
     }
     copy_kernel<<<gn, kT, 0, st>>>(W.n, x, dv);
     OT_LAUNCHED();
-    int errv = 0;
-    OT_CUDA(cudaMemcpyAsync(&errv, W.dense ? W.dense->err : C.err, sizeof(int), cudaMemcpyDeviceToHost, st));
-    OT_CUDA(cudaStreamSynchronize(st));
-    if (errv) return fail(OT_ERR_TIMEOUT, "ldl solve: grid barrier wait limit reached");
+    if (C) {
+        int errv = 0;
+        OT_CUDA(cudaMemcpyAsync(&errv, W.dense ? W.dense->err : C->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        OT_CUDA(cudaStreamSynchronize(st));
+        if (errv) return fail(OT_ERR_TIMEOUT, "ldl solve: grid barrier wait limit reached");
+    }
     ss->cg_iters = it;
-    ss->direct = 1;
+    ss->direct = C ? 1 : 0;
     ss->relres = bb > 0 ? std::sqrt(rr / bb) : 0.0;
     return ok();
 }
@@ -1195,6 +1355,10 @@ Error newton_alloc(Newton &W, int32_t m, int32_t n, int64_t cap, int num_sms) {
     OT_TRY(dev_alloc(&W.comp_sum, (int64_t)m + n));
     OT_TRY(dev_alloc(&W.comp_cnt, (int64_t)m + n));
     OT_TRY(dev_alloc(&W.part, (int64_t)SC_COUNT * kMaxPartBlocks));
+    OT_CUDA(cudaHostAlloc((void **)&W.hscal, 2 * sizeof(double) * SC_COUNT, cudaHostAllocDefault));
+    OT_CUDA(cudaEventCreateWithFlags(&W.ev_scal, cudaEventDisableTiming));
+    OT_CUDA(cudaEventCreateWithFlags(&W.ev_scal2[0], cudaEventDisableTiming));
+    OT_CUDA(cudaEventCreateWithFlags(&W.ev_scal2[1], cudaEventDisableTiming));
     OT_TRY(dev_alloc(&W.scal, SC_COUNT));
     OT_TRY(dev_alloc(&W.bar, 2));
     OT_TRY(dev_alloc(&W.err, 1));
@@ -1222,6 +1386,10 @@ void newton_free(Newton &W) {
                     W.parent, W.comp_sum, W.comp_cnt, W.part, W.scal, W.bar, W.err};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    if (W.hscal) cudaFreeHost(W.hscal);
+    if (W.ev_scal) cudaEventDestroy(W.ev_scal);
+    for (cudaEvent_t e : W.ev_scal2)
+        if (e) cudaEventDestroy(e);
     W = Newton();
 }
 
@@ -1314,7 +1482,7 @@ Error newton_solve(Newton &W, const Support &S, const Rhs &R, double cg_tol, int
     OT_TRY(project(W, W.rhs, one, st));
 
     SolveStats ss;
-    if (W.direct) {
+    if (W.direct || W.d32) {
         OT_TRY(solve_direct(W, S, cg_tol, max_cg, dv, &ss, st));
     } else if (precision == 0) {
         OT_TRY(solve_pcg64(W, S, cg_tol, max_cg, dv, &ss, st));
@@ -1395,8 +1563,9 @@ Error take_step(Newton &W, Support &S, double *u, double *v, const double *dp, c
 }
 
 Error read_scalars(Newton &W, double *host, cudaStream_t st) {
-    OT_CUDA(cudaMemcpyAsync(host, W.scal, sizeof(double) * SC_COUNT, cudaMemcpyDeviceToHost, st));
+    OT_CUDA(cudaMemcpyAsync(W.hscal, W.scal, sizeof(double) * SC_COUNT, cudaMemcpyDeviceToHost, st));
     OT_CUDA(cudaStreamSynchronize(st));
+    std::memcpy(host, W.hscal, sizeof(double) * SC_COUNT);
     return ok();
 }
 

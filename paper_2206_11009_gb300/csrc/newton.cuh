@@ -11,7 +11,9 @@ enum Scalar : int {
     SC_R1A_SQ = 0, SC_R1A_L1, SC_R1B_SQ, SC_R1B_L1, SC_R2SQ, SC_PS, SC_CP, SC_CSQ, SC_CMAX,
     SC_AP, SC_AS,            // raw minimum ratios -x/dx over dx < 0 (+inf when none)
     SC_MUAFF, SC_PSNEW, SC_SUM_A, SC_SUM_B, SC_NORM_A, SC_NORM_B, SC_ONECOMP,
-    SC_PCG_ITERS, SC_PCG_RELRES, SC_COUNT
+    SC_PCG_ITERS, SC_PCG_RELRES,
+    SC_RZ0, SC_RZ1,          // ping-pong r.z of the refinement CG (alpha, beta formed on the device)
+    SC_COUNT
 };
 
 // Per-iteration device work arrays (allocated by the solver, sized by capacity).
@@ -43,11 +45,13 @@ struct Newton {
     // reductions
     double *part = nullptr;  // [16][kMaxPartBlocks]
     double *scal = nullptr;  // [SC_COUNT]
+    double *hscal = nullptr; // [2][SC_COUNT] pinned host copies
+    cudaEvent_t ev_scal = nullptr, ev_scal2[2] = {nullptr, nullptr};
     unsigned *bar = nullptr;
     int *err = nullptr;
     int pcg_grid = 0;
-    int verbose = 0;
-    double last_pcg_ms = 0.0;  // >= 3: one line per PCG launch (support size, iterations, device ms)
+    int verbose = 0;           // >= 3: one line per PCG launch (support size, iterations, device ms)
+    double last_pcg_ms = 0.0;
     double *pcg_pb = nullptr;     // second direction buffer of the PCG (fp64 / fp32)
     float *pcg_pb32 = nullptr;
     double pcg_bytes_per_iter = 0.0;
@@ -56,6 +60,8 @@ struct Newton {
     // direct branch: when set, S_M x = rhs is solved by its LDL^T factorisation (chol.cuh)
     struct Chol *direct = nullptr;
     struct DenseLDL *dense = nullptr;   // when set (with direct), solve with the dense factor
+    // when set (and direct is not): FP64 CG preconditioned by the FP32 dense factorisation
+    struct Dense32 *d32 = nullptr;
     int fallbacks = 0;        // mixed-precision solves redone in FP64
     bool fp64_fallback = true;  // redo a failed mixed-precision solve with FP64 PCG
 };

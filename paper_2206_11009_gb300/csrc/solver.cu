@@ -2,6 +2,7 @@
 // (Section 3.4's commented listing: residuals, mu, sigma and r3, Newton direction, step lengths,
 // update, pricing, support update), with the readings stated in ot_ipm.h.
 #include "chol.cuh"
+#include "dense32.cuh"
 #include "newton.cuh"
 #include "pricing.cuh"
 #include "primitives.cuh"
@@ -73,6 +74,7 @@ constexpr double kPcgFail = 10.0;
 constexpr int kDirectCgMany = 25;
 // up to this many targets the direct branch factors S_M densely
 constexpr int kDenseMaxN = 8192;
+constexpr int kDense32MaxN = 8192;  // mixed precision: FP32 dense factor preconditions every solve
 
 // c-transform lower bound (weak duality): ubar_i = min_j (c_ij - v_j); LB = a^T ubar + b^T v.
 __global__ void ctrans_kernel(CostDev cd, const double *__restrict__ v, unsigned long long *__restrict__ rowmin) {
@@ -143,8 +145,10 @@ struct ot_ipm {
     Newton W;
     Chol chol;
     DenseLDL dense;
+    Dense32 d32;
     std::vector<int64_t> psi_hist;
     bool direct_mode = false;
+    bool d32_escalated = false;  // the FP32-preconditioned CG failed once: FP64 LDL^T from then on
     int64_t psi_min = 0;
     double max_fill = 0.0;
     double drop = 1e-8;            // drop tolerance of the LDL^T preconditioner (adapted)
@@ -342,6 +346,20 @@ Error do_step(ot_ipm *h, ot_iter_info *info) {
     }
     W.direct = nullptr;
     W.dense = nullptr;
+    W.d32 = nullptr;
+    // mixed precision on moderate n: the FP32 dense factorisation of this iteration's S_M
+    // preconditions an FP64 CG in every solve; the FP64 LDL^T branch only takes over when that CG
+    // misses its target (the switch on the support's shrinkage is for the Jacobi PCG)
+    const bool use_d32 = o.precision == 1 && o.linear_solver == 0 && n <= kDense32MaxN;
+    if (use_d32 && !h->d32_escalated) {
+        use_direct = false;
+        if (!h->d32.A) OT_TRY(d32_alloc(h->d32, n));
+        OT_TRY(d32_assemble(h->d32, W, S, st));
+        OT_TRY(d32_factor(h->d32, (float)kPivotEps, st));
+        W.d32 = &h->d32;
+    } else if (use_d32) {
+        use_direct = true;
+    }
     const int direct_cg_prev = h->direct_cg_last;
     h->direct_cg_last = 0;
     // factor S_M once for every solve of this iteration; false when the fill is over budget
@@ -399,6 +417,7 @@ Error do_step(ot_ipm *h, ot_iter_info *info) {
             if (W.direct) {
                 h->direct_mode = true;
                 h->psi_min = S.psi;
+                if (W.d32) h->d32_escalated = true;
                 OT_TRY(newton_solve(W, S, R, tol, o.max_cg, o.precision, du, dv, ds, dp, &ss, st));
             } else if (o.precision == 1) {  // fill over budget: FP64 PCG as the last resort
                 OT_TRY(newton_solve(W, S, R, tol, o.max_cg, 0, du, dv, ds, dp, &ss, st));
@@ -798,6 +817,7 @@ void ot_ipm_destroy(ot_ipm_t *h) {
     newton_free(h->W);
     chol_free(h->chol);
     dense_free(h->dense);
+    d32_free(h->d32);
     void *ptrs[] = {h->a_s, h->b_s, h->C, h->sx, h->sy, h->tx, h->ty, h->u, h->v, h->pi, h->pj, h->pd,
                     h->pcount, h->pstrong, h->rowmin, h->lbv};
     for (void *p : ptrs)

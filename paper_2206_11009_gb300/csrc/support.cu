@@ -159,6 +159,84 @@ __global__ void removal_trim_kernel(int64_t cnt, int64_t kmax, const uint32_t *_
 }
 
 // ------------------------------------------------------------------------- merge
+// ---- maximum-weight spanning forest of the support graph by Boruvka rounds.  Edge order: larger
+// p first, then smaller jlin = i + j*m (all keys distinct, so the forest is unique and equals the
+// one Kruskal's rule builds).  Vertices: sources 0..m-1, targets m..m+n-1.
+__global__ void bv_reset_kernel(int V, unsigned long long *__restrict__ bestp, unsigned long long *__restrict__ bestk) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x) {
+        bestp[v] = 0ull;
+        bestk[v] = ~0ull;
+    }
+}
+
+// heaviest p leaving each component (positive doubles order like their bit patterns)
+__global__ void bv_max_kernel(int64_t psi, int m, const int32_t *__restrict__ si, const int32_t *__restrict__ sj,
+                              const double *__restrict__ p, const int32_t *__restrict__ comp,
+                              unsigned long long *__restrict__ bestp) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < psi; e += (int64_t)gridDim.x * blockDim.x) {
+        const int cu = comp[si[e]], cv = comp[m + sj[e]];
+        if (cu == cv) continue;
+        const unsigned long long b = (unsigned long long)__double_as_longlong(p[e]);
+        atomicMax(&bestp[cu], b);
+        atomicMax(&bestp[cv], b);
+    }
+}
+
+// among the edges of that p, the smallest jlin
+__global__ void bv_tie_kernel(int64_t psi, int m, const int32_t *__restrict__ si, const int32_t *__restrict__ sj,
+                              const double *__restrict__ p, const int32_t *__restrict__ comp,
+                              const unsigned long long *__restrict__ bestp, unsigned long long *__restrict__ bestk) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < psi; e += (int64_t)gridDim.x * blockDim.x) {
+        const int cu = comp[si[e]], cv = comp[m + sj[e]];
+        if (cu == cv) continue;
+        const unsigned long long b = (unsigned long long)__double_as_longlong(p[e]);
+        const unsigned long long jl = (unsigned long long)si[e] + (unsigned long long)sj[e] * (unsigned long long)m;
+        if (bestp[cu] == b) atomicMin(&bestk[cu], jl);
+        if (bestp[cv] == b) atomicMin(&bestk[cv], jl);
+    }
+}
+
+// every component root takes its chosen edge into the forest and hooks onto the component at its
+// other end; of two components that chose the same edge, the smaller id hooks onto the larger
+__global__ void bv_hook_kernel(int V, int m, const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ sj,
+                               const int32_t *__restrict__ comp, const unsigned long long *__restrict__ bestp,
+                               const unsigned long long *__restrict__ bestk, int32_t *__restrict__ parent,
+                               uint8_t *__restrict__ flag, int *__restrict__ changed) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < V; c += gridDim.x * blockDim.x) {
+        if (comp[c] != c || bestp[c] == 0ull) continue;
+        const unsigned long long jl = bestk[c];
+        const int i = (int)(jl % (unsigned long long)m), j = (int)(jl / (unsigned long long)m);
+        int lo = row_ptr[i], hi = row_ptr[i + 1];  // the support is sorted by (i, j)
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (sj[mid] < j) lo = mid + 1; else hi = mid;
+        }
+        flag[lo] = 0;
+        const int ci = comp[i], cj = comp[m + j];
+        const int other = ci == c ? cj : ci;
+        const bool mutual = bestk[other] == jl && bestp[other] == bestp[c];
+        if (!mutual || c < other) parent[c] = other;
+        *changed = 1;
+    }
+}
+
+// comp[v] <- root of its hook chain (at most 64 steps per launch; *more when a chain is longer)
+__global__ void bv_jump_kernel(int V, const int32_t *__restrict__ parent, int32_t *__restrict__ comp, int *__restrict__ more) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x) {
+        int r = comp[v];
+        for (int s = 0; s < 64 && parent[r] != r; ++s) r = parent[r];
+        comp[v] = r;
+        if (parent[r] != r) *more = 1;
+    }
+}
+
+__global__ void bv_init_kernel(int V, int32_t *__restrict__ comp, int32_t *__restrict__ parent) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x) {
+        comp[v] = v;
+        parent[v] = v;
+    }
+}
+
 __global__ void keep_flags_kernel(int64_t psi, const uint8_t *__restrict__ flag, uint32_t *__restrict__ keep) {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < psi; e += (int64_t)gridDim.x * blockDim.x)
         keep[e] = flag ? (flag[e] ? 0u : 1u) : 1u;
@@ -315,46 +393,48 @@ Error removal_flags(const Support &S, int32_t m, int32_t n, const double *a_s, c
     removal_cand_kernel<<<grid_for(psi), 256, 0, st>>>(psi, S.i, S.j, S.p, S.s, a_s, b_s, rm_p_frac, flag);
     OT_LAUNCHED();
     // Keep a maximum-weight spanning forest of the support graph (weights p, ties: smaller jlin
-    // first; Kruskal on the host): the support stays connected, so the restricted problem cannot
-    // split into components whose masses do not balance (and no row or column empties).
-    {
-        std::vector<int32_t> hi(psi), hj(psi);
-        std::vector<double> hp(psi);
-        std::vector<uint8_t> hf(psi);
-        OT_CUDA(cudaMemcpyAsync(hi.data(), S.i, sizeof(int32_t) * psi, cudaMemcpyDeviceToHost, st));
-        OT_CUDA(cudaMemcpyAsync(hj.data(), S.j, sizeof(int32_t) * psi, cudaMemcpyDeviceToHost, st));
-        OT_CUDA(cudaMemcpyAsync(hp.data(), S.p, sizeof(double) * psi, cudaMemcpyDeviceToHost, st));
-        OT_CUDA(cudaMemcpyAsync(hf.data(), flag, psi, cudaMemcpyDeviceToHost, st));
-        OT_CUDA(cudaStreamSynchronize(st));
-        bool any = false;
-        for (int64_t e = 0; e < psi && !any; ++e) any = hf[e] != 0;
-        if (any) {
-            std::vector<int64_t> order(psi);
-            for (int64_t e = 0; e < psi; ++e) order[e] = e;
-            std::sort(order.begin(), order.end(), [&](int64_t x, int64_t y) {
-                if (hp[x] != hp[y]) return hp[x] > hp[y];
-                const uint64_t jx = (uint64_t)hi[x] + (uint64_t)hj[x] * m, jy = (uint64_t)hi[y] + (uint64_t)hj[y] * m;
-                return jx < jy;
-            });
-            std::vector<int32_t> parent(m + n);
-            for (int v = 0; v < m + n; ++v) parent[v] = v;
-            auto find = [&](int x) {
-                while (parent[x] != x) { parent[x] = parent[parent[x]]; x = parent[x]; }
-                return x;
-            };
-            for (int64_t e : order) {
-                const int ra = find(hi[e]), rb = find(m + hj[e]);
-                if (ra != rb) {
-                    parent[ra] = rb;
-                    hf[e] = 0;
-                }
-            }
-            OT_CUDA(cudaMemcpyAsync(flag, hf.data(), psi, cudaMemcpyHostToDevice, st));
-            OT_CUDA(cudaStreamSynchronize(st));
-        }
-    }
+    // first): the support stays connected, so the restricted problem cannot split into components
+    // whose masses do not balance (and no row or column empties).  Boruvka rounds on the device.
     DevTemp<uint32_t> f32, pos, tot;
     OT_TRY(f32.alloc(psi, st)); OT_TRY(pos.alloc(psi, st)); OT_TRY(tot.alloc(1, st));
+    count_flags_kernel<<<grid_for(psi), 256, 0, st>>>(psi, flag, f32.p);
+    OT_LAUNCHED();
+    OT_TRY(scan_exclusive_u32(f32.p, pos.p, psi, tot.p, st));
+    uint32_t ncand = 0;
+    OT_CUDA(cudaMemcpyAsync(&ncand, tot.p, sizeof(ncand), cudaMemcpyDeviceToHost, st));
+    OT_CUDA(cudaStreamSynchronize(st));
+    if (ncand == 0) return ok();
+    {
+        const int V = m + n;
+        DevTemp<int32_t> comp, parent;
+        DevTemp<unsigned long long> bestp, bestk;
+        DevTemp<int> flags;  // [0] a component hooked, [1] a hook chain is longer than one jump pass
+        OT_TRY(comp.alloc(V, st)); OT_TRY(parent.alloc(V, st));
+        OT_TRY(bestp.alloc(V, st)); OT_TRY(bestk.alloc(V, st));
+        OT_TRY(flags.alloc(2, st));
+        bv_init_kernel<<<grid_for(V), 256, 0, st>>>(V, comp.p, parent.p);
+        OT_LAUNCHED();
+        int hf[2] = {1, 0};
+        for (int round = 0; round < 64 && hf[0]; ++round) {
+            OT_CUDA(cudaMemsetAsync(flags.p, 0, 2 * sizeof(int), st));
+            bv_reset_kernel<<<grid_for(V), 256, 0, st>>>(V, bestp.p, bestk.p);
+            OT_LAUNCHED();
+            bv_max_kernel<<<grid_for(psi), 256, 0, st>>>(psi, m, S.i, S.j, S.p, comp.p, bestp.p);
+            OT_LAUNCHED();
+            bv_tie_kernel<<<grid_for(psi), 256, 0, st>>>(psi, m, S.i, S.j, S.p, comp.p, bestp.p, bestk.p);
+            OT_LAUNCHED();
+            bv_hook_kernel<<<grid_for(V), 256, 0, st>>>(V, m, S.row_ptr, S.j, comp.p, bestp.p, bestk.p, parent.p, flag,
+                                                        flags.p);
+            OT_LAUNCHED();
+            do {
+                OT_CUDA(cudaMemsetAsync(flags.p + 1, 0, sizeof(int), st));
+                bv_jump_kernel<<<grid_for(V), 256, 0, st>>>(V, parent.p, comp.p, flags.p + 1);
+                OT_LAUNCHED();
+                OT_CUDA(cudaMemcpyAsync(hf, flags.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+                OT_CUDA(cudaStreamSynchronize(st));
+            } while (hf[1]);
+        }
+    }
     count_flags_kernel<<<grid_for(psi), 256, 0, st>>>(psi, flag, f32.p);
     OT_LAUNCHED();
     OT_TRY(scan_exclusive_u32(f32.p, pos.p, psi, tot.p, st));
