@@ -85,6 +85,27 @@ typedef struct {
     int32_t add_max;          /* 0 = m: pairs added per pricing (end of Section 3.2)          */
     int32_t verbose;          /* 0: silent; 1: one line per iteration on stderr               */
     void *stream;             /* cudaStream_t to run on; NULL = a stream the handle creates   */
+    /* Warm start (not in the paper; its conclusion names a better starting support as future
+     * work).  warm_u (m) and warm_v (n): predicted duals, HOST pointers, the caller's cost units;
+     * NULL (either) = cold start.  The initial support then also holds the warm_count pairs
+     * outside {c_ij <= init_cost} with the least c_ij - u_i - v_j below init_cost, selected by
+     * the pricing scan (ties by jlin); 0 = 2(m+n).  warm_mode 0: only the support is warm (the
+     * starting point is Mehrotra's, computed on it); 1: the starting point also takes warm_u,
+     * warm_v as its duals, with slacks max(c_ij - u_i - v_j, 0) before Mehrotra's balancing. */
+    const double *warm_u;
+    const double *warm_v;
+    int32_t warm_count;
+    int32_t warm_mode;
+    /* Warm start by explicit pairs: warm_i, warm_j (HOST, warm_npairs entries, any order,
+     * duplicates allowed) join the cold support; pairs already in it are skipped.  Used with or
+     * without warm_u / warm_v (their pairs are added first). */
+    const int32_t *warm_i;
+    const int32_t *warm_j;
+    int64_t warm_npairs;
+    /* New pairs from pricing start at p = s = sqrt(mu) (Section 3.2): new_col_rule 0.  1: p =
+     * min(sqrt(mu), a_i, b_j) and s = mu / p (still p s = mu, but a pair never enters with more
+     * flow than its smaller mass; masses in the solver's scaling, sum(a) = m). */
+    int32_t new_col_rule;
 } ot_options;
 
 /* One outer iteration (Section 3.4's commented listing). */
@@ -113,6 +134,9 @@ typedef struct {
     int64_t psi;              /* final support size                                           */
     double max_fill;          /* max nnz(L)/n^2 * 100 over direct iterations (Table 3's fill)  */
     double seconds;           /* device time of the solve (CUDA events)                       */
+    int64_t warm_added;       /* pairs the warm start added to the initial support            */
+    int32_t warm_restarts;    /* 1 when a warm start lost ground (mu over twice its first value */
+                              /* by iteration 5) and the solve restarted from the cold support */
 } ot_result;
 
 typedef struct ot_ipm ot_ipm_t;

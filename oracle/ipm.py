@@ -27,7 +27,11 @@ Readings where the paper is silent (each listed in the design doc as well):
   * Schur complement S_M = N - V^T M^-1 V (Section 4), singular: right-hand side projected
     to mean zero on each connected component of the support graph, minimum-norm dv;
   * support enlargement: at most m new pairs (the most negative reduced costs, exact rule
-    of ``oracle.pricing``) at p = s = sqrt(mu) (Section 3.2);
+    of ``oracle.pricing``).  Section 3.2 starts them at p = s = sqrt(mu) (``new_col_rule`` 0);
+    the default (``new_col_rule`` 1) keeps the product p s = mu but caps the flow at the pair's
+    smaller scaled mass, p = min(sqrt(mu), a_i, b_j), s = mu / p: with masses scaled to sum m,
+    sqrt(mu) can exceed a pixel's whole mass many times over while mu is still large, and m such
+    pairs per iteration then dominate the primal residual;
   * support reduction, active once mu <= rm_mu_frac * mu_0: a pair leaves when
     p < rm_p_frac * min(a_i, b_j) and theta < 1; at most m leave (smallest p first, ties by
     jlin); the edges of a maximum-weight spanning forest (weights p) never leave, so the support
@@ -62,6 +66,7 @@ class Options:
     rm_p_frac: float = 1e-3
     init_cost: float = 2.0
     add_max: int | None = None      # default m
+    new_col_rule: int = 1           # 0: p = s = sqrt(mu) as Section 3.2; 1: flow capped at min(a_i, b_j)
 
 
 @dataclass
@@ -359,13 +364,21 @@ def removal_select(prob: Problem, st: State, opt: Options, kmax: int):
     return idx[o[:kmax]]
 
 
-def update_support(st: State, remove_idx, addI, addJ, p_new, n) -> State:
+def update_support(st: State, remove_idx, addI, addJ, p_new, n, cap_a=None, cap_b=None) -> State:
+    """New pairs at p = s = p_new, or with masses cap_a, cap_b given at p = min(p_new, a_i, b_j)
+    and s = p_new^2 / p."""
     keep = np.ones(len(st.p), dtype=bool)
     keep[remove_idx] = False
     I = np.concatenate([st.I[keep], addI])
     J = np.concatenate([st.J[keep], addJ])
-    p = np.concatenate([st.p[keep], np.full(len(addI), p_new)])
-    s = np.concatenate([st.s[keep], np.full(len(addI), p_new)])
+    if cap_a is None:
+        pa = np.full(len(addI), p_new)
+        sa = np.full(len(addI), p_new)
+    else:
+        pa = np.minimum(p_new, np.minimum(cap_a[addI], cap_b[addJ]))
+        sa = p_new * p_new / pa
+    p = np.concatenate([st.p[keep], pa])
+    s = np.concatenate([st.s[keep], sa])
     o = np.argsort(I * n + J, kind="stable")
     return State(I[o], J[o], p[o], s[o], st.u, st.v)
 
@@ -422,7 +435,9 @@ def one_iteration(prob: Problem, st: State, res: Residuals, opt: Options, tr: Tr
     else:
         rem = np.zeros(0, dtype=np.int64)
     stepped = st
-    st = update_support(st, rem, aI, aJ, math.sqrt(mu_new), n)
+    capped = opt.new_col_rule == 1
+    st = update_support(st, rem, aI, aJ, math.sqrt(mu_new), n, prob.as_ if capped else None,
+                        prob.bs if capped else None)
     log = IterLog(it, psi, res.mu, stop_measure(prob, res, psi), ap, as_, sigma, ncorr, len(aI), len(rem))
     return st, log, stepped, (aI, aJ, aD), rem
 

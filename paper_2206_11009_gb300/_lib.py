@@ -30,7 +30,9 @@ class OtOptions(ctypes.Structure):
                 ("max_iter", c_int32), ("max_cg", c_int32), ("max_corr", c_int32), ("step_scale", c_double),
                 ("precision", c_int32), ("linear_solver", c_int32), ("init_cost", c_double),
                 ("rm_mu_frac", c_double), ("rm_p_frac", c_double), ("add_max", c_int32), ("verbose", c_int32),
-                ("stream", c_void_p)]
+                ("stream", c_void_p), ("warm_u", c_void_p), ("warm_v", c_void_p), ("warm_count", c_int32),
+                ("warm_mode", c_int32), ("warm_i", c_void_p), ("warm_j", c_void_p), ("warm_npairs", c_int64),
+                ("new_col_rule", c_int32)]
 
 
 class OtIterInfo(ctypes.Structure):
@@ -43,7 +45,8 @@ class OtIterInfo(ctypes.Structure):
 class OtResult(ctypes.Structure):
     _fields_ = [("status", c_int32), ("obj", c_double), ("lower_bound", c_double), ("rel_gap", c_double),
                 ("r1_l1", c_double), ("mu", c_double), ("iters", c_int32), ("cg_iters", c_int32),
-                ("direct_iters", c_int32), ("psi", c_int64), ("max_fill", c_double), ("seconds", c_double)]
+                ("direct_iters", c_int32), ("psi", c_int64), ("max_fill", c_double), ("seconds", c_double),
+                ("warm_added", c_int64), ("warm_restarts", c_int32)]
 
 
 # exported symbol -> (restype, argtypes)

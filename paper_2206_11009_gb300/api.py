@@ -44,6 +44,8 @@ class Result:
     psi: int
     max_fill: float
     seconds: float
+    warm_added: int = 0
+    warm_restarts: int = 0
 
 
 class Solver:
@@ -53,7 +55,10 @@ class Solver:
     i at (i mod w, i div w)) or ``coords=(sx, sy, tx, ty)`` integer arrays.
     """
 
-    def __init__(self, a, b, grid=None, coords=None, stream=None, **options):
+    def __init__(self, a, b, grid=None, coords=None, stream=None, warm=None, warm_pairs=None, **options):
+        """warm: optional predicted duals (u, v) in cost units; the initial support then also takes
+        the pairs of least predicted reduced cost.  warm_pairs: optional (I, J) pairs that join the
+        initial support (e.g. from ``WarmStart.pairs``)."""
         self._lib = _lib.load()
         self.a = np.ascontiguousarray(a, dtype=np.float64)
         self.b = np.ascontiguousarray(b, dtype=np.float64)
@@ -74,6 +79,20 @@ class Solver:
             prob.src_w, prob.dst_w = grid
         if stream is not None:
             options["stream"] = stream
+        if warm is not None:
+            wu = np.ascontiguousarray(warm[0], dtype=np.float64)
+            wv = np.ascontiguousarray(warm[1], dtype=np.float64)
+            if wu.shape != (self.m,) or wv.shape != (self.n,):
+                raise ValueError("warm duals must have shapes (m,) and (n,)")
+            self._keep += [wu, wv]
+            options["warm_u"], options["warm_v"] = _ptr(wu), _ptr(wv)
+        if warm_pairs is not None:
+            wi = np.ascontiguousarray(warm_pairs[0], dtype=np.int32)
+            wj = np.ascontiguousarray(warm_pairs[1], dtype=np.int32)
+            if wi.shape != wj.shape:
+                raise ValueError("warm_pairs: I and J differ in length")
+            self._keep += [wi, wj]
+            options["warm_i"], options["warm_j"], options["warm_npairs"] = _ptr(wi), _ptr(wj), len(wi)
         self.options = default_options(**options)
         h = ctypes.c_void_p()
         check(self._lib.ot_ipm_create(ctypes.byref(prob), ctypes.byref(self.options), ctypes.byref(h)))

@@ -1603,8 +1603,15 @@ __global__ void add_const2_kernel(int64_t psi, double *__restrict__ p, double *_
 }
 }  // namespace
 
+// s~ = max(c - u_i - v_j, 0) for given duals (warm start)
+__global__ void warm_slack_kernel(int64_t psi, const int32_t *__restrict__ si, const int32_t *__restrict__ sj,
+                                  const double *__restrict__ c, const double *__restrict__ u,
+                                  const double *__restrict__ v, double *__restrict__ s) {
+    GRID_STRIDE(e, psi) s[e] = fmax((c[e] - u[si[e]]) - v[sj[e]], 0.0);
+}
+
 Error mehrotra_start(Newton &W, Support &S, const double *a_s, const double *b_s, double *u, double *v,
-                     int precision, double cg_tol, int max_cg, int *cg_iters, cudaStream_t st) {
+                     int precision, double cg_tol, int max_cg, int *cg_iters, cudaStream_t st, bool warm_duals) {
     const unsigned ge = grid_of(S.psi, W.num_sms);
     fill_kernel<<<ge, kT, 0, st>>>(S.psi, 1.0, S.p);
     OT_LAUNCHED();
@@ -1615,9 +1622,17 @@ Error mehrotra_start(Newton &W, Support &S, const double *a_s, const double *b_s
     // p~ = A^T (A A^T)^+ f : with theta = 1, r1 = f, r2 = r3 = 0 the direction has dp = A^T dy
     Rhs Rf{a_s, b_s, nullptr, nullptr};
     OT_TRY(newton_solve(W, S, Rf, cg_tol, max_cg, precision, W.du, W.dv, W.ds, W.dp, &s1, st));
-    // y~ = (A A^T)^+ A c : r2 = c gives dy = y~ and ds = c - A^T y~ = s~
-    Rhs Rc{nullptr, nullptr, W.c, nullptr};
-    OT_TRY(newton_solve(W, S, Rc, cg_tol, max_cg, precision, u, v, W.ds2, W.dp2, &s2, st));
+    if (warm_duals) {
+        // the caller's duals (already in u, v) replace the least-squares ones; their negative
+        // reduced costs are clipped rather than shifting every slack (Mehrotra's shift would
+        // spread one bad prediction over the whole support)
+        warm_slack_kernel<<<ge, kT, 0, st>>>(S.psi, S.i, S.j, W.c, u, v, W.ds2);
+        OT_LAUNCHED();
+    } else {
+        // y~ = (A A^T)^+ A c : r2 = c gives dy = y~ and ds = c - A^T y~ = s~
+        Rhs Rc{nullptr, nullptr, W.c, nullptr};
+        OT_TRY(newton_solve(W, S, Rc, cg_tol, max_cg, precision, u, v, W.ds2, W.dp2, &s2, st));
+    }
     if (cg_iters) *cg_iters = s1.cg_iters + s2.cg_iters;
     // dp holds p~, ds2 holds s~
     start_min_kernel<<<ge, kT, 0, st>>>(S.psi, W.dp, W.ds2, W.part);

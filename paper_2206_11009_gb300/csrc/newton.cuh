@@ -128,7 +128,8 @@ Error take_step(Newton &W, Support &S, double *u, double *v, const double *dp, c
 
 // Mehrotra's starting point on the restricted problem (Theta = I): writes S.p, S.s, u, v.
 Error mehrotra_start(Newton &W, Support &S, const double *a_s, const double *b_s, double *u, double *v,
-                     int precision, double cg_tol, int max_cg, int *cg_iters, cudaStream_t st);
+                     int precision, double cg_tol, int max_cg, int *cg_iters, cudaStream_t st,
+                     bool warm_duals = false);
 
 // Read the scalars back (synchronises the stream).
 Error read_scalars(Newton &W, double *host, cudaStream_t st);

@@ -74,7 +74,10 @@ constexpr double kPcgFail = 10.0;
 constexpr int kDirectCgMany = 25;
 // up to this many targets the direct branch factors S_M densely
 constexpr int kDenseMaxN = 8192;
-constexpr int kDense32MaxN = 8192;  // mixed precision: FP32 dense factor preconditions every solve
+constexpr int kDense32MaxN = 8192;
+constexpr int kWarmCheck = 5;       // a warm start is judged from this iteration on ...
+constexpr int kWarmSettle = 15;     // ... up to this one
+constexpr double kWarmGrowth = 2.0; // abandoned when mu exceeds this multiple of its first value  // mixed precision: FP32 dense factor preconditions every solve
 
 // c-transform lower bound (weak duality): ubar_i = min_j (c_ij - v_j); LB = a^T ubar + b^T v.
 __global__ void ctrans_kernel(CostDev cd, const double *__restrict__ v, unsigned long long *__restrict__ rowmin) {
@@ -148,7 +151,10 @@ struct ot_ipm {
     Dense32 d32;
     std::vector<int64_t> psi_hist;
     bool direct_mode = false;
-    bool d32_escalated = false;  // the FP32-preconditioned CG failed once: FP64 LDL^T from then on
+    bool d32_escalated = false;
+    int64_t warm_added = 0;      // pairs the warm start added to the cold support
+    bool warm_active = false;    // warm-started and still inside the check window
+    int32_t warm_restarts = 0;   // warm starts abandoned for the cold one  // the FP32-preconditioned CG failed once: FP64 LDL^T from then on
     int64_t psi_min = 0;
     double max_fill = 0.0;
     double drop = 1e-8;            // drop tolerance of the LDL^T preconditioner (adapted)
@@ -280,6 +286,55 @@ struct PhaseClock {
     }
 };
 
+// Stopping measure of the current point (the quantity the first iteration's test reads).
+Error start_crit(ot_ipm *h, double *crit) {
+    Newton &W = h->W;
+    Support &S = h->S[h->cur];
+    double hs[SC_COUNT];
+    OT_TRY(residuals(W, S, h->a_s, h->b_s, h->u, h->v, h->st));
+    OT_TRY(read_scalars(W, hs, h->st));
+    const double psi = (double)S.psi, mu = hs[SC_PS] / psi;
+    const double r1n = std::sqrt(hs[SC_R1A_SQ] + hs[SC_R1B_SQ]);
+    *crit = std::max({r1n / (1.0 + h->fnorm), std::sqrt(hs[SC_R2SQ]) / (1.0 + std::sqrt(hs[SC_CSQ])),
+                      psi * mu / (1.0 + std::fabs(hs[SC_CP]))});
+    if (!std::isfinite(*crit)) *crit = INFINITY;
+    return ok();
+}
+
+// Abandon a warm start: the cold initial support and Mehrotra's point, as ot_ipm_create builds
+// them; the iteration count carries on.
+Error cold_restart(ot_ipm *h) {
+    const ot_options &o = h->opt;
+    cudaStream_t st = h->st;
+    int32_t *ii = nullptr, *jj = nullptr;
+    int64_t psi0 = 0;
+    OT_TRY(initial_support(h->cd, o.init_cost, &ii, &jj, &psi0, st));
+    Error e = ensure_capacity(h, psi0);
+    Support &S = h->S[h->cur];
+    if (e.code == OT_OK) {
+        cudaMemcpyAsync(S.i, ii, sizeof(int32_t) * psi0, cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(S.j, jj, sizeof(int32_t) * psi0, cudaMemcpyDeviceToDevice, st);
+        cudaStreamSynchronize(st);
+    }
+    cudaFree(ii);
+    cudaFree(jj);
+    OT_TRY(e);
+    S.psi = psi0;
+    OT_TRY(rebuild_views(S, h->m, h->n, st));
+    OT_TRY(support_costs(h->W, h->cd, S, st));
+    int cgs = 0;
+    OT_TRY(mehrotra_start(h->W, S, h->a_s, h->b_s, h->u, h->v, o.precision, o.cg_tol_pred, 20 * o.max_cg, &cgs, st));
+    h->cg_total += cgs;
+    h->mu0 = -1.0;
+    h->psi_hist.clear();
+    h->direct_mode = false;
+    h->strong = 0;
+    h->warm_active = false;
+    h->warm_restarts++;
+    h->warm_added = 0;
+    return ok();
+}
+
 Error do_step(ot_ipm *h, ot_iter_info *info) {
     const ot_options &o = h->opt;
     cudaStream_t st = h->st;
@@ -305,6 +360,13 @@ Error do_step(ot_ipm *h, ot_iter_info *info) {
     const double cmax_red = hs[SC_CMAX];
     if (!std::isfinite(mu) || !std::isfinite(crit)) return fail(OT_ERR_NUMERIC, "non-finite mu or residual");
     if (h->mu0 < 0) h->mu0 = mu;
+    if (h->warm_active && h->iter >= kWarmCheck) {
+        if (mu > kWarmGrowth * h->mu0) {
+            OT_TRY(cold_restart(h));
+            return do_step(h, info);
+        }
+        if (h->iter >= kWarmSettle) h->warm_active = false;
+    }
     h->last_mu = mu;
     inf.mu = mu;
     inf.crit = crit;
@@ -489,7 +551,8 @@ Error do_step(ot_ipm *h, ot_iter_info *info) {
     Support &S0 = h->S[h->cur];
     Support &T = h->S[1 - h->cur];
     pc.mark("remove");
-    OT_TRY(merge_support(S0, removing ? W.flag : nullptr, h->pi, h->pj, added, std::sqrt(mu_new), m, n, T, st));
+    OT_TRY(merge_support(S0, removing ? W.flag : nullptr, h->pi, h->pj, added, std::sqrt(mu_new), m, n, T, st,
+                         o.new_col_rule == 1 ? h->a_s : nullptr, o.new_col_rule == 1 ? h->b_s : nullptr));
     h->cur = 1 - h->cur;
     OT_TRY(support_costs(W, h->cd, T, st));
     OT_CUDA(cudaStreamSynchronize(st));
@@ -516,6 +579,103 @@ Error do_step(ot_ipm *h, ot_iter_info *info) {
 int record(ot_ipm *h, const Error &e) {
     if (e.code != OT_OK) h->err = e.msg;
     return e.code;
+}
+
+// Warm start by explicit pairs: validated, deduplicated and stripped of the pairs already in the
+// support on the host, then merged (at most what the support buffers hold).
+Error warm_pairs(ot_ipm *h, const ot_options &o, cudaStream_t st) {
+    const int m = h->m, n = h->n;
+    Support &A = h->S[h->cur];
+    Support &B = h->S[1 - h->cur];
+    std::vector<int32_t> si(A.psi), sj(A.psi);
+    OT_CUDA(cudaMemcpyAsync(si.data(), A.i, sizeof(int32_t) * A.psi, cudaMemcpyDeviceToHost, st));
+    OT_CUDA(cudaMemcpyAsync(sj.data(), A.j, sizeof(int32_t) * A.psi, cudaMemcpyDeviceToHost, st));
+    OT_CUDA(cudaStreamSynchronize(st));
+    std::vector<int64_t> have(A.psi);
+    for (int64_t e = 0; e < A.psi; ++e) have[e] = (int64_t)si[e] * n + sj[e];  // sorted by (i, j)
+    std::vector<int64_t> add;
+    add.reserve(o.warm_npairs);
+    for (int64_t t = 0; t < o.warm_npairs; ++t) {
+        const int32_t i = o.warm_i[t], j = o.warm_j[t];
+        if (i < 0 || i >= m || j < 0 || j >= n) return fail(OT_ERR_ARG, "warm pairs: index out of range");
+        add.push_back((int64_t)i * n + j);
+    }
+    std::sort(add.begin(), add.end());
+    add.erase(std::unique(add.begin(), add.end()), add.end());
+    std::vector<int32_t> ni, nj;
+    const int64_t room = std::min(A.cap, B.cap) - A.psi;
+    for (int64_t key : add) {
+        if ((int64_t)ni.size() >= room) break;
+        if (std::binary_search(have.begin(), have.end(), key)) continue;
+        ni.push_back((int32_t)(key / n));
+        nj.push_back((int32_t)(key % n));
+    }
+    const int64_t k = (int64_t)ni.size();
+    if (k == 0) return ok();
+    DevTemp<int32_t> di, dj;
+    DevTemp<uint8_t> keep;
+    OT_TRY(di.alloc(k, st)); OT_TRY(dj.alloc(k, st));
+    OT_TRY(keep.alloc(std::max<int64_t>(A.psi, 1), st));
+    OT_CUDA(cudaMemcpyAsync(di.p, ni.data(), sizeof(int32_t) * k, cudaMemcpyHostToDevice, st));
+    OT_CUDA(cudaMemcpyAsync(dj.p, nj.data(), sizeof(int32_t) * k, cudaMemcpyHostToDevice, st));
+    OT_CUDA(cudaMemsetAsync(keep.p, 0, std::max<int64_t>(A.psi, 1), st));
+    OT_TRY(merge_support(A, keep.p, di.p, dj.p, k, 1.0, m, n, B, st));
+    h->cur = 1 - h->cur;
+    h->warm_added += k;
+    return ok();
+}
+
+// Warm start: the pricing scan with the predicted duals shifted by init_cost selects the pairs of
+// least predicted reduced cost c_ij - u_i - v_j < init_cost outside the cold support, and they
+// join it (the cold rule is the same test with u = v = 0).
+Error warm_support(ot_ipm *h, const ot_options &o, cudaStream_t st) {
+    const int m = h->m, n = h->n;
+    Support &A = h->S[h->cur];
+    Support &B = h->S[1 - h->cur];
+    // at most what the support buffers hold beyond the cold support (the workspace is sized after)
+    const int64_t want = o.warm_count > 0 ? o.warm_count : 2LL * (m + n);
+    const int32_t K = (int32_t)std::min<int64_t>(want, std::min(A.cap, B.cap) - A.psi);
+    if (K <= 0) return ok();
+    std::vector<double> hu(o.warm_u, o.warm_u + m), hv(o.warm_v, o.warm_v + n);
+    for (int i = 0; i < m; ++i) {
+        if (!std::isfinite(hu[i])) return fail(OT_ERR_ARG, "warm_u: non-finite value");
+        hu[i] += o.init_cost;
+    }
+    for (int j = 0; j < n; ++j)
+        if (!std::isfinite(hv[j])) return fail(OT_ERR_ARG, "warm_v: non-finite value");
+    DevTemp<double> du, dv, dd;
+    DevTemp<int32_t> wi, wj, wc;
+    DevTemp<uint8_t> keep;
+    OT_TRY(du.alloc(m, st)); OT_TRY(dv.alloc(n, st)); OT_TRY(dd.alloc(K, st));
+    OT_TRY(wi.alloc(K, st)); OT_TRY(wj.alloc(K, st)); OT_TRY(wc.alloc(1, st));
+    OT_TRY(keep.alloc(std::max<int64_t>(A.psi, 1), st));
+    OT_CUDA(cudaMemcpyAsync(du.p, hu.data(), sizeof(double) * m, cudaMemcpyHostToDevice, st));
+    OT_CUDA(cudaMemcpyAsync(dv.p, hv.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
+    OT_CUDA(cudaMemsetAsync(keep.p, 0, std::max<int64_t>(A.psi, 1), st));
+    PriceInput in;
+    in.m = m;
+    in.n = n;
+    in.sx = h->sx; in.sy = h->sy; in.tx = h->tx; in.ty = h->ty;
+    in.u = du.p;
+    in.v = dv.p;
+    in.sup_i = A.i;
+    in.sup_j = A.j;
+    in.row_ptr = A.row_ptr;
+    in.psi = A.psi;
+    in.kmax = K;
+    in.precision = o.precision;
+    in.origin_x = h->ox;
+    in.origin_y = h->oy;
+    in.num_sms = h->num_sms;
+    OT_TRY(price_topk(in, wi.p, wj.p, dd.p, wc.p, nullptr, st));
+    int32_t k = 0;
+    OT_CUDA(cudaMemcpyAsync(&k, wc.p, sizeof(k), cudaMemcpyDeviceToHost, st));
+    OT_CUDA(cudaStreamSynchronize(st));
+    if (k <= 0) return ok();
+    OT_TRY(merge_support(A, keep.p, wi.p, wj.p, k, 1.0, m, n, B, st));
+    h->cur = 1 - h->cur;
+    h->warm_added += k;
+    return ok();
 }
 
 Error create_impl(const ot_problem *P, const ot_options *O, ot_ipm *h) {
@@ -625,14 +785,37 @@ Error create_impl(const ot_problem *P, const ot_options *O, ot_ipm *h) {
     OT_TRY(e);
     h->S[0].psi = psi0;
     OT_TRY(rebuild_views(h->S[0], m, n, st));
-    OT_TRY(newton_alloc(h->W, m, n, cap, h->num_sms));
+    const bool want_warm = (o.warm_u && o.warm_v) || (o.warm_i && o.warm_j && o.warm_npairs > 0);
+    OT_TRY(newton_alloc(h->W, m, n, h->S[h->cur].cap, h->num_sms));
     h->W.verbose = h->opt.verbose;
     OT_TRY(chol_alloc(h->chol, n));
-    OT_TRY(support_costs(h->W, h->cd, h->S[0], st));
     int cgs = 0;
-    OT_TRY(mehrotra_start(h->W, h->S[0], h->a_s, h->b_s, h->u, h->v, o.precision, o.cg_tol_pred, 20 * o.max_cg,
-                          &cgs, st));
+    double crit_cold = INFINITY;
+    if (want_warm) {
+        // the cold starting point first: a warm start is kept only when its point is better
+        OT_TRY(support_costs(h->W, h->cd, h->S[h->cur], st));
+        OT_TRY(mehrotra_start(h->W, h->S[h->cur], h->a_s, h->b_s, h->u, h->v, o.precision, o.cg_tol_pred,
+                              20 * o.max_cg, &cgs, st));
+        h->cg_total += cgs;
+        OT_TRY(start_crit(h, &crit_cold));
+        if (o.warm_u && o.warm_v) OT_TRY(warm_support(h, o, st));
+        if (o.warm_i && o.warm_j && o.warm_npairs > 0) OT_TRY(warm_pairs(h, o, st));
+        h->warm_active = true;
+    }
+    OT_TRY(support_costs(h->W, h->cd, h->S[h->cur], st));
+    const bool warm = o.warm_u && o.warm_v && o.warm_mode == 1;
+    if (warm) {
+        OT_CUDA(cudaMemcpyAsync(h->u, o.warm_u, sizeof(double) * m, cudaMemcpyHostToDevice, st));
+        OT_CUDA(cudaMemcpyAsync(h->v, o.warm_v, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+    }
+    OT_TRY(mehrotra_start(h->W, h->S[h->cur], h->a_s, h->b_s, h->u, h->v, o.precision, o.cg_tol_pred, 20 * o.max_cg,
+                          &cgs, st, warm));
     h->cg_total += cgs;
+    if (want_warm) {
+        double crit_warm = INFINITY;
+        OT_TRY(start_crit(h, &crit_warm));
+        if (!(crit_warm < crit_cold)) OT_TRY(cold_restart(h));
+    }
     OT_CUDA(cudaStreamSynchronize(st));
     return ok();
 }
@@ -659,6 +842,7 @@ void ot_options_default(ot_options *o) {
     o->rm_mu_frac = 1e-3;
     o->rm_p_frac = 1e-3;
     o->add_max = 0;
+    o->new_col_rule = 1;
     o->verbose = 0;
     o->stream = nullptr;
 }
@@ -733,6 +917,8 @@ int ot_ipm_solve(ot_ipm_t *h, ot_result *res) {
         res->max_fill = h->max_fill;
         res->psi = h->S[h->cur].psi;
         res->seconds = ms * 1e-3;
+        res->warm_added = h->warm_added;
+        res->warm_restarts = h->warm_restarts;
     }
     return rc;
 }

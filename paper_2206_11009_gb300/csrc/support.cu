@@ -289,13 +289,24 @@ __global__ void merge_kept_kernel(int64_t psi, int n, const uint32_t *__restrict
 __global__ void merge_new_kernel(int64_t k, int n, const uint64_t *__restrict__ nkey, const uint32_t *__restrict__ nval,
                                  const int32_t *__restrict__ ni, const int32_t *__restrict__ nj,
                                  const int32_t *__restrict__ ki, const int32_t *__restrict__ kj, int64_t nkept,
-                                 double p_new, int32_t *__restrict__ ti, int32_t *__restrict__ tj,
+                                 double p_new, const double *__restrict__ a_cap, const double *__restrict__ b_cap,
+                                 int32_t *__restrict__ ti, int32_t *__restrict__ tj,
                                  double *__restrict__ tp, double *__restrict__ ts) {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < k; t += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t K = nkey[t];
         const int64_t q = t + count_less_kept(K, ki, kj, nkept, n);
         const uint32_t src = nval[t];
-        ti[q] = ni[src]; tj[q] = nj[src]; tp[q] = p_new; ts[q] = p_new;
+        const int i = ni[src], j = nj[src];
+        ti[q] = i; tj[q] = j;
+        if (a_cap) {
+            // p s = mu with p no larger than the pair's smaller mass
+            const double p = fmin(p_new, fmin(a_cap[i], b_cap[j]));
+            tp[q] = p;
+            ts[q] = p_new * p_new / p;
+        } else {
+            tp[q] = p_new;
+            ts[q] = p_new;
+        }
     }
 }
 
@@ -460,7 +471,8 @@ Error removal_flags(const Support &S, int32_t m, int32_t n, const double *a_s, c
 }
 
 Error merge_support(const Support &S, const uint8_t *flag, const int32_t *ni, const int32_t *nj,
-                    int64_t k, double p_new, int32_t m, int32_t n, Support &T, cudaStream_t st) {
+                    int64_t k, double p_new, int32_t m, int32_t n, Support &T, cudaStream_t st,
+                    const double *a_cap, const double *b_cap) {
     const int64_t psi = S.psi;
     DevTemp<uint32_t> keep, pos, tot;
     OT_TRY(keep.alloc(psi, st)); OT_TRY(pos.alloc(psi, st)); OT_TRY(tot.alloc(1, st));
@@ -492,8 +504,8 @@ Error merge_support(const Support &S, const uint8_t *flag, const int32_t *ni, co
         OT_LAUNCHED();
     }
     if (k > 0) {
-        merge_new_kernel<<<grid_for(k), 256, 0, st>>>(k, n, nkey.p, nval.p, ni, nj, ki.p, kj.p, nkept, p_new,
-                                                      T.i, T.j, T.p, T.s);
+        merge_new_kernel<<<grid_for(k), 256, 0, st>>>(k, n, nkey.p, nval.p, ni, nj, ki.p, kj.p, nkept, p_new, a_cap,
+                                                      b_cap, T.i, T.j, T.p, T.s);
         OT_LAUNCHED();
     }
     T.psi = total;

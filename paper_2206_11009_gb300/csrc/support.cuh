@@ -52,9 +52,11 @@ Error rebuild_views(Support &S, int32_t m, int32_t n, cudaStream_t st);
 Error removal_flags(const Support &S, int32_t m, int32_t n, const double *a_s, const double *b_s,
                     double rm_p_frac, int32_t kmax, uint8_t *flag, int64_t *count, cudaStream_t st);
 
-// New support = (S without flagged) merged with the k new pairs (ni, nj) at p = s = p_new.
+// New support = (S without flagged) merged with the k new pairs (ni, nj) at p = s = p_new, or,
+// with a_cap / b_cap (device masses) given, at p = min(p_new, a_i, b_j) and s = p_new^2 / p.
 // Writes into T (capacity >= result size) and rebuilds T's views.  S and T must differ.
 Error merge_support(const Support &S, const uint8_t *flag, const int32_t *ni, const int32_t *nj,
-                    int64_t k, double p_new, int32_t m, int32_t n, Support &T, cudaStream_t st);
+                    int64_t k, double p_new, int32_t m, int32_t n, Support &T, cudaStream_t st,
+                    const double *a_cap = nullptr, const double *b_cap = nullptr);
 
 }  // namespace ot
