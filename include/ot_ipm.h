@@ -254,6 +254,47 @@ int64_t ot_kernel_launches(void);
 void ot_kernel_timing_enable(int32_t on);
 int ot_kernel_timing_read(double *ms, int64_t *count, double *work, int32_t cap);
 
+/* ---- Warm-start network (not in the paper; its conclusion names a better starting support as
+ * future work).  A convolutional network maps the two marginals of a k x k image pair to predicted
+ * dual potentials, which ot_options.warm_u / warm_v turn into extra initial pairs:
+ *   input  x (B, 2, k, k): log(a m / sum a), log(b m / sum b), NCHW, FP32
+ *   blocks l = 0..3: h <- silu(rmsnorm_c(conv3x3(h; W_l, b_l, dilation 2^l)) * g_l), 2->32->32->32->32
+ *   head:  y = conv3x3(h; W_4, b_4), 32 -> 2: the predicted (u, v) / k^2
+ * Convolutions take BF16 operands and accumulate in FP32; parameters (FP32, the flat order: per
+ * layer W[cout][cin][3][3], b[cout], then g[cout] for the normalised blocks) are the caller's at
+ * creation.  All x / y / target / gradient pointers are DEVICE pointers; one handle is one
+ * stream's state and is not thread-safe. */
+typedef struct ot_cnn ot_cnn_t;
+
+/* Number of parameters for `channels` hidden channels (only 32 is built; -1 otherwise). */
+int64_t ot_cnn_param_count(int32_t channels);
+
+/* Copy the parameters (HOST, ot_cnn_param_count entries) to a new handle on `stream` (NULL =
+ * legacy default stream).  Errors: OT_ERR_ARG, OT_ERR_UNSUPPORTED (channels != 32), OT_ERR_OOM. */
+int ot_cnn_create(int32_t channels, const float *params, void *stream, ot_cnn_t **out);
+
+/* Parameters to a HOST buffer of capacity cap (OT_ERR_BUF_TOO_SMALL if cap is short). */
+int ot_cnn_get_params(ot_cnn_t *c, float *params, int64_t cap);
+
+/* y (B, 2, k, k) = network(x); keeps the activations for ot_cnn_loss / ot_cnn_backward.  y may be
+ * NULL (the prediction stays in the handle).  1 <= batch <= 4096. */
+int ot_cnn_forward(ot_cnn_t *c, int32_t batch, int32_t k, const float *x, float *y);
+
+/* Gauge-invariant squared error of the last forward against target (B, 2, k, k) (the pair
+ * (u + t, v - t) is the same potential pair, so the best t per image is removed first); dy
+ * (device, B*2*k*k) receives its gradient with respect to y, *loss (host) its value. */
+int ot_cnn_loss(ot_cnn_t *c, const float *target, float *dy, float *loss);
+
+/* Gradients of sum(dy * y) for the last forward: grad (device, param count, overwritten) and,
+ * when dx is not NULL, with respect to x. */
+int ot_cnn_backward(ot_cnn_t *c, const float *dy, float *grad, float *dx);
+
+/* One Adam step (step >= 1 is the bias-correction count) on the FP32 parameters. */
+int ot_cnn_adam(ot_cnn_t *c, const float *grad, float lr, float beta1, float beta2, float eps, int32_t step);
+
+const char *ot_cnn_last_error(const ot_cnn_t *c);   /* NULL: the calling thread's last error  */
+void ot_cnn_destroy(ot_cnn_t *c);                    /* NULL-safe                               */
+
 /* sizeof(ot_problem), sizeof(ot_options), sizeof(ot_iter_info), sizeof(ot_result) written to
  * out[0..3] (count >= 4), so bindings can check their struct layouts.  Returns 4. */
 int ot_abi_struct_sizes(int64_t *out, int32_t count);

@@ -75,6 +75,16 @@ SIGNATURES = {
     "ot_abi_struct_sizes": (c_int32, [c_void_p, c_int32]),
     "ot_kernel_timing_enable": (None, [c_int32]),
     "ot_kernel_timing_read": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32]),
+    "ot_cnn_param_count": (c_int64, [c_int32]),
+    "ot_cnn_create": (c_int32, [c_int32, c_void_p, c_void_p, c_void_p]),
+    "ot_cnn_get_params": (c_int32, [c_void_p, c_void_p, c_int64]),
+    "ot_cnn_forward": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, c_void_p]),
+    "ot_cnn_loss": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "ot_cnn_backward": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "ot_cnn_adam": (c_int32, [c_void_p, c_void_p, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                              c_int32]),
+    "ot_cnn_last_error": (ctypes.c_char_p, [c_void_p]),
+    "ot_cnn_destroy": (None, [c_void_p]),
 }
 
 KERNEL_IDS = ["scan_hist", "scan_gather", "recheck", "pcg64", "pcg32", "ldl_numeric", "ldl_solve",
