@@ -1,9 +1,12 @@
 """Benchmark: time-to-solution of the hybrid IPM / column-generation OT solver on GB300.
 
 Workload: one 64x64 image pair (m = n = 4096, 16.8M variables), seeded log-normal Gaussian
-random-field marginals, squared-Euclidean pixel cost, solved to relative gap 1e-6 with the mixed
-precision path (FP32 pricing scan + FP64 recheck, FP32 PCG + FP64 refinement, FP64 LDL^T near
-optimality).  A step = one full solve of that instance.  The plain FP64 path is timed beside it.
+random-field marginals, squared-Euclidean pixel cost, solved to relative gap 1e-6 with the learned
+warm start (the packaged network's predicted duals, kept only when they beat the cold starting
+point) and the mixed precision path (FP32 pricing scan + FP64 recheck, FP32 dense factorisation
+preconditioning an FP64 CG).  A step = network inference + one full solve of that instance.  The
+cold mixed solve and the plain FP64 path are timed beside it, and a batch of 64 uneven instances
+(24^2 .. 96^2, autotuned launch shapes) is solved through the library's work queue.
 
 JSON line (rank 0): metric/value/unit (seconds, lower is better), e2e through the public API
 with host buffers, pricing throughput, the roofline of the dominant instrumented kernel, the
@@ -159,12 +162,42 @@ def run_reference(args, world, rank):
 
 def config_dict(args):
     return {"workload": f"{args.k}x{args.k} image pair (m=n={args.k * args.k}, {args.k ** 4} variables), "
-                        "GRF marginals, squared-Euclidean cost, rel. gap 1e-6, mixed precision",
+                        "GRF marginals, squared-Euclidean cost, rel. gap 1e-6, learned warm start + mixed precision",
             "k": args.k, "m": args.k * args.k, "n": args.k * args.k, "tol": 1e-6,
             "l2": "flushed between steps (256 MiB write)", "seed": 0}
 
 
 # ------------------------------------------------------------------------------ GPU arm
+def run_batch(torch, synth, count: int = 64, workers: int = 8):
+    """64 uneven instances (sides 24..96, seeded), autotuned launch shapes, solved through the
+    library's queue with `workers` host threads and with one; wall time around each whole batch
+    (creation, solve, destruction: every host-device copy included)."""
+    from paper_2206_11009_gb300 import autotune
+    from paper_2206_11009_gb300.api import solve_batch
+    t0 = time.perf_counter()
+    autotune.tune([32, 64, 96], verbose=False)
+    tune_s = time.perf_counter() - t0
+    sides = synth.batch_sides(count, 24, 96, seed=1234)
+    pairs = []
+    for i, kk in enumerate(sides):
+        inst = synth.image_pair(int(kk), i)
+        pairs.append((inst.a, inst.b, int(kk)))
+    out = {"instances": count, "sides": [int(x) for x in sides], "tuning_seconds": tune_s,
+           "tuned": {key: v["options"] for key, v in autotune._load().items()}}
+    for w in (workers, 1):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        res = solve_batch(pairs, workers=w, tuning=autotune.lookup, create_threads=w)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t
+        ok = sum(1 for r in res if r.status == 0)
+        out[f"workers_{w}"] = {"wall_s": wall, "instances_per_s": count / wall, "solved": ok,
+                               "mean_device_s": statistics.mean(r.seconds for r in res),
+                               "mean_iters": statistics.mean(r.iters for r in res)}
+    out["speedup_vs_one_worker"] = out["workers_1"]["wall_s"] / out[f"workers_{workers}"]["wall_s"]
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -175,6 +208,7 @@ def main():
     ap.add_argument("--scale-iters", type=int, default=60, help="oracle extrapolation (reference arm)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     args = ap.parse_args()
     world, rank, local = dist_init()
     if args.impl == "reference":
@@ -200,8 +234,12 @@ def main():
     a_np, b_np = a_pin.numpy(), b_pin.numpy()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
-    def one_solve(precision, timing=False):
-        with Solver(a_np, b_np, grid=(k, k), tol=1e-6, precision=precision) as s:
+    from paper_2206_11009_gb300 import learn
+    net = learn.WarmNet.load() if os.path.exists(learn.WEIGHTS) else None
+
+    def one_solve(precision, warm=False):
+        wd = net.predict(a_np, b_np, k) if (warm and net is not None) else None
+        with Solver(a_np, b_np, grid=(k, k), tol=1e-6, precision=precision, warm=wd) as s:
             torch.cuda.synchronize()
             r = s.solve(raise_on_error=False)
             sol = s.solution()
@@ -209,7 +247,7 @@ def main():
 
     # warm-up (untimed)
     for _ in range(args.warmup):
-        one_solve(1)
+        one_solve(1, warm=True)
     # timed: device time of each solve (CUDA events around the iterations on the solver's stream)
     clocks = Clocks()
     dev_times, e2e_times, results = [], [], []
@@ -223,7 +261,8 @@ def main():
         flush.fill_(1)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        with Solver(a_np, b_np, grid=(k, k), tol=1e-6, precision=1) as s:
+        wd = net.predict(a_np, b_np, k) if net is not None else None   # learned warm start
+        with Solver(a_np, b_np, grid=(k, k), tol=1e-6, precision=1, warm=wd) as s:
             r = s.solve(raise_on_error=False)
             I, J, P, u, v = s.solution()
         torch.cuda.synchronize()
@@ -241,11 +280,16 @@ def main():
     t_dev = max_over_ranks(statistics.mean(dev_times), world)
     t_e2e = max_over_ranks(statistics.mean(e2e_times), world)
 
-    # plain FP64 GPU path on the same instance (the comparison the metric names)
+    # plain FP64 GPU path on the same instance (the comparison the metric names), and the mixed
+    # path without the network
     plain = None
     if not args.no_plain:
         rp, _ = one_solve(0)
         plain = {"seconds": rp.seconds, "status": rp.status, "iters": rp.iters, "rel_gap": rp.rel_gap}
+    rc, _ = one_solve(1)
+    mixed_cold = {"seconds": rc.seconds, "status": rc.status, "iters": rc.iters, "rel_gap": rc.rel_gap}
+
+    batch = None if args.no_batch else run_batch(torch, synth)
 
     # pricing throughput at this size with the final duals of a solve (realistic reduced costs)
     with Solver(a_np, b_np, grid=(k, k), tol=1e-6, precision=1) as s:
@@ -289,6 +333,9 @@ def main():
         "solve": {"status": r0.status, "iters": r0.iters, "direct_iters": r0.direct_iters, "cg_iters": r0.cg_iters,
                   "rel_gap": r0.rel_gap, "r1_l1": r0.r1_l1, "obj": r0.obj, "psi": r0.psi, "max_fill_pct": r0.max_fill},
         "plain_fp64": plain,
+        "mixed_cold": mixed_cold,
+        "warm_start": {"network": net is not None, "added_pairs": r0.warm_added, "dropped": r0.warm_restarts},
+        "batch": batch,
         "pricing": {"gcols_per_s": gcols, "ms_per_call": price_ms, "pairs": pairs, "kernels": ptable},
         "kernels": table,
         "roofline": roof,

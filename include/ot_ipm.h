@@ -106,6 +106,11 @@ typedef struct {
      * min(sqrt(mu), a_i, b_j) and s = mu / p (still p s = mu, but a pair never enters with more
      * flow than its smaller mass; masses in the solver's scaling, sum(a) = m). */
     int32_t new_col_rule;
+    /* Launch shapes (chosen by the autotuner; 0 = the library's rule).  scan_rows: source rows
+     * per pricing-scan tile, 8..256.  dense32_max_n: largest n for which the mixed-precision
+     * path preconditions with the FP32 dense factorisation (at most 8192; -1: never). */
+    int32_t scan_rows;
+    int32_t dense32_max_n;
 } ot_options;
 
 /* One outer iteration (Section 3.4's commented listing). */
@@ -156,6 +161,12 @@ int ot_ipm_step(ot_ipm_t *h, ot_iter_info *info);
 
 /* Iterate to the stopping test (or max_iter) and fill *res (may be NULL). */
 int ot_ipm_solve(ot_ipm_t *h, ot_result *res);
+
+/* Solve `count` independent instances (handles from ot_ipm_create, each with its own stream)
+ * with `workers` host threads draining one queue (0 = 8); res[i] receives instance i's result and
+ * status.  Returns OT_OK when every instance succeeded, else the first failing status.  Handles
+ * must be distinct and must not be used by other threads meanwhile. */
+int ot_ipm_solve_batch(ot_ipm_t *const *handles, int32_t count, ot_result *res, int32_t workers);
 
 /* Copy the current coupling (support pairs and their flows, caller's units) and the duals u, v
  * into caller HOST buffers of capacity cap.  *nnz receives the support size even when cap is

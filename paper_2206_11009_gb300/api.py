@@ -208,3 +208,40 @@ def kernel_timing(enable: bool | None = None) -> dict:
 
 def kernel_launches() -> int:
     return int(_lib.load().ot_kernel_launches())
+
+
+def solve_batch(pairs, workers: int = 8, tuning=None, create_threads: int = 8, errors: list | None = None, **options):
+    """Solve independent instances concurrently (``ot_ipm_solve_batch``).
+
+    pairs: sequence of (a, b, side) for k x k pixel grids (side = k).  tuning: optional callable
+    (m, n) -> dict of launch options (e.g. ``autotune.lookup``).  Handles are created by
+    `create_threads` host threads (each on its own stream), solved by the library's queue of
+    `workers` threads, and destroyed afterwards.  Returns a list of Result (status per instance);
+    `errors`, when given, receives (index, message) for every failed instance.
+    """
+    from concurrent.futures import ThreadPoolExecutor
+    lib = _lib.load()
+
+    def make(pair):
+        a, b, k = pair
+        opts = dict(options)
+        if tuning is not None:
+            opts.update(tuning(k * k, k * k))
+        return Solver(a, b, grid=(k, k), **opts)
+
+    with ThreadPoolExecutor(max_workers=max(1, create_threads)) as ex:
+        solvers = list(ex.map(make, pairs))
+    try:
+        n = len(solvers)
+        hs = (ctypes.c_void_p * n)(*[s.h.value for s in solvers])
+        rs = (OtResult * n)()
+        lib.ot_ipm_solve_batch(hs, n, rs, workers)
+        if errors is not None:
+            for i, r in enumerate(rs):
+                if r.status != 0:
+                    msg = lib.ot_ipm_last_error(solvers[i].h)
+                    errors.append((i, (msg or b"").decode(errors="replace")))
+        return [Result(*[getattr(r, f) for f, _ in OtResult._fields_]) for r in rs]
+    finally:
+        for s in solvers:
+            s.close()

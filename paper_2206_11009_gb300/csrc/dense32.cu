@@ -14,12 +14,14 @@
 #include "dense32.cuh"
 
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 namespace ot {
 namespace {
 
 constexpr int kP = 64;       // panel width
+constexpr int kMaxN = 16384; // largest n (the assembly keeps a column of n 64-bit sums in shared memory)
 constexpr int kTT = 256;     // threads per CTA
 constexpr int kTile = 128;   // update tile (rows and columns)
 constexpr int kKc = 16;      // depth of one staged slice of the update tiles
@@ -462,9 +464,16 @@ Error d32_alloc(Dense32 &F, int32_t n) {
     OT_CUDA(cudaMemset(F.A, 0, big));
     OT_CUDA(cudaMemset(F.LD, 0, sizeof(float) * (size_t)F.ld * kP));
     OT_CUDA(cudaMemset(F.Linv, 0, sizeof(float) * (size_t)F.ld * kP));
-    const int smem = (int)(sizeof(unsigned long long) * n);
-    if (smem > 48 * 1024)
-        OT_CUDA(cudaFuncSetAttribute(d32_assemble_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    // one process-wide limit, the largest any n of this path needs (a per-n value set by one
+    // handle could undercut another handle's launch on another thread)
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(once, [] {
+        attr_err = cudaFuncSetAttribute(d32_assemble_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)(sizeof(unsigned long long) * kMaxN));
+    });
+    if (attr_err != cudaSuccess) return fail(OT_ERR_CUDA, cudaGetErrorString(attr_err));
+    if (n > kMaxN) return fail(OT_ERR_ARG, "dense32: n above the supported size");
     return ok();
 }
 
@@ -485,37 +494,77 @@ Error d32_assemble(Dense32 &F, const Newton &W, const Support &S, cudaStream_t s
     return ok();
 }
 
-// the factorisation's launches for this n on stream `cs` (captured into the graph)
-static Error d32_enqueue(Dense32 &F, float eps, cudaStream_t cs, int64_t *nodes) {
+// The factorisation's launch sequence for this n as an explicit CUDA graph: a chain of kernel
+// nodes built with the graph API (no stream capture, so nothing another host thread does, such as
+// a device-synchronising cudaFree, can invalidate it).
+namespace {
+struct Chain {
+    cudaGraph_t g = nullptr;
+    cudaGraphNode_t last = nullptr;
+    int64_t nodes = 0;
+    cudaError_t err = cudaSuccess;
+    template <typename... Args>
+    void kernel(void (*fn)(Args...), unsigned grid, unsigned block, Args... args) {
+        if (err != cudaSuccess) return;
+        void *ptrs[] = {(void *)&args...};
+        cudaKernelNodeParams kp = {};
+        kp.func = (void *)fn;
+        kp.gridDim = dim3(grid);
+        kp.blockDim = dim3(block);
+        kp.sharedMemBytes = 0;
+        kp.kernelParams = ptrs;
+        kp.extra = nullptr;
+        cudaGraphNode_t node;
+        err = cudaGraphAddKernelNode(&node, g, last ? &last : nullptr, last ? 1 : 0, &kp);
+        if (err == cudaSuccess) {
+            last = node;
+            ++nodes;
+        }
+    }
+    void memset0(float *dst, size_t count) {
+        if (err != cudaSuccess) return;
+        cudaMemsetParams mp = {};
+        mp.dst = dst;
+        mp.value = 0;
+        mp.elementSize = sizeof(float);
+        mp.width = count;
+        mp.height = 1;
+        mp.pitch = 0;
+        cudaGraphNode_t node;
+        err = cudaGraphAddMemsetNode(&node, g, last ? &last : nullptr, last ? 1 : 0, &mp);
+        if (err == cudaSuccess) {
+            last = node;
+            ++nodes;
+        }
+    }
+};
+}  // namespace
+
+static Error d32_build(Dense32 &F, float eps, cudaGraph_t g, int64_t *nodes) {
     const int n = F.n, ld = F.ld;
-    int64_t cnt = 0;
-    OT_CUDA(cudaMemsetAsync(F.X, 0, sizeof(float) * (size_t)ld * n, cs));
-    ++cnt;
+    Chain c;
+    c.g = g;
+    c.memset0(F.X, (size_t)ld * n);
     int np = 1;  // partial column sums feeding the next diagonal block
     for (int k = 0; k < n; k += kP) {
         const int bs = std::min(kP, n - k), base = k + bs;
-        if (k == 0) {
-            d32_colsum_kernel<<<bs, kTT, 0, cs>>>(n, ld, bs, F.A, F.csum);
-            ++cnt;
-        }
-        d32_diag_kernel<<<1, kTT, 0, cs>>>(ld, k, bs, F.A, F.D, F.d0, F.csum, np, eps, F.Linv);
-        ++cnt;
-        if (base < n) {
-            d32_panel_kernel<<<(unsigned)ceil_div(n - base, kP), kTT, 0, cs>>>(n, ld, k, F.A, F.D, F.Linv, F.LD);
-            ++cnt;
-        }
-        d32_invrow_kernel<<<(unsigned)ceil_div(base, kP), kTT, 0, cs>>>(ld, k, bs, F.X, F.Linv);
-        ++cnt;
+        if (k == 0) c.kernel(d32_colsum_kernel, (unsigned)bs, kTT, n, ld, bs, (const float *)F.A, F.csum);
+        c.kernel(d32_diag_kernel, 1u, kTT, ld, k, bs, F.A, F.D, (const float *)F.d0, (const float *)F.csum, np, eps,
+                 F.Linv);
+        if (base < n)
+            c.kernel(d32_panel_kernel, (unsigned)ceil_div(n - base, kP), kTT, n, ld, k, F.A, (const float *)F.D,
+                     (const float *)F.Linv, F.LD);
+        c.kernel(d32_invrow_kernel, (unsigned)ceil_div(base, kP), kTT, ld, k, bs, F.X, (const float *)F.Linv);
         if (base < n) {
             const int t = (int)ceil_div(n - base, kTile);
             const int ttri = t * (t + 1) / 2, tinv = t * (int)ceil_div(base, kTile);
-            d32_update_kernel<<<(unsigned)(ttri + tinv), kTT, 0, cs>>>(n, ld, k, ttri, F.A, F.X, F.LD, F.csum);
-            ++cnt;
+            c.kernel(d32_update_kernel, (unsigned)(ttri + tinv), kTT, n, ld, k, ttri, F.A, F.X, (const float *)F.LD,
+                     F.csum);
             np = t;
         }
     }
-    OT_CUDA(cudaGetLastError());
-    *nodes = cnt;
+    if (c.err != cudaSuccess) return fail(OT_ERR_CUDA, cudaGetErrorString(c.err));
+    *nodes = c.nodes;
     return ok();
 }
 
@@ -525,27 +574,18 @@ Error d32_factor(Dense32 &F, float eps, cudaStream_t st) {
             cudaGraphExecDestroy(F.graph);
             F.graph = nullptr;
         }
-        cudaStream_t cs;
-        OT_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
         cudaGraph_t g = nullptr;
-        Error e = ok();
-        if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-            e = fail(OT_ERR_CUDA, "dense32: stream capture refused");
-        } else {
-            int64_t nodes = 0;
-            e = d32_enqueue(F, eps, cs, &nodes);
-            const cudaError_t ce = cudaStreamEndCapture(cs, &g);
-            if (e.code == OT_OK && ce != cudaSuccess) e = fail(OT_ERR_CUDA, cudaGetErrorString(ce));
-            if (e.code == OT_OK && cudaGraphInstantiate(&F.graph, g, 0) != cudaSuccess) {
-                F.graph = nullptr;
-                e = fail(OT_ERR_CUDA, "dense32: graph instantiation failed");
-            }
-            F.graph_nodes = nodes;
+        OT_CUDA(cudaGraphCreate(&g, 0));
+        int64_t nodes = 0;
+        Error e = d32_build(F, eps, g, &nodes);
+        if (e.code == OT_OK && cudaGraphInstantiate(&F.graph, g, 0) != cudaSuccess) {
+            F.graph = nullptr;
+            e = fail(OT_ERR_CUDA, "dense32: graph instantiation failed");
         }
-        if (g) cudaGraphDestroy(g);
-        cudaStreamDestroy(cs);
+        cudaGraphDestroy(g);
         cudaGetLastError();
         OT_TRY(e);
+        F.graph_nodes = nodes;
         F.eps = eps;
     }
     ktimer_begin(KT_D32_FACTOR, st);

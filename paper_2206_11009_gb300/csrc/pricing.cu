@@ -436,6 +436,7 @@ Error price_topk(const PriceInput &in, int32_t *out_i, int32_t *out_j, double *o
     const int ncb = (int)ceil_div(n, kTJ);
     int TI = 64;
     while (TI > 8 && ceil_div(m, TI) * (int64_t)ncb < 4LL * sms) TI >>= 1;
+    if (in.rows > 0) TI = std::max(8, std::min(kPT, in.rows));
     const int nrb = (int)ceil_div(m, TI);
     const int64_t ntiles = (int64_t)nrb * ncb;
 

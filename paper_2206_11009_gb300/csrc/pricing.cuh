@@ -16,6 +16,7 @@ struct PriceInput {
     int32_t precision = 1;  // 1: FP32 scan + FP64 recheck; 0: FP64 scan
     int32_t origin_x = 0, origin_y = 0;  // coordinate shift applied before the FP32 form
     int32_t num_sms = 0;
+    int32_t rows = 0;       // rows per scan tile (8..256); 0: chosen from the problem size
 };
 
 struct PriceStats {

@@ -9,9 +9,13 @@
 #include "support.cuh"
 
 #include <algorithm>
+#include <atomic>
+#include <mutex>
+#include <thread>
 #include <cmath>
 #include <chrono>
 #include <cstdarg>
+#include <cstring>
 #include <vector>
 
 namespace ot {
@@ -23,7 +27,8 @@ static thread_local std::string t_last_error;
 // ---- kernel timing registry (pairs of events per kernel id, resolved when read)
 namespace {
 struct KTimer {
-    bool on = false;
+    std::atomic<bool> on{false};
+    std::mutex mu;  // solves of a batch run on several host threads
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending[KT_COUNT];
     std::vector<cudaEvent_t> open[KT_COUNT];
     double ms[KT_COUNT] = {0};
@@ -42,17 +47,22 @@ KTimer g_kt;
 
 void ktimer_begin(int id, cudaStream_t st) {
     if (!g_kt.on) return;
+    std::lock_guard<std::mutex> lk(g_kt.mu);
     cudaEvent_t e = g_kt.get();
     cudaEventRecord(e, st);
     g_kt.open[id].push_back(e);
 }
 
 void ktimer_add_work(int id, double w) {
-    if (g_kt.on) g_kt.work[id] += w;
+    if (!g_kt.on) return;
+    std::lock_guard<std::mutex> lk(g_kt.mu);
+    g_kt.work[id] += w;
 }
 
 void ktimer_end(int id, cudaStream_t st) {
-    if (!g_kt.on || g_kt.open[id].empty()) return;
+    if (!g_kt.on) return;
+    std::lock_guard<std::mutex> lk(g_kt.mu);
+    if (g_kt.open[id].empty()) return;
     cudaEvent_t e = g_kt.get();
     cudaEventRecord(e, st);
     g_kt.pending[id].push_back({g_kt.open[id].back(), e});
@@ -75,6 +85,7 @@ constexpr int kDirectCgMany = 25;
 // up to this many targets the direct branch factors S_M densely
 constexpr int kDenseMaxN = 8192;
 constexpr int kDense32MaxN = 8192;
+constexpr int kDense32LateMaxN = 16384;  // late iterations above kDenseMaxN: FP32 dense factor
 constexpr int kWarmCheck = 5;       // a warm start is judged from this iteration on ...
 constexpr int kWarmSettle = 15;     // ... up to this one
 constexpr double kWarmGrowth = 2.0; // abandoned when mu exceeds this multiple of its first value  // mixed precision: FP32 dense factor preconditions every solve
@@ -154,6 +165,7 @@ struct ot_ipm {
     bool d32_escalated = false;
     int64_t warm_added = 0;      // pairs the warm start added to the cold support
     bool warm_active = false;    // warm-started and still inside the check window
+    int device = 0;              // CUDA device the handle lives on
     int32_t warm_restarts = 0;   // warm starts abandoned for the cold one  // the FP32-preconditioned CG failed once: FP64 LDL^T from then on
     int64_t psi_min = 0;
     double max_fill = 0.0;
@@ -258,6 +270,7 @@ Error price_support(ot_ipm *h, const Support &S, int32_t kmax, int32_t *count, P
     in.precision = h->opt.precision;
     in.origin_x = h->ox; in.origin_y = h->oy;
     in.num_sms = h->num_sms;
+    in.rows = h->opt.scan_rows;
     OT_TRY(price_topk(in, h->pi, h->pj, h->pd, h->pcount, ps, h->st));
     OT_CUDA(cudaMemcpyAsync(count, h->pcount, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st));
     OT_CUDA(cudaStreamSynchronize(h->st));
@@ -412,7 +425,8 @@ Error do_step(ot_ipm *h, ot_iter_info *info) {
     // mixed precision on moderate n: the FP32 dense factorisation of this iteration's S_M
     // preconditions an FP64 CG in every solve; the FP64 LDL^T branch only takes over when that CG
     // misses its target (the switch on the support's shrinkage is for the Jacobi PCG)
-    const bool use_d32 = o.precision == 1 && o.linear_solver == 0 && n <= kDense32MaxN;
+    const int64_t d32_max = o.dense32_max_n > 0 ? o.dense32_max_n : (o.dense32_max_n < 0 ? 0 : kDense32MaxN);
+    const bool use_d32 = o.precision == 1 && o.linear_solver == 0 && n <= std::min<int64_t>(d32_max, kDense32MaxN);
     if (use_d32 && !h->d32_escalated) {
         use_direct = false;
         if (!h->d32.A) OT_TRY(d32_alloc(h->d32, n));
@@ -426,6 +440,18 @@ Error do_step(ot_ipm *h, ot_iter_info *info) {
     h->direct_cg_last = 0;
     // factor S_M once for every solve of this iteration; false when the fill is over budget
     auto enable_direct = [&]() -> Error {
+        if (n > kDenseMaxN && n <= kDense32LateMaxN) {
+            // beyond the FP64 dense size, the late iterations precondition the FP64 CG with the
+            // FP32 dense factorisation (pivots from off-diagonal sums, exact grounding)
+            if (!h->d32.A) OT_TRY(d32_alloc(h->d32, n));
+            OT_TRY(d32_assemble(h->d32, W, S, st));
+            OT_TRY(d32_factor(h->d32, (float)kPivotEps, st));
+            W.d32 = &h->d32;
+            h->max_fill = 100.0;
+            h->direct_total++;
+            inf.direct = 1;
+            return ok();
+        }
         if (n <= kDenseMaxN) {
             // moderate n: exact assembly and a dense blocked LDL^T (the exact factor is dense-ish)
             if (!h->dense.A) OT_TRY(dense_alloc(h->dense, n));
@@ -474,9 +500,10 @@ Error do_step(ot_ipm *h, ot_iter_info *info) {
         OT_TRY(newton_solve(W, S, R, tol, o.max_cg, o.precision, du, dv, ds, dp, &ss, st));
         cg += ss.cg_iters;
         if (ss.direct) h->direct_cg_last = std::max(h->direct_cg_last, ss.cg_iters);
-        if (!W.direct && o.linear_solver == 0 && !(ss.relres <= kPcgFail * tol)) {
+        const bool late_d32 = W.d32 && n > kDenseMaxN;   // already the strongest solver here
+        if (!W.direct && !late_d32 && o.linear_solver == 0 && !(ss.relres <= kPcgFail * tol)) {
             OT_TRY(enable_direct());
-            if (W.direct) {
+            if (W.direct || (W.d32 && n > kDenseMaxN)) {
                 h->direct_mode = true;
                 h->psi_min = S.psi;
                 if (W.d32) h->d32_escalated = true;
@@ -726,6 +753,7 @@ Error create_impl(const ot_problem *P, const ot_options *O, ot_ipm *h) {
 
     int dev;
     OT_CUDA(cudaGetDevice(&dev));
+    h->device = dev;
     OT_CUDA(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev));
     {
         cudaMemPool_t pool;
@@ -923,6 +951,44 @@ int ot_ipm_solve(ot_ipm_t *h, ot_result *res) {
     return rc;
 }
 
+int ot_ipm_solve_batch(ot_ipm_t *const *hs, int32_t count, ot_result *res, int32_t workers) {
+    if (!hs || !res || count < 0) {
+        set_thread_error("ot_ipm_solve_batch: invalid argument");
+        return OT_ERR_ARG;
+    }
+    for (int32_t i = 0; i < count; ++i)
+        if (!hs[i]) {
+            set_thread_error("ot_ipm_solve_batch: NULL handle");
+            return OT_ERR_ARG;
+        }
+    if (count == 0) return OT_OK;
+    const int nw = std::max(1, std::min<int32_t>(workers > 0 ? workers : 8, count));
+    std::atomic<int32_t> next{0};
+    // a queue of instances drained by nw host threads; every handle runs on its own stream, so
+    // one instance's kernels overlap another's host-side decisions and small grids share the SMs
+    auto work = [&]() {
+        for (;;) {
+            const int32_t i = next.fetch_add(1);
+            if (i >= count) break;
+            cudaSetDevice(hs[i]->device);
+            std::memset(&res[i], 0, sizeof(ot_result));
+            const int rc = ot_ipm_solve(hs[i], &res[i]);
+            res[i].status = rc;
+        }
+    };
+    std::vector<std::thread> pool;
+    pool.reserve(nw - 1);
+    for (int t = 1; t < nw; ++t) pool.emplace_back(work);
+    work();
+    for (auto &t : pool) t.join();
+    for (int32_t i = 0; i < count; ++i)
+        if (res[i].status != OT_OK) {
+            set_thread_error("ot_ipm_solve_batch: an instance failed (see its ot_result.status)");
+            return res[i].status;
+        }
+    return OT_OK;
+}
+
 int ot_ipm_get_solution(ot_ipm_t *h, int32_t *i, int32_t *j, double *p, int64_t cap, int64_t *nnz, double *u,
                         double *v) {
     if (!h || !nnz) return OT_ERR_ARG;
@@ -1042,12 +1108,14 @@ int ot_price_topk(int32_t m, int32_t n, const int32_t *sx, const int32_t *sy, co
 int64_t ot_kernel_launches(void) { return g_launches.load(); }
 
 void ot_kernel_timing_enable(int32_t on) {
+    std::lock_guard<std::mutex> lk(g_kt.mu);
     g_kt.on = on != 0;
     for (int k = 0; k < KT_COUNT; ++k) { g_kt.ms[k] = 0; g_kt.count[k] = 0; g_kt.work[k] = 0; }
 }
 
 int ot_kernel_timing_read(double *ms, int64_t *count, double *work, int32_t cap) {
     if (!ms || !count || cap < KT_COUNT) return OT_ERR_ARG;
+    std::lock_guard<std::mutex> lk(g_kt.mu);
     for (int k = 0; k < KT_COUNT; ++k) {
         for (auto &pr : g_kt.pending[k]) {
             cudaEventSynchronize(pr.second);

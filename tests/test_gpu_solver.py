@@ -119,3 +119,27 @@ def test_unbalanced_marginals_rejected():
     with pytest.raises(_lib.OTError) as e:
         Solver(a, b, grid=(4, 4))
     assert e.value.code == _lib.OT_ERR_ARG
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("k,seed,spike,prec", [(128, 0, 0.05, 1), (93, 14, 0.0, 1), (93, 14, 0.0, 0)])
+def test_large_grids_certified_by_oracle(k, seed, spike, prec):
+    """Grids above the FP64 dense size (n > 8192): the late iterations precondition with the FP32
+    dense factor.  Pinned by the oracle's certificate: the c-transform bound LB = a.u~ + b.v
+    (computed on the CPU from the returned v) <= OPT <= c.p, with the gap within 1e-6 and the
+    marginal residual within 1e-8 (caller units)."""
+    from oracle.certificate import c_transform_lower_bound, marginal_residual_l1
+    from oracle.costs import square_grid
+    from paper_2206_11009_gb300 import Solver, synth
+    inst = synth.image_pair(k, seed, spike)
+    with Solver(inst.a, inst.b, grid=(k, k), precision=prec) as s:
+        r = s.solve()
+        I, J, P, u, v = s.solution()
+    cost = square_grid(k)
+    lb = c_transform_lower_bound(cost, inst.a, inst.b, v)
+    ctp = float(cost.pairs(I, J) @ P)
+    assert r.status == 0
+    assert marginal_residual_l1(k * k, k * k, I, J, P, inst.a, inst.b) <= 1e-8
+    assert lb <= ctp * (1 + 1e-12)
+    assert (ctp - lb) / ctp <= 1e-6
+    assert abs(r.obj - ctp) <= 1e-9 * ctp
