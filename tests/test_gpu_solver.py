@@ -28,7 +28,8 @@ def _solve(inst, k, **opts):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-@pytest.mark.parametrize("k,seed,spike", [(8, 0, 0.0), (8, 2, 0.0), (16, 0, 0.0), (16, 3, 0.0), (16, 0, 0.05)])
+@pytest.mark.parametrize("k,seed,spike", [(8, 0, 0.0), (8, 2, 0.0), (16, 0, 0.0), (16, 3, 0.0), (16, 0, 0.05),
+                                          (32, 1, 0.0), (32, 0, 0.05)])
 def test_solve_reaches_exact_optimum(precision, k, seed, spike):
     """Config 1 style (tol 1e-8): |obj - OPT| / OPT <= 1e-6 and ||f - A p||_1 <= 1e-8."""
     inst = synth.image_pair(k, seed, spike_frac=spike)
