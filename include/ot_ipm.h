@@ -111,6 +111,9 @@ typedef struct {
      * path preconditions with the FP32 dense factorisation (at most 8192; -1: never). */
     int32_t scan_rows;
     int32_t dense32_max_n;
+    /* Largest n for which the direct branch factors S_M densely in FP64 (at most 8192; 0 = 8192,
+     * -1: never, the sparse LDL^T of Section 4.2 instead). */
+    int32_t dense_max_n;
 } ot_options;
 
 /* One outer iteration (Section 3.4's commented listing). */
@@ -163,9 +166,11 @@ int ot_ipm_step(ot_ipm_t *h, ot_iter_info *info);
 int ot_ipm_solve(ot_ipm_t *h, ot_result *res);
 
 /* Solve `count` independent instances (handles from ot_ipm_create, each with its own stream)
- * with `workers` host threads draining one queue (0 = 8); res[i] receives instance i's result and
- * status.  Returns OT_OK when every instance succeeded, else the first failing status.  Handles
- * must be distinct and must not be used by other threads meanwhile. */
+ * with `workers` host threads (0 = 8): instances of at least 2500^2 pairs, which fill the GPU on
+ * their own, run one at a time, largest first; the smaller ones run concurrently on the other
+ * workers.  res[i] receives instance i's result and status.  Returns OT_OK when every instance
+ * succeeded, else the first failing status.  Handles must be distinct and must not be used by
+ * other threads meanwhile. */
 int ot_ipm_solve_batch(ot_ipm_t *const *handles, int32_t count, ot_result *res, int32_t workers);
 
 /* Copy the current coupling (support pairs and their flows, caller's units) and the duals u, v

@@ -32,7 +32,8 @@ class OtOptions(ctypes.Structure):
                 ("rm_mu_frac", c_double), ("rm_p_frac", c_double), ("add_max", c_int32), ("verbose", c_int32),
                 ("stream", c_void_p), ("warm_u", c_void_p), ("warm_v", c_void_p), ("warm_count", c_int32),
                 ("warm_mode", c_int32), ("warm_i", c_void_p), ("warm_j", c_void_p), ("warm_npairs", c_int64),
-                ("new_col_rule", c_int32), ("scan_rows", c_int32), ("dense32_max_n", c_int32)]
+                ("new_col_rule", c_int32), ("scan_rows", c_int32), ("dense32_max_n", c_int32),
+                ("dense_max_n", c_int32)]
 
 
 class OtIterInfo(ctypes.Structure):

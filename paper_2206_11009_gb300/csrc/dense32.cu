@@ -86,56 +86,157 @@ d32_colsum_kernel(int n, int ld, int bs, const float *__restrict__ A, float *__r
     if (threadIdx.x == 0) csum[l] = (float)s;
 }
 
-// One CTA factors the diagonal block in shared memory with one barrier per column: every warp
-// forms the pivot itself (minus the sum of the column's remaining entries and of its below-block
-// sum, np fixed-order partials in csum[p * kP + l]; the same reduction in every warp), the column
-// stays unscaled until the end (l_ij = S_ij / d_j is formed where it is used), and the same row
-// operations applied to the identity build the inverse of the unit block.
+// One CTA factors the diagonal block in micro-panels of 8 columns.  Warp 0 eliminates a
+// micro-panel with its 64 rows in registers (lane q: rows q and q+32; shuffles only): each pivot
+// is minus the sum of the column's remaining entries plus its below-block sum (np fixed-order
+// partials in csum[p * kP + l]), and the later columns of the micro-panel and their below-block
+// sums are updated as it goes.  Then all warps apply the micro-panel's rank-8 update to the rest of
+// the block (two barriers per micro-panel instead of one per column).  Columns stay unscaled until
+// the end (l_ij = S_ij / d_j).  The inverse of the unit block is formed afterwards by 8x8 block
+// rows: X_II = L_II^-1 by warp 0, X_IJ = -X_II sum_K L_IK X_KJ by all threads.
+constexpr int kMp = 8;   // micro-panel width
+
 __global__ void __launch_bounds__(kTT)
 d32_diag_kernel(int ld, int k, int bs, float *__restrict__ A, float *__restrict__ D, const float *__restrict__ d0,
                 const float *__restrict__ csum, int np, float eps, float *__restrict__ Linv) {
     __shared__ float S[kP][kP + 1];
     __shared__ float Xs[kP][kP + 1];
     __shared__ float g[kP], thr[kP], ids[kP];
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int t = threadIdx.x; t < kP * kP; t += blockDim.x) {
         const int i = t % kP, j = t / kP;
         S[i][j] = (i > j && i < bs) ? A[(size_t)(k + j) * ld + (k + i)] : 0.f;
-        Xs[i][j] = (i == j && i < bs) ? 1.f : 0.f;
     }
-    for (int l = threadIdx.x; l < kP; l += blockDim.x) {
-        float gs = 0.f;
-        if (l < bs)
-            for (int q = 0; q < np; ++q) gs += csum[q * kP + l];
-        g[l] = gs;
-        thr[l] = l < bs ? eps * d0[k + l] : 0.f;
+    // the np partial sums per column come through shared memory (Xs as staging, kP rows at a time)
+    // with independent loads; each column then adds its partials in order
+    float gs = 0.f;
+    for (int q0 = 0; q0 < np; q0 += kP) {
+        const int nq = min(kP, np - q0);
+        for (int t = threadIdx.x; t < nq * kP; t += blockDim.x) Xs[t / kP][t % kP] = csum[(q0 + t / kP) * kP + t % kP];
+        __syncthreads();
+        if (threadIdx.x < kP && threadIdx.x < bs)
+            for (int q = 0; q < nq; ++q) gs += Xs[q][threadIdx.x];
+        __syncthreads();
+    }
+    if (threadIdx.x < kP) {
+        g[threadIdx.x] = gs;
+        thr[threadIdx.x] = threadIdx.x < bs ? eps * d0[k + threadIdx.x] : 0.f;
     }
     __syncthreads();
-    const int lane = threadIdx.x & 31, tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    for (int j = 0; j < bs; ++j) {
-        float sum = (lane > j ? S[lane][j] : 0.f) + (lane + 32 > j ? S[lane + 32][j] : 0.f);
+    for (int c0 = 0; c0 < bs; c0 += kMp) {
+        const int nc = min(kMp, bs - c0);
+        if (warp == 0) {
+            float v0[kMp], v1[kMp], gm[kMp];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-        const float d = -(sum + g[j]);
-        const bool inf = !(d > thr[j]);
-        const float id = inf ? 0.f : 1.f / d;
-        if (threadIdx.x == 0) {
-            D[k + j] = inf ? INFINITY : d;
-            ids[j] = id;
+            for (int jj = 0; jj < kMp; ++jj) {
+                v0[jj] = jj < nc ? S[lane][c0 + jj] : 0.f;
+                v1[jj] = jj < nc ? S[lane + 32][c0 + jj] : 0.f;
+                gm[jj] = jj < nc ? g[c0 + jj] : 0.f;
+            }
+#pragma unroll
+            for (int jj = 0; jj < kMp; ++jj) {
+                if (jj < nc) {
+                    const int j = c0 + jj;
+                    float sum = (lane > j ? v0[jj] : 0.f) + (lane + 32 > j ? v1[jj] : 0.f);
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(full, sum, o);
+                    const float d = -(sum + gm[jj]);
+                    const bool inf = !(d > thr[j]);
+                    const float id = inf ? 0.f : 1.f / d;
+                    const float l0 = (lane > j) ? v0[jj] * id : 0.f, l1 = (lane + 32 > j) ? v1[jj] * id : 0.f;
+#pragma unroll
+                    for (int jj2 = jj + 1; jj2 < kMp; ++jj2) {
+                        if (jj2 < nc) {
+                            const int r = c0 + jj2;   // the row whose column-j entry multiplies
+                            const float srj = __shfl_sync(full, r < 32 ? v0[jj] : v1[jj], r & 31);
+                            if (lane > r) v0[jj2] -= l0 * srj;
+                            if (lane + 32 > r) v1[jj2] -= l1 * srj;
+                            gm[jj2] -= (srj * id) * gm[jj];
+                        }
+                    }
+                    if (inf) {
+                        v0[jj] = 0.f;
+                        v1[jj] = 0.f;
+                    }
+                    if (lane == 0) {
+                        D[k + j] = inf ? INFINITY : d;
+                        ids[j] = id;
+                    }
+                }
+            }
+#pragma unroll
+            for (int jj = 0; jj < kMp; ++jj) {
+                if (jj < nc) {
+                    S[lane][c0 + jj] = v0[jj];
+                    S[lane + 32][c0 + jj] = v1[jj];
+                    if (lane == 0) g[c0 + jj] = gm[jj];
+                }
+            }
         }
-        if (!inf) {
-            const float gj = g[j];
-            for (int i = j + 1 + ty; i < bs; i += 16) {
-                const float lij = S[i][j] * id;
-                for (int l = j + 1 + tx; l < i; l += 16) S[i][l] -= lij * S[l][j];
-                for (int c = tx; c <= j; c += 16) Xs[i][c] -= lij * Xs[j][c];
-                if (tx == 0) g[i] -= lij * gj;
+        __syncthreads();
+        // rank-nc update of the columns l >= c0 + nc: S[i][l] -= sum_jj S[i][c] S[l][c] / d_c (i > l),
+        // and of their below-block sums: g[l] -= sum_jj (S[l][c] / d_c) g[c]
+        const int lo = c0 + nc;
+        const int w = bs - lo;
+        if (w > 0) {
+            for (int t = threadIdx.x; t < w * w; t += blockDim.x) {
+                const int i = lo + t / w, l = lo + t % w;
+                if (l < i) {
+                    float acc = 0.f;
+#pragma unroll
+                    for (int jj = 0; jj < kMp; ++jj)
+                        if (jj < nc) acc += S[i][c0 + jj] * (S[l][c0 + jj] * ids[c0 + jj]);
+                    S[i][l] -= acc;
+                }
+            }
+            for (int l = lo + threadIdx.x; l < bs; l += blockDim.x) {
+                float acc = 0.f;
+#pragma unroll
+                for (int jj = 0; jj < kMp; ++jj)
+                    if (jj < nc) acc += (S[l][c0 + jj] * ids[c0 + jj]) * g[c0 + jj];
+                g[l] -= acc;
+            }
+        }
+        __syncthreads();
+    }
+    // scale the columns: L = S D^-1 (grounded columns are zero); back to A
+    for (int t = threadIdx.x; t < kP * kP; t += blockDim.x) {
+        const int i = t % kP, j = t / kP;
+        const float l = (i > j && i < bs) ? S[i][j] * ids[j] : 0.f;
+        S[i][j] = l;
+        Xs[i][j] = 0.f;
+        if (i > j && i < bs) A[(size_t)(k + j) * ld + (k + i)] = l;
+    }
+    __syncthreads();
+    // X = L^-1 by 8x8 block rows
+    for (int I = 0; I * kMp < bs; ++I) {
+        const int r0 = I * kMp;
+        // T[r][c] = sum_{k in [c, r0)} L[r][k] X[k][c] for the block's rows r and columns c < r0,
+        // stored negated in Xs (rows r0..r0+7 are still zero)
+        for (int t = threadIdx.x; t < kMp * r0; t += blockDim.x) {
+            const int r = r0 + t / r0, c = t % r0;
+            if (r < bs) {
+                float acc = 0.f;
+                for (int kk = c; kk < r0; ++kk) acc += S[r][kk] * Xs[kk][c];
+                Xs[r][c] = -acc;
+            }
+        }
+        __syncthreads();
+        // rows of the block: x_r = e_r - sum_{k in [r0, r)} L[r][k] x_k, applied to the block's
+        // columns c < r0 (entries from T) and to the identity part c in [r0, r]; one thread per
+        // column, the 8 rows in order
+        for (int c = threadIdx.x; c < r0 + kMp && c < bs; c += blockDim.x) {
+            for (int r = max(r0, c); r < r0 + kMp && r < bs; ++r) {
+                float x = (c < r0) ? Xs[r][c] : (r == c ? 1.f : 0.f);
+                for (int kk = max(r0, c); kk < r; ++kk) x -= S[r][kk] * Xs[kk][c];
+                Xs[r][c] = x;
             }
         }
         __syncthreads();
     }
     for (int t = threadIdx.x; t < bs * bs; t += blockDim.x) {
         const int i = t % bs, j = t / bs;
-        if (i > j) A[(size_t)(k + j) * ld + (k + i)] = S[i][j] * ids[j];
         Linv[(size_t)j * ld + (k + i)] = Xs[i][j];
     }
 }

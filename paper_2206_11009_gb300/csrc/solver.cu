@@ -86,6 +86,7 @@ constexpr int kDirectCgMany = 25;
 constexpr int kDenseMaxN = 8192;
 constexpr int kDense32MaxN = 8192;
 constexpr int kDense32LateMaxN = 16384;  // late iterations above kDenseMaxN: FP32 dense factor
+constexpr int64_t kBatchLargeMN = 2500LL * 2500;  // a batch instance this large runs alone
 constexpr int kWarmCheck = 5;       // a warm start is judged from this iteration on ...
 constexpr int kWarmSettle = 15;     // ... up to this one
 constexpr double kWarmGrowth = 2.0; // abandoned when mu exceeds this multiple of its first value  // mixed precision: FP32 dense factor preconditions every solve
@@ -439,8 +440,10 @@ Error do_step(ot_ipm *h, ot_iter_info *info) {
     const int direct_cg_prev = h->direct_cg_last;
     h->direct_cg_last = 0;
     // factor S_M once for every solve of this iteration; false when the fill is over budget
+    const int64_t dense_max = o.dense_max_n > 0 ? std::min<int64_t>(o.dense_max_n, kDenseMaxN)
+                                                : (o.dense_max_n < 0 ? 0 : kDenseMaxN);
     auto enable_direct = [&]() -> Error {
-        if (n > kDenseMaxN && n <= kDense32LateMaxN) {
+        if (n > kDenseMaxN && n <= kDense32LateMaxN && o.dense_max_n >= 0) {
             // beyond the FP64 dense size, the late iterations precondition the FP64 CG with the
             // FP32 dense factorisation (pivots from off-diagonal sums, exact grounding)
             if (!h->d32.A) OT_TRY(d32_alloc(h->d32, n));
@@ -452,7 +455,7 @@ Error do_step(ot_ipm *h, ot_iter_info *info) {
             inf.direct = 1;
             return ok();
         }
-        if (n <= kDenseMaxN) {
+        if (n <= dense_max) {
             // moderate n: exact assembly and a dense blocked LDL^T (the exact factor is dense-ish)
             if (!h->dense.A) OT_TRY(dense_alloc(h->dense, n));
             bool changed = false;
@@ -963,23 +966,44 @@ int ot_ipm_solve_batch(ot_ipm_t *const *hs, int32_t count, ot_result *res, int32
         }
     if (count == 0) return OT_OK;
     const int nw = std::max(1, std::min<int32_t>(workers > 0 ? workers : 8, count));
-    std::atomic<int32_t> next{0};
-    // a queue of instances drained by nw host threads; every handle runs on its own stream, so
-    // one instance's kernels overlap another's host-side decisions and small grids share the SMs
-    auto work = [&]() {
+    // Two queues, largest first.  An instance of at least kBatchLargeMN pairs keeps the GPU busy
+    // on its own (its dense factorisations fill every SM), and two of them at once only contend,
+    // so they run one at a time on worker 0; the others run concurrently on the remaining workers,
+    // which worker 0 joins once the large queue is empty.
+    std::vector<int32_t> big, small;
+    for (int32_t i = 0; i < count; ++i)
+        ((int64_t)hs[i]->m * hs[i]->n >= kBatchLargeMN ? big : small).push_back(i);
+    auto by_size = [&](int32_t x, int32_t y) {
+        return (int64_t)hs[x]->m * hs[x]->n > (int64_t)hs[y]->m * hs[y]->n;
+    };
+    std::sort(big.begin(), big.end(), by_size);
+    std::sort(small.begin(), small.end(), by_size);
+    if (nw == 1) {
+        big.insert(big.end(), small.begin(), small.end());
+        small.clear();
+    }
+    std::atomic<size_t> next_big{0}, next_small{0};
+    auto run = [&](int32_t i) {
+        cudaSetDevice(hs[i]->device);
+        std::memset(&res[i], 0, sizeof(ot_result));
+        res[i].status = ot_ipm_solve(hs[i], &res[i]);
+    };
+    auto drain_small = [&]() {
         for (;;) {
-            const int32_t i = next.fetch_add(1);
-            if (i >= count) break;
-            cudaSetDevice(hs[i]->device);
-            std::memset(&res[i], 0, sizeof(ot_result));
-            const int rc = ot_ipm_solve(hs[i], &res[i]);
-            res[i].status = rc;
+            const size_t q = next_small.fetch_add(1);
+            if (q >= small.size()) break;
+            run(small[q]);
         }
     };
     std::vector<std::thread> pool;
     pool.reserve(nw - 1);
-    for (int t = 1; t < nw; ++t) pool.emplace_back(work);
-    work();
+    for (int t = 1; t < nw; ++t) pool.emplace_back(drain_small);
+    for (;;) {
+        const size_t q = next_big.fetch_add(1);
+        if (q >= big.size()) break;
+        run(big[q]);
+    }
+    drain_small();
     for (auto &t : pool) t.join();
     for (int32_t i = 0; i < count; ++i)
         if (res[i].status != OT_OK) {

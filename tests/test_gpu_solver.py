@@ -59,6 +59,11 @@ def test_config2_64x64(precision):
     assert r.status == 0, r
     assert abs(r.obj - opt) <= 1e-6 * opt
     assert r.r1_l1 <= 1e-8
+    if precision == 1:
+        # the FP32 dense factor preconditions every solve well enough that no iteration needs the
+        # FP64 factorisation and the refinement CG stays short (a few iterations per solve)
+        assert r.direct_iters == 0
+        assert r.cg_iters <= 60 * r.iters
 
 
 def test_one_iteration_matches_oracle():
