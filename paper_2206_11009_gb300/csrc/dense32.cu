@@ -13,6 +13,7 @@
 // The sequence depends on n only, so it is captured once into a CUDA graph.
 #include "dense32.cuh"
 
+#include <algorithm>
 #include <cmath>
 #include <mutex>
 #include <vector>
@@ -336,30 +337,53 @@ d32_invrow_kernel(int ld, int k, int bs, float *__restrict__ X, const float *__r
 }
 
 // the two rank-64 updates of panel k, 128x128 tiles, 8x8 per thread
+// Tile sets of one panel's update (t row tiles of 128 below the panel, tcn column tiles of the
+// inverse's rectangle): part 1 = what the next panel needs first (trailing tiles of the first
+// column tile, inverse tiles of the first row tile), part 2 = the rest.
+__device__ __forceinline__ void tri_decode(int idx, int &ti, int &tj) {
+    ti = (int)((sqrt(8.0 * idx + 1.0) - 1.0) * 0.5);
+    while ((ti + 1) * (ti + 2) / 2 <= idx) ++ti;
+    while (ti * (ti + 1) / 2 > idx) --ti;
+    tj = idx - ti * (ti + 1) / 2;
+}
+
 __global__ void __launch_bounds__(kTT, 2)
-d32_update_kernel(int n, int ld, int k, int ttri, float *__restrict__ A, float *__restrict__ X,
+d32_update_kernel(int n, int ld, int k, int part, float *__restrict__ A, float *__restrict__ X,
                   const float *__restrict__ LD, float *__restrict__ csum) {
     __shared__ __align__(16) float As[kKc][kTile];
     __shared__ __align__(16) float Bs[kKc][kTile];
     const int base = k + kP;
-    int idx = blockIdx.x;
-    const bool tri = idx < ttri;
-    int r0, c0, climit, tile_i = 0, tile_j = 0;
+    const int t = (n - base + kTile - 1) / kTile;
+    const int tcn = (base + kTile - 1) / kTile;
+    const int idx = blockIdx.x;
+    bool tri;
+    int ti, tj;
+    if (part == 1) {
+        tri = idx < t;
+        ti = tri ? idx : 0;
+        tj = tri ? 0 : idx - t;
+    } else {
+        const int ntri2 = t * (t - 1) / 2;   // trailing tiles with tj >= 1
+        tri = idx < ntri2;
+        if (tri) {
+            tri_decode(idx, ti, tj);
+            ++ti;
+            ++tj;
+        } else {
+            const int q = idx - ntri2;       // inverse tiles with ti >= 1
+            ti = 1 + q / tcn;
+            tj = q % tcn;
+        }
+    }
+    int r0, c0, climit;
+    const int tile_i = ti, tile_j = tj;
     if (tri) {
-        int ti = (int)((sqrt(8.0 * idx + 1.0) - 1.0) * 0.5);
-        while ((ti + 1) * (ti + 2) / 2 <= idx) ++ti;
-        while (ti * (ti + 1) / 2 > idx) --ti;
-        const int tj = idx - ti * (ti + 1) / 2;
         r0 = base + ti * kTile;
         c0 = base + tj * kTile;
         climit = n;
-        tile_i = ti;
-        tile_j = tj;
     } else {
-        idx -= ttri;
-        const int tcn = (base + kTile - 1) / kTile;
-        r0 = base + (idx / tcn) * kTile;
-        c0 = (idx % tcn) * kTile;
+        r0 = base + ti * kTile;
+        c0 = tj * kTile;
         climit = base;
     }
     // A operand (l, r) = Pa[l * ld + r]; B operand (l, c) = Pb[l * ld + c] (trailing) or
@@ -554,7 +578,7 @@ Error d32_alloc(Dense32 &F, int32_t n) {
     const size_t big = sizeof(float) * (size_t)F.ld * n;
     OT_CUDA(cudaMalloc((void **)&F.A, big));
     OT_CUDA(cudaMalloc((void **)&F.X, big));
-    OT_CUDA(cudaMalloc((void **)&F.LD, sizeof(float) * (size_t)F.ld * kP));
+    OT_CUDA(cudaMalloc((void **)&F.LD, 2 * sizeof(float) * (size_t)F.ld * kP));
     OT_CUDA(cudaMalloc((void **)&F.Linv, sizeof(float) * (size_t)F.ld * kP));
     OT_CUDA(cudaMalloc((void **)&F.D, sizeof(float) * n));
     OT_CUDA(cudaMalloc((void **)&F.d0, sizeof(float) * n));
@@ -563,7 +587,7 @@ Error d32_alloc(Dense32 &F, int32_t n) {
     OT_CUDA(cudaMalloc((void **)&F.part, sizeof(float) * (size_t)F.ld * (size_t)ceil_div(n, kFc)));
     // lower bound of the unwritten upper parts, so that nothing uninitialised is ever read
     OT_CUDA(cudaMemset(F.A, 0, big));
-    OT_CUDA(cudaMemset(F.LD, 0, sizeof(float) * (size_t)F.ld * kP));
+    OT_CUDA(cudaMemset(F.LD, 0, 2 * sizeof(float) * (size_t)F.ld * kP));
     OT_CUDA(cudaMemset(F.Linv, 0, sizeof(float) * (size_t)F.ld * kP));
     // one process-wide limit, the largest any n of this path needs (a per-n value set by one
     // handle could undercut another handle's launch on another thread)
@@ -599,14 +623,15 @@ Error d32_assemble(Dense32 &F, const Newton &W, const Support &S, cudaStream_t s
 // nodes built with the graph API (no stream capture, so nothing another host thread does, such as
 // a device-synchronising cudaFree, can invalidate it).
 namespace {
-struct Chain {
+struct Dag {
     cudaGraph_t g = nullptr;
-    cudaGraphNode_t last = nullptr;
     int64_t nodes = 0;
     cudaError_t err = cudaSuccess;
     template <typename... Args>
-    void kernel(void (*fn)(Args...), unsigned grid, unsigned block, Args... args) {
-        if (err != cudaSuccess) return;
+    cudaGraphNode_t kernel(std::vector<cudaGraphNode_t> deps, void (*fn)(Args...), unsigned grid, unsigned block,
+                           Args... args) {
+        cudaGraphNode_t node = nullptr;
+        if (err != cudaSuccess) return node;
         void *ptrs[] = {(void *)&args...};
         cudaKernelNodeParams kp = {};
         kp.func = (void *)fn;
@@ -615,15 +640,14 @@ struct Chain {
         kp.sharedMemBytes = 0;
         kp.kernelParams = ptrs;
         kp.extra = nullptr;
-        cudaGraphNode_t node;
-        err = cudaGraphAddKernelNode(&node, g, last ? &last : nullptr, last ? 1 : 0, &kp);
-        if (err == cudaSuccess) {
-            last = node;
-            ++nodes;
-        }
+        deps.erase(std::remove(deps.begin(), deps.end(), nullptr), deps.end());
+        err = cudaGraphAddKernelNode(&node, g, deps.data(), deps.size(), &kp);
+        if (err == cudaSuccess) ++nodes;
+        return node;
     }
-    void memset0(float *dst, size_t count) {
-        if (err != cudaSuccess) return;
+    cudaGraphNode_t memset0(float *dst, size_t count, std::vector<cudaGraphNode_t> deps) {
+        cudaGraphNode_t node = nullptr;
+        if (err != cudaSuccess) return node;
         cudaMemsetParams mp = {};
         mp.dst = dst;
         mp.value = 0;
@@ -631,37 +655,53 @@ struct Chain {
         mp.width = count;
         mp.height = 1;
         mp.pitch = 0;
-        cudaGraphNode_t node;
-        err = cudaGraphAddMemsetNode(&node, g, last ? &last : nullptr, last ? 1 : 0, &mp);
-        if (err == cudaSuccess) {
-            last = node;
-            ++nodes;
-        }
+        err = cudaGraphAddMemsetNode(&node, g, deps.data(), deps.size(), &mp);
+        if (err == cudaSuccess) ++nodes;
+        return node;
+    }
+    cudaGraphNode_t join(std::vector<cudaGraphNode_t> deps) {
+        cudaGraphNode_t node = nullptr;
+        if (err != cudaSuccess) return node;
+        deps.erase(std::remove(deps.begin(), deps.end(), nullptr), deps.end());
+        err = cudaGraphAddEmptyNode(&node, g, deps.data(), deps.size());
+        return node;
     }
 };
 }  // namespace
 
 static Error d32_build(Dense32 &F, float eps, cudaGraph_t g, int64_t *nodes) {
     const int n = F.n, ld = F.ld;
-    Chain c;
+    Dag c;
     c.g = g;
-    c.memset0(F.X, (size_t)ld * n);
+    cudaGraphNode_t prev = c.memset0(F.X, (size_t)ld * n, {});
+    cudaGraphNode_t u1 = nullptr, u2 = nullptr;   // the previous panel's two update parts
     int np = 1;  // partial column sums feeding the next diagonal block
-    for (int k = 0; k < n; k += kP) {
+    for (int k = 0, p = 0; k < n; k += kP, ++p) {
         const int bs = std::min(kP, n - k), base = k + bs;
-        if (k == 0) c.kernel(d32_colsum_kernel, (unsigned)bs, kTT, n, ld, bs, (const float *)F.A, F.csum);
-        c.kernel(d32_diag_kernel, 1u, kTT, ld, k, bs, F.A, F.D, (const float *)F.d0, (const float *)F.csum, np, eps,
-                 F.Linv);
+        float *LDp = F.LD + (size_t)(p & 1) * ld * kP;   // double-buffered: the rest of the previous
+                                                          // update may still read the other half
+        if (k == 0) prev = c.kernel({prev}, d32_colsum_kernel, (unsigned)bs, kTT, n, ld, bs, (const float *)F.A, F.csum);
+        const cudaGraphNode_t dg = c.kernel({k == 0 ? prev : u1}, d32_diag_kernel, 1u, kTT, ld, k, bs, F.A, F.D,
+                                            (const float *)F.d0, (const float *)F.csum, np, eps, F.Linv);
+        std::vector<cudaGraphNode_t> ready;
         if (base < n)
-            c.kernel(d32_panel_kernel, (unsigned)ceil_div(n - base, kP), kTT, n, ld, k, F.A, (const float *)F.D,
-                     (const float *)F.Linv, F.LD);
-        c.kernel(d32_invrow_kernel, (unsigned)ceil_div(base, kP), kTT, ld, k, bs, F.X, (const float *)F.Linv);
+            ready.push_back(c.kernel({dg}, d32_panel_kernel, (unsigned)ceil_div(n - base, kP), kTT, n, ld, k, F.A,
+                                     (const float *)F.D, (const float *)F.Linv, LDp));
+        ready.push_back(c.kernel({dg}, d32_invrow_kernel, (unsigned)ceil_div(base, kP), kTT, ld, k, bs, F.X,
+                                 (const float *)F.Linv));
+        if (u2) ready.push_back(u2);
         if (base < n) {
-            const int t = (int)ceil_div(n - base, kTile);
-            const int ttri = t * (t + 1) / 2, tinv = t * (int)ceil_div(base, kTile);
-            c.kernel(d32_update_kernel, (unsigned)(ttri + tinv), kTT, n, ld, k, ttri, F.A, F.X, (const float *)F.LD,
-                     F.csum);
+            const int t = (int)ceil_div(n - base, kTile), tcn = (int)ceil_div(base, kTile);
+            u1 = c.kernel(ready, d32_update_kernel, (unsigned)(t + tcn), kTT, n, ld, k, 1, F.A, F.X,
+                          (const float *)LDp, F.csum);
+            const int n2 = t * (t - 1) / 2 + (t - 1) * tcn;
+            u2 = n2 > 0 ? c.kernel(ready, d32_update_kernel, (unsigned)n2, kTT, n, ld, k, 2, F.A, F.X,
+                                   (const float *)LDp, F.csum)
+                        : nullptr;
             np = t;
+        } else {
+            // the last panel: join everything so the graph ends after all writes
+            prev = c.join(ready);
         }
     }
     if (c.err != cudaSuccess) return fail(OT_ERR_CUDA, cudaGetErrorString(c.err));
