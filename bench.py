@@ -103,13 +103,20 @@ def barrier(world):
 
 
 def max_over_ranks(x: float, world: int) -> float:
+    """The slowest rank's value (replicas: each rank times its own instance)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def rank_instance_seed(rank: int) -> int:
+    """Seed of the instance a rank solves: replicas of the same workload on different data."""
+    return rank
 
 
 # ------------------------------------------------------------------------------ oracle arm
@@ -228,7 +235,7 @@ def main():
     from paper_2206_11009_gb300 import Solver, kernel_launches, kernel_timing, price_topk, synth
 
     k = args.k
-    inst = synth.image_pair(k, rank)          # each rank: its own instance (replicas, weak scaling)
+    inst = synth.image_pair(k, rank_instance_seed(rank))   # each rank: its own instance (replicas, weak scaling)
     a_pin = torch.from_numpy(inst.a).pin_memory()
     b_pin = torch.from_numpy(inst.b).pin_memory()
     a_np, b_np = a_pin.numpy(), b_pin.numpy()
