@@ -495,7 +495,7 @@ d32_update_kernel(int n, int ld, int k, int part, float *__restrict__ A, float *
 
 // partial sums of y = X r: CTA (rb, cb) covers rows [rb*512, +512) (four per thread, float4 loads)
 // and columns [cb*64, +64) for the lower-triangle tiles only (rows beyond n read the zero padding)
-constexpr int kFr = 512, kFc = 64;
+constexpr int kFr = 256, kFc = 64;
 __global__ void __launch_bounds__(kFr / 4)
 d32_fwd_kernel(int n, int ld, int ncb, const float *__restrict__ X, const double *__restrict__ r,
                float *__restrict__ part) {

@@ -1223,16 +1223,17 @@ static Error solve_direct(Newton &W, const Support &S, double tol, int max_cg, d
         Finish f{2, {SC_RZ0, SC_NORM_B}, {(int)gn, (int)gn}, {0, 0}};
         OT_TRY(finish(f, W, st));
     }
-    OT_TRY(read_scalars(W, hs, st));
-    const double bb = hs[SC_NORM_B];
-    double rr = bb;
+    // |rhs|^2 and r.z reach the host with the first iteration's scalars (no separate round trip);
+    // with r.z <= 0 that iteration's step is a no-op
+    double bb = -1.0;
+    double rr = 0.0;
     int it = 0;
     // an accurate FP32 factor gains several digits per iteration; one that needs many more has
     // met a matrix beyond FP32 and hands the system to the FP64 factorisation
     const int cap = C ? max_cg : std::min(max_cg, kD32MaxCg);
     // alpha and beta stay on the device; the host reads p.q and r.r of each iteration while the
     // GPU already applies the preconditioner for the next one (wasted only at the last iteration)
-    if (bb > 0 && hs[SC_RZ0] > 0) {
+    {
         // lanes per row / column for the FP64 products: about the average row length, <= 16
         const double avg = (double)S.psi / (double)std::max(1, std::min(W.m, W.n));
         const int G = avg >= 12 ? 16 : (avg >= 6 ? 8 : 4);
@@ -1281,6 +1282,11 @@ static Error solve_direct(Newton &W, const Support &S, double tol, int max_cg, d
             }
             OT_CUDA(cudaEventSynchronize(W.ev_scal2[it & 1]));
             const double *h = W.hscal + (it & 1) * SC_COUNT;
+            if (bb < 0) {
+                bb = h[SC_NORM_B];
+                rr = bb;
+                if (!(bb > 0) || !(h[SC_RZ0] > 0)) break;
+            }
             const double pq = h[SC_SUM_A];
             if (!(pq > 0)) break;  // breakdown: this step was a no-op
             rr = h[SC_NORM_A];
@@ -1288,6 +1294,11 @@ static Error solve_direct(Newton &W, const Support &S, double tol, int max_cg, d
             if (rr <= target * target * bb) break;
         }
         // an iteration still queued ahead completes before the copy below (stream order)
+    }
+    if (bb < 0) {  // no iteration ran (max_cg 0): the residual is the right-hand side
+        OT_TRY(read_scalars(W, hs, st));
+        bb = hs[SC_NORM_B];
+        rr = bb;
     }
     copy_kernel<<<gn, kT, 0, st>>>(W.n, x, dv);
     OT_LAUNCHED();
@@ -1440,6 +1451,10 @@ Error schur_setup(Newton &W, const Support &S, cudaStream_t st) {
     OT_LAUNCHED();
     Finish f{1, {SC_ONECOMP}, {(int)gn}, {0}};
     OT_TRY(finish(f, W, st));
+    // the support graph is fixed for the iteration: every solve's projection reads this once
+    double hs[SC_COUNT];
+    OT_TRY(read_scalars(W, hs, st));
+    W.onecomp = hs[SC_ONECOMP] == 0.0;
     return ok();
 }
 
@@ -1475,10 +1490,7 @@ Error newton_solve(Newton &W, const Support &S, const Rhs &R, double cg_tol, int
     rhs_kernel<<<gn, kT, 0, st>>>(W.n, S.col_ptr, S.col_perm, S.col_row, W.g, W.theta_col, W.Minv, W.beta1, R.r1b,
                                   W.beta2, W.rhs, W.part);
     OT_LAUNCHED();
-    double hs[SC_COUNT];
-    OT_CUDA(cudaMemcpyAsync(hs, W.scal, sizeof(hs), cudaMemcpyDeviceToHost, st));
-    OT_CUDA(cudaStreamSynchronize(st));
-    const bool one = hs[SC_ONECOMP] == 0.0;
+    const bool one = W.onecomp;
     OT_TRY(project(W, W.rhs, one, st));
 
     SolveStats ss;

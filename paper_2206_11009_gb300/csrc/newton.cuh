@@ -50,6 +50,7 @@ struct Newton {
     unsigned *bar = nullptr;
     int *err = nullptr;
     int pcg_grid = 0;
+    bool onecomp = true;       // the support graph is connected (set by schur_setup)
     int verbose = 0;           // >= 3: one line per PCG launch (support size, iterations, device ms)
     double last_pcg_ms = 0.0;
     double *pcg_pb = nullptr;     // second direction buffer of the PCG (fp64 / fp32)
