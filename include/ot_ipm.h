@@ -192,6 +192,28 @@ int ot_ipm_set_state(ot_ipm_t *h, const int32_t *i, const int32_t *j, const doub
                      const double *s, int64_t psi, const double *u, const double *v,
                      int32_t reset_mu0);
 
+
+/* Linear solvers of the Newton system (ot_ipm_newton_direction). */
+enum {
+    OT_LS_PCG64 = 0,    /* Jacobi PCG in FP64 (Section 4.2, matrix-free S_M)                      */
+    OT_LS_MIXED = 1,    /* Jacobi PCG in FP32 inside FP64 iterative refinement                     */
+    OT_LS_DENSE32 = 2,  /* FP64 CG preconditioned by the FP32 dense LDL^T of S_M (n <= 16384)      */
+    OT_LS_DENSE64 = 3,  /* FP64 dense LDL^T with the infinite-pivot rule (Section 4.3, n <= 8192)  */
+    OT_LS_SPARSE = 4    /* FP64 sparse LDL^T, fill-reducing order, no dropping (Section 4.3)       */
+};
+
+/* The predictor direction (du, dv, dp, ds) of the normal equations (Section 3, eq. redsystem with
+ * r3 = -P S e; Schur complement S_M of Section 4) at the handle's current iterate -- after
+ * ot_ipm_set_state or any step -- computed with the chosen linear solver.  Iterative solvers stop
+ * at ||S_M dv - rhs|| <= cg_tol ||rhs|| or after max_cg iterations; the direct ones refine with
+ * FP64 CG to the same tolerance.  dv is returned with mean zero on every connected component of
+ * the support graph.  Outputs are HOST buffers owned by the caller (any may be NULL): du (m),
+ * dv (n), dp and ds (cap >= the support size, entries in ot_ipm_get_state order).  The iterate
+ * and the support are not changed.  Errors: OT_ERR_ARG, OT_ERR_BUF_TOO_SMALL, OT_ERR_UNSUPPORTED
+ * (n above the dense factor's limit, sparse fill over budget), OT_ERR_CUDA, OT_ERR_TIMEOUT. */
+int ot_ipm_newton_direction(ot_ipm_t *h, int32_t solver, double cg_tol, int32_t max_cg, double *du, double *dv,
+                            double *dp, double *ds, int64_t cap, int32_t *cg_iters);
+
 /* Internal scale factor sigma_f = m / sum(a) (masses are multiplied by it). */
 double ot_ipm_mass_scale(const ot_ipm_t *h);
 

@@ -60,6 +60,8 @@ SIGNATURES = {
                                       c_void_p, c_void_p]),
     "ot_ipm_get_state": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int64, POINTER(c_int64),
                                    c_void_p, c_void_p]),
+    "ot_ipm_newton_direction": (c_int32, [c_void_p, c_int32, c_double, c_int32, c_void_p, c_void_p, c_void_p,
+                                          c_void_p, c_int64, POINTER(c_int32)]),
     "ot_ipm_set_state": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p,
                                    c_int32]),
     "ot_ipm_mass_scale": (c_double, [c_void_p]),

@@ -146,6 +146,20 @@ class Solver:
         check(self._lib.ot_ipm_set_state(self.h, _ptr(arrs[0]), _ptr(arrs[1]), _ptr(arrs[2]), _ptr(arrs[3]),
                                          len(arrs[0]), _ptr(arrs[4]), _ptr(arrs[5]), int(reset_mu0)), self.h)
 
+    LINEAR_SOLVERS = {"pcg64": 0, "mixed": 1, "dense32": 2, "dense64": 3, "sparse": 4}
+
+    def newton_direction(self, solver: str = "pcg64", cg_tol: float = 1e-12, max_cg: int = 20000):
+        """Predictor direction (du, dv, dp, ds) at the current iterate by one linear solver
+        (ot_ipm_newton_direction); returns the four arrays and the CG iteration count."""
+        psi = ctypes.c_int64(0)
+        self._lib.ot_ipm_get_state(self.h, None, None, None, None, 0, ctypes.byref(psi), None, None)
+        k = psi.value
+        du, dv, dp, ds = np.zeros(self.m), np.zeros(self.n), np.zeros(k), np.zeros(k)
+        its = ctypes.c_int32(0)
+        check(self._lib.ot_ipm_newton_direction(self.h, self.LINEAR_SOLVERS[solver], cg_tol, max_cg, _ptr(du),
+                                                _ptr(dv), _ptr(dp), _ptr(ds), k, ctypes.byref(its)), self.h)
+        return du, dv, dp, ds, its.value
+
     @property
     def mass_scale(self) -> float:
         return self._lib.ot_ipm_mass_scale(self.h)

@@ -96,12 +96,14 @@ d32_colsum_kernel(int n, int ld, int bs, const float *__restrict__ A, float *__r
 // the end (l_ij = S_ij / d_j).  The inverse of the unit block is formed afterwards by 8x8 block
 // rows: X_II = L_II^-1 by warp 0, X_IJ = -X_II sum_K L_IK X_KJ by all threads.
 constexpr int kMp = 8;   // micro-panel width
+static_assert(kTT / 32 == kP / kMp && kTT == 4 * kP, "one warp per 8x8 diagonal block, 8b threads per b-pair");
 
 __global__ void __launch_bounds__(kTT)
 d32_diag_kernel(int ld, int k, int bs, float *__restrict__ A, float *__restrict__ D, const float *__restrict__ d0,
                 const float *__restrict__ csum, int np, float eps, float *__restrict__ Linv) {
     __shared__ float S[kP][kP + 1];
     __shared__ float Xs[kP][kP + 1];
+    __shared__ float Ts[kP / 2][kP / 2 + 1];
     __shared__ float g[kP], thr[kP], ids[kP];
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -181,22 +183,25 @@ d32_diag_kernel(int ld, int k, int bs, float *__restrict__ A, float *__restrict_
         const int lo = c0 + nc;
         const int w = bs - lo;
         if (w > 0) {
-            for (int t = threadIdx.x; t < w * w; t += blockDim.x) {
-                const int i = lo + t / w, l = lo + t % w;
-                if (l < i) {
+            // thread: column l = lo + (tid % 64) with its 8 factors S[l][c] / d_c in registers,
+            // rows i = lo + tid / 64, +4, ... below it
+            const int l = lo + (threadIdx.x & (kP - 1));
+            if (l < bs) {
+                float f[kMp];
+#pragma unroll
+                for (int jj = 0; jj < kMp; ++jj) f[jj] = jj < nc ? S[l][c0 + jj] * ids[c0 + jj] : 0.f;
+                for (int i = l + 1 + (threadIdx.x >> 6); i < bs; i += kTT / kP) {
                     float acc = 0.f;
 #pragma unroll
-                    for (int jj = 0; jj < kMp; ++jj)
-                        if (jj < nc) acc += S[i][c0 + jj] * (S[l][c0 + jj] * ids[c0 + jj]);
+                    for (int jj = 0; jj < kMp; ++jj) acc += S[i][c0 + jj] * f[jj];
                     S[i][l] -= acc;
                 }
-            }
-            for (int l = lo + threadIdx.x; l < bs; l += blockDim.x) {
-                float acc = 0.f;
+                if (threadIdx.x < kP) {
+                    float acc = 0.f;
 #pragma unroll
-                for (int jj = 0; jj < kMp; ++jj)
-                    if (jj < nc) acc += (S[l][c0 + jj] * ids[c0 + jj]) * g[c0 + jj];
-                g[l] -= acc;
+                    for (int jj = 0; jj < kMp; ++jj) acc += f[jj] * g[c0 + jj];
+                    g[l] -= acc;
+                }
             }
         }
         __syncthreads();
@@ -210,30 +215,51 @@ d32_diag_kernel(int ld, int k, int bs, float *__restrict__ A, float *__restrict_
         if (i > j && i < bs) A[(size_t)(k + j) * ld + (k + i)] = l;
     }
     __syncthreads();
-    // X = L^-1 by 8x8 block rows
-    for (int I = 0; I * kMp < bs; ++I) {
-        const int r0 = I * kMp;
-        // T[r][c] = sum_{k in [c, r0)} L[r][k] X[k][c] for the block's rows r and columns c < r0,
-        // stored negated in Xs (rows r0..r0+7 are still zero)
-        for (int t = threadIdx.x; t < kMp * r0; t += blockDim.x) {
-            const int r = r0 + t / r0, c = t % r0;
-            if (r < bs) {
-                float acc = 0.f;
-                for (int kk = c; kk < r0; ++kk) acc += S[r][kk] * Xs[kk][c];
-                Xs[r][c] = -acc;
-            }
+    // X = L^-1 by recursive doubling.  Level 0: warp w inverts the diagonal 8x8 block w (lane c:
+    // column c by forward substitution).  Level b = 8, 16, 32: for each pair of b-blocks on the
+    // diagonal, X21 = -X22 (L21 X11), the product staged through Ts.  L <= 0 below the diagonal
+    // and X >= 0, so every sum has terms of one sign.  Rows and columns >= bs hold the identity.
+    if (lane < kMp) {
+        const int o = warp * kMp;
+        float x[kMp];
+#pragma unroll
+        for (int r = 0; r < kMp; ++r) {
+            float v = (r == lane) ? 1.f : 0.f;
+#pragma unroll
+            for (int q = 0; q < r; ++q) v -= S[o + r][o + q] * x[q];
+            x[r] = r < lane ? 0.f : v;
         }
+#pragma unroll
+        for (int r = 0; r < kMp; ++r) Xs[o + r][o + lane] = x[r];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int b = kMp; b < kP; b *= 2) {
+        // 8b threads per pair: column c, rows rg * (b / 8) .. + b / 8 of the pair's b x b product
+        const int pair = threadIdx.x / (8 * b), loc = threadIdx.x % (8 * b);
+        const int c = loc % b, q0 = (loc / b) * (b / 8);
+        const int o = 2 * b * pair;
+        float acc[kP / 16];
+#pragma unroll
+        for (int q = 0; q < b / 8; ++q) acc[q] = 0.f;
+        for (int kk = c; kk < b; ++kk) {
+            const float xk = Xs[o + kk][o + c];
+#pragma unroll
+            for (int q = 0; q < b / 8; ++q) acc[q] += S[o + b + q0 + q][o + kk] * xk;
+        }
+#pragma unroll
+        for (int q = 0; q < b / 8; ++q) Ts[b * pair + q0 + q][c] = acc[q];
         __syncthreads();
-        // rows of the block: x_r = e_r - sum_{k in [r0, r)} L[r][k] x_k, applied to the block's
-        // columns c < r0 (entries from T) and to the identity part c in [r0, r]; one thread per
-        // column, the 8 rows in order
-        for (int c = threadIdx.x; c < r0 + kMp && c < bs; c += blockDim.x) {
-            for (int r = max(r0, c); r < r0 + kMp && r < bs; ++r) {
-                float x = (c < r0) ? Xs[r][c] : (r == c ? 1.f : 0.f);
-                for (int kk = max(r0, c); kk < r; ++kk) x -= S[r][kk] * Xs[kk][c];
-                Xs[r][c] = x;
-            }
+#pragma unroll
+        for (int q = 0; q < b / 8; ++q) acc[q] = 0.f;
+        for (int r = 0; r < q0 + b / 8; ++r) {
+            const float t = Ts[b * pair + r][c];
+#pragma unroll
+            for (int q = 0; q < b / 8; ++q)
+                if (r <= q0 + q) acc[q] += Xs[o + b + q0 + q][o + b + r] * t;
         }
+#pragma unroll
+        for (int q = 0; q < b / 8; ++q) Xs[o + b + q0 + q][o + c] = -acc[q];
         __syncthreads();
     }
     for (int t = threadIdx.x; t < bs * bs; t += blockDim.x) {

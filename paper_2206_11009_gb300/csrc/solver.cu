@@ -1054,6 +1054,64 @@ int ot_ipm_get_state(ot_ipm_t *h, int32_t *i, int32_t *j, double *p, double *s, 
     return OT_OK;
 }
 
+int ot_ipm_newton_direction(ot_ipm_t *h, int32_t solver, double cg_tol, int32_t max_cg, double *du, double *dv,
+                            double *dp, double *ds, int64_t cap, int32_t *cg_iters) {
+    if (!h) return OT_ERR_ARG;
+    if (solver < OT_LS_PCG64 || solver > OT_LS_SPARSE || !(cg_tol > 0) || max_cg <= 0)
+        return record(h, fail(OT_ERR_ARG, "ot_ipm_newton_direction: bad solver, tolerance or iteration limit"));
+    Support &S = h->S[h->cur];
+    if (cap < S.psi) return record(h, fail(OT_ERR_BUF_TOO_SMALL, "ot_ipm_newton_direction: buffer too small"));
+    Newton &W = h->W;
+    cudaStream_t st = h->st;
+    const int n = h->n;
+    Error e = [&]() -> Error {
+        OT_TRY(residuals(W, S, h->a_s, h->b_s, h->u, h->v, st));
+        OT_TRY(schur_setup(W, S, st));
+        W.direct = nullptr;
+        W.dense = nullptr;
+        W.d32 = nullptr;
+        if (solver == OT_LS_DENSE32) {
+            if (n > kDense32LateMaxN) return fail(OT_ERR_UNSUPPORTED, "FP32 dense factor: n above its limit");
+            if (!h->d32.A) OT_TRY(d32_alloc(h->d32, n));
+            OT_TRY(d32_assemble(h->d32, W, S, st));
+            OT_TRY(d32_factor(h->d32, (float)kPivotEps, st));
+            W.d32 = &h->d32;
+        } else if (solver == OT_LS_DENSE64) {
+            if (n > kDenseMaxN) return fail(OT_ERR_UNSUPPORTED, "FP64 dense factor: n above its limit");
+            if (!h->dense.A) OT_TRY(dense_alloc(h->dense, n));
+            bool changed = false;
+            OT_TRY(chol_assemble(h->chol, W, S, 0.0, &changed, st));
+            OT_CUDA(cudaMemsetAsync(h->dense.err, 0, sizeof(int), st));
+            OT_TRY(dense_factor(h->dense, h->chol, kPivotEps, st));
+            W.direct = &h->chol;
+            W.dense = &h->dense;
+        } else if (solver == OT_LS_SPARSE) {
+            bool changed = false;
+            OT_TRY(chol_assemble(h->chol, W, S, 0.0, &changed, st));
+            if (changed || !h->chol.have_symbolic) OT_TRY(chol_symbolic(h->chol, st));
+            OT_TRY(chol_numeric(h->chol, kPivotEps, st));
+            W.direct = &h->chol;
+        }
+        W.fp64_fallback = false;
+        OT_TRY(corrector_r3(W, S, 0.0, nullptr, nullptr, st));   // predictor: r3 = -p s
+        Rhs R{W.r1a, W.r1b, W.r2, W.r3};
+        SolveStats ss;
+        OT_TRY(newton_solve(W, S, R, cg_tol, max_cg, solver == OT_LS_MIXED ? 1 : 0, W.du, W.dv, W.ds, W.dp, &ss,
+                            st));
+        if (du) OT_CUDA(cudaMemcpyAsync(du, W.du, sizeof(double) * h->m, cudaMemcpyDeviceToHost, st));
+        if (dv) OT_CUDA(cudaMemcpyAsync(dv, W.dv, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+        if (dp) OT_CUDA(cudaMemcpyAsync(dp, W.dp, sizeof(double) * S.psi, cudaMemcpyDeviceToHost, st));
+        if (ds) OT_CUDA(cudaMemcpyAsync(ds, W.ds, sizeof(double) * S.psi, cudaMemcpyDeviceToHost, st));
+        OT_CUDA(cudaStreamSynchronize(st));
+        if (cg_iters) *cg_iters = ss.cg_iters;
+        return ok();
+    }();
+    W.direct = nullptr;
+    W.dense = nullptr;
+    W.d32 = nullptr;
+    return record(h, e);
+}
+
 int ot_ipm_set_state(ot_ipm_t *h, const int32_t *i, const int32_t *j, const double *p, const double *s, int64_t psi,
                      const double *u, const double *v, int32_t reset_mu0) {
     if (!h || psi <= 0 || !i || !j || !p || !s || !u || !v) return OT_ERR_ARG;

@@ -1,0 +1,103 @@
+"""Each linear solver of the Newton system against the oracle's exact direction (Section 4).
+
+The iterate comes from the oracle's own IPM (a few, a middling and many iterations: Theta spread
+from 1e2 to about 1e12); the handle is put in that state and ot_ipm_newton_direction computes the
+predictor direction with one linear solver: FP64 Jacobi PCG, FP32 PCG inside FP64 refinement,
+FP64 CG preconditioned by the FP32 dense factor, the FP64 dense LDL^T and the sparse LDL^T.  The
+oracle solves S_M exactly (sparse LU of the grounded system, minimum-norm gauge).
+
+Bars.  dp and ds are unique; du and dv are unique after the per-component mean-zero gauge that
+both sides apply.  The solvers stop at ||S_M dv - rhs|| <= 1e-12 ||rhs|| (FP64 residual), so the
+error in dv is bounded by cond(S_M) * 1e-12 relative: 1e-9 of max|ref| while Theta spans a few
+decades, 1e-6 at the late iterate where it spans twelve (S_M's conditioning grows with it).  A wrong
+sign, index or dropped term in any solver gives O(1) errors.  The 23 x 23 grid (n = 529) spans
+nine 64-column panels of the dense factors with a ragged last one (17 columns)."""
+import numpy as np
+import pytest
+
+from oracle import costs, ipm
+from paper_2206_11009_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+SOLVERS = ["pcg64", "mixed", "dense32", "dense64", "sparse"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+_states = {}
+
+
+def oracle_state(k, seed, iters):
+    """The oracle's iterate after `iters` IPM iterations (cached per module)."""
+    key = (k, seed, iters)
+    if key not in _states:
+        inst = synth.image_pair(k, seed)
+        prob = ipm.Problem(costs.square_grid(k), inst.a, inst.b)
+        opt = ipm.Options(tol=1e-8)
+        I, J = ipm.initial_support(prob, opt)
+        st = ipm.initial_point(prob, I, J)
+        tr = ipm.Tracker()
+        for it in range(iters):
+            _, res, _ = ipm.stop_test(prob, st, opt, tr)
+            st, _, _, _, _ = ipm.one_iteration(prob, st, res, opt, tr, it)
+        _states[key] = (inst, prob, st)
+    return _states[key]
+
+
+def _err(x, ref):
+    return float(np.abs(x - ref).max() / max(np.abs(ref).max(), 1e-300))
+
+
+@pytest.mark.parametrize("solver", SOLVERS)
+@pytest.mark.parametrize("k,seed,iters,bar", [(12, 1, 3, 1e-9), (23, 1, 3, 1e-9), (23, 1, 15, 1e-9),
+                                              (23, 1, 21, 1e-6)])
+def test_direction_matches_oracle(solver, k, seed, iters, bar):
+    from paper_2206_11009_gb300 import Solver
+    inst, prob, st = oracle_state(k, seed, iters)
+    res = ipm.residuals(prob, st)
+    ref = ipm.newton_direction(prob, st, res.r1a, res.r1b, res.r2, -st.p * st.s)
+    with Solver(inst.a, inst.b, grid=(k, k), tol=1e-8) as s:
+        s.set_state(st.I, st.J, st.p, st.s, st.u, st.v)
+        du, dv, dp, ds, its = s.newton_direction(solver, cg_tol=1e-12, max_cg=20000)
+        I, J, P, S, u, v = s.state()
+    assert np.array_equal(I, st.I) and np.array_equal(P, st.p), "the call must not change the iterate"
+    e = {"du": _err(du, ref.du), "dv": _err(dv, ref.dv), "dp": _err(dp, ref.dp), "ds": _err(ds, ref.ds)}
+    print(f"{solver} k={k} it={iters}: cg {its} " + " ".join(f"{n}={x:.1e}" for n, x in e.items()))
+    assert max(e.values()) <= bar, e
+
+
+def test_newton_equations_hold_for_dense32():
+    """Properties at any size: the returned direction satisfies the linearised equations
+    A dp = r1, A^T dy + ds = r2 and S dp + P ds = r3 (eq. redsystem) to the solve tolerance."""
+    from paper_2206_11009_gb300 import Solver
+    k = 23
+    inst, prob, st = oracle_state(k, 2, 12)
+    res = ipm.residuals(prob, st)
+    with Solver(inst.a, inst.b, grid=(k, k), tol=1e-8) as s:
+        s.set_state(st.I, st.J, st.p, st.s, st.u, st.v)
+        du, dv, dp, ds, _ = s.newton_direction("dense32", cg_tol=1e-12)
+    m = n = k * k
+    r1 = np.concatenate([np.bincount(st.I, weights=dp, minlength=m), np.bincount(st.J, weights=dp, minlength=n)])
+    want = np.concatenate([res.r1a, res.r1b])
+    assert np.abs(r1 - want).max() <= 1e-8 * max(1.0, np.abs(want).max())
+    assert np.abs(du[st.I] + dv[st.J] + ds - res.r2).max() <= 1e-10 * max(1.0, np.abs(res.r2).max())
+    r3 = -st.p * st.s
+    assert np.abs(st.s * dp + st.p * ds - r3).max() <= 1e-10 * np.abs(r3).max()
+
+
+def test_bad_arguments():
+    from paper_2206_11009_gb300 import Solver, _lib
+    import ctypes
+    inst = synth.image_pair(6, 0)
+    with Solver(inst.a, inst.b, grid=(6, 6)) as s:
+        its = ctypes.c_int32(0)
+        for solver, tol, mx in [(5, 1e-8, 10), (-1, 1e-8, 10), (0, 0.0, 10), (0, 1e-8, 0)]:
+            assert s._lib.ot_ipm_newton_direction(s.h, solver, tol, mx, None, None, None, None, 1 << 20,
+                                                  ctypes.byref(its)) == _lib.OT_ERR_ARG
+        assert s._lib.ot_ipm_newton_direction(s.h, 0, 1e-8, 10, None, None, None, None, 0,
+                                              ctypes.byref(its)) == _lib.OT_ERR_BUF_TOO_SMALL
