@@ -158,7 +158,48 @@ scan_kernel(int m, int n, int TI, int ncb, int64_t ntiles,
         }
         __syncthreads();
         float tmin = INFINITY;
-        for (int r = 0; r < nrows; ++r) {
+        const float thr = GATHER ? Tg : E;
+        int r0 = 0;
+        if (!FP64) {
+            // FP32 scan in groups of 4 rows: 32 independent keys, one minimum and one branch per group
+            for (; r0 + 4 <= nrows; r0 += 4) {
+                float d[4][kRJ], mq[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float4 R = srow[r0 + q];
+                    mq[q] = INFINITY;
+#pragma unroll
+                    for (int c = 0; c < kRJ; ++c) {
+                        const float t1 = __fadd_rn(R.x, cB[c]);
+                        const float t2 = __fmaf_rn(R.z, cy[c], t1);
+                        d[q][c] = __fmaf_rn(R.y, cx[c], t2);
+                        mq[q] = fminf(mq[q], d[q][c]);
+                    }
+                }
+                const float dmin = fminf(fminf(mq[0], mq[1]), fminf(mq[2], mq[3]));
+                tmin = fminf(tmin, dmin);
+                if (dmin <= thr) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        if (mq[q] > thr) continue;
+#pragma unroll
+                        for (int c = 0; c < kRJ; ++c) {
+                            if (!GATHER) {
+                                if (d[q][c] < 0.f) atomicAdd(&sh_hist[bin_of_neg(d[q][c])], 1u);
+                                else if (d[q][c] <= E) atomicAdd(&sh_hist[4096], 1u);
+                            } else if (d[q][c] <= Tg) {
+                                const unsigned pos = atomicAdd(ncand, 1u);
+                                if (pos < cap) {
+                                    ci[pos] = i0 + r0 + q;
+                                    cj[pos] = cb * kTJ + c * kPT + threadIdx.x;
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        for (int r = r0; r < nrows; ++r) {
             float d[kRJ];
             double dd[kRJ];
             float dmin = INFINITY;
@@ -184,7 +225,6 @@ scan_kernel(int m, int n, int TI, int ncb, int64_t ntiles,
                 }
             }
             tmin = fminf(tmin, dmin);
-            const float thr = GATHER ? Tg : E;
             if (dmin <= thr) {
 #pragma unroll
                 for (int c = 0; c < kRJ; ++c) {
@@ -434,7 +474,7 @@ Error price_topk(const PriceInput &in, int32_t *out_i, int32_t *out_j, double *o
     }
     // tiles: TI rows x 2048 columns; aim for >= 4 tiles per SM
     const int ncb = (int)ceil_div(n, kTJ);
-    int TI = 64;
+    int TI = kPT;
     while (TI > 8 && ceil_div(m, TI) * (int64_t)ncb < 4LL * sms) TI >>= 1;
     if (in.rows > 0) TI = std::max(8, std::min(kPT, in.rows));
     const int nrb = (int)ceil_div(m, TI);
