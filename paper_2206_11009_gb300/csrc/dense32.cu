@@ -376,8 +376,9 @@ __device__ __forceinline__ void tri_decode(int idx, int &ti, int &tj) {
 __global__ void __launch_bounds__(kTT, 2)
 d32_update_kernel(int n, int ld, int k, int part, float *__restrict__ A, float *__restrict__ X,
                   const float *__restrict__ LD, float *__restrict__ csum) {
-    __shared__ __align__(16) float As[kKc][kTile];
-    __shared__ __align__(16) float Bs[kKc][kTile];
+    // two stages: slice s + 1 is fetched into registers while slice s is multiplied
+    __shared__ __align__(16) float As[2][kKc][kTile];
+    __shared__ __align__(16) float Bs[2][kKc][kTile];
     const int base = k + kP;
     const int t = (n - base + kTile - 1) / kTile;
     const int tcn = (base + kTile - 1) / kTile;
@@ -422,45 +423,60 @@ d32_update_kernel(int n, int ld, int k, int part, float *__restrict__ A, float *
     for (int u = 0; u < 8; ++u)
 #pragma unroll
         for (int w = 0; w < 8; ++w) acc[u][w] = 0.f;
-    for (int l0 = 0; l0 < kP; l0 += kKc) {
-        __syncthreads();
-        {
-            const int l = threadIdx.x >> 4, q = (threadIdx.x & 15) * 8;
-            const float *src = Pa + (size_t)(l0 + l) * ld + r0 + q;
-            if (r0 + q + 8 <= n) {
-                *(float4 *)&As[l][q] = *(const float4 *)src;
-                *(float4 *)&As[l][q + 4] = *(const float4 *)(src + 4);
-            } else {
+    float ra[8], rb[8];
+    const int fl = threadIdx.x >> 4, fq = (threadIdx.x & 15) * 8;       // A (and trailing B) slot
+    const int xc = threadIdx.x & (kTile - 1), xh = threadIdx.x >> 7;      // inverse B slot
+    auto fetch = [&](int l0) {
+        const float *src = Pa + (size_t)(l0 + fl) * ld + r0 + fq;
+        if (r0 + fq + 8 <= n) {
+            const float4 v0 = *(const float4 *)src, v1 = *(const float4 *)(src + 4);
+            ra[0] = v0.x; ra[1] = v0.y; ra[2] = v0.z; ra[3] = v0.w;
+            ra[4] = v1.x; ra[5] = v1.y; ra[6] = v1.z; ra[7] = v1.w;
+        } else {
 #pragma unroll
-                for (int u = 0; u < 8; ++u) As[l][q + u] = (r0 + q + u < n) ? src[u] : 0.f;
-            }
-            if (tri) {
-                const float *sb = Pb + (size_t)(l0 + l) * ld + c0 + q;
-                if (c0 + q + 8 <= climit) {
-                    *(float4 *)&Bs[l][q] = *(const float4 *)sb;
-                    *(float4 *)&Bs[l][q + 4] = *(const float4 *)(sb + 4);
-                } else {
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) Bs[l][q + u] = (c0 + q + u < climit) ? sb[u] : 0.f;
-                }
-            } else {
-                const int c = threadIdx.x & (kTile - 1), h = threadIdx.x >> 7;
-                if (c0 + c < climit) {
-                    const float *sx = X + (size_t)(c0 + c) * ld + k + l0 + h * 8;
-                    const float4 v0 = *(const float4 *)sx, v1 = *(const float4 *)(sx + 4);
-                    Bs[h * 8 + 0][c] = v0.x; Bs[h * 8 + 1][c] = v0.y; Bs[h * 8 + 2][c] = v0.z; Bs[h * 8 + 3][c] = v0.w;
-                    Bs[h * 8 + 4][c] = v1.x; Bs[h * 8 + 5][c] = v1.y; Bs[h * 8 + 6][c] = v1.z; Bs[h * 8 + 7][c] = v1.w;
-                } else {
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) Bs[h * 8 + u][c] = 0.f;
-                }
-            }
+            for (int u = 0; u < 8; ++u) ra[u] = (r0 + fq + u < n) ? src[u] : 0.f;
         }
+        if (tri) {
+            const float *sb = Pb + (size_t)(l0 + fl) * ld + c0 + fq;
+            if (c0 + fq + 8 <= climit) {
+                const float4 v0 = *(const float4 *)sb, v1 = *(const float4 *)(sb + 4);
+                rb[0] = v0.x; rb[1] = v0.y; rb[2] = v0.z; rb[3] = v0.w;
+                rb[4] = v1.x; rb[5] = v1.y; rb[6] = v1.z; rb[7] = v1.w;
+            } else {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) rb[u] = (c0 + fq + u < climit) ? sb[u] : 0.f;
+            }
+        } else if (c0 + xc < climit) {
+            const float *sx = X + (size_t)(c0 + xc) * ld + k + l0 + xh * 8;
+            const float4 v0 = *(const float4 *)sx, v1 = *(const float4 *)(sx + 4);
+            rb[0] = v0.x; rb[1] = v0.y; rb[2] = v0.z; rb[3] = v0.w;
+            rb[4] = v1.x; rb[5] = v1.y; rb[6] = v1.z; rb[7] = v1.w;
+        } else {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) rb[u] = 0.f;
+        }
+    };
+    auto stash = [&](int b) {
+        *(float4 *)&As[b][fl][fq] = make_float4(ra[0], ra[1], ra[2], ra[3]);
+        *(float4 *)&As[b][fl][fq + 4] = make_float4(ra[4], ra[5], ra[6], ra[7]);
+        if (tri) {
+            *(float4 *)&Bs[b][fl][fq] = make_float4(rb[0], rb[1], rb[2], rb[3]);
+            *(float4 *)&Bs[b][fl][fq + 4] = make_float4(rb[4], rb[5], rb[6], rb[7]);
+        } else {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) Bs[b][xh * 8 + u][xc] = rb[u];
+        }
+    };
+    fetch(0);
+    int buf = 0;
+    for (int l0 = 0; l0 < kP; l0 += kKc) {
+        stash(buf);
         __syncthreads();
+        if (l0 + kKc < kP) fetch(l0 + kKc);
 #pragma unroll
         for (int l = 0; l < kKc; ++l) {
-            const float4 a0 = *(const float4 *)&As[l][tr * 8], a1 = *(const float4 *)&As[l][tr * 8 + 4];
-            const float4 b0 = *(const float4 *)&Bs[l][tc * 8], b1 = *(const float4 *)&Bs[l][tc * 8 + 4];
+            const float4 a0 = *(const float4 *)&As[buf][l][tr * 8], a1 = *(const float4 *)&As[buf][l][tr * 8 + 4];
+            const float4 b0 = *(const float4 *)&Bs[buf][l][tc * 8], b1 = *(const float4 *)&Bs[buf][l][tc * 8 + 4];
             const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
             const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
@@ -468,6 +484,7 @@ d32_update_kernel(int n, int ld, int k, int part, float *__restrict__ A, float *
 #pragma unroll
                 for (int w = 0; w < 8; ++w) acc[u][w] += a[u] * b[w];
         }
+        buf ^= 1;
     }
     float *C = tri ? A : X;
     // the first column tile of the trailing part holds the next panel's columns: their sums below
