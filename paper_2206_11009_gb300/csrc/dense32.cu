@@ -98,6 +98,65 @@ d32_colsum_kernel(int n, int ld, int bs, const float *__restrict__ A, float *__r
 constexpr int kMp = 8;   // micro-panel width
 static_assert(kTT / 32 == kP / kMp && kTT == 4 * kP, "one warp per 8x8 diagonal block, 8b threads per b-pair");
 
+// Warp 0's elimination of one micro-panel (columns c0 .. c0 + nc - 1) with the block's 64 rows in
+// registers (lane q: rows q and q + 32).  kFull: nc == kMp known at compile time, so the whole
+// micro-panel is one straight-line block and the shuffles of successive columns overlap.
+template <bool kFull>
+__device__ __forceinline__ void d32_micro_panel(int lane, int k, int c0, int nc, float (*S)[kP + 1], float *g,
+                                                const float *thr, float *ids, float *D) {
+    const unsigned full = 0xffffffffu;
+    const int ncc = kFull ? kMp : nc;
+    float v0[kMp], v1[kMp], gm[kMp], tl[kMp], dv[kMp], iv[kMp];
+#pragma unroll
+    for (int jj = 0; jj < kMp; ++jj) {
+        v0[jj] = jj < ncc ? S[lane][c0 + jj] : 0.f;
+        v1[jj] = jj < ncc ? S[lane + 32][c0 + jj] : 0.f;
+        gm[jj] = jj < ncc ? g[c0 + jj] : 0.f;
+        tl[jj] = jj < ncc ? thr[c0 + jj] : 0.f;
+    }
+#pragma unroll
+    for (int jj = 0; jj < kMp; ++jj) {
+        dv[jj] = INFINITY;
+        iv[jj] = 0.f;
+        if (jj < ncc) {
+            const int j = c0 + jj;
+            float sum = (lane > j ? v0[jj] : 0.f) + (lane + 32 > j ? v1[jj] : 0.f);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(full, sum, o);
+            const float d = -(sum + gm[jj]);
+            const bool inf = !(d > tl[jj]);
+            const float id = inf ? 0.f : 1.f / d;
+            const float l0 = (lane > j) ? v0[jj] * id : 0.f, l1 = (lane + 32 > j) ? v1[jj] * id : 0.f;
+#pragma unroll
+            for (int jj2 = jj + 1; jj2 < kMp; ++jj2) {
+                if (jj2 < ncc) {
+                    const int r = c0 + jj2;   // the row whose column-j entry multiplies
+                    const float srj = __shfl_sync(full, r < 32 ? v0[jj] : v1[jj], r & 31);
+                    if (lane > r) v0[jj2] -= l0 * srj;
+                    if (lane + 32 > r) v1[jj2] -= l1 * srj;
+                    gm[jj2] -= (srj * id) * gm[jj];
+                }
+            }
+            v0[jj] = inf ? 0.f : v0[jj];
+            v1[jj] = inf ? 0.f : v1[jj];
+            dv[jj] = inf ? INFINITY : d;
+            iv[jj] = id;
+        }
+    }
+#pragma unroll
+    for (int jj = 0; jj < kMp; ++jj) {
+        if (jj < ncc) {
+            S[lane][c0 + jj] = v0[jj];
+            S[lane + 32][c0 + jj] = v1[jj];
+            if (lane == jj) {
+                g[c0 + jj] = gm[jj];
+                D[k + c0 + jj] = dv[jj];
+                ids[c0 + jj] = iv[jj];
+            }
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kTT)
 d32_diag_kernel(int ld, int k, int bs, float *__restrict__ A, float *__restrict__ D, const float *__restrict__ d0,
                 const float *__restrict__ csum, int np, float eps, float *__restrict__ Linv) {
@@ -105,7 +164,6 @@ d32_diag_kernel(int ld, int k, int bs, float *__restrict__ A, float *__restrict_
     __shared__ float Xs[kP][kP + 1];
     __shared__ float Ts[kP / 2][kP / 2 + 1];
     __shared__ float g[kP], thr[kP], ids[kP];
-    const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int t = threadIdx.x; t < kP * kP; t += blockDim.x) {
         const int i = t % kP, j = t / kP;
@@ -130,78 +188,45 @@ d32_diag_kernel(int ld, int k, int bs, float *__restrict__ A, float *__restrict_
     for (int c0 = 0; c0 < bs; c0 += kMp) {
         const int nc = min(kMp, bs - c0);
         if (warp == 0) {
-            float v0[kMp], v1[kMp], gm[kMp];
-#pragma unroll
-            for (int jj = 0; jj < kMp; ++jj) {
-                v0[jj] = jj < nc ? S[lane][c0 + jj] : 0.f;
-                v1[jj] = jj < nc ? S[lane + 32][c0 + jj] : 0.f;
-                gm[jj] = jj < nc ? g[c0 + jj] : 0.f;
-            }
-#pragma unroll
-            for (int jj = 0; jj < kMp; ++jj) {
-                if (jj < nc) {
-                    const int j = c0 + jj;
-                    float sum = (lane > j ? v0[jj] : 0.f) + (lane + 32 > j ? v1[jj] : 0.f);
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(full, sum, o);
-                    const float d = -(sum + gm[jj]);
-                    const bool inf = !(d > thr[j]);
-                    const float id = inf ? 0.f : 1.f / d;
-                    const float l0 = (lane > j) ? v0[jj] * id : 0.f, l1 = (lane + 32 > j) ? v1[jj] * id : 0.f;
-#pragma unroll
-                    for (int jj2 = jj + 1; jj2 < kMp; ++jj2) {
-                        if (jj2 < nc) {
-                            const int r = c0 + jj2;   // the row whose column-j entry multiplies
-                            const float srj = __shfl_sync(full, r < 32 ? v0[jj] : v1[jj], r & 31);
-                            if (lane > r) v0[jj2] -= l0 * srj;
-                            if (lane + 32 > r) v1[jj2] -= l1 * srj;
-                            gm[jj2] -= (srj * id) * gm[jj];
-                        }
-                    }
-                    if (inf) {
-                        v0[jj] = 0.f;
-                        v1[jj] = 0.f;
-                    }
-                    if (lane == 0) {
-                        D[k + j] = inf ? INFINITY : d;
-                        ids[j] = id;
-                    }
-                }
-            }
-#pragma unroll
-            for (int jj = 0; jj < kMp; ++jj) {
-                if (jj < nc) {
-                    S[lane][c0 + jj] = v0[jj];
-                    S[lane + 32][c0 + jj] = v1[jj];
-                    if (lane == 0) g[c0 + jj] = gm[jj];
-                }
-            }
+            if (nc == kMp) d32_micro_panel<true>(lane, k, c0, nc, S, g, thr, ids, D);
+            else d32_micro_panel<false>(lane, k, c0, nc, S, g, thr, ids, D);
         }
         __syncthreads();
         // rank-nc update of the columns l >= c0 + nc: S[i][l] -= sum_jj S[i][c] S[l][c] / d_c (i > l),
-        // and of their below-block sums: g[l] -= sum_jj (S[l][c] / d_c) g[c]
+        // and of their below-block sums: g[l] -= sum_jj (S[l][c] / d_c) g[c].  Thread (ty, tx): the
+        // columns la = lo + tx and lb = la + 32 with their 8 factors S[l][c] / d_c in registers, the
+        // rows lo + ty, +8, ... (each row's 8 entries read once for both columns)
         const int lo = c0 + nc;
-        const int w = bs - lo;
-        if (w > 0) {
-            // thread: column l = lo + (tid % 64) with its 8 factors S[l][c] / d_c in registers,
-            // rows i = lo + tid / 64, +4, ... below it
-            const int l = lo + (threadIdx.x & (kP - 1));
-            if (l < bs) {
-                float f[kMp];
+        if (lo < bs) {
+            const int tx = lane, ty = warp;
+            const int la = lo + tx, lb = la + 32;
+            float fa[kMp], fb[kMp];
 #pragma unroll
-                for (int jj = 0; jj < kMp; ++jj) f[jj] = jj < nc ? S[l][c0 + jj] * ids[c0 + jj] : 0.f;
-                for (int i = l + 1 + (threadIdx.x >> 6); i < bs; i += kTT / kP) {
-                    float acc = 0.f;
+            for (int jj = 0; jj < kMp; ++jj) {
+                fa[jj] = (la < bs) ? S[la][c0 + jj] * ids[c0 + jj] : 0.f;
+                fb[jj] = (lb < bs) ? S[lb][c0 + jj] * ids[c0 + jj] : 0.f;
+            }
+            for (int i = lo + ty; i < bs; i += kTT / 32) {
+                if (i <= la) continue;
+                float sa = 0.f, sb = 0.f;
 #pragma unroll
-                    for (int jj = 0; jj < kMp; ++jj) acc += S[i][c0 + jj] * f[jj];
-                    S[i][l] -= acc;
+                for (int jj = 0; jj < kMp; ++jj) {
+                    const float x = S[i][c0 + jj];
+                    sa += x * fa[jj];
+                    sb += x * fb[jj];
                 }
-                if (threadIdx.x < kP) {
-                    float acc = 0.f;
+                S[i][la] -= sa;
+                if (i > lb) S[i][lb] -= sb;
+            }
+            if (ty == 0) {
+                float ga = 0.f, gb = 0.f;
 #pragma unroll
-                    for (int jj = 0; jj < kMp; ++jj) acc += f[jj] * g[c0 + jj];
-                    g[l] -= acc;
+                for (int jj = 0; jj < kMp; ++jj) {
+                    ga += fa[jj] * g[c0 + jj];
+                    gb += fb[jj] * g[c0 + jj];
                 }
+                if (la < bs) g[la] -= ga;
+                if (lb < bs) g[lb] -= gb;
             }
         }
         __syncthreads();
