@@ -99,13 +99,17 @@ constexpr int kMp = 8;   // micro-panel width
 static_assert(kTT / 32 == kP / kMp && kTT == 4 * kP, "one warp per 8x8 diagonal block, 8b threads per b-pair");
 
 // Warp 0's elimination of one micro-panel (columns c0 .. c0 + nc - 1) with the block's 64 rows in
-// registers (lane q: rows q and q + 32).  kFull: nc == kMp known at compile time, so the whole
-// micro-panel is one straight-line block and the shuffles of successive columns overlap.
+// registers (lane q: rows q and q + 32).  prev >= 0: the micro-panel's columns first receive the
+// rank-8 update of the micro-panel starting at prev (eliminated by this warp just before), in the
+// same order as the other warps apply it to the later columns.  kFull: nc == kMp known at compile
+// time, so the whole micro-panel is one straight-line block and the shuffles of successive
+// columns overlap.
 template <bool kFull>
-__device__ __forceinline__ void d32_micro_panel(int lane, int k, int c0, int nc, float (*S)[kP + 1], float *g,
-                                                const float *thr, float *ids, float *D) {
+__device__ __forceinline__ void d32_micro_panel(int lane, int k, int c0, int nc, int prev, float (*S)[kP + 1],
+                                                float *g, const float *thr, float *ids, float *D) {
     const unsigned full = 0xffffffffu;
     const int ncc = kFull ? kMp : nc;
+    __syncwarp();
     float v0[kMp], v1[kMp], gm[kMp], tl[kMp], dv[kMp], iv[kMp];
 #pragma unroll
     for (int jj = 0; jj < kMp; ++jj) {
@@ -113,6 +117,33 @@ __device__ __forceinline__ void d32_micro_panel(int lane, int k, int c0, int nc,
         v1[jj] = jj < ncc ? S[lane + 32][c0 + jj] : 0.f;
         gm[jj] = jj < ncc ? g[c0 + jj] : 0.f;
         tl[jj] = jj < ncc ? thr[c0 + jj] : 0.f;
+    }
+    if (prev >= 0) {
+        float a0[kMp], a1[kMp], gp[kMp], ip[kMp];
+#pragma unroll
+        for (int q = 0; q < kMp; ++q) {
+            a0[q] = S[lane][prev + q];
+            a1[q] = S[lane + 32][prev + q];
+            gp[q] = g[prev + q];
+            ip[q] = ids[prev + q];
+        }
+#pragma unroll
+        for (int jj = 0; jj < kMp; ++jj) {
+            if (jj < ncc) {
+                const int l = c0 + jj;
+                float s0 = 0.f, s1 = 0.f, sg = 0.f;
+#pragma unroll
+                for (int q = 0; q < kMp; ++q) {
+                    const float f = S[l][prev + q] * ip[q];
+                    s0 += a0[q] * f;
+                    s1 += a1[q] * f;
+                    sg += f * gp[q];
+                }
+                if (lane > l) v0[jj] -= s0;
+                if (lane + 32 > l) v1[jj] -= s1;
+                gm[jj] -= sg;
+            }
+        }
     }
 #pragma unroll
     for (int jj = 0; jj < kMp; ++jj) {
@@ -185,48 +216,55 @@ d32_diag_kernel(int ld, int k, int bs, float *__restrict__ A, float *__restrict_
         thr[threadIdx.x] = threadIdx.x < bs ? eps * d0[k + threadIdx.x] : 0.f;
     }
     __syncthreads();
+    // micro-panel 0, then per step: warp 0 updates and eliminates the next micro-panel while the
+    // other warps apply the current one's rank-8 update to the columns after it
+    if (warp == 0) {
+        if (bs >= kMp) d32_micro_panel<true>(lane, k, 0, kMp, -1, S, g, thr, ids, D);
+        else d32_micro_panel<false>(lane, k, 0, bs, -1, S, g, thr, ids, D);
+    }
+    __syncthreads();
     for (int c0 = 0; c0 < bs; c0 += kMp) {
-        const int nc = min(kMp, bs - c0);
+        const int c1 = c0 + kMp, nc1 = min(kMp, bs - c1);   // micro-panel c0 is full when c1 < bs
         if (warp == 0) {
-            if (nc == kMp) d32_micro_panel<true>(lane, k, c0, nc, S, g, thr, ids, D);
-            else d32_micro_panel<false>(lane, k, c0, nc, S, g, thr, ids, D);
-        }
-        __syncthreads();
-        // rank-nc update of the columns l >= c0 + nc: S[i][l] -= sum_jj S[i][c] S[l][c] / d_c (i > l),
-        // and of their below-block sums: g[l] -= sum_jj (S[l][c] / d_c) g[c].  Thread (ty, tx): the
-        // columns la = lo + tx and lb = la + 32 with their 8 factors S[l][c] / d_c in registers, the
-        // rows lo + ty, +8, ... (each row's 8 entries read once for both columns)
-        const int lo = c0 + nc;
-        if (lo < bs) {
-            const int tx = lane, ty = warp;
-            const int la = lo + tx, lb = la + 32;
-            float fa[kMp], fb[kMp];
-#pragma unroll
-            for (int jj = 0; jj < kMp; ++jj) {
-                fa[jj] = (la < bs) ? S[la][c0 + jj] * ids[c0 + jj] : 0.f;
-                fb[jj] = (lb < bs) ? S[lb][c0 + jj] * ids[c0 + jj] : 0.f;
-            }
-            for (int i = lo + ty; i < bs; i += kTT / 32) {
-                if (i <= la) continue;
-                float sa = 0.f, sb = 0.f;
+            if (nc1 == kMp) d32_micro_panel<true>(lane, k, c1, kMp, c0, S, g, thr, ids, D);
+            else if (nc1 > 0) d32_micro_panel<false>(lane, k, c1, nc1, c0, S, g, thr, ids, D);
+        } else {
+            // rank-8 update of the columns l >= lo: S[i][l] -= sum_jj S[i][c] S[l][c] / d_c (i > l),
+            // and of their below-block sums: g[l] -= sum_jj (S[l][c] / d_c) g[c].  Thread (ty, tx):
+            // the columns la = lo + tx and lb = la + 32 with their 8 factors in registers, the rows
+            // lo + ty, +7, ... (each row's 8 entries read once for both columns)
+            const int lo = c1 + max(nc1, 0);
+            if (lo < bs) {
+                const int tx = lane, ty = warp - 1;
+                const int la = lo + tx, lb = la + 32;
+                float fa[kMp], fb[kMp];
 #pragma unroll
                 for (int jj = 0; jj < kMp; ++jj) {
-                    const float x = S[i][c0 + jj];
-                    sa += x * fa[jj];
-                    sb += x * fb[jj];
+                    fa[jj] = (la < bs) ? S[la][c0 + jj] * ids[c0 + jj] : 0.f;
+                    fb[jj] = (lb < bs) ? S[lb][c0 + jj] * ids[c0 + jj] : 0.f;
                 }
-                S[i][la] -= sa;
-                if (i > lb) S[i][lb] -= sb;
-            }
-            if (ty == 0) {
-                float ga = 0.f, gb = 0.f;
+                for (int i = lo + ty; i < bs; i += kTT / 32 - 1) {
+                    if (i <= la) continue;
+                    float sa = 0.f, sb = 0.f;
 #pragma unroll
-                for (int jj = 0; jj < kMp; ++jj) {
-                    ga += fa[jj] * g[c0 + jj];
-                    gb += fb[jj] * g[c0 + jj];
+                    for (int jj = 0; jj < kMp; ++jj) {
+                        const float x = S[i][c0 + jj];
+                        sa += x * fa[jj];
+                        sb += x * fb[jj];
+                    }
+                    S[i][la] -= sa;
+                    if (i > lb) S[i][lb] -= sb;
                 }
-                if (la < bs) g[la] -= ga;
-                if (lb < bs) g[lb] -= gb;
+                if (ty == 0) {
+                    float ga = 0.f, gb = 0.f;
+#pragma unroll
+                    for (int jj = 0; jj < kMp; ++jj) {
+                        ga += fa[jj] * g[c0 + jj];
+                        gb += fb[jj] * g[c0 + jj];
+                    }
+                    if (la < bs) g[la] -= ga;
+                    if (lb < bs) g[lb] -= gb;
+                }
             }
         }
         __syncthreads();
@@ -713,6 +751,13 @@ struct Dag {
         if (err == cudaSuccess) ++nodes;
         return node;
     }
+    // launch priority of a kernel node (stream-priority scale: lower values run first)
+    void priority(cudaGraphNode_t node, int value) {
+        if (err != cudaSuccess || !node) return;
+        cudaKernelNodeAttrValue v = {};
+        v.priority = value;
+        err = cudaGraphKernelNodeSetAttribute(node, cudaKernelNodeAttributePriority, &v);
+    }
     cudaGraphNode_t memset0(float *dst, size_t count, std::vector<cudaGraphNode_t> deps) {
         cudaGraphNode_t node = nullptr;
         if (err != cudaSuccess) return node;
@@ -744,6 +789,10 @@ static Error d32_build(Dense32 &F, float eps, cudaGraph_t g, int64_t *nodes) {
     cudaGraphNode_t prev = c.memset0(F.X, (size_t)ld * n, {});
     cudaGraphNode_t u1 = nullptr, u2 = nullptr;   // the previous panel's two update parts
     int np = 1;  // partial column sums feeding the next diagonal block
+    // the chain diag -> panel / invrow -> first update part runs ahead of the bulk update, whose
+    // CTAs would otherwise take the SMs the chain's small grids wait for
+    int lo_prio = 0, hi_prio = 0;
+    if (cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio) != cudaSuccess) lo_prio = hi_prio = 0;
     for (int k = 0, p = 0; k < n; k += kP, ++p) {
         const int bs = std::min(kP, n - k), base = k + bs;
         float *LDp = F.LD + (size_t)(p & 1) * ld * kP;   // double-buffered: the rest of the previous
@@ -751,21 +800,25 @@ static Error d32_build(Dense32 &F, float eps, cudaGraph_t g, int64_t *nodes) {
         if (k == 0) prev = c.kernel({prev}, d32_colsum_kernel, (unsigned)bs, kTT, n, ld, bs, (const float *)F.A, F.csum);
         const cudaGraphNode_t dg = c.kernel({k == 0 ? prev : u1}, d32_diag_kernel, 1u, kTT, ld, k, bs, F.A, F.D,
                                             (const float *)F.d0, (const float *)F.csum, np, eps, F.Linv);
+        c.priority(dg, hi_prio);
         std::vector<cudaGraphNode_t> ready;
         if (base < n)
             ready.push_back(c.kernel({dg}, d32_panel_kernel, (unsigned)ceil_div(n - base, kP), kTT, n, ld, k, F.A,
                                      (const float *)F.D, (const float *)F.Linv, LDp));
         ready.push_back(c.kernel({dg}, d32_invrow_kernel, (unsigned)ceil_div(base, kP), kTT, ld, k, bs, F.X,
                                  (const float *)F.Linv));
+        for (cudaGraphNode_t r : ready) c.priority(r, hi_prio);
         if (u2) ready.push_back(u2);
         if (base < n) {
             const int t = (int)ceil_div(n - base, kTile), tcn = (int)ceil_div(base, kTile);
             u1 = c.kernel(ready, d32_update_kernel, (unsigned)(t + tcn), kTT, n, ld, k, 1, F.A, F.X,
                           (const float *)LDp, F.csum);
+            c.priority(u1, hi_prio);
             const int n2 = t * (t - 1) / 2 + (t - 1) * tcn;
             u2 = n2 > 0 ? c.kernel(ready, d32_update_kernel, (unsigned)n2, kTT, n, ld, k, 2, F.A, F.X,
                                    (const float *)LDp, F.csum)
                         : nullptr;
+            c.priority(u2, lo_prio);
             np = t;
         } else {
             // the last panel: join everything so the graph ends after all writes
