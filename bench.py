@@ -175,6 +175,40 @@ def config_dict(args):
 
 
 # ------------------------------------------------------------------------------ GPU arm
+def pricing_at(torch, synth, k: int, seed: int, reps: int = 5):
+    """Pricing + selection on a k x k pair with the duals and support of its 4th IPM iteration;
+    full-call throughput and the scan pass against the FP32 ALU peak (4 lane-ops per pair)."""
+    import numpy as np
+    from paper_2206_11009_gb300 import Solver, kernel_timing, price_topk
+    inst = synth.image_pair(k, seed)
+    with Solver(inst.a, inst.b, grid=(k, k), tol=1e-6, precision=1, max_iter=4) as s:
+        s.solve(raise_on_error=False)
+        Is, Js, _, _, us, vs = s.state()
+    x, y = synth.grid_coords(k)
+    T = lambda arr, dt: torch.as_tensor(np.ascontiguousarray(arr), dtype=dt, device="cuda")
+    tx, ty, tu, tv, ti, tj = (T(x, torch.int32), T(y, torch.int32), T(us, torch.float64), T(vs, torch.float64),
+                              T(Is, torch.int32), T(Js, torch.int32))
+    for _ in range(3):
+        price_topk(tx, ty, tx, ty, tu, tv, ti, tj, kmax=k * k, precision=1)
+    torch.cuda.synchronize()
+    kernel_timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        gi, _, _ = price_topk(tx, ty, tx, ty, tu, tv, ti, tj, kmax=k * k, precision=1)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    kt = kernel_timing()
+    kernel_timing(False)
+    pairs = float(k * k) ** 2
+    pk_d, src = peaks()
+    table = kernel_table(kt, pk_d, src)
+    return {"k": k, "pairs": pairs, "support": int(len(Is)), "selected": int(gi.numel()), "ms_per_call": ms,
+            "gcols_per_s": pairs / (ms * 1e-3) / 1e9, "scan_pass": table.get("scan_hist"),
+            "gather_pass": table.get("scan_gather")}
+
+
 def run_batch(torch, synth, count: int = 64, workers: int = 8):
     """64 uneven instances (sides 24..96, seeded), autotuned launch shapes, solved through the
     library's queue with `workers` host threads and with one; wall time around each whole batch
@@ -216,6 +250,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-big-pricing", action="store_true")
     args = ap.parse_args()
     world, rank, local = dist_init()
     if args.impl == "reference":
@@ -324,6 +359,8 @@ def main():
     pairs = (k * k) ** 2
     gcols = pairs / (price_ms * 1e-3) / 1e9
 
+    big = None if args.no_big_pricing else pricing_at(torch, synth, 256, 10000)
+
     pk_d, src = peaks()
     table = kernel_table(ktimes, pk_d, src)
     roof = roofline(table)
@@ -343,7 +380,8 @@ def main():
         "mixed_cold": mixed_cold,
         "warm_start": {"network": net is not None, "added_pairs": r0.warm_added, "dropped": r0.warm_restarts},
         "batch": batch,
-        "pricing": {"gcols_per_s": gcols, "ms_per_call": price_ms, "pairs": pairs, "kernels": ptable},
+        "pricing": {"gcols_per_s": gcols, "ms_per_call": price_ms, "pairs": pairs, "kernels": ptable,
+                    "at_256x256": big},
         "kernels": table,
         "roofline": roof,
         "clocks": clk,
