@@ -425,10 +425,10 @@ d32_invrow_kernel(int ld, int k, int bs, float *__restrict__ X, const float *__r
     }
 }
 
-// the two rank-64 updates of panel k, 128x128 tiles, 8x8 per thread
-// Tile sets of one panel's update (t row tiles of 128 below the panel, tcn column tiles of the
-// inverse's rectangle): part 1 = what the next panel needs first (trailing tiles of the first
-// column tile, inverse tiles of the first row tile), part 2 = the rest.
+// The two rank-64 updates of panel k (trailing triangle A22 -= LD L21^T, rows of L^-1 below the
+// panel B -= L21 X_k) are split in two launches: d32_update1_kernel covers what the next panel
+// needs (its 64 columns of A22 and its 64 rows of B, 64x64 tiles) and d32_update_kernel the rest
+// (rows and columns from base2 = k + 128 on, 128x128 tiles, 8x8 per thread).
 __device__ __forceinline__ void tri_decode(int idx, int &ti, int &tj) {
     ti = (int)((sqrt(8.0 * idx + 1.0) - 1.0) * 0.5);
     while ((ti + 1) * (ti + 2) / 2 <= idx) ++ti;
@@ -436,46 +436,123 @@ __device__ __forceinline__ void tri_decode(int idx, int &ti, int &tj) {
     tj = idx - ti * (ti + 1) / 2;
 }
 
+// the next panel's part: blocks [0, ts) are the 64-column strip of A22 in 64-row tiles (with the
+// strip's column sums below the next diagonal block, csum[s * 64 + c], fixed-order partials),
+// blocks [ts, ts + tx) the next panel's 64 rows of B in 64-column tiles; all of K = 64 staged once
+__global__ void __launch_bounds__(kTT)
+d32_update1_kernel(int n, int ld, int k, float *__restrict__ A, float *__restrict__ X,
+                   const float *__restrict__ LD, float *__restrict__ csum) {
+    __shared__ __align__(16) float As[kP][kP];   // As[l][r] = A operand (row r0 + r, depth l)
+    __shared__ __align__(16) float Bs[kP][kP];   // Bs[l][c] = B operand (column c0 + c, depth l)
+    const int base = k + kP;
+    const int ts = (n - base + kP - 1) / kP;
+    const bool strip = (int)blockIdx.x < ts;
+    const int r0 = strip ? base + (int)blockIdx.x * kP : base;
+    const int c0 = strip ? base : ((int)blockIdx.x - ts) * kP;
+    const int climit = strip ? n : base;
+    const float *Pa = strip ? LD : A + (size_t)k * ld;
+    const float *Pb = A + (size_t)k * ld;
+    for (int t = threadIdx.x; t < kP * (kP / 4); t += kTT) {
+        const int l = t / (kP / 4), q = (t % (kP / 4)) * 4;
+        const float *src = Pa + (size_t)l * ld + r0 + q;
+        float4 v;
+        if (r0 + q + 4 <= n) v = *(const float4 *)src;
+        else {
+            v.x = r0 + q < n ? src[0] : 0.f;
+            v.y = r0 + q + 1 < n ? src[1] : 0.f;
+            v.z = r0 + q + 2 < n ? src[2] : 0.f;
+            v.w = r0 + q + 3 < n ? src[3] : 0.f;
+        }
+        *(float4 *)&As[l][q] = v;
+        if (strip) {
+            const float *sb = Pb + (size_t)l * ld + c0 + q;
+            float4 w;
+            if (c0 + q + 4 <= climit) w = *(const float4 *)sb;
+            else {
+                w.x = c0 + q < climit ? sb[0] : 0.f;
+                w.y = c0 + q + 1 < climit ? sb[1] : 0.f;
+                w.z = c0 + q + 2 < climit ? sb[2] : 0.f;
+                w.w = c0 + q + 3 < climit ? sb[3] : 0.f;
+            }
+            *(float4 *)&Bs[l][q] = w;
+        } else {
+            const int c = t % kP, lq = (t / kP) * 4;
+            float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (c0 + c < climit) w = *(const float4 *)(X + (size_t)(c0 + c) * ld + k + lq);
+            Bs[lq][c] = w.x;
+            Bs[lq + 1][c] = w.y;
+            Bs[lq + 2][c] = w.z;
+            Bs[lq + 3][c] = w.w;
+        }
+    }
+    __syncthreads();
+    const int tr = threadIdx.x & 15, tc = threadIdx.x >> 4;   // rows tr*4.., columns tc*4..
+    float acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int w = 0; w < 4; ++w) acc[u][w] = 0.f;
+#pragma unroll 16
+    for (int l = 0; l < kP; ++l) {
+        const float4 a = *(const float4 *)&As[l][tr * 4];
+        const float4 b = *(const float4 *)&Bs[l][tc * 4];
+        const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int w = 0; w < 4; ++w) acc[u][w] += av[u] * bv[w];
+    }
+    float *C = strip ? A : X;
+    float cs[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        const int c = c0 + tc * 4 + w;
+        if (c >= climit) continue;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int r = r0 + tr * 4 + u;
+            if (r < n && (!strip || r > c)) {
+                const float v = C[(size_t)c * ld + r] - acc[u][w];
+                C[(size_t)c * ld + r] = v;
+                if (r >= base + kP) cs[w] += v;
+            }
+        }
+    }
+    if (strip) {
+        // the 16 threads with this tc are one half-warp (lanes tr = 0..15)
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            float v = cs[w];
+#pragma unroll
+            for (int o = 1; o < 16; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (tr == 0) csum[(size_t)blockIdx.x * kP + tc * 4 + w] = v;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kTT, 2)
-d32_update_kernel(int n, int ld, int k, int part, float *__restrict__ A, float *__restrict__ X,
-                  const float *__restrict__ LD, float *__restrict__ csum) {
+d32_update_kernel(int n, int ld, int k, float *__restrict__ A, float *__restrict__ X,
+                  const float *__restrict__ LD) {
     // two stages: slice s + 1 is fetched into registers while slice s is multiplied
     __shared__ __align__(16) float As[2][kKc][kTile];
     __shared__ __align__(16) float Bs[2][kKc][kTile];
-    const int base = k + kP;
-    const int t = (n - base + kTile - 1) / kTile;
-    const int tcn = (base + kTile - 1) / kTile;
+    const int base = k + kP, base2 = base + kP;
+    const int t = (n - base2 + kTile - 1) / kTile;   // row / column tiles from base2 on
+    const int tcn = (base + kTile - 1) / kTile;      // column tiles of the rows of L^-1
     const int idx = blockIdx.x;
-    bool tri;
+    const int ntri = t * (t + 1) / 2;                // trailing tiles, diagonal ones included
+    const bool tri = idx < ntri;
     int ti, tj;
-    if (part == 1) {
-        tri = idx < t;
-        ti = tri ? idx : 0;
-        tj = tri ? 0 : idx - t;
-    } else {
-        const int ntri2 = t * (t - 1) / 2;   // trailing tiles with tj >= 1
-        tri = idx < ntri2;
-        if (tri) {
-            tri_decode(idx, ti, tj);
-            ++ti;
-            ++tj;
-        } else {
-            const int q = idx - ntri2;       // inverse tiles with ti >= 1
-            ti = 1 + q / tcn;
-            tj = q % tcn;
-        }
-    }
-    int r0, c0, climit;
-    const int tile_i = ti, tile_j = tj;
     if (tri) {
-        r0 = base + ti * kTile;
-        c0 = base + tj * kTile;
-        climit = n;
+        tri_decode(idx, ti, tj);
     } else {
-        r0 = base + ti * kTile;
-        c0 = tj * kTile;
-        climit = base;
+        const int q = idx - ntri;
+        ti = q / tcn;
+        tj = q % tcn;
     }
+    const int r0 = base2 + ti * kTile;
+    const int c0 = tri ? base2 + tj * kTile : tj * kTile;
+    const int climit = tri ? n : base;
     // A operand (l, r) = Pa[l * ld + r]; B operand (l, c) = Pb[l * ld + c] (trailing) or
     // X[c * ld + k + l] (inverse)
     const float *Pa = tri ? LD : A + (size_t)k * ld;
@@ -489,8 +566,9 @@ d32_update_kernel(int n, int ld, int k, int part, float *__restrict__ A, float *
     float ra[8], rb[8];
     const int fl = threadIdx.x >> 4, fq = (threadIdx.x & 15) * 8;       // A (and trailing B) slot
     const int xc = threadIdx.x & (kTile - 1), xh = threadIdx.x >> 7;      // inverse B slot
+    const float *pa0 = Pa + (size_t)fl * ld + r0 + fq, *pb0 = Pb + (size_t)fl * ld + c0 + fq;
     auto fetch = [&](int l0) {
-        const float *src = Pa + (size_t)(l0 + fl) * ld + r0 + fq;
+        const float *src = pa0 + (size_t)l0 * ld;
         if (r0 + fq + 8 <= n) {
             const float4 v0 = *(const float4 *)src, v1 = *(const float4 *)(src + 4);
             ra[0] = v0.x; ra[1] = v0.y; ra[2] = v0.z; ra[3] = v0.w;
@@ -500,7 +578,7 @@ d32_update_kernel(int n, int ld, int k, int part, float *__restrict__ A, float *
             for (int u = 0; u < 8; ++u) ra[u] = (r0 + fq + u < n) ? src[u] : 0.f;
         }
         if (tri) {
-            const float *sb = Pb + (size_t)(l0 + fl) * ld + c0 + fq;
+            const float *sb = pb0 + (size_t)l0 * ld;
             if (c0 + fq + 8 <= climit) {
                 const float4 v0 = *(const float4 *)sb, v1 = *(const float4 *)(sb + 4);
                 rb[0] = v0.x; rb[1] = v0.y; rb[2] = v0.z; rb[3] = v0.w;
@@ -550,12 +628,6 @@ d32_update_kernel(int n, int ld, int k, int part, float *__restrict__ A, float *
         buf ^= 1;
     }
     float *C = tri ? A : X;
-    // the first column tile of the trailing part holds the next panel's columns: their sums below
-    // the next diagonal block (rows >= base + 64) go to csum[tile_i][.] (fixed-order partials)
-    const bool sums = tri && tile_j == 0 && tc < kP / 8;
-    float cs[8];
-#pragma unroll
-    for (int w = 0; w < 8; ++w) cs[w] = 0.f;
     const bool full = r0 + kTile <= n && c0 + kTile <= climit && (!tri || r0 > c0);
     if (full) {
 #pragma unroll
@@ -566,7 +638,6 @@ d32_update_kernel(int n, int ld, int k, int part, float *__restrict__ A, float *
             v1.x -= acc[4][w]; v1.y -= acc[5][w]; v1.z -= acc[6][w]; v1.w -= acc[7][w];
             *(float4 *)dst = v0;
             *(float4 *)(dst + 4) = v1;
-            cs[w] = ((v0.x + v0.y) + (v0.z + v0.w)) + ((v1.x + v1.y) + (v1.z + v1.w));
         }
     } else {
 #pragma unroll
@@ -576,25 +647,8 @@ d32_update_kernel(int n, int ld, int k, int part, float *__restrict__ A, float *
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const int r = r0 + tr * 8 + u;
-                if (r < n && (!tri || r > c)) {
-                    const float v = C[(size_t)c * ld + r] - acc[u][w];
-                    C[(size_t)c * ld + r] = v;
-                    if (r >= base + kP) cs[w] += v;
-                }
+                if (r < n && (!tri || r > c)) C[(size_t)c * ld + r] -= acc[u][w];
             }
-        }
-    }
-    if (tri && tile_j == 0) {
-        // rows of the next diagonal block (tile 0, rows < base + 64) are not part of the sums; a
-        // full tile 0 starts at base, so its first 64 rows are dropped here
-        const bool drop = full && tile_i == 0 && tr * 8 < kP;
-#pragma unroll
-        for (int w = 0; w < 8; ++w) {
-            float v = (sums && !drop) ? cs[w] : 0.f;
-            // the 16 threads with this tc are lanes tr = 0..15 of one half-warp
-#pragma unroll
-            for (int o = 1; o < 16; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (sums && tr == 0) csum[tile_i * kP + tc * 8 + w] = v;
         }
     }
 }
@@ -688,7 +742,7 @@ Error d32_alloc(Dense32 &F, int32_t n) {
     OT_CUDA(cudaMalloc((void **)&F.Linv, sizeof(float) * (size_t)F.ld * kP));
     OT_CUDA(cudaMalloc((void **)&F.D, sizeof(float) * n));
     OT_CUDA(cudaMalloc((void **)&F.d0, sizeof(float) * n));
-    OT_CUDA(cudaMalloc((void **)&F.csum, sizeof(float) * kP * (size_t)ceil_div(n, kTile)));
+    OT_CUDA(cudaMalloc((void **)&F.csum, sizeof(float) * kP * (size_t)ceil_div(n, kP)));
     OT_CUDA(cudaMalloc((void **)&F.w, sizeof(float) * n));
     OT_CUDA(cudaMalloc((void **)&F.part, sizeof(float) * (size_t)F.ld * (size_t)ceil_div(n, kFc)));
     // lower bound of the unwritten upper parts, so that nothing uninitialised is ever read
@@ -810,16 +864,17 @@ static Error d32_build(Dense32 &F, float eps, cudaGraph_t g, int64_t *nodes) {
         for (cudaGraphNode_t r : ready) c.priority(r, hi_prio);
         if (u2) ready.push_back(u2);
         if (base < n) {
-            const int t = (int)ceil_div(n - base, kTile), tcn = (int)ceil_div(base, kTile);
-            u1 = c.kernel(ready, d32_update_kernel, (unsigned)(t + tcn), kTT, n, ld, k, 1, F.A, F.X,
+            const int ts = (int)ceil_div(n - base, kP), tx = (int)ceil_div(base, kP);
+            u1 = c.kernel(ready, d32_update1_kernel, (unsigned)(ts + tx), kTT, n, ld, k, F.A, F.X,
                           (const float *)LDp, F.csum);
             c.priority(u1, hi_prio);
-            const int n2 = t * (t - 1) / 2 + (t - 1) * tcn;
-            u2 = n2 > 0 ? c.kernel(ready, d32_update_kernel, (unsigned)n2, kTT, n, ld, k, 2, F.A, F.X,
-                                   (const float *)LDp, F.csum)
+            const int base2 = base + kP;
+            const int t2 = base2 < n ? (int)ceil_div(n - base2, kTile) : 0, tcn = (int)ceil_div(base, kTile);
+            const int n2 = t2 * (t2 + 1) / 2 + t2 * tcn;
+            u2 = n2 > 0 ? c.kernel(ready, d32_update_kernel, (unsigned)n2, kTT, n, ld, k, F.A, F.X, (const float *)LDp)
                         : nullptr;
             c.priority(u2, lo_prio);
-            np = t;
+            np = ts;
         } else {
             // the last panel: join everything so the graph ends after all writes
             prev = c.join(ready);
