@@ -209,7 +209,7 @@ def pricing_at(torch, synth, k: int, seed: int, reps: int = 5):
             "gather_pass": table.get("scan_gather")}
 
 
-def run_batch(torch, synth, count: int = 64, workers: int = 8):
+def run_batch(torch, synth, count: int = 64, workers: int = 2):
     """64 uneven instances (sides 24..96, seeded), autotuned launch shapes, solved through the
     library's queue with `workers` host threads and with one; wall time around each whole batch
     (creation, solve, destruction: every host-device copy included)."""
@@ -228,7 +228,7 @@ def run_batch(torch, synth, count: int = 64, workers: int = 8):
     for w in (workers, 1):
         torch.cuda.synchronize()
         t = time.perf_counter()
-        res = solve_batch(pairs, workers=w, tuning=autotune.lookup, create_threads=w)
+        res = solve_batch(pairs, workers=w, tuning=autotune.lookup, create_threads=8)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t
         ok = sum(1 for r in res if r.status == 0)

@@ -166,9 +166,8 @@ int ot_ipm_step(ot_ipm_t *h, ot_iter_info *info);
 int ot_ipm_solve(ot_ipm_t *h, ot_result *res);
 
 /* Solve `count` independent instances (handles from ot_ipm_create, each with its own stream)
- * with `workers` host threads (0 = 8): instances of at least 2500^2 pairs, which fill the GPU on
- * their own, run one at a time, largest first; the smaller ones run concurrently on the other
- * workers.  res[i] receives instance i's result and status.  Returns OT_OK when every instance
+ * with `workers` host threads (0 = 2) drawing from one queue, largest instance (m * n) first.
+ * res[i] receives instance i's result and status.  Returns OT_OK when every instance
  * succeeded, else the first failing status.  Handles must be distinct and must not be used by
  * other threads meanwhile. */
 int ot_ipm_solve_batch(ot_ipm_t *const *handles, int32_t count, ot_result *res, int32_t workers);

@@ -224,7 +224,7 @@ def kernel_launches() -> int:
     return int(_lib.load().ot_kernel_launches())
 
 
-def solve_batch(pairs, workers: int = 8, tuning=None, create_threads: int = 8, errors: list | None = None, **options):
+def solve_batch(pairs, workers: int = 2, tuning=None, create_threads: int = 8, errors: list | None = None, **options):
     """Solve independent instances concurrently (``ot_ipm_solve_batch``).
 
     pairs: sequence of (a, b, side) for k x k pixel grids (side = k).  tuning: optional callable

@@ -86,7 +86,7 @@ constexpr int kDirectCgMany = 25;
 constexpr int kDenseMaxN = 8192;
 constexpr int kDense32MaxN = 8192;
 constexpr int kDense32LateMaxN = 16384;  // late iterations above kDenseMaxN: FP32 dense factor
-constexpr int64_t kBatchLargeMN = 2500LL * 2500;  // a batch instance this large runs alone
+constexpr int kBatchWorkers = 2;            // host threads of a batch (ot_ipm_solve_batch)
 constexpr int kWarmCheck = 5;       // a warm start is judged from this iteration on ...
 constexpr int kWarmSettle = 15;     // ... up to this one
 constexpr double kWarmGrowth = 2.0; // abandoned when mu exceeds this multiple of its first value  // mixed precision: FP32 dense factor preconditions every solve
@@ -965,45 +965,33 @@ int ot_ipm_solve_batch(ot_ipm_t *const *hs, int32_t count, ot_result *res, int32
             return OT_ERR_ARG;
         }
     if (count == 0) return OT_OK;
-    const int nw = std::max(1, std::min<int32_t>(workers > 0 ? workers : 8, count));
-    // Two queues, largest first.  An instance of at least kBatchLargeMN pairs keeps the GPU busy
-    // on its own (its dense factorisations fill every SM), and two of them at once only contend,
-    // so they run one at a time on worker 0; the others run concurrently on the remaining workers,
-    // which worker 0 joins once the large queue is empty.
-    std::vector<int32_t> big, small;
-    for (int32_t i = 0; i < count; ++i)
-        ((int64_t)hs[i]->m * hs[i]->n >= kBatchLargeMN ? big : small).push_back(i);
-    auto by_size = [&](int32_t x, int32_t y) {
+    const int nw = std::max(1, std::min<int32_t>(workers > 0 ? workers : kBatchWorkers, count));
+    // One queue, largest instance first, drained by nw host threads (one stream per handle).  The
+    // mixed solve of one instance leaves the GPU partly idle (its factorisation is a chain of
+    // latency-bound launches, its refinement CG waits on host checks), so a second instance in
+    // flight fills the gaps; more than two contend for the SMs the chains wait on.
+    std::vector<int32_t> order(count);
+    for (int32_t i = 0; i < count; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
         return (int64_t)hs[x]->m * hs[x]->n > (int64_t)hs[y]->m * hs[y]->n;
-    };
-    std::sort(big.begin(), big.end(), by_size);
-    std::sort(small.begin(), small.end(), by_size);
-    if (nw == 1) {
-        big.insert(big.end(), small.begin(), small.end());
-        small.clear();
-    }
-    std::atomic<size_t> next_big{0}, next_small{0};
+    });
+    std::atomic<size_t> next{0};
     auto run = [&](int32_t i) {
         cudaSetDevice(hs[i]->device);
         std::memset(&res[i], 0, sizeof(ot_result));
         res[i].status = ot_ipm_solve(hs[i], &res[i]);
     };
-    auto drain_small = [&]() {
+    auto drain = [&]() {
         for (;;) {
-            const size_t q = next_small.fetch_add(1);
-            if (q >= small.size()) break;
-            run(small[q]);
+            const size_t q = next.fetch_add(1);
+            if (q >= order.size()) break;
+            run(order[q]);
         }
     };
     std::vector<std::thread> pool;
     pool.reserve(nw - 1);
-    for (int t = 1; t < nw; ++t) pool.emplace_back(drain_small);
-    for (;;) {
-        const size_t q = next_big.fetch_add(1);
-        if (q >= big.size()) break;
-        run(big[q]);
-    }
-    drain_small();
+    for (int t = 1; t < nw; ++t) pool.emplace_back(drain);
+    drain();
     for (auto &t : pool) t.join();
     for (int32_t i = 0; i < count; ++i)
         if (res[i].status != OT_OK) {
