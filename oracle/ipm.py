@@ -8,7 +8,7 @@ update, pricing, support update).  The Newton direction is computed exactly (a d
 solve of the Schur complement, its pseudo-inverse on each connected component) because
 this is the definition the GPU's iterative and direct solvers approximate.
 
-Readings where the paper is silent (each listed in the design doc as well):
+Readings where the paper is silent:
   * data scale: masses are scaled internally to mean 1 (sigma_f = m / sum a); the LP
     solution scales exactly with it and results are reported in the caller's units;
   * initial support: pairs with c_ij <= init_cost (2 on pixel grids: the 3x3 neighbourhood),
