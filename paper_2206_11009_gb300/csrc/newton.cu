@@ -926,36 +926,6 @@ __global__ void axpy_kernel(int64_t count, double a, const double *__restrict__ 
 }
 
 
-// y = S_M x ; partial x.y  (host-driven PCG with the LDL^T preconditioner)
-__global__ void mv_cols_kernel(int n, const int32_t *__restrict__ cp, const int32_t *__restrict__ crow,
-                               const double *__restrict__ thc, const double *__restrict__ w,
-                               const double *__restrict__ x, double *__restrict__ y, double *part) {
-    __shared__ double sh[kT / 32];
-    double acc2 = 0;
-    GRID_STRIDE(j, n) {
-        const double xj = x[j];
-        double acc = 0;
-        for (int k = cp[j]; k < cp[j + 1]; ++k) acc += thc[k] * (xj - w[crow[k]]);
-        y[j] = acc;
-        acc2 += xj * acc;
-    }
-    put_sum(acc2, part, SC_SUM_A, sh);
-}
-
-// x += a p ; r -= a q ; partial r.r
-__global__ void pcg_step_kernel(int n, double a, const double *__restrict__ p, const double *__restrict__ q,
-                                double *__restrict__ x, double *__restrict__ r, double *part) {
-    __shared__ double sh[kT / 32];
-    double rr = 0;
-    GRID_STRIDE(j, n) {
-        x[j] += a * p[j];
-        const double rj = r[j] - a * q[j];
-        r[j] = rj;
-        rr += rj * rj;
-    }
-    put_sum(rr, part, SC_NORM_A, sh);
-}
-
 __global__ void dot_kernel(int n, const double *__restrict__ a, const double *__restrict__ b, double *part,
                            int slot) {
     __shared__ double sh[kT / 32];
@@ -966,31 +936,6 @@ __global__ void dot_kernel(int n, const double *__restrict__ a, const double *__
 
 // p = z + b p   (b = 0 starts the recurrence)
 __global__ void pcg_dir_kernel(int n, double b, const double *__restrict__ z, double *__restrict__ p) {
-    GRID_STRIDE(j, n) p[j] = z[j] + b * p[j];
-}
-
-// the same two steps with alpha = r.z / p.q and beta = r.z(new) / r.z(old) read from the device
-// scalars (no host round trip; a non-positive denominator makes the step a no-op)
-__global__ void dcg_step_kernel(int n, const double *__restrict__ scal, int rz_slot, const double *__restrict__ p,
-                                const double *__restrict__ q, double *__restrict__ x, double *__restrict__ r,
-                                double *part) {
-    __shared__ double sh[kT / 32];
-    const double pq = scal[SC_SUM_A], rz = scal[rz_slot];
-    const double a = (pq > 0 && rz > 0) ? rz / pq : 0.0;
-    double rr = 0;
-    GRID_STRIDE(j, n) {
-        x[j] += a * p[j];
-        const double rj = r[j] - a * q[j];
-        r[j] = rj;
-        rr += rj * rj;
-    }
-    put_sum(rr, part, SC_NORM_A, sh);
-}
-
-__global__ void dcg_dir_kernel(int n, const double *__restrict__ scal, int old_slot, int new_slot,
-                               const double *__restrict__ z, double *__restrict__ p) {
-    const double rzo = scal[old_slot], rzn = scal[new_slot];
-    const double b = (rzo > 0 && rzn > 0) ? rzn / rzo : 0.0;
     GRID_STRIDE(j, n) p[j] = z[j] + b * p[j];
 }
 
