@@ -1102,7 +1102,7 @@ static Error solve_mixed(Newton &W, const Support &S, double tol, int max_cg, do
     OT_CUDA(cudaMemsetAsync(dv, 0, sizeof(double) * W.n, st));
     copy_kernel<<<gn, kT, 0, st>>>(W.n, W.rhs, W.res64);
     OT_LAUNCHED();
-    double nrm0;
+    double nrm0 = 0.0;
     OT_TRY(rhs_norm(W, &nrm0, st));
     double nrm = nrm0;
     int budget = max_cg;
