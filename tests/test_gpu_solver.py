@@ -50,6 +50,18 @@ def test_solve_reaches_exact_optimum(precision, k, seed, spike):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("k,seed", [(16, 0), (16, 3), (32, 1)])
+def test_papers_new_pair_rule_reaches_exact_optimum(precision, k, seed):
+    """Section 3.2's rule for new pairs (p = s = sqrt(mu), new_col_rule 0) end to end."""
+    inst = synth.image_pair(k, seed)
+    opt = U.opt_value(k, seed)
+    r, _ = _solve(inst, k, tol=1e-8, precision=precision, new_col_rule=0)
+    assert r.status == 0, r
+    assert abs(r.obj - opt) <= 1e-6 * opt
+    assert r.r1_l1 <= 1e-8 and r.rel_gap <= 1e-8
+
+
+@pytest.mark.parametrize("precision", [0, 1])
 def test_config2_64x64(precision):
     """64x64 image pair (16.8M variables) at tol 1e-6, both precisions, against the exact optimum."""
     k = 64
@@ -66,14 +78,16 @@ def test_config2_64x64(precision):
         assert r.cg_iters <= 60 * r.iters
 
 
-def test_one_iteration_matches_oracle():
+@pytest.mark.parametrize("rule", [1, 0])
+def test_one_iteration_matches_oracle(rule):
     """From the oracle's iterate after a few iterations, one GPU iteration (tight CG tolerance)
-    reproduces mu, the stopping measure, the step lengths, sigma, the new duals and the new support."""
+    reproduces mu, the stopping measure, the step lengths, sigma, the new duals and the new support.
+    rule 0 is Section 3.2's p = s = sqrt(mu) for new pairs, rule 1 the capped variant."""
     from paper_2206_11009_gb300 import Solver
     k = 10
     inst = synth.image_pair(k, 1)
     c = costs.square_grid(k)
-    opt = ipm.Options(tol=1e-8)
+    opt = ipm.Options(tol=1e-8, new_col_rule=rule)
     prob = ipm.Problem(c, inst.a, inst.b)
     I, J = ipm.initial_support(prob, opt)
     st = ipm.initial_point(prob, I, J)
@@ -85,7 +99,7 @@ def test_one_iteration_matches_oracle():
     new, lg, stepped, (aI, aJ, aD), rem = ipm.one_iteration(prob, st, res, opt, tr, 4)
 
     with Solver(inst.a, inst.b, grid=(k, k), tol=1e-8, precision=0, cg_tol_pred=1e-13, cg_tol_corr=1e-13,
-                max_cg=20000) as s:
+                max_cg=20000, new_col_rule=rule) as s:
         assert abs(s.mass_scale - prob.sigma_f) <= 1e-15 * prob.sigma_f
         s.set_state(st.I, st.J, st.p, st.s, st.u, st.v, reset_mu0=True)
         info = s.step()

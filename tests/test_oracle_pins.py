@@ -232,13 +232,140 @@ def test_removal_keeps_last_entry_of_each_row_and_column():
 
 # ----------------------------------------------------------------------------- O2 vs O1
 
+@pytest.mark.parametrize("rule", [1, 0])
 @pytest.mark.parametrize("k,seed,spike", [(6, 0, 0.0), (8, 1, 0.0), (8, 2, 0.05), (12, 3, 0.0), (16, 0, 0.0)])
-def test_ipm_oracle_reaches_exact_optimum(k, seed, spike):
+def test_ipm_oracle_reaches_exact_optimum(k, seed, spike, rule):
+    """Both new-pair rules: rule 0 is Section 3.2's p = s = sqrt(mu); rule 1 caps the flow."""
     inst = synth.image_pair(k, seed, spike_frac=spike)
     c = costs.square_grid(k)
     ref = netsimplex.solve(c, inst.a, inst.b)
-    r = ipm.solve(c, inst.a, inst.b, ipm.Options(tol=1e-8))
+    r = ipm.solve(c, inst.a, inst.b, ipm.Options(tol=1e-8, new_col_rule=rule))
     assert r.status == "optimal"
     assert abs(r.obj - ref.obj) <= 1e-7 * ref.obj
     assert r.r1_l1 <= 1e-8
     assert r.lb <= ref.obj * (1 + 1e-12) and r.gap <= 1e-8
+
+
+def test_new_pairs_enter_at_sqrt_mu_under_the_papers_rule():
+    """Section 3.2: a pair added by pricing starts at p = s = sqrt(mu); rule 1 keeps p s = mu
+    with p capped at min(a_i, b_j)."""
+    k = 8
+    inst = synth.image_pair(k, 1)
+    c = costs.square_grid(k)
+    prob = ipm.Problem(c, inst.a, inst.b)
+    I, J = ipm.initial_support(prob, ipm.Options())
+    st0 = ipm.initial_point(prob, I, J)
+    for rule in (0, 1):
+        opt = ipm.Options(new_col_rule=rule)
+        tr = ipm.Tracker()
+        _, res, _ = ipm.stop_test(prob, st0, opt, tr)
+        st1, lg, stepped, (aI, aJ, _), rem = ipm.one_iteration(prob, st0, res, opt, tr)
+        assert len(aI) > 0 and len(rem) == 0
+        mu_new = float(stepped.p @ stepped.s) / len(stepped.p)
+        key = st1.I * (k * k) + st1.J
+        pos = np.searchsorted(key, aI * (k * k) + aJ)
+        p_new, s_new = st1.p[pos], st1.s[pos]
+        r = np.sqrt(mu_new)
+        if rule == 0:
+            assert np.all(p_new == r) and np.all(s_new == r)
+        else:
+            cap = np.minimum(prob.as_[aI], prob.bs[aJ])
+            assert np.allclose(p_new, np.minimum(r, cap), rtol=0, atol=0)
+            assert np.allclose(p_new * s_new, mu_new, rtol=1e-14)
+
+
+# ----------------------------------------------------------------------------- certificate
+
+def test_min_reduced_cost_hand_fixture():
+    """min over all pairs of (c_ij - u_i) - v_j, worked out by hand:
+       C = [[4, 1, 3], [2, 5, 0]], u = (1, -2), v = (0, 3, -1)
+       d = [[3, -3, 3], [4, 4, 3]]  ->  -3 at (0, 1)."""
+    C = np.array([[4.0, 1.0, 3.0], [2.0, 5.0, 0.0]])
+    u = np.array([1.0, -2.0])
+    v = np.array([0.0, 3.0, -1.0])
+    assert certificate.min_reduced_cost(costs.Cost.dense(C), u, v) == -3.0
+    # dual feasible after the c-transform of v: u_i = min_j (c_ij - v_j) makes the minimum 0
+    ubar = np.array([min(C[i, j] - v[j] for j in range(3)) for i in range(2)])
+    assert certificate.min_reduced_cost(costs.Cost.dense(C), ubar, v) == 0.0
+
+
+@pytest.mark.parametrize("kind", ["sqeuclid", "euclid", "l1", "linf"])
+def test_min_reduced_cost_matches_python_loops(kind):
+    """Against pure-Python loops over every pair, on point sets with a row count that spans
+    several of the function's row chunks."""
+    m, n = 37, 29
+    rng = synth.uniform01(4242, 2 * m + 2 * n + m + n)
+    sx, sy = np.floor(rng[:m] * 9), np.floor(rng[m:2 * m] * 9)
+    tx, ty = np.floor(rng[2 * m:2 * m + n] * 9), np.floor(rng[2 * m + n:2 * m + 2 * n] * 9)
+    u = rng[2 * m + 2 * n:2 * m + 2 * n + m] * 20 - 5
+    v = rng[2 * m + 2 * n + m:] * 20 - 5
+    c = costs.Cost.points(sx, sy, tx, ty, kind)
+    f = {"sqeuclid": lambda dx, dy: dx * dx + dy * dy,
+         "euclid": lambda dx, dy: float(np.sqrt(dx * dx + dy * dy)),
+         "l1": lambda dx, dy: abs(dx) + abs(dy),
+         "linf": lambda dx, dy: max(abs(dx), abs(dy))}[kind]
+    best = min((f(float(sx[i] - tx[j]), float(sy[i] - ty[j])) - float(u[i])) - float(v[j])
+               for i in range(m) for j in range(n))
+    assert certificate.min_reduced_cost(c, u, v) == best
+
+
+# ----------------------------------------------------------------------------- removal guard
+
+def _n_components(m, n, I, J):
+    parent = list(range(m + n))
+
+    def find(x):
+        while parent[x] != x:
+            x = parent[x]
+        return x
+
+    for i, j in zip(I.tolist(), J.tolist()):
+        a, b = find(i), find(m + j)
+        if a != b:
+            parent[a] = b
+    # vertices that carry at least one edge, counted by their roots
+    used = set(I.tolist()) | {m + j for j in J.tolist()}
+    return len({find(x) for x in used})
+
+
+def test_removal_guard_breaks_a_cycle_at_its_lightest_edge():
+    """Hand-built case: sources {0, 1}, targets {0, 1}, all four pairs in the support (one
+    4-cycle), every pair a removal candidate.  The maximum-weight spanning forest (Kruskal by
+    decreasing p) keeps the three heaviest edges, so exactly the lightest one may leave and the
+    support stays one connected component."""
+    m = n = 2
+    prob = ipm.Problem(costs.Cost.dense(np.array([[0.0, 1.0], [1.0, 0.0]])), np.array([0.5, 0.5]),
+                       np.array([0.5, 0.5]))
+    I = np.array([0, 0, 1, 1], dtype=np.int64)
+    J = np.array([0, 1, 0, 1], dtype=np.int64)
+    p = np.array([4e-9, 3e-9, 1e-9, 2e-9])        # lightest: (1, 0)
+    st = ipm.State(I, J, p, np.ones(4), np.zeros(m), np.zeros(n))
+    rem = ipm.removal_select(prob, st, ipm.Options(), kmax=4)
+    assert rem.tolist() == [2]
+    keep = np.ones(4, bool)
+    keep[rem] = False
+    assert _n_components(m, n, I[keep], J[keep]) == 1
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_removal_guard_keeps_the_component_count(seed):
+    """Random supports with many cycles, every pair a candidate: the number of connected
+    components of the support graph is the same before and after removal."""
+    k = 5
+    m = n = k * k
+    inst = synth.image_pair(k, seed)
+    prob = ipm.Problem(costs.square_grid(k), inst.a, inst.b)
+    rng = synth.uniform01(900 + seed, m * n + m * n)
+    mask = rng[:m * n].reshape(m, n) < 0.15
+    I, J = np.nonzero(mask)
+    I, J = I.astype(np.int64), J.astype(np.int64)
+    p = 1e-12 * (1.0 + rng[m * n:m * n + len(I)])
+    st = ipm.State(I, J, p, np.ones(len(I)), np.zeros(m), np.zeros(n))
+    before = _n_components(m, n, I, J)
+    rem = ipm.removal_select(prob, st, ipm.Options(), kmax=m * n)
+    keep = np.ones(len(I), bool)
+    keep[rem] = False
+    assert len(rem) > 0
+    assert _n_components(m, n, I[keep], J[keep]) == before
+    # what is left is a forest exactly when nothing else held the removal back (kmax large)
+    assert certificate.is_forest(m, n, I[keep], J[keep])
