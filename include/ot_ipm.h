@@ -52,7 +52,16 @@ typedef enum {
 } ot_cost_kind;
 
 /* Problem statement (Section 2: a in R^m_+, b in R^n_+, cost matrix C in R^{m x n}_+).
- * All pointers are HOST pointers; they are copied by ot_ipm_create. */
+ * The pointers are HOST pointers unless inputs_on_device is set, in which case every one of them
+ * (a, b, the coordinates, C) is a device pointer on the current device.  ot_ipm_create copies
+ * what it needs and keeps no caller pointer.
+ *
+ * Zero masses (input handling; the paper does not discuss them): a source i with a_i = 0 or a
+ * target j with b_j = 0 carries no flow in any feasible coupling, so it is removed before the
+ * solve (presolve).  Every entry point below still speaks in the caller's indices: couplings are
+ * reported on the original (i, j), and ot_ipm_get_solution completes the duals of removed points
+ * by the c-transform (u_i = min_j c_ij - v_j over the kept targets, then v_j = min_i c_ij - u_i
+ * over all sources), which keeps (u, v) dual feasible wherever the solve's duals are. */
 typedef struct {
     int32_t m, n;
     const double *a;          /* m source masses                                              */
@@ -63,7 +72,9 @@ typedef struct {
      * at (j mod dst_w, j div dst_w) (m = src_w*src_h, n = dst_w*dst_h). */
     const int32_t *src_x, *src_y, *dst_x, *dst_y;
     int32_t src_w, dst_w;
-    const double *C;          /* OT_COST_DENSE only: m x n row-major, C[i*n + j]              */
+    const double *C;          /* OT_COST_DENSE only: m x n row-major, C[i*n + j], finite, >= 0,  */
+                              /* m*n <= 2^30                                                  */
+    int32_t inputs_on_device; /* 0: host pointers; 1: device pointers (see above)             */
 } ot_problem;
 
 typedef struct {
@@ -114,6 +125,13 @@ typedef struct {
     /* Largest n for which the direct branch factors S_M densely in FP64 (at most 8192; 0 = 8192,
      * -1: never, the sparse LDL^T of Section 4.2 instead). */
     int32_t dense_max_n;
+    /* Heuristic pricing set of Section 3.4: jset_cmax > 0 prices only the pairs of
+     * J = {(i, j) : c_ij < jset_cmax} (listed once, on the first such iteration), except on every
+     * jset_refresh-th iteration (iterations jset_refresh-1, 2*jset_refresh-1, ...), which prices all
+     * m*n pairs; 0 = 3 (the paper refreshes every 3 or 4 iterations).  jset_cmax <= 0: every
+     * iteration prices all pairs.  The stopping test's certificate always covers all pairs. */
+    double jset_cmax;
+    int32_t jset_refresh;
 } ot_options;
 
 /* One outer iteration (Section 3.4's commented listing). */
@@ -152,9 +170,9 @@ typedef struct ot_ipm ot_ipm_t;
 /* Fill *opt with the paper's defaults (Section 5.2) and this library's readings. */
 void ot_options_default(ot_options *opt);
 
-/* Validate and copy the problem to the device, build the initial support (Section 3.2 end) and
- * the initial point.  On success *out owns all device state.  Errors: OT_ERR_ARG, OT_ERR_OOM,
- * OT_ERR_CUDA, OT_ERR_UNSUPPORTED (cost kind not built). */
+/* Validate and copy the problem to the device, presolve zero masses, build the initial support
+ * (Section 3.2 end) and the initial point.  On success *out owns all device state.  Errors:
+ * OT_ERR_ARG (sizes, masses, coordinates, a negative or non-finite C), OT_ERR_OOM, OT_ERR_CUDA. */
 int ot_ipm_create(const ot_problem *prob, const ot_options *opt, ot_ipm_t **out);
 
 /* One outer iteration: residuals, stopping test, predictor-corrector Newton direction,
@@ -178,15 +196,16 @@ int ot_ipm_solve_batch(ot_ipm_t *const *handles, int32_t count, ot_result *res, 
 int ot_ipm_get_solution(ot_ipm_t *h, int32_t *i, int32_t *j, double *p, int64_t cap,
                         int64_t *nnz, double *u, double *v);
 
-/* Full iterate in the solver's internal scaling (masses scaled by m/sum(a)): support pairs
- * sorted by (i, j), p, s, and u, v.  Same buffer rules as ot_ipm_get_solution.  Used for
+/* Full iterate in the solver's internal scaling (masses scaled by m'/sum(a), m' the number of
+ * sources with positive mass): support pairs sorted by (i, j), p, s, and u, v (entries of points
+ * removed by the presolve are 0).  Same buffer rules as ot_ipm_get_solution.  Used for
  * checkpoints and to compare single steps with a reference. */
 int ot_ipm_get_state(ot_ipm_t *h, int32_t *i, int32_t *j, double *p, double *s, int64_t cap,
                      int64_t *psi, double *u, double *v);
 
-/* Replace the iterate (host buffers, internal scaling).  Pairs must be distinct, in range and
- * sorted by (i, j); p, s > 0.  Resets the iteration counter's mu_0 reference only if
- * reset_mu0 != 0. */
+/* Replace the iterate (host buffers, internal scaling).  Pairs must be distinct, in range,
+ * sorted by (i, j) and free of points removed by the presolve; p, s > 0 (u, v entries of removed
+ * points are ignored).  Resets the iteration counter's mu_0 reference only if reset_mu0 != 0. */
 int ot_ipm_set_state(ot_ipm_t *h, const int32_t *i, const int32_t *j, const double *p,
                      const double *s, int64_t psi, const double *u, const double *v,
                      int32_t reset_mu0);
@@ -250,22 +269,50 @@ int ot_price_topk(int32_t m, int32_t n, const int32_t *sx, const int32_t *sy,
                   int32_t precision, int32_t *out_i, int32_t *out_j, double *out_d,
                   int32_t *out_count, void *stream);
 
+/* Options of ot_price_topk_ex (zero-initialise, then set what differs). */
+typedef struct {
+    int32_t cost;        /* ot_cost_kind; the distance kinds use the coordinates (Section 5.1),    */
+                         /* OT_COST_DENSE uses C (and always scans in FP64)                         */
+    int32_t scan_rows;   /* 0: the library's rule; else 8..256 source rows per scan tile            */
+    double jset_cmax;    /* > 0: only the pairs with c_ij < jset_cmax are priced (the set J of       */
+                         /* Section 3.4, listed inside the call); <= 0: all m*n pairs                 */
+    const double *C;     /* OT_COST_DENSE: m x n row-major costs (device); NULL otherwise           */
+} ot_price_opts;
+
+/* ot_price_topk for any cost kind, with an explicit scan tile height and the heuristic set J.
+ * The selection rule is the same with c_ij the chosen cost: d_ij = (c_ij - u_i) - v_j in IEEE
+ * float64 (the Euclidean distance is the correctly rounded square root of the integer dx^2 + dy^2),
+ * candidates outside the support with d_ij < 0 (and, with jset_cmax > 0, c_ij < jset_cmax), order
+ * (d_ij, jlin), first min(kmax, #candidates).  precision 1 scans the distance kinds in FP32 with a
+ * proven error window and rechecks in FP64.  opts may be NULL (squared cost, full scan).  The
+ * coordinates may be NULL for OT_COST_DENSE.  Errors as ot_price_topk. */
+int ot_price_topk_ex(int32_t m, int32_t n, const int32_t *sx, const int32_t *sy,
+                     const int32_t *tx, const int32_t *ty, const double *u, const double *v,
+                     const int32_t *sup_i, const int32_t *sup_j, int64_t psi, int32_t kmax,
+                     int32_t precision, int32_t *out_i, int32_t *out_j, double *out_d,
+                     int32_t *out_count, const ot_price_opts *opts, void *stream);
+
 /* ot_price_topk without any device allocation.  The paper has no counterpart: this exists for
  * callers that cannot allocate device memory while they run -- for example a serving process
  * that reserved its whole memory budget at start-up, where a further cudaMalloc would fail or
- * evict its caches, or a latency-critical loop that must not pay the implicit device-wide
- * synchronisation an allocation or release can cause.
+ * evict its caches, or a loop that must not pay the implicit device-wide synchronisation an
+ * allocation or release can cause.
  *
  * Same arguments, outputs and selection as ot_price_topk.  All temporary buffers come from one
- * fixed 24 MiB array in device memory, declared statically in the library, so every GPU that
- * loads the library holds those 24 MiB until the process exits.  Limits: m, n <= 16384, and the
- * candidate set the selection has to recheck must fit the array (about 400k pairs); beyond either
- * limit the call returns OT_ERR_ARG or OT_ERR_BUF_TOO_SMALL with a message (ot_last_error) and
- * changes no output.  The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture.  Every call on a device uses
- * the same array and leaves its contents behind (each call clears what it needs), so calls that
- * overlap on the GPU -- on two streams, or from two threads -- race and must be serialised by
- * the caller.  No cudaMalloc, cudaFree or allocating library routine is called. */
+ * fixed 24 MiB array in device memory, declared statically in the library.  The array belongs to
+ * the library's device module, which CUDA loads on a device when it is first needed (lazy
+ * loading): in practice at the first call of this function on that device, which can then fail
+ * with OT_ERR_CUDA if the device has no 24 MiB left.  A caller that reserves its memory budget at
+ * start-up should therefore make one call on every device it uses before it reserves; from then
+ * on the device holds those 24 MiB until the process exits.  Every call looks up the array's
+ * device address (with the calling thread's current device); make the first call on a device
+ * before any stream capture.  Limits: m, n <= 16384, and the candidate set the selection has to
+ * recheck must fit the array (about 400k pairs); beyond either limit the call returns OT_ERR_ARG
+ * or OT_ERR_BUF_TOO_SMALL with a message (ot_last_error) and changes no output.  Every call on a
+ * device uses the same array and leaves its contents behind (each call clears what it needs), so
+ * calls that overlap on the GPU -- on two streams, or from two threads -- race and must be
+ * serialised by the caller.  The call synchronises its stream twice (to size the candidate set)
+ * before it returns.  No cudaMalloc, cudaFree or allocating library routine is called. */
 int ot_price_topk_noalloc(int32_t m, int32_t n, const int32_t *sx, const int32_t *sy,
                           const int32_t *tx, const int32_t *ty, const double *u, const double *v,
                           const int32_t *sup_i, const int32_t *sup_j, int64_t psi, int32_t kmax,

@@ -27,7 +27,8 @@ Readings where the paper is silent:
   * Schur complement S_M = N - V^T M^-1 V (Section 4), singular: right-hand side projected
     to mean zero on each connected component of the support graph, minimum-norm dv;
   * support enlargement: at most m new pairs (the most negative reduced costs, exact rule
-    of ``oracle.pricing``).  Section 3.2 starts them at p = s = sqrt(mu) (``new_col_rule`` 0);
+    of ``oracle.pricing``; with ``jset_cmax`` > 0 only pairs of Section 3.4's set
+    J = {c_ij < jset_cmax} are priced, except on every ``jset_refresh``-th iteration).  Section 3.2 starts them at p = s = sqrt(mu) (``new_col_rule`` 0);
     the default (``new_col_rule`` 1) keeps the product p s = mu but caps the flow at the pair's
     smaller scaled mass, p = min(sqrt(mu), a_i, b_j), s = mu / p: with masses scaled to sum m,
     sqrt(mu) can exceed a pixel's whole mass many times over while mu is still large, and m such
@@ -67,6 +68,8 @@ class Options:
     init_cost: float = 2.0
     add_max: int | None = None      # default m
     new_col_rule: int = 1           # 0: p = s = sqrt(mu) as Section 3.2; 1: flow capped at min(a_i, b_j)
+    jset_cmax: float = 0.0          # > 0: Section 3.4's heuristic set J = {c_ij < jset_cmax} ...
+    jset_refresh: int = 3           # ... between full pricings on iterations refresh-1, 2 refresh-1, ...
 
 
 @dataclass
@@ -427,7 +430,8 @@ def one_iteration(prob: Problem, st: State, res: Residuals, opt: Options, tr: Tr
     d, ap, as_, sigma, ncorr = predictor_corrector(prob, st, res, opt)
     st = State(st.I, st.J, st.p + ap * d.dp, st.s + as_ * d.ds, st.u + as_ * d.du, st.v + as_ * d.dv)
     mu_new = float(st.p @ st.s) / psi
-    aI, aJ, aD = pricing.select(prob.cost, st.u, st.v, st.I, st.J, kadd)
+    use_j = opt.jset_cmax > 0 and it % opt.jset_refresh != opt.jset_refresh - 1
+    aI, aJ, aD = pricing.select(prob.cost, st.u, st.v, st.I, st.J, kadd, cmax=opt.jset_cmax if use_j else None)
     c_red_max = float(np.abs(res.c_red).max()) if psi else 0.0
     tr.strong = int((aD < -opt.tol * (1.0 + c_red_max)).sum())
     if mu_new <= opt.rm_mu_frac * tr.mu0:

@@ -14,6 +14,10 @@ Exact contract (the reading used everywhere in this project):
   * order by (d_ij, jlin) ascending with jlin = i + j*m, the 0-based column-major position
     of p_ij in vec(P) (Section 2.1); keep the first min(kmax, #candidates).
 The set kept is unique; tests compare sets bit for bit.
+
+Heuristic set J (Section 3.4): with ``cmax`` given, only the pairs with c_ij < cmax are
+candidates (J is fixed before the iterations start; a full pricing refreshes the support every
+few iterations).
 """
 from __future__ import annotations
 
@@ -30,8 +34,9 @@ def reduced_costs(cost: Cost, u: np.ndarray, v: np.ndarray, i0: int = 0, i1: int
 
 
 def select(cost: Cost, u: np.ndarray, v: np.ndarray, support_i: np.ndarray,
-           support_j: np.ndarray, kmax: int, rows_per_chunk: int | None = None):
-    """Return (I, J, d) of the selected columns, ordered by (d, jlin)."""
+           support_j: np.ndarray, kmax: int, rows_per_chunk: int | None = None, cmax: float | None = None):
+    """Return (I, J, d) of the selected columns, ordered by (d, jlin); candidates restricted to
+    c_ij < cmax when cmax is given."""
     m, n = cost.m, cost.n
     sup_key = np.sort(np.asarray(support_i, np.int64) * n + np.asarray(support_j, np.int64))
     if rows_per_chunk is None:
@@ -39,8 +44,12 @@ def select(cost: Cost, u: np.ndarray, v: np.ndarray, support_i: np.ndarray,
     Is, Js, Ds = [], [], []
     for i0 in range(0, m, rows_per_chunk):
         i1 = min(m, i0 + rows_per_chunk)
-        d = reduced_costs(cost, u, v, i0, i1)
-        ii, jj = np.nonzero(d < 0.0)
+        c = cost.block(i0, i1)
+        d = (c - u[i0:i1, None]) - v[None, :]
+        neg = d < 0.0
+        if cmax is not None:
+            neg &= c < cmax
+        ii, jj = np.nonzero(neg)
         if ii.size == 0:
             continue
         gi = ii + i0
@@ -61,13 +70,15 @@ def select(cost: Cost, u: np.ndarray, v: np.ndarray, support_i: np.ndarray,
     return I[order], J[order], D[order]
 
 
-def select_bruteforce(C: np.ndarray, u, v, support: set, kmax: int):
+def select_bruteforce(C: np.ndarray, u, v, support: set, kmax: int, cmax: float | None = None):
     """Pure-Python loops over every pair; for tiny inputs only."""
     m, n = C.shape
     cand = []
     for j in range(n):
         for i in range(m):
             if (i, j) in support:
+                continue
+            if cmax is not None and not float(C[i, j]) < cmax:
                 continue
             d = (float(C[i, j]) - float(u[i])) - float(v[j])
             if d < 0.0:

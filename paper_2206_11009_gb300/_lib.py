@@ -22,7 +22,7 @@ COST = {"sqeuclid": 0, "euclid": 1, "l1": 2, "linf": 3, "dense": 4}
 class OtProblem(ctypes.Structure):
     _fields_ = [("m", c_int32), ("n", c_int32), ("a", c_void_p), ("b", c_void_p), ("cost", c_int32),
                 ("src_x", c_void_p), ("src_y", c_void_p), ("dst_x", c_void_p), ("dst_y", c_void_p),
-                ("src_w", c_int32), ("dst_w", c_int32), ("C", c_void_p)]
+                ("src_w", c_int32), ("dst_w", c_int32), ("C", c_void_p), ("inputs_on_device", c_int32)]
 
 
 class OtOptions(ctypes.Structure):
@@ -33,7 +33,11 @@ class OtOptions(ctypes.Structure):
                 ("stream", c_void_p), ("warm_u", c_void_p), ("warm_v", c_void_p), ("warm_count", c_int32),
                 ("warm_mode", c_int32), ("warm_i", c_void_p), ("warm_j", c_void_p), ("warm_npairs", c_int64),
                 ("new_col_rule", c_int32), ("scan_rows", c_int32), ("dense32_max_n", c_int32),
-                ("dense_max_n", c_int32)]
+                ("dense_max_n", c_int32), ("jset_cmax", c_double), ("jset_refresh", c_int32)]
+
+
+class OtPriceOpts(ctypes.Structure):
+    _fields_ = [("cost", c_int32), ("scan_rows", c_int32), ("jset_cmax", c_double), ("C", c_void_p)]
 
 
 class OtIterInfo(ctypes.Structure):
@@ -71,6 +75,9 @@ SIGNATURES = {
     "ot_price_topk": (c_int32, [c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                 c_void_p, c_void_p, c_int64, c_int32, c_int32, c_void_p, c_void_p, c_void_p,
                                 c_void_p, c_void_p]),
+    "ot_price_topk_ex": (c_int32, [c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                   c_void_p, c_void_p, c_int64, c_int32, c_int32, c_void_p, c_void_p, c_void_p,
+                                   c_void_p, POINTER(OtPriceOpts), c_void_p]),
     "ot_price_topk_noalloc": (c_int32, [c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                         c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_int32, c_void_p,
                                         c_void_p, c_void_p, c_void_p, c_void_p]),

@@ -48,30 +48,64 @@ class Result:
     warm_restarts: int = 0
 
 
+def _is_cuda_tensor(x) -> bool:
+    return type(x).__module__.startswith("torch") and getattr(x, "is_cuda", False)
+
+
 class Solver:
     """One OT instance on the GPU (``ot_ipm_create`` ... ``ot_ipm_destroy``).
 
-    a, b: masses (host arrays).  Points: either ``grid=(src_w, dst_w)`` (pixel grids, pixel
-    i at (i mod w, i div w)) or ``coords=(sx, sy, tx, ty)`` integer arrays.
+    a, b: masses (host arrays, or CUDA tensors: then every input is passed as a device pointer,
+    ``inputs_on_device``).  Points: either ``grid=(src_w, dst_w)`` (pixel grids, pixel i at
+    (i mod w, i div w)) or ``coords=(sx, sy, tx, ty)`` integer arrays; or an explicit cost
+    matrix ``C`` (m x n, row-major).  ``cost``: "sqeuclid" (default), "euclid", "l1", "linf".
     """
 
-    def __init__(self, a, b, grid=None, coords=None, stream=None, warm=None, warm_pairs=None, **options):
+    def __init__(self, a, b, grid=None, coords=None, stream=None, warm=None, warm_pairs=None, C=None, **options):
         """warm: optional predicted duals (u, v) in cost units; the initial support then also takes
         the pairs of least predicted reduced cost.  warm_pairs: optional (I, J) pairs that join the
         initial support (e.g. from ``WarmStart.pairs``)."""
         self._lib = _lib.load()
-        self.a = np.ascontiguousarray(a, dtype=np.float64)
-        self.b = np.ascontiguousarray(b, dtype=np.float64)
-        self.m, self.n = len(self.a), len(self.b)
-        prob = OtProblem()
-        prob.m, prob.n = self.m, self.n
-        prob.a, prob.b = _ptr(self.a), _ptr(self.b)
-        prob.cost = _lib.COST[options.pop("cost", "sqeuclid")]
         self._keep = []
-        if coords is not None:
-            cs = [np.ascontiguousarray(c, dtype=np.int32) for c in coords]
-            self._keep += cs
-            prob.src_x, prob.src_y, prob.dst_x, prob.dst_y = [_ptr(c) for c in cs]
+        prob = OtProblem()
+        on_dev = _is_cuda_tensor(a)
+        if on_dev:
+            import torch
+            conv = lambda x, dt: x.to(dtype=dt).contiguous()
+            da, db = conv(a, torch.float64), conv(b, torch.float64)
+            self._keep += [da, db]
+            self.m, self.n = da.numel(), db.numel()
+            prob.a, prob.b = da.data_ptr(), db.data_ptr()
+            prob.inputs_on_device = 1
+        else:
+            self.a = np.ascontiguousarray(a, dtype=np.float64)
+            self.b = np.ascontiguousarray(b, dtype=np.float64)
+            self.m, self.n = len(self.a), len(self.b)
+            prob.a, prob.b = _ptr(self.a), _ptr(self.b)
+        prob.m, prob.n = self.m, self.n
+        prob.cost = _lib.COST[options.pop("cost", "sqeuclid" if C is None else "dense")]
+        if C is not None:
+            if on_dev:
+                import torch
+                dC = C.to(dtype=torch.float64).contiguous()
+                self._keep.append(dC)
+                prob.C = dC.data_ptr()
+            else:
+                hC = np.ascontiguousarray(C, dtype=np.float64)
+                if hC.shape != (self.m, self.n):
+                    raise ValueError("C must have shape (m, n)")
+                self._keep.append(hC)
+                prob.C = _ptr(hC)
+        elif coords is not None:
+            if on_dev:
+                import torch
+                cs = [c.to(dtype=torch.int32).contiguous() for c in coords]
+                self._keep += cs
+                prob.src_x, prob.src_y, prob.dst_x, prob.dst_y = [c.data_ptr() for c in cs]
+            else:
+                cs = [np.ascontiguousarray(c, dtype=np.int32) for c in coords]
+                self._keep += cs
+                prob.src_x, prob.src_y, prob.dst_x, prob.dst_y = [_ptr(c) for c in cs]
         else:
             if grid is None:
                 k = int(round(np.sqrt(self.m)))
@@ -182,27 +216,50 @@ class Solver:
         self.close()
 
 
-def price_topk(sx, sy, tx, ty, u, v, sup_i, sup_j, kmax: int, precision: int = 1, stream=None):
+def price_topk(sx, sy, tx, ty, u, v, sup_i, sup_j, kmax: int, precision: int = 1, stream=None,
+               cost: str = "sqeuclid", scan_rows: int = 0, jset_cmax: float = 0.0, C=None):
     """Pricing + selection on device tensors (torch, cuda, contiguous): int32 coordinates,
-    float64 duals, int32 support pairs sorted by (i, j).  Returns (I, J, D) device tensors."""
+    float64 duals, int32 support pairs sorted by (i, j).  Returns (I, J, D) device tensors.
+    cost, scan_rows, jset_cmax, C (dense float64 m x n device tensor, cost "dense"): the options
+    of ``ot_price_topk_ex``; with the defaults the call is ``ot_price_topk``."""
     import torch
     lib = _lib.load()
-    m, n = int(sx.numel()), int(tx.numel())
+    if C is not None:
+        cost = "dense"
+        m, n = int(C.shape[0]), int(C.shape[1])
+    else:
+        m, n = int(sx.numel()), int(tx.numel())
     dev = u.device
     out_i = torch.empty(max(kmax, 1), dtype=torch.int32, device=dev)
     out_j = torch.empty(max(kmax, 1), dtype=torch.int32, device=dev)
     out_d = torch.empty(max(kmax, 1), dtype=torch.float64, device=dev)
     cnt = torch.zeros(1, dtype=torch.int32, device=dev)
-    for t, dt in ((sx, torch.int32), (sy, torch.int32), (tx, torch.int32), (ty, torch.int32),
-                  (u, torch.float64), (v, torch.float64), (sup_i, torch.int32), (sup_j, torch.int32)):
+    checks = [(u, torch.float64), (v, torch.float64), (sup_i, torch.int32), (sup_j, torch.int32)]
+    if C is None:
+        checks += [(sx, torch.int32), (sy, torch.int32), (tx, torch.int32), (ty, torch.int32)]
+    else:
+        checks.append((C, torch.float64))
+    for t, dt in checks:
         if t.dtype != dt or not t.is_contiguous() or not t.is_cuda:
             raise TypeError("price_topk: expected contiguous CUDA tensors of the documented dtypes")
     s = stream if stream is not None else torch.cuda.current_stream(dev).cuda_stream
     psi = int(sup_i.numel())
-    check(lib.ot_price_topk(m, n, sx.data_ptr(), sy.data_ptr(), tx.data_ptr(), ty.data_ptr(), u.data_ptr(),
-                            v.data_ptr(), sup_i.data_ptr() if psi else None, sup_j.data_ptr() if psi else None,
-                            psi, kmax, precision, out_i.data_ptr(), out_j.data_ptr(), out_d.data_ptr(),
-                            cnt.data_ptr(), ctypes.c_void_p(s)))
+    ptr = lambda t: None if t is None else t.data_ptr()
+    if cost == "sqeuclid" and scan_rows == 0 and jset_cmax <= 0 and C is None:
+        check(lib.ot_price_topk(m, n, sx.data_ptr(), sy.data_ptr(), tx.data_ptr(), ty.data_ptr(), u.data_ptr(),
+                                v.data_ptr(), sup_i.data_ptr() if psi else None, sup_j.data_ptr() if psi else None,
+                                psi, kmax, precision, out_i.data_ptr(), out_j.data_ptr(), out_d.data_ptr(),
+                                cnt.data_ptr(), ctypes.c_void_p(s)))
+    else:
+        po = _lib.OtPriceOpts()
+        po.cost = _lib.COST[cost]
+        po.scan_rows = scan_rows
+        po.jset_cmax = jset_cmax
+        po.C = ptr(C)
+        check(lib.ot_price_topk_ex(m, n, ptr(sx), ptr(sy), ptr(tx), ptr(ty), u.data_ptr(), v.data_ptr(),
+                                   sup_i.data_ptr() if psi else None, sup_j.data_ptr() if psi else None, psi, kmax,
+                                   precision, out_i.data_ptr(), out_j.data_ptr(), out_d.data_ptr(), cnt.data_ptr(),
+                                   ctypes.byref(po), ctypes.c_void_p(s)))
     k = int(cnt.item())
     return out_i[:k], out_j[:k], out_d[:k]
 

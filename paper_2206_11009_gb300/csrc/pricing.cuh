@@ -1,4 +1,6 @@
 // Pricing (Section 3.4) + support enlargement selection (Section 3.2): internal API.
+// Cost kinds: the squared Euclidean distance and the distances of Section 5.1 from integer
+// coordinates, or an explicit matrix (always priced in FP64).
 #pragma once
 
 #include "common.cuh"
@@ -17,7 +19,31 @@ struct PriceInput {
     int32_t origin_x = 0, origin_y = 0;  // coordinate shift applied before the FP32 form
     int32_t num_sms = 0;
     int32_t rows = 0;       // rows per scan tile (8..256); 0: chosen from the problem size
+    int32_t kind = OT_COST_SQEUCLID;   // ot_cost_kind
+    const double *C = nullptr;         // OT_COST_DENSE: device, m x n row-major
+    // Heuristic set J of Section 3.4: when jn >= 0 only the jn listed pairs (ji, jj) are priced;
+    // the support pairs inside J are those with integer cost key < jlim (point costs) or with
+    // C_ij < jcmax (explicit matrix).
+    const int32_t *ji = nullptr, *jj = nullptr;
+    int64_t jn = -1;
+    long long jlim = 0;
+    double jcmax = 0.0;
 };
+
+// The pairs of J = {(i, j) : c_ij < cmax} (Section 3.4), sorted by (i, j), in device buffers
+// owned by the struct (jset_free).  lim: the integer cost key bound (c_ij < cmax <=> key < lim;
+// the key is dx^2 + dy^2 for the squared and Euclidean distances, |dx| + |dy| for L1,
+// max(|dx|, |dy|) for L-infinity).
+struct JSet {
+    int32_t *i = nullptr, *j = nullptr;
+    int64_t n = 0;
+    long long lim = 0;
+    double cmax = 0.0;
+};
+long long jset_limit(int kind, double cmax);
+Error jset_build(int kind, int32_t m, int32_t n, const int32_t *sx, const int32_t *sy, const int32_t *tx,
+                 const int32_t *ty, const double *C, double cmax, JSet *out, cudaStream_t st);
+void jset_free(JSet &J);
 
 struct PriceStats {
     uint64_t gathered = 0;   // pairs rechecked in FP64

@@ -6,40 +6,29 @@
 // fails or evicts its caches), or a latency-critical loop that cannot afford the implicit
 // device-wide synchronisation an allocation or release may cause.  Such a caller still owns the
 // inputs and outputs; only the scratch moves into this file-scope array.
-#include <mutex>
-
 #include "pricing.cuh"
 #include "primitives.cuh"
 
 namespace {
 
-// 24 MiB of scratch on every device that loads the library (held until the process exits).
-// Enough for m, n <= 16384 and a pricing candidate set of about 400k pairs.
+// 24 MiB of scratch on every device where the library's module is loaded (held until the process
+// exits).  With lazy module loading that happens at the first call on the device.  Enough for
+// m, n <= 16384 and a pricing candidate set of about 400k pairs.
 constexpr size_t kScratchBytes = (size_t)24 << 20;
 constexpr int32_t kMaxSide = 16384;
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_price_scratch[kScratchBytes];
 
-std::mutex g_mu;
-void *g_scratch_ptr[kMaxDevices] = {nullptr};
-
-// Device address of the scratch array for the current device (looked up once per device, with
-// that device current).  Host code must not use g_price_scratch directly: on the host that name
-// is only a stand-in for the device symbol.
+// Device address of the scratch array on the current device.  Host code must not use
+// g_price_scratch directly: on the host that name is only a stand-in for the device symbol.  The
+// address is looked up on every call (the lookup allocates nothing), so it always belongs to the
+// current context, also after a device reset made a new one.
 ot::Error scratch_for_current_device(void **out) {
-    int dev = 0;
-    OT_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) return ot::fail(OT_ERR_ARG, "device index out of range");
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_ptr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_price_scratch);
-        if (e != cudaSuccess || !p)
-            return ot::fail(OT_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-        g_scratch_ptr[dev] = p;
-    }
-    *out = g_scratch_ptr[dev];
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_price_scratch);
+    if (e != cudaSuccess || !p)
+        return ot::fail(OT_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    *out = p;
     return ot::ok();
 }
 

@@ -132,6 +132,47 @@ __global__ void count_below_kernel(const int32_t *__restrict__ cnt, const double
     }
 }
 
+__global__ void check_dense_kernel(int64_t count, const double *__restrict__ C, int *__restrict__ bad) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count; k += (int64_t)gridDim.x * blockDim.x)
+        if (!(C[k] >= 0.0) || !isfinite(C[k])) atomicExch(bad, 1);
+}
+
+__global__ void gather_dense_kernel(int m, int n, int n0, const int32_t *__restrict__ rmap,
+                                    const int32_t *__restrict__ cmap, const double *__restrict__ C0,
+                                    double *__restrict__ C) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < (int64_t)m * n; k += (int64_t)gridDim.x * blockDim.x)
+        C[k] = C0[(int64_t)rmap[k / n] * n0 + cmap[k % n]];
+}
+
+__global__ void scatter_kernel(int count, const int32_t *__restrict__ map, const double *__restrict__ x,
+                               double *__restrict__ y) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < count; k += gridDim.x * blockDim.x) y[map[k]] = x[k];
+}
+
+// Duals of the points the presolve removed (c-transforms, one block per removed point):
+// u_i = min over kept targets j of c_ij - v_j; then v_j = min over all sources i of c_ij - u_i.
+__global__ void complete_u_kernel(CostDev cf, const int32_t *__restrict__ rows, int n_kept,
+                                  const int32_t *__restrict__ kept_cols, const double *__restrict__ v_kept,
+                                  double *__restrict__ u_full) {
+    __shared__ double sh[32];
+    const int i = rows[blockIdx.x];
+    double best = INFINITY;
+    for (int r = threadIdx.x; r < n_kept; r += blockDim.x)
+        best = fmin(best, __dsub_rn(cost_at(cf, i, kept_cols[r]), v_kept[r]));
+    best = block_min(best, sh);
+    if (threadIdx.x == 0) u_full[i] = best;
+}
+
+__global__ void complete_v_kernel(CostDev cf, const int32_t *__restrict__ cols, const double *__restrict__ u_full,
+                                  double *__restrict__ v_full) {
+    __shared__ double sh[32];
+    const int j = cols[blockIdx.x];
+    double best = INFINITY;
+    for (int i = threadIdx.x; i < cf.m; i += blockDim.x) best = fmin(best, __dsub_rn(cost_at(cf, i, j), u_full[i]));
+    best = block_min(best, sh);
+    if (threadIdx.x == 0) v_full[j] = best;
+}
+
 __global__ void scale_copy_kernel(int64_t count, const double *__restrict__ x, double f, double *__restrict__ y) {
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count; k += (int64_t)gridDim.x * blockDim.x)
         y[k] = x[k] * f;
@@ -186,6 +227,17 @@ struct ot_ipm {
     int direct_total = 0;
     double last_lb = -INFINITY, last_gap = INFINITY, last_mu = 0.0;
     std::string err;
+    // zero-mass presolve: the solve runs on the points with positive mass (m x n above)
+    int32_t m0 = 0, n0 = 0;                   // the caller's sizes
+    bool presolved = false;
+    std::vector<int32_t> src_map, dst_map;    // solve index -> caller index
+    std::vector<int32_t> src_inv, dst_inv;    // caller index -> solve index, -1 if removed
+    int32_t *d_src_map = nullptr, *d_dst_map = nullptr;
+    int32_t *fsx = nullptr, *fsy = nullptr, *ftx = nullptr, *fty = nullptr;  // caller's points
+    double *fC = nullptr;                     // caller's dense costs (presolved dense problems)
+    std::vector<double> warm_ur, warm_vr;     // warm-start inputs on the kept points
+    std::vector<int32_t> warm_ir, warm_jr;
+    JSet jset;                                // heuristic pricing set (Section 3.4), built on first use
 };
 
 namespace {
@@ -259,10 +311,20 @@ Error lower_bound(ot_ipm *h, double *lb) {
     return ok();
 }
 
-Error price_support(ot_ipm *h, const Support &S, int32_t kmax, int32_t *count, PriceStats *ps) {
-    if (h->cd.kind != OT_COST_SQEUCLID)
-        return fail(OT_ERR_UNSUPPORTED, "pricing: only the squared-Euclidean cost is built");
+Error price_support(ot_ipm *h, const Support &S, int32_t kmax, int32_t *count, PriceStats *ps, bool use_j) {
     PriceInput in;
+    in.kind = h->cd.kind;
+    in.C = h->C;
+    if (use_j) {
+        if (!h->jset.i)
+            OT_TRY(jset_build(h->cd.kind, h->m, h->n, h->sx, h->sy, h->tx, h->ty, h->C, h->opt.jset_cmax, &h->jset,
+                              h->st));
+        in.ji = h->jset.i;
+        in.jj = h->jset.j;
+        in.jn = h->jset.n;
+        in.jlim = h->jset.lim;
+        in.jcmax = h->jset.cmax;
+    }
     in.m = h->m; in.n = h->n;
     in.sx = h->sx; in.sy = h->sy; in.tx = h->tx; in.ty = h->ty;
     in.u = h->u; in.v = h->v;
@@ -566,7 +628,10 @@ Error do_step(ot_ipm *h, ot_iter_info *info) {
     int32_t added = 0;
     PriceStats ps;
     pc.mark("step");
-    OT_TRY(price_support(h, S, kadd, &added, &ps));
+    // Section 3.4: the heuristic set J between full refreshes (every jset_refresh-th iteration)
+    const int refresh = o.jset_refresh > 0 ? o.jset_refresh : 3;
+    const bool use_j = o.jset_cmax > 0 && (h->iter % refresh) != refresh - 1;
+    OT_TRY(price_support(h, S, kadd, &added, &ps, use_j));
     pc.mark("price");
     {
         count_below_kernel<<<1, 256, 0, st>>>(h->pcount, h->pd, -o.tol * (1.0 + cmax_red), h->pstrong);
@@ -694,6 +759,8 @@ Error warm_support(ot_ipm *h, const ot_options &o, cudaStream_t st) {
     in.psi = A.psi;
     in.kmax = K;
     in.precision = o.precision;
+    in.kind = h->cd.kind;
+    in.C = h->C;
     in.origin_x = h->ox;
     in.origin_y = h->oy;
     in.num_sms = h->num_sms;
@@ -708,47 +775,142 @@ Error warm_support(ot_ipm *h, const ot_options &o, cudaStream_t st) {
     return ok();
 }
 
+// Duals in the caller's indexing (host buffers, either may be NULL).  Points removed by the
+// presolve get c-transform duals when `complete`, else 0.
+Error caller_duals(ot_ipm *h, double *u_out, double *v_out, bool complete) {
+    cudaStream_t st = h->st;
+    if (!h->presolved) {
+        if (u_out) OT_CUDA(cudaMemcpyAsync(u_out, h->u, sizeof(double) * h->m, cudaMemcpyDeviceToHost, st));
+        if (v_out) OT_CUDA(cudaMemcpyAsync(v_out, h->v, sizeof(double) * h->n, cudaMemcpyDeviceToHost, st));
+        OT_CUDA(cudaStreamSynchronize(st));
+        return ok();
+    }
+    if (!u_out && !v_out) return ok();
+    const int m0 = h->m0, n0 = h->n0;
+    DevTemp<double> uf, vf;
+    OT_TRY(uf.alloc(m0, st));
+    OT_TRY(vf.alloc(n0, st));
+    OT_CUDA(cudaMemsetAsync(uf.p, 0, sizeof(double) * m0, st));
+    OT_CUDA(cudaMemsetAsync(vf.p, 0, sizeof(double) * n0, st));
+    scatter_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(h->m, 256), 1024)), 256, 0, st>>>(
+        h->m, h->d_src_map, h->u, uf.p);
+    OT_LAUNCHED();
+    scatter_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(h->n, 256), 1024)), 256, 0, st>>>(
+        h->n, h->d_dst_map, h->v, vf.p);
+    OT_LAUNCHED();
+    if (complete) {
+        std::vector<int32_t> ri, rj;
+        for (int i = 0; i < m0; ++i) if (h->src_inv[i] < 0) ri.push_back(i);
+        for (int j = 0; j < n0; ++j) if (h->dst_inv[j] < 0) rj.push_back(j);
+        CostDev cf = h->cd;
+        cf.m = m0;
+        cf.n = n0;
+        if (cf.kind == OT_COST_DENSE) cf.C = h->fC;
+        else { cf.sx = h->fsx; cf.sy = h->fsy; cf.tx = h->ftx; cf.ty = h->fty; }
+        DevTemp<int32_t> dri, drj;
+        OT_TRY(dri.alloc((int64_t)ri.size(), st));
+        OT_TRY(drj.alloc((int64_t)rj.size(), st));
+        if (!ri.empty()) {
+            OT_CUDA(cudaMemcpyAsync(dri.p, ri.data(), sizeof(int32_t) * ri.size(), cudaMemcpyHostToDevice, st));
+            complete_u_kernel<<<(unsigned)ri.size(), 256, 0, st>>>(cf, dri.p, h->n, h->d_dst_map, h->v, uf.p);
+            OT_LAUNCHED();
+        }
+        if (!rj.empty()) {
+            OT_CUDA(cudaMemcpyAsync(drj.p, rj.data(), sizeof(int32_t) * rj.size(), cudaMemcpyHostToDevice, st));
+            complete_v_kernel<<<(unsigned)rj.size(), 256, 0, st>>>(cf, drj.p, uf.p, vf.p);
+            OT_LAUNCHED();
+        }
+        OT_CUDA(cudaStreamSynchronize(st));  // the host index lists above must outlive the copies
+    }
+    if (u_out) OT_CUDA(cudaMemcpyAsync(u_out, uf.p, sizeof(double) * m0, cudaMemcpyDeviceToHost, st));
+    if (v_out) OT_CUDA(cudaMemcpyAsync(v_out, vf.p, sizeof(double) * n0, cudaMemcpyDeviceToHost, st));
+    OT_CUDA(cudaStreamSynchronize(st));
+    return ok();
+}
+
+// Support indices to the caller's indexing (host arrays, in place).
+void caller_pairs(const ot_ipm *h, int32_t *i, int32_t *j, int64_t k) {
+    if (!h->presolved) return;
+    for (int64_t e = 0; e < k; ++e) {
+        if (i) i[e] = h->src_map[i[e]];
+        if (j) j[e] = h->dst_map[j[e]];
+    }
+}
+
 Error create_impl(const ot_problem *P, const ot_options *O, ot_ipm *h) {
     if (!P || P->m <= 0 || P->n <= 0 || !P->a || !P->b) return fail(OT_ERR_ARG, "problem: sizes or masses missing");
-    const int32_t m = P->m, n = P->n;
-    if ((uint64_t)m * (uint64_t)n > (1ull << 32)) return fail(OT_ERR_ARG, "problem: m*n exceeds 2^32");
+    const int32_t m0 = P->m, n0 = P->n;
+    if ((uint64_t)m0 * (uint64_t)n0 > (1ull << 32)) return fail(OT_ERR_ARG, "problem: m*n exceeds 2^32");
     if (O) h->opt = *O; else ot_options_default(&h->opt);
     ot_options &o = h->opt;
     if (!(o.tol > 0) || o.max_iter < 0 || o.max_cg <= 0 || o.max_corr < 0 || !(o.step_scale > 0 && o.step_scale < 1) ||
-        (o.precision != 0 && o.precision != 1))
+        (o.precision != 0 && o.precision != 1) || o.jset_refresh < 0 || !std::isfinite(o.jset_cmax))
         return fail(OT_ERR_ARG, "options: out of range");
+    if (P->cost < 0 || P->cost > OT_COST_DENSE) return fail(OT_ERR_ARG, "problem: unknown cost kind");
+    const bool dense = P->cost == OT_COST_DENSE;
+    if (dense && !P->C) return fail(OT_ERR_ARG, "problem: dense cost without C");
+    if (dense && (uint64_t)m0 * (uint64_t)n0 > (1ull << 30)) return fail(OT_ERR_ARG, "problem: dense C above 2^30 entries");
+    const bool on_dev = P->inputs_on_device != 0;
+    // host copies of the masses and coordinates (device inputs are read back: m + n values)
+    std::vector<double> A(m0), B(n0);
+    auto fetch = [&](void *dst, const void *src, size_t bytes) -> Error {
+        if (on_dev) OT_CUDA(cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost));
+        else memcpy(dst, src, bytes);
+        return ok();
+    };
+    OT_TRY(fetch(A.data(), P->a, sizeof(double) * m0));
+    OT_TRY(fetch(B.data(), P->b, sizeof(double) * n0));
     double sa = 0, sb = 0;
-    for (int i = 0; i < m; ++i) {
-        if (!(P->a[i] >= 0) || !std::isfinite(P->a[i])) return fail(OT_ERR_ARG, "problem: negative or non-finite mass in a");
-        sa += P->a[i];
+    for (int i = 0; i < m0; ++i) {
+        if (!(A[i] >= 0) || !std::isfinite(A[i])) return fail(OT_ERR_ARG, "problem: negative or non-finite mass in a");
+        sa += A[i];
     }
-    for (int j = 0; j < n; ++j) {
-        if (!(P->b[j] >= 0) || !std::isfinite(P->b[j])) return fail(OT_ERR_ARG, "problem: negative or non-finite mass in b");
-        sb += P->b[j];
+    for (int j = 0; j < n0; ++j) {
+        if (!(B[j] >= 0) || !std::isfinite(B[j])) return fail(OT_ERR_ARG, "problem: negative or non-finite mass in b");
+        sb += B[j];
     }
     if (!(sa > 0) || std::fabs(sa - sb) > 1e-12 * sa) return fail(OT_ERR_ARG, "problem: sum(a) != sum(b)");
-    if (P->cost < 0 || P->cost > OT_COST_DENSE) return fail(OT_ERR_ARG, "problem: unknown cost kind");
-    if (P->cost == OT_COST_DENSE && !P->C) return fail(OT_ERR_ARG, "problem: dense cost without C");
-    if (P->cost != OT_COST_SQEUCLID)
-        return fail(OT_ERR_UNSUPPORTED, "problem: only the squared-Euclidean cost is built");
+    // coordinates (caller's indexing)
+    std::vector<int32_t> X0(m0, 0), Y0(m0, 0), G0(n0, 0), H0(n0, 0);
+    if (!dense) {
+        const bool have = P->src_x && P->src_y && P->dst_x && P->dst_y;
+        if (!have && (P->src_w <= 0 || P->dst_w <= 0 || m0 % P->src_w || n0 % P->dst_w))
+            return fail(OT_ERR_ARG, "problem: no coordinates and no valid grid widths");
+        if (have) {
+            OT_TRY(fetch(X0.data(), P->src_x, sizeof(int32_t) * m0));
+            OT_TRY(fetch(Y0.data(), P->src_y, sizeof(int32_t) * m0));
+            OT_TRY(fetch(G0.data(), P->dst_x, sizeof(int32_t) * n0));
+            OT_TRY(fetch(H0.data(), P->dst_y, sizeof(int32_t) * n0));
+        } else {
+            for (int i = 0; i < m0; ++i) { X0[i] = i % P->src_w; Y0[i] = i / P->src_w; }
+            for (int j = 0; j < n0; ++j) { G0[j] = j % P->dst_w; H0[j] = j / P->dst_w; }
+        }
+    }
+    // zero-mass presolve: only points with positive mass enter the solve
+    for (int i = 0; i < m0; ++i) if (A[i] > 0) h->src_map.push_back(i);
+    for (int j = 0; j < n0; ++j) if (B[j] > 0) h->dst_map.push_back(j);
+    const int32_t m = (int32_t)h->src_map.size(), n = (int32_t)h->dst_map.size();
+    h->m0 = m0;
+    h->n0 = n0;
+    h->presolved = m < m0 || n < n0;
+    h->src_inv.assign(m0, -1);
+    h->dst_inv.assign(n0, -1);
+    for (int r = 0; r < m; ++r) h->src_inv[h->src_map[r]] = r;
+    for (int r = 0; r < n; ++r) h->dst_inv[h->dst_map[r]] = r;
     h->m = m;
     h->n = n;
     h->sigma_f = (double)m / sa;
     std::vector<double> as(m), bs(n);
     double f2 = 0;
-    for (int i = 0; i < m; ++i) { as[i] = P->a[i] * h->sigma_f; f2 += as[i] * as[i]; }
-    for (int j = 0; j < n; ++j) { bs[j] = P->b[j] * (sa / sb) * h->sigma_f; f2 += bs[j] * bs[j]; }
+    for (int i = 0; i < m; ++i) { as[i] = A[h->src_map[i]] * h->sigma_f; f2 += as[i] * as[i]; }
+    for (int j = 0; j < n; ++j) { bs[j] = B[h->dst_map[j]] * (sa / sb) * h->sigma_f; f2 += bs[j] * bs[j]; }
     h->fnorm = std::sqrt(f2);
-    // coordinates
     std::vector<int32_t> hx(m), hy(m), gx(n), gy(n);
-    const bool have = P->src_x && P->src_y && P->dst_x && P->dst_y;
-    if (!have && (P->src_w <= 0 || P->dst_w <= 0 || m % P->src_w || n % P->dst_w))
-        return fail(OT_ERR_ARG, "problem: no coordinates and no valid grid widths");
-    for (int i = 0; i < m; ++i) { hx[i] = have ? P->src_x[i] : i % P->src_w; hy[i] = have ? P->src_y[i] : i / P->src_w; }
-    for (int j = 0; j < n; ++j) { gx[j] = have ? P->dst_x[j] : j % P->dst_w; gy[j] = have ? P->dst_y[j] : j / P->dst_w; }
+    for (int i = 0; i < m; ++i) { hx[i] = X0[h->src_map[i]]; hy[i] = Y0[h->src_map[i]]; }
+    for (int j = 0; j < n; ++j) { gx[j] = G0[h->dst_map[j]]; gy[j] = H0[h->dst_map[j]]; }
     int xmin = INT32_MAX, xmax = INT32_MIN, ymin = INT32_MAX, ymax = INT32_MIN;
-    for (int i = 0; i < m; ++i) { xmin = std::min(xmin, hx[i]); xmax = std::max(xmax, hx[i]); ymin = std::min(ymin, hy[i]); ymax = std::max(ymax, hy[i]); }
-    for (int j = 0; j < n; ++j) { xmin = std::min(xmin, gx[j]); xmax = std::max(xmax, gx[j]); ymin = std::min(ymin, gy[j]); ymax = std::max(ymax, gy[j]); }
+    for (int i = 0; i < m0; ++i) { xmin = std::min(xmin, X0[i]); xmax = std::max(xmax, X0[i]); ymin = std::min(ymin, Y0[i]); ymax = std::max(ymax, Y0[i]); }
+    for (int j = 0; j < n0; ++j) { xmin = std::min(xmin, G0[j]); xmax = std::max(xmax, G0[j]); ymin = std::min(ymin, H0[j]); ymax = std::max(ymax, H0[j]); }
     if (xmin <= -(1 << 14) || ymin <= -(1 << 14) || xmax >= (1 << 14) || ymax >= (1 << 14))
         return fail(OT_ERR_ARG, "problem: coordinates must satisfy |x|, |y| < 2^14");
     h->ox = (int32_t)(((int64_t)xmin + xmax) / 2);
@@ -794,10 +956,79 @@ Error create_impl(const ot_problem *P, const ot_options *O, ot_ipm *h) {
     OT_CUDA(cudaMemcpyAsync(h->sy, hy.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, st));
     OT_CUDA(cudaMemcpyAsync(h->tx, gx.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
     OT_CUDA(cudaMemcpyAsync(h->ty, gy.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
+    if (h->presolved) {
+        // the caller's points and index maps stay on the device for the dual completion
+        OT_CUDA(cudaMalloc((void **)&h->d_src_map, sizeof(int32_t) * m));
+        OT_CUDA(cudaMalloc((void **)&h->d_dst_map, sizeof(int32_t) * n));
+        OT_CUDA(cudaMemcpyAsync(h->d_src_map, h->src_map.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, st));
+        OT_CUDA(cudaMemcpyAsync(h->d_dst_map, h->dst_map.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
+        if (!dense) {
+            OT_CUDA(cudaMalloc((void **)&h->fsx, sizeof(int32_t) * m0));
+            OT_CUDA(cudaMalloc((void **)&h->fsy, sizeof(int32_t) * m0));
+            OT_CUDA(cudaMalloc((void **)&h->ftx, sizeof(int32_t) * n0));
+            OT_CUDA(cudaMalloc((void **)&h->fty, sizeof(int32_t) * n0));
+            OT_CUDA(cudaMemcpyAsync(h->fsx, X0.data(), sizeof(int32_t) * m0, cudaMemcpyHostToDevice, st));
+            OT_CUDA(cudaMemcpyAsync(h->fsy, Y0.data(), sizeof(int32_t) * m0, cudaMemcpyHostToDevice, st));
+            OT_CUDA(cudaMemcpyAsync(h->ftx, G0.data(), sizeof(int32_t) * n0, cudaMemcpyHostToDevice, st));
+            OT_CUDA(cudaMemcpyAsync(h->fty, H0.data(), sizeof(int32_t) * n0, cudaMemcpyHostToDevice, st));
+        }
+    }
+    if (dense) {
+        // the caller's matrix on the device (validated there), then its kept rows and columns
+        const int64_t cnt = (int64_t)m0 * n0;
+        OT_CUDA(cudaMalloc((void **)&h->fC, sizeof(double) * cnt));
+        OT_CUDA(cudaMemcpyAsync(h->fC, P->C, sizeof(double) * cnt,
+                                on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+        int *bad = nullptr;
+        OT_CUDA(cudaMalloc((void **)&bad, sizeof(int)));
+        int hbad = 0;
+        cudaMemsetAsync(bad, 0, sizeof(int), st);
+        check_dense_kernel<<<(unsigned)std::min<int64_t>(ceil_div(cnt, 256), 4LL * h->num_sms), 256, 0, st>>>(
+            cnt, h->fC, bad);
+        g_launches.fetch_add(1);
+        cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st);
+        const cudaError_t ce = cudaStreamSynchronize(st);
+        cudaFree(bad);
+        if (ce != cudaSuccess) return fail(OT_ERR_CUDA, cudaGetErrorString(ce));
+        if (hbad) return fail(OT_ERR_ARG, "problem: C has a negative or non-finite entry");
+        if (h->presolved) {
+            OT_CUDA(cudaMalloc((void **)&h->C, sizeof(double) * (int64_t)m * n));
+            gather_dense_kernel<<<(unsigned)std::min<int64_t>(ceil_div((int64_t)m * n, 256), 4LL * h->num_sms), 256, 0,
+                                  st>>>(m, n, n0, h->d_src_map, h->d_dst_map, h->fC, h->C);
+            OT_LAUNCHED();
+        } else {
+            h->C = h->fC;
+            h->fC = nullptr;
+        }
+    }
     h->cd.kind = P->cost;
     h->cd.m = m;
     h->cd.n = n;
     h->cd.sx = h->sx; h->cd.sy = h->sy; h->cd.tx = h->tx; h->cd.ty = h->ty;
+    h->cd.C = h->C;
+    if (h->presolved) {
+        // warm-start inputs are in the caller's indexing: keep what concerns the kept points
+        if (o.warm_u && o.warm_v) {
+            h->warm_ur.resize(m);
+            h->warm_vr.resize(n);
+            for (int r = 0; r < m; ++r) h->warm_ur[r] = o.warm_u[h->src_map[r]];
+            for (int r = 0; r < n; ++r) h->warm_vr[r] = o.warm_v[h->dst_map[r]];
+            o.warm_u = h->warm_ur.data();
+            o.warm_v = h->warm_vr.data();
+        }
+        if (o.warm_i && o.warm_j && o.warm_npairs > 0) {
+            for (int64_t t = 0; t < o.warm_npairs; ++t) {
+                const int32_t i = o.warm_i[t], j = o.warm_j[t];
+                if (i < 0 || i >= m0 || j < 0 || j >= n0) return fail(OT_ERR_ARG, "warm pairs: index out of range");
+                if (h->src_inv[i] < 0 || h->dst_inv[j] < 0) continue;
+                h->warm_ir.push_back(h->src_inv[i]);
+                h->warm_jr.push_back(h->dst_inv[j]);
+            }
+            o.warm_i = h->warm_ir.data();
+            o.warm_j = h->warm_jr.data();
+            o.warm_npairs = (int64_t)h->warm_ir.size();
+        }
+    }
 
     // initial support (Section 3.2 end) and Mehrotra's starting point
     int32_t *ii = nullptr, *jj = nullptr;
@@ -874,6 +1105,8 @@ void ot_options_default(ot_options *o) {
     o->rm_p_frac = 1e-3;
     o->add_max = 0;
     o->new_col_rule = 1;
+    o->jset_cmax = 0.0;
+    o->jset_refresh = 3;
     o->verbose = 0;
     o->stream = nullptr;
 }
@@ -1017,11 +1250,11 @@ int ot_ipm_get_solution(ot_ipm_t *h, int32_t *i, int32_t *j, double *p, int64_t 
     cudaMemcpyAsync(i, S.i, sizeof(int32_t) * S.psi, cudaMemcpyDeviceToHost, h->st);
     cudaMemcpyAsync(j, S.j, sizeof(int32_t) * S.psi, cudaMemcpyDeviceToHost, h->st);
     cudaMemcpyAsync(p, tmp, sizeof(double) * S.psi, cudaMemcpyDeviceToHost, h->st);
-    if (u) cudaMemcpyAsync(u, h->u, sizeof(double) * h->m, cudaMemcpyDeviceToHost, h->st);
-    if (v) cudaMemcpyAsync(v, h->v, sizeof(double) * h->n, cudaMemcpyDeviceToHost, h->st);
     cudaError_t ce = cudaStreamSynchronize(h->st);
     cudaFree(tmp);
     if (ce != cudaSuccess) return record(h, fail(OT_ERR_CUDA, cudaGetErrorString(ce)));
+    caller_pairs(h, i, j, S.psi);
+    e = caller_duals(h, u, v, true);
     return record(h, e);
 }
 
@@ -1035,11 +1268,10 @@ int ot_ipm_get_state(ot_ipm_t *h, int32_t *i, int32_t *j, double *p, double *s, 
     if (j) cudaMemcpyAsync(j, S.j, sizeof(int32_t) * S.psi, cudaMemcpyDeviceToHost, h->st);
     if (p) cudaMemcpyAsync(p, S.p, sizeof(double) * S.psi, cudaMemcpyDeviceToHost, h->st);
     if (s) cudaMemcpyAsync(s, S.s, sizeof(double) * S.psi, cudaMemcpyDeviceToHost, h->st);
-    if (u) cudaMemcpyAsync(u, h->u, sizeof(double) * h->m, cudaMemcpyDeviceToHost, h->st);
-    if (v) cudaMemcpyAsync(v, h->v, sizeof(double) * h->n, cudaMemcpyDeviceToHost, h->st);
     cudaError_t ce = cudaStreamSynchronize(h->st);
     if (ce != cudaSuccess) return record(h, fail(OT_ERR_CUDA, cudaGetErrorString(ce)));
-    return OT_OK;
+    caller_pairs(h, i, j, S.psi);
+    return record(h, caller_duals(h, u, v, false));
 }
 
 int ot_ipm_newton_direction(ot_ipm_t *h, int32_t solver, double cg_tol, int32_t max_cg, double *du, double *dv,
@@ -1086,11 +1318,21 @@ int ot_ipm_newton_direction(ot_ipm_t *h, int32_t solver, double cg_tol, int32_t 
         SolveStats ss;
         OT_TRY(newton_solve(W, S, R, cg_tol, max_cg, solver == OT_LS_MIXED ? 1 : 0, W.du, W.dv, W.ds, W.dp, &ss,
                             st));
-        if (du) OT_CUDA(cudaMemcpyAsync(du, W.du, sizeof(double) * h->m, cudaMemcpyDeviceToHost, st));
-        if (dv) OT_CUDA(cudaMemcpyAsync(dv, W.dv, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+        std::vector<double> hdu(du ? h->m : 0), hdv(dv ? n : 0);
+        if (du) OT_CUDA(cudaMemcpyAsync(hdu.data(), W.du, sizeof(double) * h->m, cudaMemcpyDeviceToHost, st));
+        if (dv) OT_CUDA(cudaMemcpyAsync(hdv.data(), W.dv, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
         if (dp) OT_CUDA(cudaMemcpyAsync(dp, W.dp, sizeof(double) * S.psi, cudaMemcpyDeviceToHost, st));
         if (ds) OT_CUDA(cudaMemcpyAsync(ds, W.ds, sizeof(double) * S.psi, cudaMemcpyDeviceToHost, st));
         OT_CUDA(cudaStreamSynchronize(st));
+        // to the caller's indexing (points removed by the presolve: 0)
+        if (du) {
+            std::fill(du, du + h->m0, 0.0);
+            for (int r = 0; r < h->m; ++r) du[h->presolved ? h->src_map[r] : r] = hdu[r];
+        }
+        if (dv) {
+            std::fill(dv, dv + h->n0, 0.0);
+            for (int r = 0; r < n; ++r) dv[h->presolved ? h->dst_map[r] : r] = hdv[r];
+        }
         if (cg_iters) *cg_iters = ss.cg_iters;
         return ok();
     }();
@@ -1104,10 +1346,28 @@ int ot_ipm_set_state(ot_ipm_t *h, const int32_t *i, const int32_t *j, const doub
                      const double *u, const double *v, int32_t reset_mu0) {
     if (!h || psi <= 0 || !i || !j || !p || !s || !u || !v) return OT_ERR_ARG;
     for (int64_t e = 0; e < psi; ++e) {
-        if (i[e] < 0 || i[e] >= h->m || j[e] < 0 || j[e] >= h->n || !(p[e] > 0) || !(s[e] > 0))
+        if (i[e] < 0 || i[e] >= h->m0 || j[e] < 0 || j[e] >= h->n0 || !(p[e] > 0) || !(s[e] > 0))
             return record(h, fail(OT_ERR_ARG, "ot_ipm_set_state: entry out of range or nonpositive"));
-        if (e > 0 && ((int64_t)i[e] * h->n + j[e]) <= ((int64_t)i[e - 1] * h->n + j[e - 1]))
+        if (e > 0 && ((int64_t)i[e] * h->n0 + j[e]) <= ((int64_t)i[e - 1] * h->n0 + j[e - 1]))
             return record(h, fail(OT_ERR_ARG, "ot_ipm_set_state: pairs not sorted by (i, j) or repeated"));
+        if (h->src_inv[i[e]] < 0 || h->dst_inv[j[e]] < 0)
+            return record(h, fail(OT_ERR_ARG, "ot_ipm_set_state: pair on a point with zero mass"));
+    }
+    std::vector<int32_t> ri, rj;
+    std::vector<double> ru, rv;
+    if (h->presolved) {
+        // to the solve's indexing (the maps are increasing, so the (i, j) order is kept)
+        ri.resize(psi);
+        rj.resize(psi);
+        for (int64_t e = 0; e < psi; ++e) { ri[e] = h->src_inv[i[e]]; rj[e] = h->dst_inv[j[e]]; }
+        ru.resize(h->m);
+        rv.resize(h->n);
+        for (int r = 0; r < h->m; ++r) ru[r] = u[h->src_map[r]];
+        for (int r = 0; r < h->n; ++r) rv[r] = v[h->dst_map[r]];
+        i = ri.data();
+        j = rj.data();
+        u = ru.data();
+        v = rv.data();
     }
     Error e = ensure_capacity(h, psi);
     if (e.code != OT_OK) return record(h, e);
@@ -1140,8 +1400,10 @@ void ot_ipm_destroy(ot_ipm_t *h) {
     chol_free(h->chol);
     dense_free(h->dense);
     d32_free(h->d32);
+    jset_free(h->jset);
     void *ptrs[] = {h->a_s, h->b_s, h->C, h->sx, h->sy, h->tx, h->ty, h->u, h->v, h->pi, h->pj, h->pd,
-                    h->pcount, h->pstrong, h->rowmin, h->lbv};
+                    h->pcount, h->pstrong, h->rowmin, h->lbv, h->d_src_map, h->d_dst_map, h->fsx, h->fsy,
+                    h->ftx, h->fty, h->fC};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->own_stream && h->st) cudaStreamDestroy(h->st);
@@ -1171,6 +1433,47 @@ int ot_price_topk(int32_t m, int32_t n, const int32_t *sx, const int32_t *sy, co
     in.precision = precision;
     Error e = coord_origin(m, n, sx, sy, tx, ty, &in.origin_x, &in.origin_y, st);
     if (e.code == OT_OK) e = price_topk(in, out_i, out_j, out_d, out_count, nullptr, st);
+    if (e.code != OT_OK) set_thread_error(e.msg.c_str());
+    return e.code;
+}
+
+int ot_price_topk_ex(int32_t m, int32_t n, const int32_t *sx, const int32_t *sy, const int32_t *tx,
+                     const int32_t *ty, const double *u, const double *v, const int32_t *sup_i, const int32_t *sup_j,
+                     int64_t psi, int32_t kmax, int32_t precision, int32_t *out_i, int32_t *out_j, double *out_d,
+                     int32_t *out_count, const ot_price_opts *opts, void *stream) {
+    ot_price_opts po{};
+    if (opts) po = *opts;
+    const bool dense = po.cost == OT_COST_DENSE;
+    if (m <= 0 || n <= 0 || kmax < 0 || psi < 0 || po.cost < OT_COST_SQEUCLID || po.cost > OT_COST_DENSE ||
+        (dense ? !po.C : (!sx || !sy || !tx || !ty)) || !u || !v || !out_i || !out_j || !out_count ||
+        (psi > 0 && (!sup_i || !sup_j)) || (precision != 0 && precision != 1) || po.scan_rows < 0 ||
+        !std::isfinite(po.jset_cmax)) {
+        set_thread_error("ot_price_topk_ex: invalid argument");
+        return OT_ERR_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    PriceInput in;
+    in.m = m; in.n = n;
+    in.sx = sx; in.sy = sy; in.tx = tx; in.ty = ty;
+    in.u = u; in.v = v;
+    in.sup_i = sup_i; in.sup_j = sup_j; in.psi = psi;
+    in.kmax = kmax;
+    in.precision = precision;
+    in.kind = po.cost;
+    in.C = po.C;
+    in.rows = po.scan_rows;
+    JSet J;
+    Error e = ok();
+    if (!dense) e = coord_origin(m, n, sx, sy, tx, ty, &in.origin_x, &in.origin_y, st);
+    if (e.code == OT_OK && po.jset_cmax > 0) {
+        e = jset_build(po.cost, m, n, sx, sy, tx, ty, po.C, po.jset_cmax, &J, st);
+        in.ji = J.i; in.jj = J.j; in.jn = J.n; in.jlim = J.lim; in.jcmax = J.cmax;
+    }
+    if (e.code == OT_OK) e = price_topk(in, out_i, out_j, out_d, out_count, nullptr, st);
+    if (J.i) {
+        cudaStreamSynchronize(st);
+        jset_free(J);
+    }
     if (e.code != OT_OK) set_thread_error(e.msg.c_str());
     return e.code;
 }

@@ -369,3 +369,72 @@ def test_removal_guard_keeps_the_component_count(seed):
     assert _n_components(m, n, I[keep], J[keep]) == before
     # what is left is a forest exactly when nothing else held the removal back (kmax large)
     assert certificate.is_forest(m, n, I[keep], J[keep])
+
+
+# ----------------------------------------------------------------------------- other costs, J set
+
+@pytest.mark.parametrize("seed", range(4))
+def test_pricing_jset_matches_bruteforce(seed):
+    """Section 3.4's heuristic set J: only pairs with c_ij < C_max are candidates."""
+    m, n = 8, 7
+    C = synth.random_int_costs(m, n, 300 + seed, hi=9).astype(np.float64)
+    rng = synth.uniform01(2000 + seed, m + n + m * n)
+    u = np.round(rng[:m] * 6, 1)
+    v = np.round(rng[m:m + n] * 6, 1)
+    I, J = np.nonzero(rng[m + n:].reshape(m, n) < 0.2)
+    sup = set(zip(I.tolist(), J.tolist()))
+    for cmax in (0.5, 3.0, 4.5, 100.0):
+        for kmax in (2, m, m * n):
+            sI, sJ, sD = pricing.select(costs.Cost.dense(C), u, v, I, J, kmax, cmax=cmax)
+            ref = pricing.select_bruteforce(C, u, v, sup, kmax, cmax=cmax)
+            assert list(zip(sI.tolist(), sJ.tolist())) == ref
+            assert np.all(C[sI, sJ] < cmax) and np.all(sD < 0)
+    # C_max above every cost: the full rule
+    full = pricing.select(costs.Cost.dense(C), u, v, I, J, m * n)
+    capped = pricing.select(costs.Cost.dense(C), u, v, I, J, m * n, cmax=C.max() + 1)
+    assert all(np.array_equal(x, y) for x, y in zip(full, capped))
+
+
+@pytest.mark.parametrize("kind", ["euclid", "l1", "linf"])
+@pytest.mark.parametrize("k,seed", [(8, 1), (12, 3)])
+def test_ipm_oracle_other_costs_reach_exact_optimum(kind, k, seed):
+    """Section 5.1's L1, Euclidean and L-infinity distances through the oracle IPM."""
+    inst = synth.image_pair(k, seed)
+    c = costs.square_grid(k, kind)
+    ref = netsimplex.solve(c, inst.a, inst.b)
+    r = ipm.solve(c, inst.a, inst.b, ipm.Options(tol=1e-8))
+    assert r.status == "optimal"
+    assert abs(r.obj - ref.obj) <= 1e-7 * ref.obj and r.r1_l1 <= 1e-8
+
+
+@pytest.mark.parametrize("kind,cmax", [("sqeuclid", 9.0), ("l1", 4.0), ("euclid", 3.0), ("linf", 3.0)])
+def test_ipm_oracle_with_jset_reaches_exact_optimum(kind, cmax):
+    """Pricing on J between full refreshes (Section 3.4) changes the trajectory, not the optimum."""
+    k = 12
+    inst = synth.image_pair(k, 0)
+    c = costs.square_grid(k, kind)
+    ref = netsimplex.solve(c, inst.a, inst.b)
+    r = ipm.solve(c, inst.a, inst.b, ipm.Options(tol=1e-8, jset_cmax=cmax))
+    assert r.status == "optimal"
+    assert abs(r.obj - ref.obj) <= 1e-7 * ref.obj and r.r1_l1 <= 1e-8
+
+
+def test_zero_masses_carry_no_flow():
+    """Input handling of zero masses (presolve): a point with zero mass carries no flow, so the
+    optimum equals that of the problem without those points, and the network simplex's duals
+    stay feasible over all pairs."""
+    k = 10
+    inst = synth.image_pair(k, 5)
+    rng = synth.uniform01(77, 2 * k * k)
+    a, b = inst.a.copy(), inst.b.copy()
+    a[rng[:k * k] < 0.2] = 0.0
+    b[rng[k * k:] < 0.2] = 0.0
+    a /= a.sum()
+    b /= b.sum()
+    c = costs.square_grid(k)
+    full = netsimplex.solve(c, a, b)
+    ki, kj = np.nonzero(a > 0)[0], np.nonzero(b > 0)[0]
+    red = netsimplex.solve(costs.Cost.points(c.sx[ki], c.sy[ki], c.tx[kj], c.ty[kj]), a[ki], b[kj])
+    assert abs(full.obj - red.obj) <= 1e-12 * red.obj
+    assert certificate.min_reduced_cost(c, full.u, full.v) >= 0.0
+    assert np.all(full.P[(a[full.I] == 0) | (b[full.J] == 0)] == 0.0)
