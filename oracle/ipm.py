@@ -12,7 +12,9 @@ Readings where the paper is silent:
   * data scale: masses are scaled internally to mean 1 (sigma_f = m / sum a); the LP
     solution scales exactly with it and results are reported in the caller's units;
   * initial support: pairs with c_ij <= init_cost (2 on pixel grids: the 3x3 neighbourhood),
-    plus every row's and column's cheapest pair (ties: smaller index)  (Section 3.2 end);
+    plus every row's and column's cheapest pair (ties: smaller index)  (Section 3.2 end); when
+    that support graph is not connected, plus the north-west-corner coupling's pairs (a feasible
+    plan), so that the restricted problem is feasible;
   * initial point: Mehrotra's heuristic (Mehrotra 1992, SIAM J. Optim. 2:575) on the
     restricted problem: least-squares p and y from A A^T (Theta = I), shifted to positivity;
   * stop: max(|r1|/(1+|f|), |r2|/(1+|c_red|), psi*mu/(1+|c^T p|)) < tol (2-norms; the last
@@ -182,7 +184,39 @@ def initial_support(prob: Problem, opt: Options):
         colarg[better] = carg[better]
     keys.append(colarg * n + np.arange(n))
     key = np.unique(np.concatenate(keys))
-    return key // n, key % n
+    I, J = key // n, key % n
+    ncomp, _ = components(m, n, I, J)
+    if ncomp > 1:
+        # point sets that do not overlap: the support splits and the restricted problem would be
+        # infeasible; the north-west-corner coupling's pairs make it feasible
+        nI, nJ = north_west_corner(prob.as_, prob.bs)
+        key = np.unique(np.concatenate([key, nI * n + nJ]))
+        I, J = key // n, key % n
+    return I, J
+
+
+def north_west_corner(a, b):
+    """Support of the north-west-corner coupling (sources and targets in index order): a feasible
+    plan on at most m + n - 1 pairs; equal partial sums advance both sides."""
+    m, n = len(a), len(b)
+    I, J = [], []
+    i = j = 0
+    A, B = float(a[0]), float(b[0])
+    while i < m and j < n:
+        I.append(i)
+        J.append(j)
+        if A < B:
+            i += 1
+            A = A + float(a[i]) if i < m else A
+        elif B < A:
+            j += 1
+            B = B + float(b[j]) if j < n else B
+        else:
+            i += 1
+            j += 1
+            A = A + float(a[i]) if i < m else A
+            B = B + float(b[j]) if j < n else B
+    return np.array(I, dtype=np.int64), np.array(J, dtype=np.int64)
 
 
 def initial_point(prob: Problem, I, J) -> State:

@@ -1403,6 +1403,25 @@ Error schur_setup(Newton &W, const Support &S, cudaStream_t st) {
     return ok();
 }
 
+Error support_connected(Newton &W, const Support &S, bool *one, cudaStream_t st) {
+    const int nn = W.m + W.n;
+    const unsigned gnn = grid_of(nn, W.num_sms), ge = grid_of(S.psi, W.num_sms), gn = grid_of(W.n, W.num_sms);
+    uf_init_kernel<<<gnn, kT, 0, st>>>(nn, W.parent);
+    OT_LAUNCHED();
+    uf_hook_kernel<<<ge, kT, 0, st>>>(S.psi, W.m, S.i, S.j, W.parent);
+    OT_LAUNCHED();
+    uf_final_kernel<<<gnn, kT, 0, st>>>(nn, W.parent);
+    OT_LAUNCHED();
+    onecomp_kernel<<<gn, kT, 0, st>>>(W.m, W.n, W.parent, W.part);
+    OT_LAUNCHED();
+    Finish f{1, {SC_ONECOMP}, {(int)gn}, {0}};
+    OT_TRY(finish(f, W, st));
+    double hs[SC_COUNT];
+    OT_TRY(read_scalars(W, hs, st));
+    *one = hs[SC_ONECOMP] == 0.0;
+    return ok();
+}
+
 // project x to mean zero on every connected component (reads scal[SC_ONECOMP] on the host)
 static Error project(Newton &W, double *x, bool one_comp, cudaStream_t st) {
     const unsigned gn = grid_of(W.n, W.num_sms);

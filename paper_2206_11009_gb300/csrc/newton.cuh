@@ -84,6 +84,9 @@ Error residuals(Newton &W, const Support &S, const double *a_s, const double *b_
 // connected components of the support graph.
 Error schur_setup(Newton &W, const Support &S, cudaStream_t st);
 
+// *one = whether the support graph is connected (every row has a pair; columns are compared).
+Error support_connected(Newton &W, const Support &S, bool *one, cudaStream_t st);
+
 // Which right-hand side pieces to use in newton_solve.
 struct Rhs {
     const double *r1a, *r1b, *r2, *r3;  // nullptr = zero

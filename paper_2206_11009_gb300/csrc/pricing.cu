@@ -184,15 +184,16 @@ __global__ void bound_kernel(Geo *geo, int fp64, int kind) {
 }
 
 // One key into the histogram (pass 1) or the candidate list (pass 2).
+// Padding columns (j >= n) carry key +inf and never qualify; the gather also checks j < n.
 template <bool FP64, bool GATHER>
 __device__ __forceinline__ void take_key(float d, bool neg64, float E, float Tg, unsigned *sh_hist, int i, int j,
-                                         int32_t *ci, int32_t *cj, unsigned long long cap, unsigned *ncand) {
+                                         int n, int32_t *ci, int32_t *cj, unsigned long long cap, unsigned *ncand) {
     const bool neg = FP64 ? neg64 : (d < 0.f);
     if (!GATHER) {
         if (neg) atomicAdd(&sh_hist[bin_of_neg(d)], 1u);
         else if (!FP64 && d <= E) atomicAdd(&sh_hist[4096], 1u);
     } else {
-        const bool take = FP64 ? (neg && d <= Tg) : (d <= Tg);
+        const bool take = (FP64 ? (neg && d <= Tg) : (d <= Tg)) && j < n;
         if (take) {
             const unsigned pos = atomicAdd(ncand, 1u);
             if (pos < cap) { ci[pos] = i; cj[pos] = j; }
@@ -250,7 +251,9 @@ scan_kernel(int m, int n, int TI, int ncb, int64_t ntiles,
                 if (j < n) { if (K != K_DN) { ix[c] = tx[j]; iy[c] = ty[j]; } dv[c] = v[j]; }
                 else { ix[c] = 0; iy[c] = 0; dv[c] = -INFINITY; }  // d = +inf
             } else {
-                float4 q = j < n ? cols[j] : make_float4(INFINITY, 0.f, 0.f, 0.f);
+                // padding columns get key +inf: cB = +inf in the squared form (d = ... + B_j),
+                // -inf in the direct form (d = ... - v_j)
+                float4 q = j < n ? cols[j] : make_float4(K == K_SQ ? INFINITY : -INFINITY, 0.f, 0.f, 0.f);
                 cB[c] = q.x; cx[c] = q.y; cy[c] = q.z;
             }
         }
@@ -280,7 +283,7 @@ scan_kernel(int m, int n, int TI, int ncb, int64_t ntiles,
 #pragma unroll
                         for (int c = 0; c < kRJ; ++c)
                             take_key<false, GATHER>(d[q][c], false, E, Tg, sh_hist, i0 + r0 + q,
-                                                    cb * kTJ + c * kPT + threadIdx.x, ci, cj, cap, ncand);
+                                                    cb * kTJ + c * kPT + threadIdx.x, n, ci, cj, cap, ncand);
                     }
                 }
             }
@@ -318,7 +321,7 @@ scan_kernel(int m, int n, int TI, int ncb, int64_t ntiles,
 #pragma unroll
                 for (int c = 0; c < kRJ; ++c)
                     take_key<FP64, GATHER>(d[c], FP64 ? (dd[c] < 0.0) : false, E, Tg, sh_hist, i0 + r,
-                                           cb * kTJ + c * kPT + threadIdx.x, ci, cj, cap, ncand);
+                                           cb * kTJ + c * kPT + threadIdx.x, n, ci, cj, cap, ncand);
             }
         }
         if (!GATHER) {
@@ -390,7 +393,7 @@ jscan_kernel(int n, int64_t jn, int64_t ntiles, const int32_t *__restrict__ ji, 
             }
             tmin = fminf(tmin, d);
             if (d <= (GATHER ? Tg : E))
-                take_key<FP64, GATHER>(d, neg64, E, Tg, sh_hist, i, j, ci, cj, cap, ncand);
+                take_key<FP64, GATHER>(d, neg64, E, Tg, sh_hist, i, j, n, ci, cj, cap, ncand);
         }
         if (!GATHER) {
             float w = tmin;

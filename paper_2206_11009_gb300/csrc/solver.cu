@@ -238,6 +238,7 @@ struct ot_ipm {
     std::vector<double> warm_ur, warm_vr;     // warm-start inputs on the kept points
     std::vector<int32_t> warm_ir, warm_jr;
     JSet jset;                                // heuristic pricing set (Section 3.4), built on first use
+    std::vector<double> as_host, bs_host;     // scaled masses (for the initial support's completion)
 };
 
 namespace {
@@ -377,26 +378,15 @@ Error start_crit(ot_ipm *h, double *crit) {
     return ok();
 }
 
+Error cold_support(ot_ipm *h, cudaStream_t st);
+
 // Abandon a warm start: the cold initial support and Mehrotra's point, as ot_ipm_create builds
 // them; the iteration count carries on.
 Error cold_restart(ot_ipm *h) {
     const ot_options &o = h->opt;
     cudaStream_t st = h->st;
-    int32_t *ii = nullptr, *jj = nullptr;
-    int64_t psi0 = 0;
-    OT_TRY(initial_support(h->cd, o.init_cost, &ii, &jj, &psi0, st));
-    Error e = ensure_capacity(h, psi0);
+    OT_TRY(cold_support(h, st));
     Support &S = h->S[h->cur];
-    if (e.code == OT_OK) {
-        cudaMemcpyAsync(S.i, ii, sizeof(int32_t) * psi0, cudaMemcpyDeviceToDevice, st);
-        cudaMemcpyAsync(S.j, jj, sizeof(int32_t) * psi0, cudaMemcpyDeviceToDevice, st);
-        cudaStreamSynchronize(st);
-    }
-    cudaFree(ii);
-    cudaFree(jj);
-    OT_TRY(e);
-    S.psi = psi0;
-    OT_TRY(rebuild_views(S, h->m, h->n, st));
     OT_TRY(support_costs(h->W, h->cd, S, st));
     int cgs = 0;
     OT_TRY(mehrotra_start(h->W, S, h->a_s, h->b_s, h->u, h->v, o.precision, o.cg_tol_pred, 20 * o.max_cg, &cgs, st));
@@ -676,10 +666,12 @@ int record(ot_ipm *h, const Error &e) {
     return e.code;
 }
 
-// Warm start by explicit pairs: validated, deduplicated and stripped of the pairs already in the
-// support on the host, then merged (at most what the support buffers hold).
-Error warm_pairs(ot_ipm *h, const ot_options &o, cudaStream_t st) {
+// Explicit pairs join the support: validated, deduplicated and stripped of the pairs already in
+// it on the host, then merged (at most what the support buffers hold).  *added (may be NULL)
+// receives the number merged.
+Error add_pairs(ot_ipm *h, const int32_t *pi, const int32_t *pj, int64_t count, cudaStream_t st, int64_t *added) {
     const int m = h->m, n = h->n;
+    if (added) *added = 0;
     Support &A = h->S[h->cur];
     Support &B = h->S[1 - h->cur];
     std::vector<int32_t> si(A.psi), sj(A.psi);
@@ -689,9 +681,9 @@ Error warm_pairs(ot_ipm *h, const ot_options &o, cudaStream_t st) {
     std::vector<int64_t> have(A.psi);
     for (int64_t e = 0; e < A.psi; ++e) have[e] = (int64_t)si[e] * n + sj[e];  // sorted by (i, j)
     std::vector<int64_t> add;
-    add.reserve(o.warm_npairs);
-    for (int64_t t = 0; t < o.warm_npairs; ++t) {
-        const int32_t i = o.warm_i[t], j = o.warm_j[t];
+    add.reserve(count);
+    for (int64_t t = 0; t < count; ++t) {
+        const int32_t i = pi[t], j = pj[t];
         if (i < 0 || i >= m || j < 0 || j >= n) return fail(OT_ERR_ARG, "warm pairs: index out of range");
         add.push_back((int64_t)i * n + j);
     }
@@ -716,8 +708,69 @@ Error warm_pairs(ot_ipm *h, const ot_options &o, cudaStream_t st) {
     OT_CUDA(cudaMemsetAsync(keep.p, 0, std::max<int64_t>(A.psi, 1), st));
     OT_TRY(merge_support(A, keep.p, di.p, dj.p, k, 1.0, m, n, B, st));
     h->cur = 1 - h->cur;
+    if (added) *added = k;
+    return ok();
+}
+
+Error warm_pairs(ot_ipm *h, const ot_options &o, cudaStream_t st) {
+    int64_t k = 0;
+    OT_TRY(add_pairs(h, o.warm_i, o.warm_j, o.warm_npairs, st, &k));
     h->warm_added += k;
     return ok();
+}
+
+// Pairs of the north-west-corner coupling of the scaled masses, sources and targets in index order
+// (a feasible transportation plan: a staircase of at most m + n - 1 pairs; equal partial sums
+// advance both sides).
+void nw_corner_pairs(const std::vector<double> &a, const std::vector<double> &b, std::vector<int32_t> &I,
+                     std::vector<int32_t> &J) {
+    const size_t m = a.size(), n = b.size();
+    double A = 0.0, B = 0.0;
+    size_t i = 0, j = 0;
+    if (m && n) { A = a[0]; B = b[0]; }
+    while (i < m && j < n) {
+        I.push_back((int32_t)i);
+        J.push_back((int32_t)j);
+        if (A < B) { if (++i < m) A += a[i]; }
+        else if (B < A) { if (++j < n) B += b[j]; }
+        else {
+            if (++i < m) A += a[i];
+            if (++j < n) B += b[j];
+        }
+    }
+}
+
+// Initial support (Section 3.2 end), in S[cur]: {c_ij <= init_cost} plus every row's and column's
+// cheapest pair; when that support graph splits into several components (point sets that do not
+// overlap, where the restricted problem would be infeasible), the north-west-corner coupling's
+// pairs join it, which makes the restricted problem feasible.
+Error complete_feasible(ot_ipm *h, cudaStream_t st) {
+    bool one = true;
+    OT_TRY(support_connected(h->W, h->S[h->cur], &one, st));
+    if (one) return ok();
+    std::vector<int32_t> I, J;
+    nw_corner_pairs(h->as_host, h->bs_host, I, J);
+    OT_TRY(ensure_capacity(h, h->S[h->cur].psi + (int64_t)I.size()));
+    return add_pairs(h, I.data(), J.data(), (int64_t)I.size(), st, nullptr);
+}
+
+Error cold_support(ot_ipm *h, cudaStream_t st) {
+    int32_t *ii = nullptr, *jj = nullptr;
+    int64_t psi0 = 0;
+    OT_TRY(initial_support(h->cd, h->opt.init_cost, &ii, &jj, &psi0, st));
+    Error e = ensure_capacity(h, psi0);
+    Support &S = h->S[h->cur];
+    if (e.code == OT_OK) {
+        cudaMemcpyAsync(S.i, ii, sizeof(int32_t) * psi0, cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(S.j, jj, sizeof(int32_t) * psi0, cudaMemcpyDeviceToDevice, st);
+        cudaStreamSynchronize(st);
+    }
+    cudaFree(ii);
+    cudaFree(jj);
+    OT_TRY(e);
+    S.psi = psi0;
+    OT_TRY(rebuild_views(S, h->m, h->n, st));
+    return complete_feasible(h, st);
 }
 
 // Warm start: the pricing scan with the predicted duals shifted by init_cost selects the pairs of
@@ -905,6 +958,8 @@ Error create_impl(const ot_problem *P, const ot_options *O, ot_ipm *h) {
     for (int i = 0; i < m; ++i) { as[i] = A[h->src_map[i]] * h->sigma_f; f2 += as[i] * as[i]; }
     for (int j = 0; j < n; ++j) { bs[j] = B[h->dst_map[j]] * (sa / sb) * h->sigma_f; f2 += bs[j] * bs[j]; }
     h->fnorm = std::sqrt(f2);
+    h->as_host = as;
+    h->bs_host = bs;
     std::vector<int32_t> hx(m), hy(m), gx(n), gy(n);
     for (int i = 0; i < m; ++i) { hx[i] = X0[h->src_map[i]]; hy[i] = Y0[h->src_map[i]]; }
     for (int j = 0; j < n; ++j) { gx[j] = G0[h->dst_map[j]]; gy[j] = H0[h->dst_map[j]]; }
@@ -1050,6 +1105,7 @@ Error create_impl(const ot_problem *P, const ot_options *O, ot_ipm *h) {
     const bool want_warm = (o.warm_u && o.warm_v) || (o.warm_i && o.warm_j && o.warm_npairs > 0);
     OT_TRY(newton_alloc(h->W, m, n, h->S[h->cur].cap, h->num_sms));
     h->W.verbose = h->opt.verbose;
+    OT_TRY(complete_feasible(h, st));
     OT_TRY(chol_alloc(h->chol, n));
     int cgs = 0;
     double crit_cold = INFINITY;

@@ -90,7 +90,7 @@ def test_jset_empty_and_full(precision):
     sx, sy = U.rect_coords(20, 20)
     tx, ty = U.rect_coords(20, 20, 100, 0)            # every cost >= 81^2
     u, v = U.banded_duals(sx, sy, tx, ty, seed=2, amp=3.0, noise=1.0)
-    v = v - 20000.0                                    # many negative reduced costs
+    v = v + 20000.0                                    # every reduced cost negative
     si = np.zeros(0, np.int32)
     # C_max below every cost: J is empty
     assert _check("sqeuclid", sx, sy, tx, ty, u, v, si, si, 400, precision, cmax=50.0) == 0

@@ -438,3 +438,34 @@ def test_zero_masses_carry_no_flow():
     assert abs(full.obj - red.obj) <= 1e-12 * red.obj
     assert certificate.min_reduced_cost(c, full.u, full.v) >= 0.0
     assert np.all(full.P[(a[full.I] == 0) | (b[full.J] == 0)] == 0.0)
+
+
+def test_north_west_corner_is_a_feasible_staircase():
+    """The north-west-corner rule (textbook transportation start): worked by hand for
+    a = (0.5, 0.3, 0.2), b = (0.2, 0.4, 0.4): pairs (0,0) (0,1) (1,1) (1,2) (2,2); in general a
+    staircase of at most m + n - 1 pairs that carries a feasible plan."""
+    I, J = ipm.north_west_corner(np.array([0.5, 0.3, 0.2]), np.array([0.2, 0.4, 0.4]))
+    assert list(zip(I.tolist(), J.tolist())) == [(0, 0), (0, 1), (1, 1), (1, 2), (2, 2)]
+    a, b = synth.random_masses(30, 1), synth.random_masses(45, 2)
+    I, J = ipm.north_west_corner(a * 30, b * 30)
+    assert len(I) <= 74 and np.all(np.diff(I) >= 0) and np.all(np.diff(J) >= 0)
+    # the restricted problem on these pairs is feasible: the network simplex on costs that are
+    # 0 on the staircase and huge elsewhere finds a zero-cost plan
+    C = np.full((30, 45), 1e6)
+    C[I, J] = 0.0
+    assert netsimplex.solve(costs.Cost.dense(C), a, b).obj == 0.0
+
+
+def test_ipm_oracle_on_point_sets_that_do_not_overlap():
+    """A vertical line of 30 sources against a 5 x 9 target grid to its right: the initial
+    support {c <= 2} is empty apart from the cheapest pairs and splits; with the north-west-corner
+    completion the oracle IPM reaches the exact optimum."""
+    sx = np.zeros(30)
+    sy = np.arange(30.0)
+    t = np.arange(45)
+    tx, ty = (t % 5 + 3).astype(float), (t // 5 - 1).astype(float)
+    c = costs.Cost.points(sx, sy, tx, ty)
+    a, b = synth.random_masses(30, 70), synth.random_masses(45, 95)
+    ref = netsimplex.solve(c, a, b)
+    r = ipm.solve(c, a, b, ipm.Options(tol=1e-8))
+    assert r.status == "optimal" and abs(r.obj - ref.obj) <= 1e-7 * ref.obj
