@@ -326,11 +326,12 @@ int64_t ot_kernel_launches(void);
  * is launched on.  enable(1) clears the totals and starts recording; read() resolves the events
  * (synchronising on them) and writes, per kernel id, the total milliseconds, the launch count and
  * (work != NULL) the algorithmic work of those launches: FP32 operations for the pricing scan
- * (4 per pair), bytes for the PCG (per CG iteration: theta, index and gathered vector entry per
- * support pair in both passes, plus the row/column vectors), FP64 flops for the LDL^T numeric
- * factorisation (2n^3/3 when dense), bytes for the LDL^T solves (L read twice), FP32 flops for
- * the FP32 dense factorisation with its inverse factor (n^3) and bytes for its application (the
- * triangle of L^-1 read twice):
+ * (4 per pair for the squared cost, 6 for L1 / L-infinity, 8 for the Euclidean distance; pairs
+ * of the J list only when it is used), bytes for the PCG (per CG iteration: theta, index and
+ * gathered vector entry per support pair in both passes, plus the row/column vectors), FP64 flops
+ * for the LDL^T numeric factorisation (n^3/3 when dense), bytes for the LDL^T solves (L read
+ * twice), FP32 flops for the FP32 dense factorisation with its inverse factor (n^3/3 + n^3/3) and
+ * bytes for its application (the triangle of L^-1 read twice):
  *   0 pricing scan (histogram pass)   1 pricing scan (gather pass)   2 FP64 recheck
  *   3 PCG FP64 (persistent kernel)    4 PCG FP32                     5 LDL^T numeric (FP64)
  *   6 LDL^T solve (FP64)              7 FP32 dense LDL^T + L^-1      8 FP32 dense apply

@@ -322,7 +322,7 @@ Error dense_factor(DenseLDL &M, const Chol &C, double eps, cudaStream_t st) {
         }
     }
     ktimer_end(KT_LDL_NUMERIC, st);
-    ktimer_add_work(KT_LDL_NUMERIC, 2.0 * (double)n * n * n / 3.0);
+    ktimer_add_work(KT_LDL_NUMERIC, (double)n * n * n / 3.0);  // L D L^T: n^3/3 flops
     return ok();
 }
 

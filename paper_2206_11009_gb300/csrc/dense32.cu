@@ -909,8 +909,8 @@ Error d32_factor(Dense32 &F, float eps, cudaStream_t st) {
     OT_CUDA(cudaGraphLaunch(F.graph, st));
     g_launches.fetch_add(F.graph_nodes, std::memory_order_relaxed);
     ktimer_end(KT_D32_FACTOR, st);
-    // FP32 flops: 2n^3/3 for L D L^T and n^3/3 for L^-1
-    ktimer_add_work(KT_D32_FACTOR, (double)F.n * F.n * F.n);
+    // FP32 flops: n^3/3 for L D L^T (n^3/6 multiply-adds) plus n^3/3 for the unit triangular inverse
+    ktimer_add_work(KT_D32_FACTOR, 2.0 * (double)F.n * F.n * F.n / 3.0);
     return ok();
 }
 
