@@ -477,11 +477,20 @@ def kernel_table(ktimes, pk_d, src):
     return out
 
 
+# DRAM bytes (read + write) per launch from one ncu capture of the kernel as it stands, and the
+# summary under profiles/ that gives the command; a kernel changed since then reports null.
+NCU_TRAFFIC = {
+    # one FP32 factorisation (n = 4096, all 317 launches of its graph): 1,667.3 MB read + 0.37 MB
+    # written; profiles/d32_factor_64x64.md
+    "d32_factor": 1.6677e9,
+}
+
+
 def roofline(table):
     """Roofline object of the dominant instrumented kernel (largest total device time)."""
     name, row = max(table.items(), key=lambda kv: kv[1]["ms"])
     return {"kernel": name, "bound": row.get("bound"), "achieved": row.get("achieved"), "peak": row.get("peak"),
-            "unit": row.get("unit"), "frac": row.get("frac"), "traffic": None,
+            "unit": row.get("unit"), "frac": row.get("frac"), "traffic": NCU_TRAFFIC.get(name),
             "ms_per_launch": row["ms_per_launch"], "launches": row["launches"],
             "peak_source": row.get("peak_source")}
 
