@@ -132,6 +132,17 @@ typedef struct {
      * iteration prices all pairs.  The stopping test's certificate always covers all pairs. */
     double jset_cmax;
     int32_t jset_refresh;
+    /* Multiscale warm start (not in the paper; its conclusion names a better starting support as
+     * future work): multiscale = L > 0 first solves the problem coarsened by binning the points
+     * into 2 x 2 cells (cell masses summed), itself with L - 1 coarser levels, to relative
+     * tolerance ms_tol (0 = max(tol, 1e-4); also the coarse ||f - A p||_1 bound relative to the
+     * total mass); its duals, interpolated bilinearly at the points and
+     * scaled by the cost's degree (x4 for the squared distance, x2 for the others), are used as
+     * warm_u, warm_v (warm_count 0 then means 10(m+n), warm_mode as given).  Skipped for explicit
+     * cost matrices, for caller-given warm_u / warm_v, and below 256 points per side.  Runs inside
+     * ot_ipm_create (ot_result.create_seconds). */
+    int32_t multiscale;
+    double ms_tol;
 } ot_options;
 
 /* One outer iteration (Section 3.4's commented listing). */
@@ -163,6 +174,9 @@ typedef struct {
     int64_t warm_added;       /* pairs the warm start added to the initial support            */
     int32_t warm_restarts;    /* 1 when a warm start lost ground (mu over twice its first value */
                               /* by iteration 5) and the solve restarted from the cold support */
+    double create_seconds;    /* wall time of ot_ipm_create (initial support, starting point,    */
+                              /* coarse solves of the multiscale warm start), synchronised      */
+    int32_t ms_levels;        /* coarse levels solved by the multiscale warm start              */
 } ot_result;
 
 typedef struct ot_ipm ot_ipm_t;

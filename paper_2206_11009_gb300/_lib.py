@@ -33,7 +33,8 @@ class OtOptions(ctypes.Structure):
                 ("stream", c_void_p), ("warm_u", c_void_p), ("warm_v", c_void_p), ("warm_count", c_int32),
                 ("warm_mode", c_int32), ("warm_i", c_void_p), ("warm_j", c_void_p), ("warm_npairs", c_int64),
                 ("new_col_rule", c_int32), ("scan_rows", c_int32), ("dense32_max_n", c_int32),
-                ("dense_max_n", c_int32), ("jset_cmax", c_double), ("jset_refresh", c_int32)]
+                ("dense_max_n", c_int32), ("jset_cmax", c_double), ("jset_refresh", c_int32),
+                ("multiscale", c_int32), ("ms_tol", c_double)]
 
 
 class OtPriceOpts(ctypes.Structure):
@@ -51,7 +52,8 @@ class OtResult(ctypes.Structure):
     _fields_ = [("status", c_int32), ("obj", c_double), ("lower_bound", c_double), ("rel_gap", c_double),
                 ("r1_l1", c_double), ("mu", c_double), ("iters", c_int32), ("cg_iters", c_int32),
                 ("direct_iters", c_int32), ("psi", c_int64), ("max_fill", c_double), ("seconds", c_double),
-                ("warm_added", c_int64), ("warm_restarts", c_int32)]
+                ("warm_added", c_int64), ("warm_restarts", c_int32), ("create_seconds", c_double),
+                ("ms_levels", c_int32)]
 
 
 # exported symbol -> (restype, argtypes)

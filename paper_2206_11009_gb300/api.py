@@ -46,6 +46,8 @@ class Result:
     seconds: float
     warm_added: int = 0
     warm_restarts: int = 0
+    create_seconds: float = 0.0
+    ms_levels: int = 0
 
 
 def _is_cuda_tensor(x) -> bool:

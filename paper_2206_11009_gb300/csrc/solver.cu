@@ -173,6 +173,34 @@ __global__ void complete_v_kernel(CostDev cf, const int32_t *__restrict__ cols, 
     if (threadIdx.x == 0) v_full[j] = best;
 }
 
+// Multiscale warm start: the duals of the 2x2-binned problem at the fine points.  Cell (bx, by)
+// holds the fine coordinates (o + 2b, o + 2b + 1), so a fine point sits at the continuous coarse
+// coordinate (x - o - 0.5) / 2; the four surrounding cells are blended bilinearly over those that
+// are occupied (the point's own cell is always among them and always occupied).
+__global__ void upsample_kernel(int count, const int32_t *__restrict__ x, const int32_t *__restrict__ y, int ox,
+                                int oy, int W, int H, const int32_t *__restrict__ lattice,
+                                const double *__restrict__ uc, double scale, double *__restrict__ out) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < count; k += gridDim.x * blockDim.x) {
+        const double xi = (x[k] - ox - 0.5) * 0.5, eta = (y[k] - oy - 0.5) * 0.5;
+        const int bx = (int)floor(xi), by = (int)floor(eta);
+        const double fx = xi - bx, fy = eta - by;
+        double acc = 0.0, wsum = 0.0;
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+            for (int dx = 0; dx < 2; ++dx) {
+                const int cx = bx + dx, cy = by + dy;
+                if (cx < 0 || cy < 0 || cx >= W || cy >= H) continue;
+                const int idx = lattice[(int64_t)cy * W + cx];
+                if (idx < 0) continue;
+                const double w = (dx ? fx : 1.0 - fx) * (dy ? fy : 1.0 - fy);
+                acc += w * uc[idx];
+                wsum += w;
+            }
+        out[k] = wsum > 0.0 ? scale * acc / wsum : 0.0;
+    }
+}
+
 __global__ void scale_copy_kernel(int64_t count, const double *__restrict__ x, double f, double *__restrict__ y) {
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count; k += (int64_t)gridDim.x * blockDim.x)
         y[k] = x[k] * f;
@@ -239,6 +267,9 @@ struct ot_ipm {
     std::vector<int32_t> warm_ir, warm_jr;
     JSet jset;                                // heuristic pricing set (Section 3.4), built on first use
     std::vector<double> as_host, bs_host;     // scaled masses (for the initial support's completion)
+    std::vector<double> ms_u, ms_v;           // multiscale warm-start duals (host)
+    int32_t ms_levels = 0;                    // coarse levels solved for the warm start
+    double create_seconds = 0.0;
 };
 
 namespace {
@@ -890,6 +921,106 @@ void caller_pairs(const ot_ipm *h, int32_t *i, int32_t *j, int64_t k) {
     }
 }
 
+Error create_impl(const ot_problem *P, const ot_options *O, ot_ipm *h);
+Error do_step(ot_ipm *h, ot_iter_info *info);
+
+constexpr int kMsMinPoints = 256;             // no coarser level below this many points per side
+constexpr int64_t kMsMaxCells = 1LL << 26;    // bound of the coarse lattice
+
+// Multiscale warm start (see ot_options.multiscale): solve the 2x2-binned problem (recursively
+// coarser itself), interpolate its duals at the points, and hand them to the warm start.  A coarse
+// solve that fails leaves the cold start.
+Error multiscale_start(ot_ipm *h, const std::vector<double> &as, const std::vector<double> &bs,
+                       const std::vector<int32_t> &hx, const std::vector<int32_t> &hy,
+                       const std::vector<int32_t> &gx, const std::vector<int32_t> &gy, cudaStream_t st) {
+    ot_options &o = h->opt;
+    const int m = h->m, n = h->n;
+    if (o.multiscale <= 0 || h->cd.kind == OT_COST_DENSE || (o.warm_u && o.warm_v) || m < kMsMinPoints ||
+        n < kMsMinPoints)
+        return ok();
+    int ox = INT32_MAX, oy = INT32_MAX, xmax = INT32_MIN, ymax = INT32_MIN;
+    for (int i = 0; i < m; ++i) { ox = std::min(ox, hx[i]); oy = std::min(oy, hy[i]); xmax = std::max(xmax, hx[i]); ymax = std::max(ymax, hy[i]); }
+    for (int j = 0; j < n; ++j) { ox = std::min(ox, gx[j]); oy = std::min(oy, gy[j]); xmax = std::max(xmax, gx[j]); ymax = std::max(ymax, gy[j]); }
+    const int W = (xmax - ox) / 2 + 1, H = (ymax - oy) / 2 + 1;
+    if ((int64_t)W * H > kMsMaxCells) return ok();
+    // cells: masses summed, coordinates = cell index
+    std::vector<int32_t> slat((size_t)W * H, -1), tlat((size_t)W * H, -1);
+    std::vector<double> ca, cb;
+    std::vector<int32_t> csx, csy, ctx, cty;
+    for (int i = 0; i < m; ++i) {
+        const int bx = (hx[i] - ox) / 2, by = (hy[i] - oy) / 2;
+        int32_t &c = slat[(size_t)by * W + bx];
+        if (c < 0) { c = (int32_t)ca.size(); ca.push_back(0.0); csx.push_back(bx); csy.push_back(by); }
+        ca[c] += as[i];
+    }
+    for (int j = 0; j < n; ++j) {
+        const int bx = (gx[j] - ox) / 2, by = (gy[j] - oy) / 2;
+        int32_t &c = tlat[(size_t)by * W + bx];
+        if (c < 0) { c = (int32_t)cb.size(); cb.push_back(0.0); ctx.push_back(bx); cty.push_back(by); }
+        cb[c] += bs[j];
+    }
+    ot_problem cp{};
+    cp.m = (int32_t)ca.size();
+    cp.n = (int32_t)cb.size();
+    cp.a = ca.data();
+    cp.b = cb.data();
+    cp.cost = h->cd.kind;
+    cp.src_x = csx.data(); cp.src_y = csy.data(); cp.dst_x = ctx.data(); cp.dst_y = cty.data();
+    ot_options co = o;
+    co.multiscale = o.multiscale - 1;
+    // the coarse duals only guide the fine start: relative tolerance ms_tol on every test
+    co.tol = o.ms_tol > 0 ? o.ms_tol : std::max(o.tol, 1e-4);
+    double cmass = 0.0;
+    for (double x : ca) cmass += x;
+    co.feas_l1 = co.tol * cmass;
+    co.max_iter = std::max(o.max_iter, 200);
+    co.warm_u = co.warm_v = nullptr;
+    co.warm_i = co.warm_j = nullptr;
+    co.warm_npairs = 0;
+    co.warm_count = 0;
+    co.add_max = 0;
+    co.stream = st;
+    ot_ipm *hc = new (std::nothrow) ot_ipm();
+    if (!hc) return fail(OT_ERR_OOM, "multiscale: host allocation failed");
+    Error e = create_impl(&cp, &co, hc);
+    while (e.code == OT_OK && !hc->done) e = do_step(hc, nullptr);
+    if (e.code == OT_OK) {
+        const double scale = h->cd.kind == OT_COST_SQEUCLID ? 4.0 : 2.0;
+        e = [&]() -> Error {
+            DevTemp<int32_t> dsl, dtl;
+            DevTemp<double> wu, wv;
+            OT_TRY(dsl.alloc((int64_t)W * H, st));
+            OT_TRY(dtl.alloc((int64_t)W * H, st));
+            OT_TRY(wu.alloc(m, st));
+            OT_TRY(wv.alloc(n, st));
+            OT_CUDA(cudaMemcpyAsync(dsl.p, slat.data(), sizeof(int32_t) * slat.size(), cudaMemcpyHostToDevice, st));
+            OT_CUDA(cudaMemcpyAsync(dtl.p, tlat.data(), sizeof(int32_t) * tlat.size(), cudaMemcpyHostToDevice, st));
+            upsample_kernel<<<(unsigned)std::min<int64_t>(ceil_div(m, 256), 1024), 256, 0, st>>>(
+                m, h->sx, h->sy, ox, oy, W, H, dsl.p, hc->u, scale, wu.p);
+            OT_LAUNCHED();
+            upsample_kernel<<<(unsigned)std::min<int64_t>(ceil_div(n, 256), 1024), 256, 0, st>>>(
+                n, h->tx, h->ty, ox, oy, W, H, dtl.p, hc->v, scale, wv.p);
+            OT_LAUNCHED();
+            h->ms_u.resize(m);
+            h->ms_v.resize(n);
+            OT_CUDA(cudaMemcpyAsync(h->ms_u.data(), wu.p, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
+            OT_CUDA(cudaMemcpyAsync(h->ms_v.data(), wv.p, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+            OT_CUDA(cudaStreamSynchronize(st));
+            return ok();
+        }();
+        if (e.code == OT_OK) {
+            o.warm_u = h->ms_u.data();
+            o.warm_v = h->ms_v.data();
+            if (o.warm_count <= 0) o.warm_count = (int32_t)std::min<int64_t>(10LL * (m + n), INT32_MAX);
+            h->ms_levels = 1 + hc->ms_levels;
+        }
+    }
+    const bool cuda_failed = e.code == OT_ERR_CUDA;
+    ot_ipm_destroy(hc);
+    if (cuda_failed) return e;
+    return ok();
+}
+
 Error create_impl(const ot_problem *P, const ot_options *O, ot_ipm *h) {
     if (!P || P->m <= 0 || P->n <= 0 || !P->a || !P->b) return fail(OT_ERR_ARG, "problem: sizes or masses missing");
     const int32_t m0 = P->m, n0 = P->n;
@@ -1085,6 +1216,8 @@ Error create_impl(const ot_problem *P, const ot_options *O, ot_ipm *h) {
         }
     }
 
+    OT_TRY(multiscale_start(h, as, bs, hx, hy, gx, gy, st));
+
     // initial support (Section 3.2 end) and Mehrotra's starting point
     int32_t *ii = nullptr, *jj = nullptr;
     int64_t psi0 = 0;
@@ -1163,6 +1296,8 @@ void ot_options_default(ot_options *o) {
     o->new_col_rule = 1;
     o->jset_cmax = 0.0;
     o->jset_refresh = 3;
+    o->multiscale = 0;
+    o->ms_tol = 0.0;
     o->verbose = 0;
     o->stream = nullptr;
 }
@@ -1172,7 +1307,9 @@ int ot_ipm_create(const ot_problem *prob, const ot_options *opt, ot_ipm_t **out)
     *out = nullptr;
     ot_ipm *h = new (std::nothrow) ot_ipm();
     if (!h) { set_thread_error("ot_ipm_create: host allocation failed"); return OT_ERR_OOM; }
+    const auto t0 = std::chrono::steady_clock::now();
     Error e = create_impl(prob, opt, h);
+    h->create_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (e.code != OT_OK) {
         set_thread_error(e.msg.c_str());
         ot_ipm_destroy(h);
@@ -1239,6 +1376,8 @@ int ot_ipm_solve(ot_ipm_t *h, ot_result *res) {
         res->seconds = ms * 1e-3;
         res->warm_added = h->warm_added;
         res->warm_restarts = h->warm_restarts;
+        res->create_seconds = h->create_seconds;
+        res->ms_levels = h->ms_levels;
     }
     return rc;
 }
