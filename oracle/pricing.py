@@ -85,3 +85,65 @@ def select_bruteforce(C: np.ndarray, u, v, support: set, kmax: int, cmax: float 
                 cand.append((d, i + j * m, i, j))
     cand.sort()
     return [(i, j) for _, _, i, j in cand[:kmax]]
+
+
+def _chunk_topk(args):
+    cost, u, v, sup_key, i0, i1, kmax, cmax, rows_per_chunk = args
+    m, n = cost.m, cost.n
+    best_I = np.zeros(0, np.int64)
+    best_J = np.zeros(0, np.int64)
+    best_D = np.zeros(0)
+    for r0 in range(i0, i1, rows_per_chunk):
+        r1 = min(i1, r0 + rows_per_chunk)
+        c = cost.block(r0, r1)
+        d = (c - u[r0:r1, None]) - v[None, :]
+        neg = d < 0.0
+        if cmax is not None:
+            neg &= c < cmax
+        ii, jj = np.nonzero(neg)
+        if ii.size == 0:
+            continue
+        gi = (ii + r0).astype(np.int64)
+        jj = jj.astype(np.int64)
+        key = gi * n + jj
+        if len(sup_key):
+            pos = np.searchsorted(sup_key, key)
+            member = (pos < len(sup_key)) & (sup_key[np.minimum(pos, len(sup_key) - 1)] == key)
+            keep = ~member
+            gi, jj = gi[keep], jj[keep]
+            dd = d[ii[keep], jj]
+        else:
+            dd = d[ii, jj]
+        I = np.concatenate([best_I, gi])
+        J = np.concatenate([best_J, jj])
+        D = np.concatenate([best_D, dd])
+        o = np.lexsort((I + J * m, D))[:kmax]
+        best_I, best_J, best_D = I[o], J[o], D[o]
+    return best_I, best_J, best_D
+
+
+def select_streaming(cost: Cost, u: np.ndarray, v: np.ndarray, support_i, support_j, kmax: int,
+                     cmax: float | None = None, rows_per_chunk: int | None = None, workers: int = 1):
+    """The same selection as ``select`` for inputs too large to hold every candidate: each block of
+    rows keeps its own first kmax candidates in (d, jlin) order, and the blocks' lists are merged
+    the same way (the overall first kmax are among the blocks' first kmax).  ``workers`` > 1 runs
+    the blocks in a process pool started with 'spawn'."""
+    m, n = cost.m, cost.n
+    sup_key = np.sort(np.asarray(support_i, np.int64) * n + np.asarray(support_j, np.int64))
+    if rows_per_chunk is None:
+        rows_per_chunk = max(1, (1 << 22) // max(n, 1))
+    nblk = max(1, workers * 4)
+    edges = np.linspace(0, m, nblk + 1).astype(int)
+    jobs = [(cost, u, v, sup_key, int(edges[b]), int(edges[b + 1]), kmax, cmax, rows_per_chunk)
+            for b in range(nblk) if edges[b + 1] > edges[b]]
+    if workers > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(workers) as pool:
+            parts = pool.map(_chunk_topk, jobs)
+    else:
+        parts = [_chunk_topk(j) for j in jobs]
+    I = np.concatenate([p[0] for p in parts])
+    J = np.concatenate([p[1] for p in parts])
+    D = np.concatenate([p[2] for p in parts])
+    o = np.lexsort((I + J * m, D))[:kmax]
+    return I[o], J[o], D[o]

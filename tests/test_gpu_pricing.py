@@ -92,3 +92,23 @@ def test_full_size_configs(k):
     si, sj = U.neighbourhood_support(sx, sy, sx, sy)
     n = _check(sx, sy, sx, sy, u, v, si, sj, k * k, 1)
     assert n == k * k          # more candidates than kmax: the threshold path is exercised
+
+
+def test_full_size_256x256_against_oracle():
+    """Config 5's full size (256x256: 4.29e9 pairs) in the launch configuration the benchmark times
+    (FP32 scan with 256-row tiles, FP64 recheck; and the FP64 scan), kmax = m, support = the 3x3
+    neighbourhood, seeded duals with the structure of IPM iterates; compared pair for pair with
+    the oracle's exact rule evaluated blockwise over all pairs in 16 processes."""
+    from paper_2206_11009_gb300 import price_topk
+    k = 256
+    sx, sy = U.rect_coords(k, k)
+    u, v = U.banded_duals(sx, sy, sx, sy, seed=k, amp=6.0, noise=2.0)
+    si, sj = U.neighbourhood_support(sx, sy, sx, sy)
+    c = costs.Cost.points(sx, sy, sx, sy, "sqeuclid")
+    oi, oj, od = pricing.select_streaming(c, u, v, si.astype(np.int64), sj.astype(np.int64), k * k, workers=16)
+    assert len(oi) == k * k
+    T = U.cuda_tensors(sx, sy, sx, sy, u, v, si, sj)
+    for precision in (1, 0):
+        gi, gj, gd = price_topk(*T, kmax=k * k, precision=precision)
+        assert np.array_equal(gi.cpu().numpy(), oi) and np.array_equal(gj.cpu().numpy(), oj)
+        assert np.array_equal(gd.cpu().numpy(), od)

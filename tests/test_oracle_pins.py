@@ -469,3 +469,20 @@ def test_ipm_oracle_on_point_sets_that_do_not_overlap():
     ref = netsimplex.solve(c, a, b)
     r = ipm.solve(c, a, b, ipm.Options(tol=1e-8))
     assert r.status == "optimal" and abs(r.obj - ref.obj) <= 1e-7 * ref.obj
+
+
+@pytest.mark.parametrize("workers", [1, 2])
+def test_streaming_selection_equals_the_plain_rule(workers):
+    """The blockwise top-k selection (for 4.29e9 pairs) against the plain rule: exact same pairs,
+    order and values, ties included, with and without J."""
+    k = 24
+    c = costs.square_grid(k)
+    rng = synth.uniform01(66, 2 * k * k)
+    u = np.round(rng[:k * k] * 30, 1)
+    v = np.round(rng[k * k:] * 30, 1) - 20
+    I, J = np.nonzero(synth.uniform01(67, (k * k) ** 2).reshape(k * k, k * k) < 0.01)
+    for kmax in (1, 37, 576, 10 ** 6):
+        for cmax in (None, 20.0):
+            a = pricing.select(c, u, v, I, J, kmax, cmax=cmax)
+            b = pricing.select_streaming(c, u, v, I, J, kmax, cmax=cmax, rows_per_chunk=50, workers=workers)
+            assert all(np.array_equal(x, y) for x, y in zip(a, b))
