@@ -143,6 +143,16 @@ typedef struct {
      * ot_ipm_create (ot_result.create_seconds). */
     int32_t multiscale;
     double ms_tol;
+    /* Preconditioner of the iterative phase (Section 4.2).  0: the library's choice (mixed
+     * precision: the FP32 dense factorisation for n <= 8192, Jacobi PCG otherwise; FP64: Jacobi
+     * PCG).  1: incomplete Cholesky with a drop tolerance -- the factor keeps S_M's pattern in a
+     * multicolour order (every colour's rows in parallel), drops l_rs when |l_rs d_s| <
+     * tau sqrt(S_rr S_ss) and grounds pivots d_r <= 1e-12 S_rr -- preconditioning an FP64 CG to the
+     * PCG tolerance; tau starts at ic_tau (0 = 1e-2) and is divided by 10 (down to 1e-6) after an
+     * iteration whose solves needed more than 200 CG iterations.  The switch to the direct branch
+     * (Section 4.3) is unchanged. */
+    int32_t precond;
+    double ic_tau;
 } ot_options;
 
 /* One outer iteration (Section 3.4's commented listing). */
@@ -231,7 +241,9 @@ enum {
     OT_LS_MIXED = 1,    /* Jacobi PCG in FP32 inside FP64 iterative refinement                     */
     OT_LS_DENSE32 = 2,  /* FP64 CG preconditioned by the FP32 dense LDL^T of S_M (n <= 16384)      */
     OT_LS_DENSE64 = 3,  /* FP64 dense LDL^T with the infinite-pivot rule (Section 4.3, n <= 8192)  */
-    OT_LS_SPARSE = 4    /* FP64 sparse LDL^T, fill-reducing order, no dropping (Section 4.3)       */
+    OT_LS_SPARSE = 4,   /* FP64 sparse LDL^T, fill-reducing order, no dropping (Section 4.3)       */
+    OT_LS_IC = 5        /* FP64 CG preconditioned by the incomplete Cholesky factor, drop tolerance */
+                        /* 1e-2 (Section 4.2; ot_options.precond 1)                                 */
 };
 
 /* The predictor direction (du, dv, dp, ds) of the normal equations (Section 3, eq. redsystem with
@@ -245,6 +257,13 @@ enum {
  * (n above the dense factor's limit, sparse fill over budget), OT_ERR_CUDA, OT_ERR_TIMEOUT. */
 int ot_ipm_newton_direction(ot_ipm_t *h, int32_t solver, double cg_tol, int32_t max_cg, double *du, double *dv,
                             double *dp, double *ds, int64_t cap, int32_t *cg_iters);
+
+/* The incomplete Cholesky preconditioner (Section 4.2; the factor of ot_options.precond 1, see
+ * there) of S_M at the handle's current iterate, with drop tolerance tau >= 0, applied to b:
+ * x = L^-T D^-1 L^-1 b (grounded pivots contribute 0).  b and x are HOST buffers of n entries in
+ * the caller's target indexing (entries of targets removed by the presolve: ignored / 0).  The
+ * iterate is not changed.  The parity hook of the factor.  Errors: OT_ERR_ARG, OT_ERR_CUDA. */
+int ot_ipm_ic_apply(ot_ipm_t *h, double tau, const double *b, double *x);
 
 /* Internal scale factor sigma_f = m / sum(a) (masses are multiplied by it). */
 double ot_ipm_mass_scale(const ot_ipm_t *h);

@@ -34,7 +34,7 @@ class OtOptions(ctypes.Structure):
                 ("warm_mode", c_int32), ("warm_i", c_void_p), ("warm_j", c_void_p), ("warm_npairs", c_int64),
                 ("new_col_rule", c_int32), ("scan_rows", c_int32), ("dense32_max_n", c_int32),
                 ("dense_max_n", c_int32), ("jset_cmax", c_double), ("jset_refresh", c_int32),
-                ("multiscale", c_int32), ("ms_tol", c_double)]
+                ("multiscale", c_int32), ("ms_tol", c_double), ("precond", c_int32), ("ic_tau", c_double)]
 
 
 class OtPriceOpts(ctypes.Structure):
@@ -71,6 +71,7 @@ SIGNATURES = {
     "ot_ipm_set_state": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p,
                                    c_int32]),
     "ot_ipm_mass_scale": (c_double, [c_void_p]),
+    "ot_ipm_ic_apply": (c_int32, [c_void_p, c_double, c_void_p, c_void_p]),
     "ot_ipm_destroy": (None, [c_void_p]),
     "ot_ipm_last_error": (c_char_p, [c_void_p]),
     "ot_last_error": (c_char_p, []),

@@ -182,7 +182,7 @@ class Solver:
         check(self._lib.ot_ipm_set_state(self.h, _ptr(arrs[0]), _ptr(arrs[1]), _ptr(arrs[2]), _ptr(arrs[3]),
                                          len(arrs[0]), _ptr(arrs[4]), _ptr(arrs[5]), int(reset_mu0)), self.h)
 
-    LINEAR_SOLVERS = {"pcg64": 0, "mixed": 1, "dense32": 2, "dense64": 3, "sparse": 4}
+    LINEAR_SOLVERS = {"pcg64": 0, "mixed": 1, "dense32": 2, "dense64": 3, "sparse": 4, "ic": 5}
 
     def newton_direction(self, solver: str = "pcg64", cg_tol: float = 1e-12, max_cg: int = 20000):
         """Predictor direction (du, dv, dp, ds) at the current iterate by one linear solver
@@ -195,6 +195,14 @@ class Solver:
         check(self._lib.ot_ipm_newton_direction(self.h, self.LINEAR_SOLVERS[solver], cg_tol, max_cg, _ptr(du),
                                                 _ptr(dv), _ptr(dp), _ptr(ds), k, ctypes.byref(its)), self.h)
         return du, dv, dp, ds, its.value
+
+    def ic_apply(self, b, tau: float = 1e-2):
+        """The incomplete Cholesky preconditioner of the current iterate applied to b
+        (ot_ipm_ic_apply)."""
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        x = np.zeros(self.n)
+        check(self._lib.ot_ipm_ic_apply(self.h, tau, _ptr(b), _ptr(x)), self.h)
+        return x
 
     @property
     def mass_scale(self) -> float:

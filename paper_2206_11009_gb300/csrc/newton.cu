@@ -2,6 +2,7 @@
 // (eq. normalequationsipm) and the Schur complement S_M = N - V^T M^-1 V (Section 4), solved
 // matrix-free by PCG.  All reductions are deterministic (fixed-order two-stage sums).
 #include "newton.cuh"
+#include "ic.cuh"
 #include "dense32.cuh"
 #include "chol.cuh"
 #include "primitives.cuh"
@@ -1145,17 +1146,20 @@ static Error solve_direct(Newton &W, const Support &S, double tol, int max_cg, d
                           cudaStream_t st) {
     const unsigned gm = grid_of(W.m, W.num_sms), gn = grid_of(W.n, W.num_sms);
     Chol *C = W.direct;
+    const bool ic_only = !C && !W.d32 && W.ic;
     // near optimality the primal-infeasibility part of the right-hand side is tiny next to the
-    // complementarity part, so the direct branch solves far below the PCG tolerance
-    const double target = std::min(tol, 1e-10);
+    // complementarity part, so the direct branch solves far below the PCG tolerance; the incomplete
+    // factor is the iterative phase's preconditioner and stops at the PCG tolerance
+    const double target = ic_only ? tol : std::min(tol, 1e-10);
     double *x = W.x64, *r = W.r64, *z = W.z64, *p = W.p64, *q = W.q64;
     double hs[SC_COUNT];
     OT_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * W.n, st));
     copy_kernel<<<gn, kT, 0, st>>>(W.n, W.rhs, r);
     OT_LAUNCHED();
     auto precond = [&](const double *in, double *out) -> Error {
-        if (!C) return d32_apply(*W.d32, in, out, st);
-        return W.dense ? dense_solve(*W.dense, in, out, st) : chol_solve(*C, in, out, st);
+        if (C) return W.dense ? dense_solve(*W.dense, in, out, st) : chol_solve(*C, in, out, st);
+        if (W.d32) return d32_apply(*W.d32, in, out, st);
+        return ic_apply(*W.ic, in, out, st);
     };
     OT_TRY(precond(r, z));
     pcg_dir_kernel<<<gn, kT, 0, st>>>(W.n, 0.0, z, p);
@@ -1175,7 +1179,7 @@ static Error solve_direct(Newton &W, const Support &S, double tol, int max_cg, d
     int it = 0;
     // an accurate FP32 factor gains several digits per iteration; one that needs many more has
     // met a matrix beyond FP32 and hands the system to the FP64 factorisation
-    const int cap = C ? max_cg : std::min(max_cg, kD32MaxCg);
+    const int cap = (C || ic_only) ? max_cg : std::min(max_cg, kD32MaxCg);
     // alpha and beta stay on the device; the host reads p.q and r.r of each iteration while the
     // GPU already applies the preconditioner for the next one (wasted only at the last iteration)
     {
@@ -1458,7 +1462,7 @@ Error newton_solve(Newton &W, const Support &S, const Rhs &R, double cg_tol, int
     OT_TRY(project(W, W.rhs, one, st));
 
     SolveStats ss;
-    if (W.direct || W.d32) {
+    if (W.direct || W.d32 || W.ic) {
         OT_TRY(solve_direct(W, S, cg_tol, max_cg, dv, &ss, st));
     } else if (precision == 0) {
         OT_TRY(solve_pcg64(W, S, cg_tol, max_cg, dv, &ss, st));

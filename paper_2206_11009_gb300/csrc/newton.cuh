@@ -63,6 +63,9 @@ struct Newton {
     struct DenseLDL *dense = nullptr;   // when set (with direct), solve with the dense factor
     // when set (and direct is not): FP64 CG preconditioned by the FP32 dense factorisation
     struct Dense32 *d32 = nullptr;
+    // when set (and neither of the above): FP64 CG preconditioned by the incomplete Cholesky factor
+    // (ic.cuh), stopped at the CG tolerance of the solve
+    struct IncChol *ic = nullptr;
     int fallbacks = 0;        // mixed-precision solves redone in FP64
     bool fp64_fallback = true;  // redo a failed mixed-precision solve with FP64 PCG
 };

@@ -3,6 +3,7 @@
 // update, pricing, support update), with the readings stated in ot_ipm.h.
 #include "chol.cuh"
 #include "dense32.cuh"
+#include "ic.cuh"
 #include "newton.cuh"
 #include "pricing.cuh"
 #include "primitives.cuh"
@@ -82,6 +83,10 @@ constexpr double kPivotEps = 1e-12;
 constexpr double kPcgFail = 10.0;
 // preconditioned-CG iterations above which the next factorisation drops less
 constexpr int kDirectCgMany = 25;
+// incomplete Cholesky drop tolerance: divided by 10 after more than kIcManyCg CG iterations in one
+// solve, never below kIcTauFloor
+constexpr int kIcManyCg = 200;
+constexpr double kIcTauFloor = 1e-6;
 // up to this many targets the direct branch factors S_M densely
 constexpr int kDenseMaxN = 8192;
 constexpr int kDense32MaxN = 8192;
@@ -266,6 +271,9 @@ struct ot_ipm {
     std::vector<double> warm_ur, warm_vr;     // warm-start inputs on the kept points
     std::vector<int32_t> warm_ir, warm_jr;
     JSet jset;                                // heuristic pricing set (Section 3.4), built on first use
+    IncChol ic;                               // incomplete Cholesky preconditioner (precond 1)
+    double ic_tau = 1e-2;                     // its current drop tolerance
+    int ic_cg_max = 0;                        // most CG iterations of one solve this iteration
     std::vector<double> as_host, bs_host;     // scaled masses (for the initial support's completion)
     std::vector<double> ms_u, ms_v;           // multiscale warm-start duals (host)
     int32_t ms_levels = 0;                    // coarse levels solved for the warm start
@@ -506,11 +514,13 @@ Error do_step(ot_ipm *h, ot_iter_info *info) {
     W.direct = nullptr;
     W.dense = nullptr;
     W.d32 = nullptr;
+    W.ic = nullptr;
     // mixed precision on moderate n: the FP32 dense factorisation of this iteration's S_M
     // preconditions an FP64 CG in every solve; the FP64 LDL^T branch only takes over when that CG
     // misses its target (the switch on the support's shrinkage is for the Jacobi PCG)
     const int64_t d32_max = o.dense32_max_n > 0 ? o.dense32_max_n : (o.dense32_max_n < 0 ? 0 : kDense32MaxN);
-    const bool use_d32 = o.precision == 1 && o.linear_solver == 0 && n <= std::min<int64_t>(d32_max, kDense32MaxN);
+    const bool use_d32 = o.precision == 1 && o.linear_solver == 0 && o.precond != 1 &&
+                         n <= std::min<int64_t>(d32_max, kDense32MaxN);
     if (use_d32 && !h->d32_escalated) {
         use_direct = false;
         if (!h->d32.A) OT_TRY(d32_alloc(h->d32, n));
@@ -576,6 +586,15 @@ Error do_step(ot_ipm *h, ot_iter_info *info) {
         return e.code == OT_ERR_UNSUPPORTED ? ok() : e;
     };
     if (use_direct) OT_TRY(enable_direct());
+    // Section 4.2: the iterative phase preconditioned by the incomplete Cholesky factor
+    h->ic_cg_max = 0;
+    if (o.precond == 1 && !W.direct && !W.d32) {
+        if (!h->ic.perm) OT_TRY(ic_alloc(h->ic, n));
+        bool changed = false;
+        OT_TRY(chol_assemble(h->chol, W, S, 0.0, &changed, st));
+        OT_TRY(ic_factor(h->ic, h->chol, h->ic_tau, kPivotEps, st));
+        W.ic = &h->ic;
+    }
     pc.mark("factor");
     int cg = 0;
     SolveStats ss;
@@ -586,6 +605,7 @@ Error do_step(ot_ipm *h, ot_iter_info *info) {
         OT_TRY(newton_solve(W, S, R, tol, o.max_cg, o.precision, du, dv, ds, dp, &ss, st));
         cg += ss.cg_iters;
         if (ss.direct) h->direct_cg_last = std::max(h->direct_cg_last, ss.cg_iters);
+        if (W.ic && !W.direct) h->ic_cg_max = std::max(h->ic_cg_max, ss.cg_iters);
         const bool late_d32 = W.d32 && n > kDenseMaxN;   // already the strongest solver here
         if (!W.direct && !late_d32 && o.linear_solver == 0 && !(ss.relres <= kPcgFail * tol)) {
             OT_TRY(enable_direct());
@@ -674,6 +694,8 @@ Error do_step(ot_ipm *h, ot_iter_info *info) {
     OT_CUDA(cudaStreamSynchronize(st));
     pc.mark("merge");
 
+    // the drop tolerance schedule of the incomplete factor (reading of Section 4.2)
+    if (h->ic_cg_max > kIcManyCg) h->ic_tau = std::max(h->ic_tau * 0.1, kIcTauFloor);
     h->iter++;
     h->cg_total += cg;
     inf.alpha_p = ap;
@@ -684,6 +706,9 @@ Error do_step(ot_ipm *h, ot_iter_info *info) {
     inf.added = added;
     inf.removed = removed;
     if (o.verbose >= 2) fprintf(stderr, "   phases(ms):%s\n", pc.line.c_str());
+    if (o.verbose >= 2 && W.ic)
+        fprintf(stderr, "   incomplete Cholesky: %d colours, %lld entries, drop tolerance %.1e, most CG %d\n",
+                h->ic.ncolors, (long long)h->ic.nnzL, h->ic.tau, h->ic_cg_max);
     if (o.verbose)
         fprintf(stderr, "it %3d psi %8lld mu %.3e crit %.3e ap %.3f as %.3f sig %.2e corr %d cg %d %s +%d -%lld\n",
                 inf.iter, (long long)inf.psi, mu, crit, ap, as, sigma, ncorr, cg, inf.direct ? "LDL" : "PCG", added,
@@ -1028,7 +1053,8 @@ Error create_impl(const ot_problem *P, const ot_options *O, ot_ipm *h) {
     if (O) h->opt = *O; else ot_options_default(&h->opt);
     ot_options &o = h->opt;
     if (!(o.tol > 0) || o.max_iter < 0 || o.max_cg <= 0 || o.max_corr < 0 || !(o.step_scale > 0 && o.step_scale < 1) ||
-        (o.precision != 0 && o.precision != 1) || o.jset_refresh < 0 || !std::isfinite(o.jset_cmax))
+        (o.precision != 0 && o.precision != 1) || o.jset_refresh < 0 || !std::isfinite(o.jset_cmax) ||
+        o.precond < 0 || o.precond > 1 || !(o.ic_tau >= 0 && o.ic_tau < 1))
         return fail(OT_ERR_ARG, "options: out of range");
     if (P->cost < 0 || P->cost > OT_COST_DENSE) return fail(OT_ERR_ARG, "problem: unknown cost kind");
     const bool dense = P->cost == OT_COST_DENSE;
@@ -1136,6 +1162,7 @@ Error create_impl(const ot_problem *P, const ot_options *O, ot_ipm *h) {
     OT_CUDA(cudaMalloc((void **)&h->rowmin, sizeof(unsigned long long) * m));
     OT_CUDA(cudaMalloc((void **)&h->lbv, sizeof(double)));
     if (o.add_max > m) o.add_max = m;
+    h->ic_tau = o.ic_tau > 0 ? o.ic_tau : 1e-2;
     OT_CUDA(cudaMemcpyAsync(h->a_s, as.data(), sizeof(double) * m, cudaMemcpyHostToDevice, st));
     OT_CUDA(cudaMemcpyAsync(h->b_s, bs.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
     OT_CUDA(cudaMemcpyAsync(h->sx, hx.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, st));
@@ -1298,6 +1325,8 @@ void ot_options_default(ot_options *o) {
     o->jset_refresh = 3;
     o->multiscale = 0;
     o->ms_tol = 0.0;
+    o->precond = 0;
+    o->ic_tau = 0.0;
     o->verbose = 0;
     o->stream = nullptr;
 }
@@ -1472,7 +1501,7 @@ int ot_ipm_get_state(ot_ipm_t *h, int32_t *i, int32_t *j, double *p, double *s, 
 int ot_ipm_newton_direction(ot_ipm_t *h, int32_t solver, double cg_tol, int32_t max_cg, double *du, double *dv,
                             double *dp, double *ds, int64_t cap, int32_t *cg_iters) {
     if (!h) return OT_ERR_ARG;
-    if (solver < OT_LS_PCG64 || solver > OT_LS_SPARSE || !(cg_tol > 0) || max_cg <= 0)
+    if (solver < OT_LS_PCG64 || solver > OT_LS_IC || !(cg_tol > 0) || max_cg <= 0)
         return record(h, fail(OT_ERR_ARG, "ot_ipm_newton_direction: bad solver, tolerance or iteration limit"));
     Support &S = h->S[h->cur];
     if (cap < S.psi) return record(h, fail(OT_ERR_BUF_TOO_SMALL, "ot_ipm_newton_direction: buffer too small"));
@@ -1485,6 +1514,7 @@ int ot_ipm_newton_direction(ot_ipm_t *h, int32_t solver, double cg_tol, int32_t 
         W.direct = nullptr;
         W.dense = nullptr;
         W.d32 = nullptr;
+        W.ic = nullptr;
         if (solver == OT_LS_DENSE32) {
             if (n > kDense32LateMaxN) return fail(OT_ERR_UNSUPPORTED, "FP32 dense factor: n above its limit");
             if (!h->d32.A) OT_TRY(d32_alloc(h->d32, n));
@@ -1506,6 +1536,12 @@ int ot_ipm_newton_direction(ot_ipm_t *h, int32_t solver, double cg_tol, int32_t 
             if (changed || !h->chol.have_symbolic) OT_TRY(chol_symbolic(h->chol, st));
             OT_TRY(chol_numeric(h->chol, kPivotEps, st));
             W.direct = &h->chol;
+        } else if (solver == OT_LS_IC) {
+            if (!h->ic.perm) OT_TRY(ic_alloc(h->ic, n));
+            bool changed = false;
+            OT_TRY(chol_assemble(h->chol, W, S, 0.0, &changed, st));
+            OT_TRY(ic_factor(h->ic, h->chol, 1e-2, kPivotEps, st));
+            W.ic = &h->ic;
         }
         W.fp64_fallback = false;
         OT_TRY(corrector_r3(W, S, 0.0, nullptr, nullptr, st));   // predictor: r3 = -p s
@@ -1534,6 +1570,7 @@ int ot_ipm_newton_direction(ot_ipm_t *h, int32_t solver, double cg_tol, int32_t 
     W.direct = nullptr;
     W.dense = nullptr;
     W.d32 = nullptr;
+    W.ic = nullptr;
     return record(h, e);
 }
 
@@ -1584,6 +1621,34 @@ int ot_ipm_set_state(ot_ipm_t *h, const int32_t *i, const int32_t *j, const doub
     return record(h, e);
 }
 
+int ot_ipm_ic_apply(ot_ipm_t *h, double tau, const double *b, double *x) {
+    if (!h || !b || !x || !(tau >= 0)) return OT_ERR_ARG;
+    Newton &W = h->W;
+    cudaStream_t st = h->st;
+    const int n = h->n;
+    Error e = [&]() -> Error {
+        Support &S = h->S[h->cur];
+        OT_TRY(schur_setup(W, S, st));
+        if (!h->ic.perm) OT_TRY(ic_alloc(h->ic, n));
+        bool changed = false;
+        OT_TRY(chol_assemble(h->chol, W, S, 0.0, &changed, st));
+        OT_TRY(ic_factor(h->ic, h->chol, tau, kPivotEps, st));
+        std::vector<double> hb(n), hx(n);
+        for (int r = 0; r < n; ++r) hb[r] = b[h->presolved ? h->dst_map[r] : r];
+        DevTemp<double> db, dx;
+        OT_TRY(db.alloc(n, st));
+        OT_TRY(dx.alloc(n, st));
+        OT_CUDA(cudaMemcpyAsync(db.p, hb.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
+        OT_TRY(ic_apply(h->ic, db.p, dx.p, st));
+        OT_CUDA(cudaMemcpyAsync(hx.data(), dx.p, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+        OT_CUDA(cudaStreamSynchronize(st));
+        std::fill(x, x + h->n0, 0.0);
+        for (int r = 0; r < n; ++r) x[h->presolved ? h->dst_map[r] : r] = hx[r];
+        return ok();
+    }();
+    return record(h, e);
+}
+
 double ot_ipm_mass_scale(const ot_ipm_t *h) { return h ? h->sigma_f : 0.0; }
 
 void ot_ipm_destroy(ot_ipm_t *h) {
@@ -1596,6 +1661,7 @@ void ot_ipm_destroy(ot_ipm_t *h) {
     dense_free(h->dense);
     d32_free(h->d32);
     jset_free(h->jset);
+    ic_free(h->ic);
     void *ptrs[] = {h->a_s, h->b_s, h->C, h->sx, h->sy, h->tx, h->ty, h->u, h->v, h->pi, h->pj, h->pd,
                     h->pcount, h->pstrong, h->rowmin, h->lbv, h->d_src_map, h->d_dst_map, h->fsx, h->fsy,
                     h->ftx, h->fty, h->fC};

@@ -3,7 +3,8 @@
 The iterate comes from the oracle's own IPM (a few, a middling and many iterations: Theta spread
 from 1e2 to about 1e12); the handle is put in that state and ot_ipm_newton_direction computes the
 predictor direction with one linear solver: FP64 Jacobi PCG, FP32 PCG inside FP64 refinement,
-FP64 CG preconditioned by the FP32 dense factor, the FP64 dense LDL^T and the sparse LDL^T.  The
+FP64 CG preconditioned by the FP32 dense factor, the FP64 dense LDL^T, the sparse LDL^T and FP64 CG
+preconditioned by the incomplete Cholesky factor with a drop tolerance (Section 4.2).  The
 oracle solves S_M exactly (sparse LU of the grounded system, minimum-norm gauge).
 
 Bars.  dp and ds are unique; du and dv are unique after the per-component mean-zero gauge that
@@ -13,6 +14,7 @@ decades, 1e-6 at the late iterate where it spans twelve (S_M's conditioning grow
 sign, index or dropped term in any solver gives O(1) errors.  The 23 x 23 grid (n = 529) spans
 nine 64-column panels of the dense factors with a ragged last one (17 columns)."""
 import numpy as np
+import scipy.sparse as sp
 import pytest
 
 from oracle import costs, ipm
@@ -20,7 +22,7 @@ from paper_2206_11009_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-SOLVERS = ["pcg64", "mixed", "dense32", "dense64", "sparse"]
+SOLVERS = ["pcg64", "mixed", "dense32", "dense64", "sparse", "ic"]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -96,8 +98,48 @@ def test_bad_arguments():
     inst = synth.image_pair(6, 0)
     with Solver(inst.a, inst.b, grid=(6, 6)) as s:
         its = ctypes.c_int32(0)
-        for solver, tol, mx in [(5, 1e-8, 10), (-1, 1e-8, 10), (0, 0.0, 10), (0, 1e-8, 0)]:
+        for solver, tol, mx in [(6, 1e-8, 10), (-1, 1e-8, 10), (0, 0.0, 10), (0, 1e-8, 0)]:
             assert s._lib.ot_ipm_newton_direction(s.h, solver, tol, mx, None, None, None, None, 1 << 20,
                                                   ctypes.byref(its)) == _lib.OT_ERR_ARG
         assert s._lib.ot_ipm_newton_direction(s.h, 0, 1e-8, 10, None, None, None, None, 0,
                                               ctypes.byref(its)) == _lib.OT_ERR_BUF_TOO_SMALL
+
+
+def test_incomplete_cholesky_cuts_cg_iterations():
+    """What the paper's preconditioner buys over Jacobi on the same systems: fewer CG iterations
+    to the same tolerance at early, middle and late iterates."""
+    from paper_2206_11009_gb300 import Solver
+    k = 23
+    for iters in (3, 15, 21):
+        inst, prob, st = oracle_state(k, 1, iters)
+        with Solver(inst.a, inst.b, grid=(k, k), tol=1e-8) as s:
+            s.set_state(st.I, st.J, st.p, st.s, st.u, st.v)
+            *_, its_j = s.newton_direction("pcg64", cg_tol=1e-10, max_cg=20000)
+            *_, its_ic = s.newton_direction("ic", cg_tol=1e-10, max_cg=20000)
+        print(f"k={k} it={iters}: Jacobi {its_j} CG iterations, incomplete Cholesky {its_ic}")
+        assert its_ic < its_j
+
+
+@pytest.mark.parametrize("tau", [0.0, 1e-2])
+@pytest.mark.parametrize("k,iters", [(12, 3), (23, 15)])
+def test_incomplete_cholesky_factor_matches_oracle(tau, k, iters):
+    """The preconditioner itself: the library's multicolour incomplete Cholesky factor of S_M at
+    an oracle iterate, applied to a seeded vector, against the oracle's factor (same colouring,
+    pattern, drop and pivot rules) element by element.  tau = 1e-2 drops entries, so a decision
+    at the threshold could in principle flip on rounding; none does at these iterates."""
+    from oracle import ic
+    from paper_2206_11009_gb300 import Solver
+    inst, prob, st = oracle_state(k, 1, iters)
+    m = n = k * k
+    S, V, M, N, Minv = ipm.schur_matrix(m, n, st.I, st.J, st.p / st.s)
+    # the cancellation-free diagonal (the library's S_jj): sum_i theta_ij (M_i - theta_ij) / M_i
+    th = st.p / st.s
+    diag = np.bincount(st.J, weights=th * (M[st.I] - th) / M[st.I], minlength=n)
+    off = S - sp.diags(S.diagonal())
+    perm, rows, D = ic.factor(off, diag, tau=tau)
+    b = synth.normal(3, n)
+    ref = ic.apply(perm, rows, D, b)
+    with Solver(inst.a, inst.b, grid=(k, k), tol=1e-8) as s:
+        s.set_state(st.I, st.J, st.p, st.s, st.u, st.v)
+        x = s.ic_apply(b, tau)
+    assert _err(x, ref) <= 1e-10, _err(x, ref)

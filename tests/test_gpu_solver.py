@@ -163,3 +163,15 @@ def test_large_grids_certified_by_oracle(k, seed, spike, prec):
     assert lb <= ctp * (1 + 1e-12)
     assert (ctp - lb) / ctp <= 1e-6
     assert abs(r.obj - ctp) <= 1e-9 * ctp
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("k,seed", [(16, 0), (32, 1)])
+def test_incomplete_cholesky_preconditioner_reaches_exact_optimum(precision, k, seed):
+    """The paper's iterative phase: CG preconditioned by the incomplete Cholesky factor with a
+    drop tolerance (Section 4.2), then the direct branch near optimality (Section 4.3)."""
+    inst = synth.image_pair(k, seed)
+    opt = U.opt_value(k, seed)
+    r, _ = _solve(inst, k, tol=1e-8, precision=precision, precond=1)
+    assert r.status == 0, r
+    assert abs(r.obj - opt) <= 1e-6 * opt and r.r1_l1 <= 1e-8 and r.rel_gap <= 1e-8

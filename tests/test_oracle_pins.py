@@ -7,6 +7,7 @@ from __future__ import annotations
 
 import numpy as np
 import pytest
+import scipy.sparse as sp
 
 from oracle import brute, certificate, costs, ipm, netsimplex, pricing
 from paper_2206_11009_gb300 import synth
@@ -486,3 +487,66 @@ def test_streaming_selection_equals_the_plain_rule(workers):
             a = pricing.select(c, u, v, I, J, kmax, cmax=cmax)
             b = pricing.select_streaming(c, u, v, I, J, kmax, cmax=cmax, rows_per_chunk=50, workers=workers)
             assert all(np.array_equal(x, y) for x, y in zip(a, b))
+
+
+# ----------------------------------------------------------------------------- incomplete Cholesky
+
+def _schur_of_random_support(k=7, seed=3, frac=0.12):
+    m = n = k * k
+    rng = synth.uniform01(500 + seed, m * n + m * n)
+    mask = rng[:m * n].reshape(m, n) < frac
+    I, J = np.nonzero(mask)
+    theta = 0.1 + rng[m * n:m * n + len(I)] * 10.0
+    S, V, M, N, Minv = ipm.schur_matrix(m, n, I, J, theta)
+    return S
+
+
+def test_ic_greedy_colouring_is_proper():
+    from oracle import ic
+    S = _schur_of_random_support()
+    color = ic.greedy_coloring(S)
+    C = S.tocoo()
+    off = C.row != C.col
+    assert np.all(color[C.row[off]] != color[C.col[off]])
+    perm = ic.multicolor_order(color)
+    assert sorted(perm.tolist()) == list(range(S.shape[0])) and np.all(np.diff(color[perm]) >= 0)
+
+
+def test_ic0_reproduces_the_matrix_on_its_pattern():
+    """The defining property of incomplete Cholesky without dropping: L D L^T equals S on every
+    position of S's pattern (the error lives only where fill was discarded).  S: a Schur complement
+    of a random support, shifted to be nonsingular."""
+    from oracle import ic
+    S = _schur_of_random_support()
+    n = S.shape[0]
+    diag = S.diagonal() + 0.05
+    off = S - sp.diags(S.diagonal())
+    perm, rows, D = ic.factor(off, diag, tau=0.0)
+    L = np.eye(n)
+    for r, row in enumerate(rows):
+        for s, l in row.items():
+            L[r, s] = l
+    assert np.all(np.isfinite(D)) and np.all(D > 0)
+    M = L @ np.diag(D) @ L.T
+    A = (off + sp.diags(diag)).toarray()[np.ix_(perm, perm)]
+    pat = A != 0
+    assert np.abs((M - A)[pat]).max() <= 1e-12 * np.abs(A).max()
+    # and the preconditioner applies M^-1 (in the original order)
+    b = synth.normal(4, n)
+    x = ic.apply(perm, rows, D, b)
+    Mo = np.empty_like(M)
+    Mo[np.ix_(perm, perm)] = M
+    assert np.abs(Mo @ x - b).max() <= 1e-10 * np.abs(b).max()
+
+
+def test_ic_with_a_large_drop_tolerance_is_jacobi():
+    """Weak diagonal dominance gives |S_rs| <= sqrt(S_rr S_ss), so tau = 1.01 drops every entry
+    (the first one of each row is S_rs itself) and the factor is the diagonal."""
+    from oracle import ic
+    S = _schur_of_random_support(seed=5)
+    diag = S.diagonal()
+    off = S - sp.diags(diag)
+    perm, rows, D = ic.factor(off, diag, tau=1.01)
+    assert all(all(l == 0.0 for l in row.values()) for row in rows)
+    b = synth.normal(9, S.shape[0])
+    assert np.allclose(ic.apply(perm, rows, D, b), b / diag, rtol=1e-15, atol=0)
