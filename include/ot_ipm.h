@@ -242,8 +242,12 @@ enum {
     OT_LS_DENSE32 = 2,  /* FP64 CG preconditioned by the FP32 dense LDL^T of S_M (n <= 16384)      */
     OT_LS_DENSE64 = 3,  /* FP64 dense LDL^T with the infinite-pivot rule (Section 4.3, n <= 8192)  */
     OT_LS_SPARSE = 4,   /* FP64 sparse LDL^T, fill-reducing order, no dropping (Section 4.3)       */
-    OT_LS_IC = 5        /* FP64 CG preconditioned by the incomplete Cholesky factor, drop tolerance */
+    OT_LS_IC = 5,       /* FP64 CG preconditioned by the incomplete Cholesky factor, drop tolerance */
                         /* 1e-2 (Section 4.2; ot_options.precond 1)                                 */
+    OT_LS_TREE = 6      /* exact solve on a forest support (Section 4.3, Theorem 2): the normal     */
+                        /* equations as a tree Laplacian, by the Euler-tour technique; used         */
+                        /* automatically whenever the support is a forest (linear_solver != 1);     */
+                        /* OT_ERR_UNSUPPORTED when the support has a cycle                           */
 };
 
 /* The predictor direction (du, dv, dp, ds) of the normal equations (Section 3, eq. redsystem with

@@ -182,7 +182,7 @@ class Solver:
         check(self._lib.ot_ipm_set_state(self.h, _ptr(arrs[0]), _ptr(arrs[1]), _ptr(arrs[2]), _ptr(arrs[3]),
                                          len(arrs[0]), _ptr(arrs[4]), _ptr(arrs[5]), int(reset_mu0)), self.h)
 
-    LINEAR_SOLVERS = {"pcg64": 0, "mixed": 1, "dense32": 2, "dense64": 3, "sparse": 4, "ic": 5}
+    LINEAR_SOLVERS = {"pcg64": 0, "mixed": 1, "dense32": 2, "dense64": 3, "sparse": 4, "ic": 5, "tree": 6}
 
     def newton_direction(self, solver: str = "pcg64", cg_tol: float = 1e-12, max_cg: int = 20000):
         """Predictor direction (du, dv, dp, ds) at the current iterate by one linear solver

@@ -3,6 +3,7 @@
 // matrix-free by PCG.  All reductions are deterministic (fixed-order two-stage sums).
 #include "newton.cuh"
 #include "ic.cuh"
+#include "tree.cuh"
 #include "dense32.cuh"
 #include "chol.cuh"
 #include "primitives.cuh"
@@ -1146,7 +1147,7 @@ static Error solve_direct(Newton &W, const Support &S, double tol, int max_cg, d
                           cudaStream_t st) {
     const unsigned gm = grid_of(W.m, W.num_sms), gn = grid_of(W.n, W.num_sms);
     Chol *C = W.direct;
-    const bool ic_only = !C && !W.d32 && W.ic;
+    const bool ic_only = !C && !W.d32 && !W.tree && W.ic;
     // near optimality the primal-infeasibility part of the right-hand side is tiny next to the
     // complementarity part, so the direct branch solves far below the PCG tolerance; the incomplete
     // factor is the iterative phase's preconditioner and stops at the PCG tolerance
@@ -1157,6 +1158,7 @@ static Error solve_direct(Newton &W, const Support &S, double tol, int max_cg, d
     copy_kernel<<<gn, kT, 0, st>>>(W.n, W.rhs, r);
     OT_LAUNCHED();
     auto precond = [&](const double *in, double *out) -> Error {
+        if (W.tree) return tree_solve(*W.tree, S, W.theta, in, out, st);
         if (C) return W.dense ? dense_solve(*W.dense, in, out, st) : chol_solve(*C, in, out, st);
         if (W.d32) return d32_apply(*W.d32, in, out, st);
         return ic_apply(*W.ic, in, out, st);
@@ -1179,7 +1181,7 @@ static Error solve_direct(Newton &W, const Support &S, double tol, int max_cg, d
     int it = 0;
     // an accurate FP32 factor gains several digits per iteration; one that needs many more has
     // met a matrix beyond FP32 and hands the system to the FP64 factorisation
-    const int cap = (C || ic_only) ? max_cg : std::min(max_cg, kD32MaxCg);
+    const int cap = (C || ic_only || W.tree) ? max_cg : std::min(max_cg, kD32MaxCg);
     // alpha and beta stay on the device; the host reads p.q and r.r of each iteration while the
     // GPU already applies the preconditioner for the next one (wasted only at the last iteration)
     {
@@ -1407,6 +1409,26 @@ Error schur_setup(Newton &W, const Support &S, cudaStream_t st) {
     return ok();
 }
 
+__global__ void count_roots_kernel(int nn, const int32_t *__restrict__ parent, double *part) {
+    __shared__ double sh[kT / 32];
+    double c = 0;
+    GRID_STRIDE(v, nn) c += parent[v] == (int32_t)v ? 1.0 : 0.0;
+    put_sum(c, part, SC_ONECOMP, sh);
+}
+
+Error support_components(Newton &W, int64_t *ncomp, cudaStream_t st) {
+    const int nn = W.m + W.n;
+    const unsigned gnn = grid_of(nn, W.num_sms);
+    count_roots_kernel<<<gnn, kT, 0, st>>>(nn, W.parent, W.part);
+    OT_LAUNCHED();
+    Finish f{1, {SC_ONECOMP}, {(int)gnn}, {0}};
+    OT_TRY(finish(f, W, st));
+    double hs[SC_COUNT];
+    OT_TRY(read_scalars(W, hs, st));
+    *ncomp = (int64_t)hs[SC_ONECOMP];
+    return ok();
+}
+
 Error support_connected(Newton &W, const Support &S, bool *one, cudaStream_t st) {
     const int nn = W.m + W.n;
     const unsigned gnn = grid_of(nn, W.num_sms), ge = grid_of(S.psi, W.num_sms), gn = grid_of(W.n, W.num_sms);
@@ -1462,7 +1484,7 @@ Error newton_solve(Newton &W, const Support &S, const Rhs &R, double cg_tol, int
     OT_TRY(project(W, W.rhs, one, st));
 
     SolveStats ss;
-    if (W.direct || W.d32 || W.ic) {
+    if (W.direct || W.d32 || W.ic || W.tree) {
         OT_TRY(solve_direct(W, S, cg_tol, max_cg, dv, &ss, st));
     } else if (precision == 0) {
         OT_TRY(solve_pcg64(W, S, cg_tol, max_cg, dv, &ss, st));

@@ -66,6 +66,9 @@ struct Newton {
     // when set (and neither of the above): FP64 CG preconditioned by the incomplete Cholesky factor
     // (ic.cuh), stopped at the CG tolerance of the solve
     struct IncChol *ic = nullptr;
+    // when set: the support is a forest and the Newton system is solved exactly on the tree
+    // (tree.cuh); takes precedence over every other solver
+    struct TreeSolver *tree = nullptr;
     int fallbacks = 0;        // mixed-precision solves redone in FP64
     bool fp64_fallback = true;  // redo a failed mixed-precision solve with FP64 PCG
 };
@@ -86,6 +89,10 @@ Error residuals(Newton &W, const Support &S, const double *a_s, const double *b_
 // theta = p/s, M, N, M^-1, Jacobi diagonal of S_M (cancellation-free), column-order copies;
 // connected components of the support graph.
 Error schur_setup(Newton &W, const Support &S, cudaStream_t st);
+
+// Number of connected components of the support graph, from the labels schur_setup left in
+// W.parent (one host read).
+Error support_components(Newton &W, int64_t *ncomp, cudaStream_t st);
 
 // *one = whether the support graph is connected (every row has a pair; columns are compared).
 Error support_connected(Newton &W, const Support &S, bool *one, cudaStream_t st);

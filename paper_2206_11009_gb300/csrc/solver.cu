@@ -4,6 +4,7 @@
 #include "chol.cuh"
 #include "dense32.cuh"
 #include "ic.cuh"
+#include "tree.cuh"
 #include "newton.cuh"
 #include "pricing.cuh"
 #include "primitives.cuh"
@@ -272,6 +273,8 @@ struct ot_ipm {
     std::vector<int32_t> warm_ir, warm_jr;
     JSet jset;                                // heuristic pricing set (Section 3.4), built on first use
     IncChol ic;                               // incomplete Cholesky preconditioner (precond 1)
+    TreeSolver tree;                          // exact solver for forest supports
+    int64_t tree_iters = 0;                   // iterations solved on a forest support
     double ic_tau = 1e-2;                     // its current drop tolerance
     int ic_cg_max = 0;                        // most CG iterations of one solve this iteration
     std::vector<double> as_host, bs_host;     // scaled masses (for the initial support's completion)
@@ -348,6 +351,20 @@ Error lower_bound(ot_ipm *h, double *lb) {
     OT_LAUNCHED();
     OT_CUDA(cudaMemcpyAsync(lb, h->lbv, sizeof(double), cudaMemcpyDeviceToHost, h->st));
     OT_CUDA(cudaStreamSynchronize(h->st));
+    return ok();
+}
+
+// A forest support (psi == m + n - #components: Theorem 2's structure near optimality) is solved
+// exactly on the tree; *is_forest tells whether this iteration's support is one.
+Error forest_setup(ot_ipm *h, const Support &S, bool *is_forest, cudaStream_t st) {
+    *is_forest = false;
+    if (S.psi > (int64_t)h->m + h->n - 1) return ok();
+    int64_t ncomp = 0;
+    OT_TRY(support_components(h->W, &ncomp, st));
+    if (S.psi != (int64_t)h->m + h->n - ncomp) return ok();
+    if (!h->tree.order) OT_TRY(tree_alloc(h->tree, h->m, h->n, std::max<int64_t>(S.psi, (int64_t)h->m + h->n)));
+    OT_TRY(tree_build(h->tree, S, h->W.parent, st));
+    *is_forest = true;
     return ok();
 }
 
@@ -515,13 +532,24 @@ Error do_step(ot_ipm *h, ot_iter_info *info) {
     W.dense = nullptr;
     W.d32 = nullptr;
     W.ic = nullptr;
+    W.tree = nullptr;
+    // Section 4.3 / Theorem 2: a forest support needs no factorisation at all
+    bool forest = false;
+    if (o.linear_solver != 1) OT_TRY(forest_setup(h, S, &forest, st));
+    if (forest) {
+        W.tree = &h->tree;
+        h->tree_iters++;
+        inf.direct = 1;
+    }
     // mixed precision on moderate n: the FP32 dense factorisation of this iteration's S_M
     // preconditions an FP64 CG in every solve; the FP64 LDL^T branch only takes over when that CG
     // misses its target (the switch on the support's shrinkage is for the Jacobi PCG)
     const int64_t d32_max = o.dense32_max_n > 0 ? o.dense32_max_n : (o.dense32_max_n < 0 ? 0 : kDense32MaxN);
     const bool use_d32 = o.precision == 1 && o.linear_solver == 0 && o.precond != 1 &&
                          n <= std::min<int64_t>(d32_max, kDense32MaxN);
-    if (use_d32 && !h->d32_escalated) {
+    if (forest) {
+        use_direct = false;
+    } else if (use_d32 && !h->d32_escalated) {
         use_direct = false;
         if (!h->d32.A) OT_TRY(d32_alloc(h->d32, n));
         OT_TRY(d32_assemble(h->d32, W, S, st));
@@ -588,7 +616,7 @@ Error do_step(ot_ipm *h, ot_iter_info *info) {
     if (use_direct) OT_TRY(enable_direct());
     // Section 4.2: the iterative phase preconditioned by the incomplete Cholesky factor
     h->ic_cg_max = 0;
-    if (o.precond == 1 && !W.direct && !W.d32) {
+    if (o.precond == 1 && !W.direct && !W.d32 && !W.tree) {
         if (!h->ic.perm) OT_TRY(ic_alloc(h->ic, n));
         bool changed = false;
         OT_TRY(chol_assemble(h->chol, W, S, 0.0, &changed, st));
@@ -607,7 +635,7 @@ Error do_step(ot_ipm *h, ot_iter_info *info) {
         if (ss.direct) h->direct_cg_last = std::max(h->direct_cg_last, ss.cg_iters);
         if (W.ic && !W.direct) h->ic_cg_max = std::max(h->ic_cg_max, ss.cg_iters);
         const bool late_d32 = W.d32 && n > kDenseMaxN;   // already the strongest solver here
-        if (!W.direct && !late_d32 && o.linear_solver == 0 && !(ss.relres <= kPcgFail * tol)) {
+        if (!W.direct && !W.tree && !late_d32 && o.linear_solver == 0 && !(ss.relres <= kPcgFail * tol)) {
             OT_TRY(enable_direct());
             if (W.direct || (W.d32 && n > kDenseMaxN)) {
                 h->direct_mode = true;
@@ -1501,7 +1529,7 @@ int ot_ipm_get_state(ot_ipm_t *h, int32_t *i, int32_t *j, double *p, double *s, 
 int ot_ipm_newton_direction(ot_ipm_t *h, int32_t solver, double cg_tol, int32_t max_cg, double *du, double *dv,
                             double *dp, double *ds, int64_t cap, int32_t *cg_iters) {
     if (!h) return OT_ERR_ARG;
-    if (solver < OT_LS_PCG64 || solver > OT_LS_IC || !(cg_tol > 0) || max_cg <= 0)
+    if (solver < OT_LS_PCG64 || solver > OT_LS_TREE || !(cg_tol > 0) || max_cg <= 0)
         return record(h, fail(OT_ERR_ARG, "ot_ipm_newton_direction: bad solver, tolerance or iteration limit"));
     Support &S = h->S[h->cur];
     if (cap < S.psi) return record(h, fail(OT_ERR_BUF_TOO_SMALL, "ot_ipm_newton_direction: buffer too small"));
@@ -1515,6 +1543,7 @@ int ot_ipm_newton_direction(ot_ipm_t *h, int32_t solver, double cg_tol, int32_t 
         W.dense = nullptr;
         W.d32 = nullptr;
         W.ic = nullptr;
+        W.tree = nullptr;
         if (solver == OT_LS_DENSE32) {
             if (n > kDense32LateMaxN) return fail(OT_ERR_UNSUPPORTED, "FP32 dense factor: n above its limit");
             if (!h->d32.A) OT_TRY(d32_alloc(h->d32, n));
@@ -1536,6 +1565,11 @@ int ot_ipm_newton_direction(ot_ipm_t *h, int32_t solver, double cg_tol, int32_t 
             if (changed || !h->chol.have_symbolic) OT_TRY(chol_symbolic(h->chol, st));
             OT_TRY(chol_numeric(h->chol, kPivotEps, st));
             W.direct = &h->chol;
+        } else if (solver == OT_LS_TREE) {
+            bool forest = false;
+            OT_TRY(forest_setup(h, S, &forest, st));
+            if (!forest) return fail(OT_ERR_UNSUPPORTED, "forest solver: the support graph has a cycle");
+            W.tree = &h->tree;
         } else if (solver == OT_LS_IC) {
             if (!h->ic.perm) OT_TRY(ic_alloc(h->ic, n));
             bool changed = false;
@@ -1571,6 +1605,7 @@ int ot_ipm_newton_direction(ot_ipm_t *h, int32_t solver, double cg_tol, int32_t 
     W.dense = nullptr;
     W.d32 = nullptr;
     W.ic = nullptr;
+    W.tree = nullptr;
     return record(h, e);
 }
 
@@ -1662,6 +1697,7 @@ void ot_ipm_destroy(ot_ipm_t *h) {
     d32_free(h->d32);
     jset_free(h->jset);
     ic_free(h->ic);
+    tree_free(h->tree);
     void *ptrs[] = {h->a_s, h->b_s, h->C, h->sx, h->sy, h->tx, h->ty, h->u, h->v, h->pi, h->pj, h->pd,
                     h->pcount, h->pstrong, h->rowmin, h->lbv, h->d_src_map, h->d_dst_map, h->fsx, h->fsy,
                     h->ftx, h->fty, h->fC};

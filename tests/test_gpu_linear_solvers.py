@@ -98,7 +98,7 @@ def test_bad_arguments():
     inst = synth.image_pair(6, 0)
     with Solver(inst.a, inst.b, grid=(6, 6)) as s:
         its = ctypes.c_int32(0)
-        for solver, tol, mx in [(6, 1e-8, 10), (-1, 1e-8, 10), (0, 0.0, 10), (0, 1e-8, 0)]:
+        for solver, tol, mx in [(7, 1e-8, 10), (-1, 1e-8, 10), (0, 0.0, 10), (0, 1e-8, 0)]:
             assert s._lib.ot_ipm_newton_direction(s.h, solver, tol, mx, None, None, None, None, 1 << 20,
                                                   ctypes.byref(its)) == _lib.OT_ERR_ARG
         assert s._lib.ot_ipm_newton_direction(s.h, 0, 1e-8, 10, None, None, None, None, 0,
@@ -143,3 +143,85 @@ def test_incomplete_cholesky_factor_matches_oracle(tau, k, iters):
         s.set_state(st.I, st.J, st.p, st.s, st.u, st.v)
         x = s.ic_apply(b, tau)
     assert _err(x, ref) <= 1e-10, _err(x, ref)
+
+
+def _forest_state(k, seed, cut):
+    """A forest support: the network simplex's optimal spanning tree (m + n - 1 pairs), with every
+    `cut`-th pair removed (a forest of several components) when cut > 0; interior p, s > 0 drawn
+    around the tree's flows, duals = the simplex potentials."""
+    from oracle import netsimplex
+    inst = synth.image_pair(k, seed)
+    tree = netsimplex.solve(costs.square_grid(k), inst.a, inst.b)
+    I, J = tree.I.astype(np.int64), tree.J.astype(np.int64)
+    if cut:
+        keep = np.ones(len(I), bool)
+        keep[::cut] = False
+        # keep every row and column covered
+        m = n = k * k
+        for lab, size in ((I, m), (J, n)):
+            miss = np.setdiff1d(np.arange(size), lab[keep])
+            for x in miss:
+                keep[np.nonzero(lab == x)[0][0]] = True
+        I, J = I[keep], J[keep]
+    o = np.lexsort((J, I))
+    I, J = I[o], J[o]
+    rng = synth.uniform01(77 + seed, 2 * len(I))
+    prob = ipm.Problem(costs.square_grid(k), inst.a, inst.b)
+    p = 0.05 + rng[:len(I)]
+    s_ = 0.05 + rng[len(I):] * 3.0
+    st = ipm.State(I, J, p, s_, tree.u.copy(), tree.v.copy())
+    return inst, prob, st
+
+
+@pytest.mark.parametrize("k,seed,cut", [(8, 0, 0), (12, 2, 0), (12, 2, 7), (20, 1, 5)])
+def test_forest_solver_matches_oracle(k, seed, cut):
+    """Section 4.3 / Theorem 2: on a forest support the Newton system is a tree Laplacian, solved
+    exactly by the Euler-tour solver (no CG beyond the exact first step), against the oracle's exact
+    direction."""
+    from paper_2206_11009_gb300 import Solver
+    inst, prob, st = _forest_state(k, seed, cut)
+    m = n = k * k
+    ncomp, _ = ipm.components(m, n, st.I, st.J)
+    assert len(st.I) == m + n - ncomp          # a forest
+    res = ipm.residuals(prob, st)
+    ref = ipm.newton_direction(prob, st, res.r1a, res.r1b, res.r2, -st.p * st.s)
+    with Solver(inst.a, inst.b, grid=(k, k), tol=1e-8) as s:
+        s.set_state(st.I, st.J, st.p, st.s, st.u, st.v)
+        du, dv, dp, ds, its = s.newton_direction("tree", cg_tol=1e-12, max_cg=50)
+    e = {"du": _err(du, ref.du), "dv": _err(dv, ref.dv), "dp": _err(dp, ref.dp), "ds": _err(ds, ref.ds)}
+    print(f"tree k={k} cut={cut} comps={ncomp}: cg {its} " + " ".join(f"{n_}={x:.1e}" for n_, x in e.items()))
+    assert max(e.values()) <= 1e-10, e
+    assert its <= 2
+
+
+def test_forest_solver_rejects_a_cycle():
+    from paper_2206_11009_gb300 import Solver, _lib
+    inst, prob, st = oracle_state(12, 1, 3)
+    with Solver(inst.a, inst.b, grid=(12, 12), tol=1e-8) as s:
+        s.set_state(st.I, st.J, st.p, st.s, st.u, st.v)
+        with pytest.raises(_lib.OTError) as e:
+            s.newton_direction("tree")
+        assert e.value.code == _lib.OT_ERR_UNSUPPORTED
+
+
+def test_step_on_a_forest_support_matches_oracle():
+    """One GPU iteration from a forest iterate (solved on the tree, flagged direct) against the
+    oracle's iteration: mu, step lengths, the new duals and the new support."""
+    from paper_2206_11009_gb300 import Solver
+    k = 12
+    inst, prob, st = _forest_state(k, 2, 0)
+    opt = ipm.Options(tol=1e-8)
+    tr = ipm.Tracker()
+    _, res, crit = ipm.stop_test(prob, st, opt, tr)
+    new, lg, stepped, _, _ = ipm.one_iteration(prob, st, res, opt, tr, 0)
+    with Solver(inst.a, inst.b, grid=(k, k), tol=1e-8, precision=0, cg_tol_pred=1e-13, cg_tol_corr=1e-13,
+                max_cg=200) as s:
+        s.set_state(st.I, st.J, st.p, st.s, st.u, st.v, reset_mu0=True)
+        info = s.step()
+        gI, gJ, gP, gS, gu, gv = s.state()
+    assert info["direct"] == 1
+    assert abs(info["mu"] - res.mu) <= 1e-12 * res.mu
+    assert abs(info["alpha_p"] - lg.alpha_p) <= 1e-7 and abs(info["alpha_s"] - lg.alpha_s) <= 1e-7
+    assert np.array_equal(gI, new.I) and np.array_equal(gJ, new.J)
+    scale = max(1.0, np.abs(new.u).max())
+    assert np.abs(gu - new.u).max() <= 1e-7 * scale and np.abs(gv - new.v).max() <= 1e-7 * scale
