@@ -119,7 +119,8 @@ typedef struct {
     int32_t new_col_rule;
     /* Launch shapes (chosen by the autotuner; 0 = the library's rule).  scan_rows: source rows
      * per pricing-scan tile, 8..256.  dense32_max_n: largest n for which the mixed-precision
-     * path preconditions with the FP32 dense factorisation (at most 8192; -1: never). */
+     * path preconditions every iteration with the FP32 dense factorisation (0 = 8192; at most
+     * 65536, where its two n x n factors take 2 x 4 n^2 bytes = 34 GB; -1: never). */
     int32_t scan_rows;
     int32_t dense32_max_n;
     /* Largest n for which the direct branch factors S_M densely in FP64 (at most 8192; 0 = 8192,

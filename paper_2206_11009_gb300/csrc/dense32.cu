@@ -12,6 +12,7 @@
 //           A22 -= LD L21^T and the rows of X below the panel, B -= L21 X_k.
 // The sequence depends on n only, so it is captured once into a CUDA graph.
 #include "dense32.cuh"
+#include "primitives.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -22,7 +23,8 @@ namespace ot {
 namespace {
 
 constexpr int kP = 64;       // panel width
-constexpr int kMaxN = 16384; // largest n (the assembly keeps a column of n 64-bit sums in shared memory)
+constexpr int kMaxN = 65536;  // largest n
+constexpr int kSlice = 16384; // rows per assembly block (a column slice of 64-bit sums in shared memory)
 constexpr int kTT = 256;     // threads per CTA
 constexpr int kTile = 128;   // update tile (rows and columns)
 constexpr int kKc = 16;      // depth of one staged slice of the update tiles
@@ -35,16 +37,19 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x)
 
 // One CTA per column j: S_jj' = -sum_i theta_ij theta_ij' / M_i over the sources i shared by j and
 // j', accumulated in fixed point (2^62 / N_j per unit: each |S_jj'| <= N_j, and so is their sum).
+// Above kSlice rows, block (j, y) keeps only the rows [y kSlice, (y + 1) kSlice) of column j and
+// adds its part of the diagonal's sum to tot[j] (an integer sum: the same in any order).
 __global__ void __launch_bounds__(kTT)
 d32_assemble_kernel(int n, int ld, const int32_t *__restrict__ col_ptr, const int32_t *__restrict__ col_row,
                     const double *__restrict__ theta_col, const int32_t *__restrict__ row_ptr,
                     const int32_t *__restrict__ sj, const double *__restrict__ theta,
                     const double *__restrict__ Minv, const double *__restrict__ Nc, float *__restrict__ A,
-                    float *__restrict__ d0) {
+                    float *__restrict__ d0, unsigned long long *__restrict__ tot) {
     extern __shared__ unsigned long long acc[];
     __shared__ unsigned long long red[kTT / 32];
     const int j = blockIdx.x;
-    for (int t = threadIdx.x; t < n; t += blockDim.x) acc[t] = 0ull;
+    const int lo = blockIdx.y * kSlice, hi = min(n, lo + kSlice), len = hi - lo;
+    for (int t = threadIdx.x; t < len; t += blockDim.x) acc[t] = 0ull;
     __syncthreads();
     const double Nj = Nc[j];
     const double scale = Nj > 0 ? 4611686018427387904.0 / Nj : 0.0;  // 2^62 / N_j
@@ -55,23 +60,36 @@ d32_assemble_kernel(int n, int ld, const int32_t *__restrict__ col_ptr, const in
             const double f = theta_col[k] * Minv[i] * scale;
             for (int e = row_ptr[i] + lane; e < row_ptr[i + 1]; e += 32) {
                 const int jp = sj[e];
-                if (jp != j) atomicAdd(&acc[jp], (unsigned long long)__double2ull_rn(f * theta[e]));
+                if (jp != j && jp >= lo && jp < hi)
+                    atomicAdd(&acc[jp - lo], (unsigned long long)__double2ull_rn(f * theta[e]));
             }
         }
     }
     __syncthreads();
     unsigned long long s = 0;
-    for (int t = threadIdx.x; t < n; t += blockDim.x) s += acc[t];
+    for (int t = threadIdx.x; t < len; t += blockDim.x) s += acc[t];
     s = warp_sum_u64(s);
     if (lane == 0) red[warp] = s;
     __syncthreads();
     if (threadIdx.x == 0) {
-        unsigned long long tot = 0;
-        for (int w = 0; w < nw; ++w) tot += red[w];
-        d0[j] = scale > 0 ? (float)((double)tot / scale) : 0.f;
+        unsigned long long t = 0;
+        for (int w = 0; w < nw; ++w) t += red[w];
+        if (tot) atomicAdd(&tot[j], t);
+        else d0[j] = scale > 0 ? (float)((double)t / scale) : 0.f;
     }
     const double inv = scale > 0 ? 1.0 / scale : 0.0;
-    for (int r = j + 1 + threadIdx.x; r < n; r += blockDim.x) A[(size_t)j * ld + r] = -(float)((double)acc[r] * inv);
+    for (int r = max(j + 1, lo) + threadIdx.x; r < hi; r += blockDim.x)
+        A[(size_t)j * ld + r] = -(float)((double)acc[r - lo] * inv);
+}
+
+// the diagonal from the slices' integer sums (the same scaling as the single-block case)
+__global__ void d32_diag_total_kernel(int n, const double *__restrict__ Nc, const unsigned long long *__restrict__ tot,
+                                      float *__restrict__ d0) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        const double Nj = Nc[j];
+        const double scale = Nj > 0 ? 4611686018427387904.0 / Nj : 0.0;
+        d0[j] = scale > 0 ? (float)((double)tot[j] / scale) : 0.f;
+    }
 }
 
 // csum[l] = sum of column l over the rows [bs, n) (first panel; later panels receive these sums
@@ -755,7 +773,7 @@ Error d32_alloc(Dense32 &F, int32_t n) {
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [] {
         attr_err = cudaFuncSetAttribute(d32_assemble_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)(sizeof(unsigned long long) * kMaxN));
+                                        (int)(sizeof(unsigned long long) * kSlice));
     });
     if (attr_err != cudaSuccess) return fail(OT_ERR_CUDA, cudaGetErrorString(attr_err));
     if (n > kMaxN) return fail(OT_ERR_ARG, "dense32: n above the supported size");
@@ -772,9 +790,21 @@ void d32_free(Dense32 &F) {
 
 Error d32_assemble(Dense32 &F, const Newton &W, const Support &S, cudaStream_t st) {
     const int n = F.n;
-    const size_t smem = sizeof(unsigned long long) * n;
-    d32_assemble_kernel<<<n, kTT, smem, st>>>(n, F.ld, S.col_ptr, S.col_row, W.theta_col, S.row_ptr, S.j, W.theta,
-                                               W.Minv, W.N, F.A, F.d0);
+    const int slices = (int)ceil_div(n, kSlice);
+    const size_t smem = sizeof(unsigned long long) * std::min(n, kSlice);
+    if (slices == 1) {
+        d32_assemble_kernel<<<n, kTT, smem, st>>>(n, F.ld, S.col_ptr, S.col_row, W.theta_col, S.row_ptr, S.j,
+                                                   W.theta, W.Minv, W.N, F.A, F.d0, nullptr);
+        OT_LAUNCHED();
+        return ok();
+    }
+    DevTemp<unsigned long long> tot;
+    OT_TRY(tot.alloc(n, st));
+    OT_CUDA(cudaMemsetAsync(tot.p, 0, sizeof(unsigned long long) * n, st));
+    d32_assemble_kernel<<<dim3(n, slices), kTT, smem, st>>>(n, F.ld, S.col_ptr, S.col_row, W.theta_col, S.row_ptr,
+                                                             S.j, W.theta, W.Minv, W.N, F.A, F.d0, tot.p);
+    OT_LAUNCHED();
+    d32_diag_total_kernel<<<(unsigned)ceil_div(n, kTT), kTT, 0, st>>>(n, W.N, tot.p, F.d0);
     OT_LAUNCHED();
     return ok();
 }

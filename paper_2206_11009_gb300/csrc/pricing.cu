@@ -35,6 +35,8 @@ constexpr int kBins = 4097;       // bins 0..4095: d < 0 by magnitude (large fir
 constexpr int kPT = 256;          // threads per scan CTA
 constexpr int kRJ = 8;            // columns held in registers per thread
 constexpr int kTJ = kPT * kRJ;    // columns per tile
+// above this many pairs inside the FP32 gather window the selection is redone with the FP64 scan
+constexpr unsigned long long kMaxWindowPairs = 1ull << 27;
 
 struct Geo {
     unsigned long long umax_bits, vmax_bits;     // max |u|, max |v| (nonneg double bit patterns)
@@ -888,6 +890,13 @@ Error price_topk(const PriceInput &in, int32_t *out_i, int32_t *out_j, double *o
     OT_CUDA(cudaMemcpyAsync(&hg, geo.p, sizeof(Geo), cudaMemcpyDeviceToHost, st));
     OT_CUDA(cudaStreamSynchronize(st));
     const unsigned long long cap = hg.gather_bound;
+    if (!fp64 && cap > kMaxWindowPairs) {
+        // fewer negative keys than kmax and a flood of pairs inside the FP32 window [0, E] (duals
+        // near a degenerate optimum): the exact FP64 scan gathers only the pairs with d < 0
+        PriceInput in64 = in;
+        in64.precision = 0;
+        return price_topk(in64, out_i, out_j, out_d, out_count, stats, st);
+    }
     if (cap > 0x7fffffffull) return fail(OT_ERR_OOM, "price_topk: candidate set exceeds 2^31 pairs");
 
     DevTemp<int32_t> ci, cj;

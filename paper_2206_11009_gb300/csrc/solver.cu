@@ -92,6 +92,7 @@ constexpr double kIcTauFloor = 1e-6;
 constexpr int kDenseMaxN = 8192;
 constexpr int kDense32MaxN = 8192;
 constexpr int kDense32LateMaxN = 16384;  // late iterations above kDenseMaxN: FP32 dense factor
+constexpr int kDense32AbsMaxN = 65536;   // the FP32 dense factor's largest n (2 x 4 n^2 bytes: 34 GB)
 constexpr int kBatchWorkers = 2;            // host threads of a batch (ot_ipm_solve_batch)
 constexpr int kWarmCheck = 5;       // a warm start is judged from this iteration on ...
 constexpr int kWarmSettle = 15;     // ... up to this one
@@ -544,9 +545,10 @@ Error do_step(ot_ipm *h, ot_iter_info *info) {
     // mixed precision on moderate n: the FP32 dense factorisation of this iteration's S_M
     // preconditions an FP64 CG in every solve; the FP64 LDL^T branch only takes over when that CG
     // misses its target (the switch on the support's shrinkage is for the Jacobi PCG)
-    const int64_t d32_max = o.dense32_max_n > 0 ? o.dense32_max_n : (o.dense32_max_n < 0 ? 0 : kDense32MaxN);
-    const bool use_d32 = o.precision == 1 && o.linear_solver == 0 && o.precond != 1 &&
-                         n <= std::min<int64_t>(d32_max, kDense32MaxN);
+    // every iteration up to kDense32MaxN by default; a caller may raise the limit to kDense32AbsMaxN
+    const int64_t d32_max = o.dense32_max_n > 0 ? std::min<int64_t>(o.dense32_max_n, kDense32AbsMaxN)
+                                                : (o.dense32_max_n < 0 ? 0 : kDense32MaxN);
+    const bool use_d32 = o.precision == 1 && o.linear_solver == 0 && o.precond != 1 && n <= d32_max;
     if (forest) {
         use_direct = false;
     } else if (use_d32 && !h->d32_escalated) {

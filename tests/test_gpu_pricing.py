@@ -112,3 +112,26 @@ def test_full_size_256x256_against_oracle():
         gi, gj, gd = price_topk(*T, kmax=k * k, precision=precision)
         assert np.array_equal(gi.cpu().numpy(), oi) and np.array_equal(gj.cpu().numpy(), oj)
         assert np.array_equal(gd.cpu().numpy(), od)
+
+
+def test_window_flood_falls_back_to_the_fp64_scan():
+    """Near a degenerate optimum most reduced costs can sit inside the FP32 error window [0, E]
+    while fewer than kmax are negative: here every point is at the origin (c = 0 for all 151M
+    pairs), u = 1e5 and v = -1e5 except three targets, so d = 0 almost everywhere and d < 0 on
+    three columns only.  The selection (redone by the exact FP64 scan once the window holds more
+    than 2^27 pairs) must still be the oracle's."""
+    from paper_2206_11009_gb300 import price_topk
+    m = n = 12288
+    z = np.zeros(m, np.int32)
+    u = np.full(m, 1e5)
+    v = np.full(n, -1e5)
+    v[[17, 4000, 9001]] += np.array([1.0, 3.0, 2.0])
+    si = np.zeros(0, np.int32)
+    c = costs.Cost.points(z, z, z, z, "sqeuclid")
+    kmax = 50000
+    oi, oj, od = pricing.select_streaming(c, u, v, si, si, kmax, workers=16)
+    assert len(oi) == 3 * m and set(oj.tolist()) == {17, 4000, 9001}
+    T = U.cuda_tensors(z, z, z, z, u, v, si, si)
+    gi, gj, gd = price_topk(*T, kmax=kmax, precision=1)
+    assert np.array_equal(gi.cpu().numpy(), oi) and np.array_equal(gj.cpu().numpy(), oj)
+    assert np.array_equal(gd.cpu().numpy(), od)
