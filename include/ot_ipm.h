@@ -154,6 +154,13 @@ typedef struct {
      * (Section 4.3) is unchanged. */
     int32_t precond;
     double ic_tau;
+    /* Bulk update of the FP32 dense factorisation on the tensor cores: 1 = tcgen05 MMAs in split
+     * TF32 (a = a_hi + a_lo, three products per term, FP32 accumulation in tensor memory; FP32
+     * accuracy), operands pre-split per panel and fetched by bulk copies; 0 or -1 = the FP32 SIMT
+     * update (the default: a rank-64 update reads and writes the trailing matrix once per panel,
+     * about 16 flops per byte, so the tensor-core form is bound by that traffic and its per-tile
+     * latency; it measured 306 ms against 99 ms per factorisation at n = 16384). */
+    int32_t tc_update;
 } ot_options;
 
 /* One outer iteration (Section 3.4's commented listing). */

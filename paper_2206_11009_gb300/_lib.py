@@ -34,7 +34,8 @@ class OtOptions(ctypes.Structure):
                 ("warm_mode", c_int32), ("warm_i", c_void_p), ("warm_j", c_void_p), ("warm_npairs", c_int64),
                 ("new_col_rule", c_int32), ("scan_rows", c_int32), ("dense32_max_n", c_int32),
                 ("dense_max_n", c_int32), ("jset_cmax", c_double), ("jset_refresh", c_int32),
-                ("multiscale", c_int32), ("ms_tol", c_double), ("precond", c_int32), ("ic_tau", c_double)]
+                ("multiscale", c_int32), ("ms_tol", c_double), ("precond", c_int32), ("ic_tau", c_double),
+                ("tc_update", c_int32)]
 
 
 class OtPriceOpts(ctypes.Structure):

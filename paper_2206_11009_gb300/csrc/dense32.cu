@@ -671,6 +671,216 @@ d32_update_kernel(int n, int ld, int k, float *__restrict__ A, float *__restrict
     }
 }
 
+// ------------------------------------------------------------------ tensor-core bulk update
+// The bulk update C -= A_op B_op^T (depth 64, one panel) on the fifth-generation tensor cores in
+// split TF32: a = a_hi + a_lo with a_hi the TF32 rounding of a, and C -= a_hi b_hi + a_hi b_lo +
+// a_lo b_hi (the a_lo b_lo term is below FP32 rounding), accumulated in FP32 in tensor memory.
+// Once per panel the operands are split and written in the MMA's shared-memory layout (K-major,
+// no swizzle: 8-row x 16-byte core matrices; core matrix (row / 8, k / 4) of an R-row block at
+// byte ((k / 4) (R / 8) + row / 8) 128, its row (row % 8) at 16-byte steps), so a tile fetches its
+// operands with four bulk copies completing on one mbarrier, one thread issues 3 x 8 MMAs
+// (M = 128, N = 64, K = 8 each), and all four warps read the accumulator back (each warp its 32
+// lanes) and subtract it from C.  Every wait is bounded: a wait that gives up records the failure
+// in *err, waits once more for its own copies or MMAs, releases the tensor memory and returns.
+constexpr int kTcM = 128, kTcN = 64;                  // tile rows, tile columns
+constexpr int kTcApiece = kTcM * kP * 4;              // one A piece (hi or lo): 32 KB
+constexpr int kTcBpiece = kTcN * kP * 4;              // one B piece: 16 KB
+constexpr int kTcSmem = 2 * kTcApiece + 2 * kTcBpiece + 64;
+constexpr int kTcThreads = 128;
+constexpr long long kTcWaitLimit = 1LL << 24;
+
+__device__ __forceinline__ uint32_t tc_smem_u32(const void *ptr) { return (uint32_t)__cvta_generic_to_shared(ptr); }
+
+__device__ __forceinline__ float tc_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// shared-memory matrix descriptor: start, leading (K) and stride (M / N) byte offsets >> 4,
+// descriptor version 1 at bit 46, no swizzle
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo) {
+    uint64_t d = (uint64_t)((addr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((128u >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// kind::tf32 instruction descriptor: D = F32, A = B = TF32, both K-major, N = 64, M = 128
+constexpr uint32_t kTcIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
+                              ((uint32_t)(kTcM >> 4) << 24);
+
+__device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity) {
+    for (long long i = 0; i < kTcWaitLimit; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// Rows [row0 + b RB, +RB) of an operand, depth 64, split into TF32 hi / lo pieces in the layout
+// above: piece (b, hi) at out + 2 b P, (b, lo) at out + (2 b + 1) P (P = RB * 64 floats).  The
+// element (row r, depth l) is src[l * ld + r] (a column-major panel) or, kmaj, src[r * ld + l]
+// (rows of L^-1 held by column); rows at or beyond `rows` are zero.
+template <int RB, bool KMAJ>
+__global__ void __launch_bounds__(kTT)
+d32_tc_split_kernel(int rows, int ld, const float *__restrict__ src, int row0, float *__restrict__ out) {
+    const int b = blockIdx.x;
+    float *hi = out + (size_t)(2 * b) * RB * kP, *lo = hi + (size_t)RB * kP;
+    for (int t = threadIdx.x; t < RB * (kP / 4); t += blockDim.x) {
+        const int r = t % RB, kq = t / RB;
+        const int row = row0 + b * RB + r;
+        float v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int l = kq * 4 + q;
+            v[q] = row < rows ? (KMAJ ? src[(size_t)row * ld + l] : src[(size_t)l * ld + row]) : 0.f;
+        }
+        float h[4], w[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            h[q] = tc_tf32(v[q]);
+            w[q] = v[q] - h[q];
+        }
+        const size_t off = ((size_t)kq * (RB / 8) + (r >> 3)) * 32 + (size_t)(r & 7) * 4;  // in floats
+        *(float4 *)(hi + off) = make_float4(h[0], h[1], h[2], h[3]);
+        *(float4 *)(lo + off) = make_float4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+// One CTA per tile.  Tiles [0, T (T + 1)): the trailing triangle from base2 (row block ti of 128,
+// column block tj of 64 with tj <= 2 ti + 1; C = A, rows > columns); then T x tcx tiles of the
+// rows of L^-1 (C = X, columns below base).  Operand pieces: trailing A = split L D rows, B =
+// split panel rows (64-row blocks); inverse A = split panel rows (128-row blocks), B = split rows
+// of L^-1 (64-column blocks).
+__global__ void __launch_bounds__(kTcThreads, 2)
+d32_tc_update_kernel(int n, int ld, int base, int base2, int T, const float *__restrict__ LDs,
+                     const float *__restrict__ PBs, const float *__restrict__ PAs, const float *__restrict__ XBs,
+                     float *__restrict__ A, float *__restrict__ X, int *__restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int idx = blockIdx.x, ntri = T * (T + 1);
+    const bool tri = idx < ntri;
+    int ti, tj;
+    if (tri) {
+        ti = (int)floorf((sqrtf(4.f * (float)idx + 1.f) - 1.f) * 0.5f);
+        while ((ti + 1) * (ti + 2) <= idx) ++ti;
+        while (ti * (ti + 1) > idx) --ti;
+        tj = idx - ti * (ti + 1);
+    } else {
+        const int tcx = (int)ceil_div(base, kTcN);
+        ti = (idx - ntri) / tcx;
+        tj = (idx - ntri) % tcx;
+    }
+    const int r0 = base2 + ti * kTcM;
+    const int c0 = tri ? base2 + tj * kTcN : tj * kTcN;
+    const int climit = tri ? n : base;
+    if (r0 >= n || c0 >= climit) return;   // outside the matrix: uniform over the CTA, nothing started
+    uint64_t *mb_load = (uint64_t *)(smem + 2 * kTcApiece + 2 * kTcBpiece);
+    uint64_t *mb_mma = mb_load + 1;
+    uint32_t *tslot = (uint32_t *)(mb_load + 2);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(tc_smem_u32(tslot)), "r"(kTcN) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(tc_smem_u32(mb_load)) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(tc_smem_u32(mb_mma)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+    const float *pa = (tri ? LDs : PAs) + (size_t)(2 * ti) * kTcM * kP;
+    const float *pb = (tri ? PBs : XBs) + (size_t)(2 * tj) * kTcN * kP;
+    int ok = 1;
+    if (threadIdx.x == 0) {
+        const uint32_t mbl = tc_smem_u32(mb_load), sbase = tc_smem_u32(smem);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                     :: "r"(mbl), "r"((uint32_t)(2 * kTcApiece + 2 * kTcBpiece)) : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                     :: "r"(sbase), "l"(pa), "r"((uint32_t)(2 * kTcApiece)), "r"(mbl) : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                     :: "r"(sbase + 2 * kTcApiece), "l"(pb), "r"((uint32_t)(2 * kTcBpiece)), "r"(mbl) : "memory");
+        if (!tc_wait(mbl, 0)) {
+            ok = 0;
+            atomicExch(err, 1);
+            tc_wait(mbl, 0);   // the copies target this CTA's shared memory: give them time to land
+        }
+        if (ok) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t ah = sbase, al = sbase + kTcApiece;
+            const uint32_t bh = sbase + 2 * kTcApiece, bl = bh + kTcBpiece;
+            const uint32_t lboA = (kTcM / 8) * 128, lboB = (kTcN / 8) * 128;
+#pragma unroll
+            for (int ks = 0; ks < kP / 8; ++ks) {
+                const uint32_t ka = (uint32_t)ks * 2 * lboA, kb = (uint32_t)ks * 2 * lboB;
+                const uint64_t dah = tc_desc(ah + ka, lboA), dal = tc_desc(al + ka, lboA);
+                const uint64_t dbh = tc_desc(bh + kb, lboB), dbl = tc_desc(bl + kb, lboB);
+                asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                             " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+                             :: "r"(tmem), "l"(dah), "l"(dbh), "r"(kTcIdesc), "r"(ks > 0 ? 1u : 0u) : "memory");
+                asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                             " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+                             :: "r"(tmem), "l"(dah), "l"(dbl), "r"(kTcIdesc), "r"(1u) : "memory");
+                asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                             " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+                             :: "r"(tmem), "l"(dal), "l"(dbh), "r"(kTcIdesc), "r"(1u) : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(tc_smem_u32(mb_mma)) : "memory");
+        }
+    }
+    ok = __syncthreads_and(ok);
+    if (ok) {
+        const bool done = tc_wait(tc_smem_u32(mb_mma), 0);
+        ok = __syncthreads_and(done ? 1 : 0);
+        if (!ok) {
+            if (threadIdx.x == 0) atomicExch(err, 1);
+            tc_wait(tc_smem_u32(mb_mma), 0);   // the MMAs write this CTA's tensor memory
+        }
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+        // warp w: TMEM lanes (tile rows) 32 w .. 32 w + 31, all 64 columns in two loads
+        float *C = tri ? A : X;
+        const int r = r0 + warp * 32 + lane;
+#pragma unroll
+        for (int part = 0; part < 2; ++part) {
+            uint32_t v[32];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(part * 32);
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+                "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                  "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                  "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+                  "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (r < n) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int c = c0 + part * 32 + j;
+                    if (c < climit && (!tri || r > c)) C[(size_t)c * ld + r] -= __uint_as_float(v[j]);
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kTcN) : "memory");
+}
+
 // partial sums of y = X r: CTA (rb, cb) covers rows [rb*512, +512) (four per thread, float4 loads)
 // and columns [cb*64, +64) for the lower-triangle tiles only (rows beyond n read the zero padding)
 constexpr int kFr = 256, kFc = 64;
@@ -783,8 +993,9 @@ Error d32_alloc(Dense32 &F, int32_t n) {
 void d32_free(Dense32 &F) {
     if (F.graph) cudaGraphExecDestroy(F.graph);
     for (void *p : {(void *)F.A, (void *)F.X, (void *)F.LD, (void *)F.Linv, (void *)F.D, (void *)F.d0, (void *)F.csum,
-                    (void *)F.w, (void *)F.part})
+                    (void *)F.w, (void *)F.part, (void *)F.tc, (void *)F.tc_err})
         if (p) cudaFree(p);
+    if (F.tc_err_host) cudaFreeHost(F.tc_err_host);
     F = Dense32();
 }
 
@@ -842,6 +1053,24 @@ struct Dag {
         v.priority = value;
         err = cudaGraphKernelNodeSetAttribute(node, cudaKernelNodeAttributePriority, &v);
     }
+    template <typename... Args>
+    cudaGraphNode_t kernel_smem(std::vector<cudaGraphNode_t> deps, void (*fn)(Args...), unsigned grid,
+                                unsigned block, unsigned smem, Args... args) {
+        cudaGraphNode_t node = nullptr;
+        if (err != cudaSuccess) return node;
+        void *ptrs[] = {(void *)&args...};
+        cudaKernelNodeParams kp = {};
+        kp.func = (void *)fn;
+        kp.gridDim = dim3(grid);
+        kp.blockDim = dim3(block);
+        kp.sharedMemBytes = smem;
+        kp.kernelParams = ptrs;
+        kp.extra = nullptr;
+        deps.erase(std::remove(deps.begin(), deps.end(), nullptr), deps.end());
+        err = cudaGraphAddKernelNode(&node, g, deps.data(), deps.size(), &kp);
+        if (err == cudaSuccess) ++nodes;
+        return node;
+    }
     cudaGraphNode_t memset0(float *dst, size_t count, std::vector<cudaGraphNode_t> deps) {
         cudaGraphNode_t node = nullptr;
         if (err != cudaSuccess) return node;
@@ -866,6 +1095,10 @@ struct Dag {
 };
 }  // namespace
 
+// split operand storage for one panel parity: two 128-row-block operands and two 64-row-block ones
+static size_t tc_a_floats(int n) { return (size_t)ceil_div(n, kTcM) * 2 * kTcM * kP; }
+static size_t tc_b_floats(int n) { return (size_t)ceil_div(n, kTcN) * 2 * kTcN * kP; }
+static size_t tc_per_parity(int n) { return 2 * tc_a_floats(n) + 2 * tc_b_floats(n); }
 static Error d32_build(Dense32 &F, float eps, cudaGraph_t g, int64_t *nodes) {
     const int n = F.n, ld = F.ld;
     Dag c;
@@ -901,8 +1134,32 @@ static Error d32_build(Dense32 &F, float eps, cudaGraph_t g, int64_t *nodes) {
             const int base2 = base + kP;
             const int t2 = base2 < n ? (int)ceil_div(n - base2, kTile) : 0, tcn = (int)ceil_div(base, kTile);
             const int n2 = t2 * (t2 + 1) / 2 + t2 * tcn;
-            u2 = n2 > 0 ? c.kernel(ready, d32_update_kernel, (unsigned)n2, kTT, n, ld, k, F.A, F.X, (const float *)LDp)
-                        : nullptr;
+            if (n2 > 0 && F.use_tc) {
+                // the operands of this panel's bulk update split for the tensor cores (buffers by
+                // panel parity: the previous panel's update may still read the other half)
+                const int T = (int)ceil_div(n - base2, kTcM), nb = (int)ceil_div(n - base2, kTcN);
+                const int nx = (int)ceil_div(base, kTcN);
+                float *LDs = F.tc + (size_t)(p & 1) * tc_per_parity(n);
+                float *PAs = LDs + tc_a_floats(n), *PBs = PAs + tc_a_floats(n), *XBs = PBs + tc_b_floats(n);
+                const float *panel = F.A + (size_t)k * ld;
+                std::vector<cudaGraphNode_t> sp;
+                sp.push_back(c.kernel(ready, d32_tc_split_kernel<kTcM, false>, (unsigned)T, kTT, n, ld,
+                                      (const float *)LDp, base2, LDs));
+                sp.push_back(c.kernel(ready, d32_tc_split_kernel<kTcN, false>, (unsigned)nb, kTT, n, ld, panel, base2,
+                                      PBs));
+                sp.push_back(c.kernel(ready, d32_tc_split_kernel<kTcM, false>, (unsigned)T, kTT, n, ld, panel, base2,
+                                      PAs));
+                sp.push_back(c.kernel(ready, d32_tc_split_kernel<kTcN, true>, (unsigned)nx, kTT, base, ld,
+                                      (const float *)(F.X + k), 0, XBs));
+                for (cudaGraphNode_t q : sp) c.priority(q, lo_prio);
+                u2 = c.kernel_smem(sp, d32_tc_update_kernel, (unsigned)(T * (T + 1) + T * nx), kTcThreads,
+                                   (unsigned)kTcSmem, n, ld, base, base2, T, (const float *)LDs, (const float *)PBs,
+                                   (const float *)PAs, (const float *)XBs, F.A, F.X, F.tc_err);
+            } else {
+                u2 = n2 > 0 ? c.kernel(ready, d32_update_kernel, (unsigned)n2, kTT, n, ld, k, F.A, F.X,
+                                       (const float *)LDp)
+                            : nullptr;
+            }
             c.priority(u2, lo_prio);
             np = ts;
         } else {
@@ -916,7 +1173,24 @@ static Error d32_build(Dense32 &F, float eps, cudaGraph_t g, int64_t *nodes) {
 }
 
 Error d32_factor(Dense32 &F, float eps, cudaStream_t st) {
+    if (F.tc_err_host && *F.tc_err_host)
+        return fail(OT_ERR_TIMEOUT, "dense32: a bounded wait of the tensor-core update gave up");
     if (!F.graph || F.eps != eps) {
+        const bool want_tc = F.tc_mode > 0;
+        if (want_tc && !F.tc) {
+            OT_CUDA(cudaMalloc((void **)&F.tc, sizeof(float) * 2 * tc_per_parity(F.n)));
+            OT_CUDA(cudaMalloc((void **)&F.tc_err, sizeof(int)));
+            OT_CUDA(cudaMemset(F.tc_err, 0, sizeof(int)));
+            OT_CUDA(cudaMallocHost((void **)&F.tc_err_host, sizeof(int)));
+            *F.tc_err_host = 0;
+            static std::once_flag once;
+            static cudaError_t attr = cudaSuccess;
+            std::call_once(once, [] {
+                attr = cudaFuncSetAttribute(d32_tc_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+            });
+            if (attr != cudaSuccess) return fail(OT_ERR_CUDA, cudaGetErrorString(attr));
+        }
+        F.use_tc = want_tc;
         if (F.graph) {
             cudaGraphExecDestroy(F.graph);
             F.graph = nullptr;
@@ -939,6 +1213,7 @@ Error d32_factor(Dense32 &F, float eps, cudaStream_t st) {
     OT_CUDA(cudaGraphLaunch(F.graph, st));
     g_launches.fetch_add(F.graph_nodes, std::memory_order_relaxed);
     ktimer_end(KT_D32_FACTOR, st);
+    if (F.use_tc) OT_CUDA(cudaMemcpyAsync(F.tc_err_host, F.tc_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     // FP32 flops: n^3/3 for L D L^T (n^3/6 multiply-adds) plus n^3/3 for the unit triangular inverse
     ktimer_add_work(KT_D32_FACTOR, 2.0 * (double)F.n * F.n * F.n / 3.0);
     return ok();

@@ -553,7 +553,7 @@ Error do_step(ot_ipm *h, ot_iter_info *info) {
         use_direct = false;
     } else if (use_d32 && !h->d32_escalated) {
         use_direct = false;
-        if (!h->d32.A) OT_TRY(d32_alloc(h->d32, n));
+        if (!h->d32.A) { OT_TRY(d32_alloc(h->d32, n)); h->d32.tc_mode = h->opt.tc_update; }
         OT_TRY(d32_assemble(h->d32, W, S, st));
         OT_TRY(d32_factor(h->d32, (float)kPivotEps, st));
         W.d32 = &h->d32;
@@ -569,7 +569,7 @@ Error do_step(ot_ipm *h, ot_iter_info *info) {
         if (n > kDenseMaxN && n <= kDense32LateMaxN && o.dense_max_n >= 0) {
             // beyond the FP64 dense size, the late iterations precondition the FP64 CG with the
             // FP32 dense factorisation (pivots from off-diagonal sums, exact grounding)
-            if (!h->d32.A) OT_TRY(d32_alloc(h->d32, n));
+            if (!h->d32.A) { OT_TRY(d32_alloc(h->d32, n)); h->d32.tc_mode = h->opt.tc_update; }
             OT_TRY(d32_assemble(h->d32, W, S, st));
             OT_TRY(d32_factor(h->d32, (float)kPivotEps, st));
             W.d32 = &h->d32;
@@ -1084,7 +1084,7 @@ Error create_impl(const ot_problem *P, const ot_options *O, ot_ipm *h) {
     ot_options &o = h->opt;
     if (!(o.tol > 0) || o.max_iter < 0 || o.max_cg <= 0 || o.max_corr < 0 || !(o.step_scale > 0 && o.step_scale < 1) ||
         (o.precision != 0 && o.precision != 1) || o.jset_refresh < 0 || !std::isfinite(o.jset_cmax) ||
-        o.precond < 0 || o.precond > 1 || !(o.ic_tau >= 0 && o.ic_tau < 1))
+        o.precond < 0 || o.precond > 1 || !(o.ic_tau >= 0 && o.ic_tau < 1) || o.tc_update < -1 || o.tc_update > 1)
         return fail(OT_ERR_ARG, "options: out of range");
     if (P->cost < 0 || P->cost > OT_COST_DENSE) return fail(OT_ERR_ARG, "problem: unknown cost kind");
     const bool dense = P->cost == OT_COST_DENSE;
@@ -1357,6 +1357,7 @@ void ot_options_default(ot_options *o) {
     o->ms_tol = 0.0;
     o->precond = 0;
     o->ic_tau = 0.0;
+    o->tc_update = 0;
     o->verbose = 0;
     o->stream = nullptr;
 }
@@ -1548,7 +1549,7 @@ int ot_ipm_newton_direction(ot_ipm_t *h, int32_t solver, double cg_tol, int32_t 
         W.tree = nullptr;
         if (solver == OT_LS_DENSE32) {
             if (n > kDense32LateMaxN) return fail(OT_ERR_UNSUPPORTED, "FP32 dense factor: n above its limit");
-            if (!h->d32.A) OT_TRY(d32_alloc(h->d32, n));
+            if (!h->d32.A) { OT_TRY(d32_alloc(h->d32, n)); h->d32.tc_mode = h->opt.tc_update; }
             OT_TRY(d32_assemble(h->d32, W, S, st));
             OT_TRY(d32_factor(h->d32, (float)kPivotEps, st));
             W.d32 = &h->d32;

@@ -225,3 +225,23 @@ def test_step_on_a_forest_support_matches_oracle():
     assert np.array_equal(gI, new.I) and np.array_equal(gJ, new.J)
     scale = max(1.0, np.abs(new.u).max())
     assert np.abs(gu - new.u).max() <= 1e-7 * scale and np.abs(gv - new.v).max() <= 1e-7 * scale
+
+
+@pytest.mark.parametrize("k,iters,bar", [(12, 3, 1e-9), (23, 15, 1e-9), (23, 21, 1e-6)])
+def test_dense32_with_tensor_core_update_matches_oracle(k, iters, bar):
+    """The FP32 factor's bulk update on the tensor cores (split TF32 tcgen05, tc_update = 1): the
+    preconditioned CG still reaches the oracle's exact direction, in as few iterations as with the
+    FP32 SIMT update (the factor is FP32-accurate)."""
+    from paper_2206_11009_gb300 import Solver
+    inst, prob, st = oracle_state(k, 1, iters)
+    res = ipm.residuals(prob, st)
+    ref = ipm.newton_direction(prob, st, res.r1a, res.r1b, res.r2, -st.p * st.s)
+    its = {}
+    for tc in (-1, 1):
+        with Solver(inst.a, inst.b, grid=(k, k), tol=1e-8, tc_update=tc) as s:
+            s.set_state(st.I, st.J, st.p, st.s, st.u, st.v)
+            du, dv, dp, ds, its[tc] = s.newton_direction("dense32", cg_tol=1e-12, max_cg=20000)
+        e = {"du": _err(du, ref.du), "dv": _err(dv, ref.dv), "dp": _err(dp, ref.dp), "ds": _err(ds, ref.ds)}
+        print(f"dense32 tc={tc} k={k} it={iters}: cg {its[tc]} " + " ".join(f"{n}={x:.1e}" for n, x in e.items()))
+        assert max(e.values()) <= bar, e
+    assert its[1] <= its[-1] + 2

@@ -175,3 +175,21 @@ def test_incomplete_cholesky_preconditioner_reaches_exact_optimum(precision, k, 
     r, _ = _solve(inst, k, tol=1e-8, precision=precision, precond=1)
     assert r.status == 0, r
     assert abs(r.obj - opt) <= 1e-6 * opt and r.r1_l1 <= 1e-8 and r.rel_gap <= 1e-8
+
+
+def test_tensor_core_factor_update_solve_93x93():
+    """A full solve whose late iterations factor S_M (n = 8649) with the tensor-core bulk update:
+    certified by the oracle's c-transform bound like the SIMT path."""
+    from oracle.certificate import c_transform_lower_bound
+    from oracle.costs import square_grid
+    from paper_2206_11009_gb300 import Solver
+    k = 93
+    inst = synth.image_pair(k, 14)
+    with Solver(inst.a, inst.b, grid=(k, k), precision=1, tc_update=1) as s:
+        r = s.solve()
+        I, J, P, u, v = s.solution()
+    cost = square_grid(k)
+    lb = c_transform_lower_bound(cost, inst.a, inst.b, v)
+    ctp = float(cost.pairs(I, J) @ P)
+    assert r.status == 0 and r.direct_iters > 0
+    assert lb <= ctp * (1 + 1e-12) and (ctp - lb) / ctp <= 1e-6
