@@ -161,6 +161,10 @@ typedef struct {
      * about 16 flops per byte, so the tensor-core form is bound by that traffic and its per-tile
      * latency; it measured 306 ms against 99 ms per factorisation at n = 16384). */
     int32_t tc_update;
+    /* Relative residual at which the CG preconditioned by a factorisation (the FP32 dense factor,
+     * the direct branch) stops: 0 = min(CG tolerance, 1e-10) (near-exact Newton directions);
+     * > 0: max(direct_cg_tol, min(CG tolerance, 1e-10)). */
+    double direct_cg_tol;
 } ot_options;
 
 /* One outer iteration (Section 3.4's commented listing). */

@@ -35,7 +35,7 @@ class OtOptions(ctypes.Structure):
                 ("new_col_rule", c_int32), ("scan_rows", c_int32), ("dense32_max_n", c_int32),
                 ("dense_max_n", c_int32), ("jset_cmax", c_double), ("jset_refresh", c_int32),
                 ("multiscale", c_int32), ("ms_tol", c_double), ("precond", c_int32), ("ic_tau", c_double),
-                ("tc_update", c_int32)]
+                ("tc_update", c_int32), ("direct_cg_tol", c_double)]
 
 
 class OtPriceOpts(ctypes.Structure):

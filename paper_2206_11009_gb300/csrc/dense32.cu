@@ -881,44 +881,59 @@ d32_tc_update_kernel(int n, int ld, int base, int base2, int T, const float *__r
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kTcN) : "memory");
 }
 
-// partial sums of y = X r: CTA (rb, cb) covers rows [rb*512, +512) (four per thread, float4 loads)
-// and columns [cb*64, +64) for the lower-triangle tiles only (rows beyond n read the zero padding)
+// partial sums of y = X r: CTA (rb, cb) covers rows [rb*256, +256) (four per thread, float4 loads)
+// and columns [cb*64, +64) for the lower-triangle tiles only (rows beyond n read the zero padding);
+// the tile's 64 columns are split over four thread groups of 16 columns, reduced in shared memory
 constexpr int kFr = 256, kFc = 64;
-__global__ void __launch_bounds__(kFr / 4)
+__global__ void __launch_bounds__(kFr)
 d32_fwd_kernel(int n, int ld, int ncb, const float *__restrict__ X, const double *__restrict__ r,
                float *__restrict__ part) {
     __shared__ float rs[kFc];
+    __shared__ float4 red[3][kFr / 4];
     // tile index -> (rb, cb) with cb*kFc < (rb+1)*kFr
     const int per = kFr / kFc;
     int idx = blockIdx.x, rb = 0;
     while (idx >= min(ncb, (rb + 1) * per)) { idx -= min(ncb, (rb + 1) * per); ++rb; }
     const int cb = idx;
-    const int c0 = cb * kFc, i = rb * kFr + threadIdx.x * 4;
+    const int rq = threadIdx.x & (kFr / 4 - 1), cg = threadIdx.x / (kFr / 4);
+    const int c0 = cb * kFc, i = rb * kFr + rq * 4;
     if (threadIdx.x < kFc) rs[threadIdx.x] = c0 + (int)threadIdx.x < n ? (float)r[c0 + threadIdx.x] : 0.f;
     __syncthreads();
-    if (i >= n || i + 3 < c0) return;
+    const bool live = i < n && i + 3 >= c0;
     const int jn = min(kFc, n - c0);
+    const int jlo = cg * (kFc / 4), jhi = min(jlo + kFc / 4, jn);
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    const float *col = X + (size_t)c0 * ld + i;
-    if (i >= c0 + kFc - 1) {
+    if (live) {
+        const float *col = X + (size_t)c0 * ld + i;
+        if (i >= c0 + kFc - 1) {
 #pragma unroll 16
-        for (int jj = 0; jj < jn; ++jj) {
-            const float4 v = *(const float4 *)(col + (size_t)jj * ld);
-            const float rj = rs[jj];
-            acc.x += v.x * rj; acc.y += v.y * rj; acc.z += v.z * rj; acc.w += v.w * rj;
-        }
-    } else {
-        for (int jj = 0; jj < jn; ++jj) {
-            const int j = c0 + jj;
-            const float4 v = *(const float4 *)(col + (size_t)jj * ld);
-            const float rj = rs[jj];
-            if (j <= i) acc.x += v.x * rj;
-            if (j <= i + 1) acc.y += v.y * rj;
-            if (j <= i + 2) acc.z += v.z * rj;
-            if (j <= i + 3) acc.w += v.w * rj;
+            for (int jj = jlo; jj < jhi; ++jj) {
+                const float4 v = *(const float4 *)(col + (size_t)jj * ld);
+                const float rj = rs[jj];
+                acc.x += v.x * rj; acc.y += v.y * rj; acc.z += v.z * rj; acc.w += v.w * rj;
+            }
+        } else {
+            for (int jj = jlo; jj < jhi; ++jj) {
+                const int j = c0 + jj;
+                const float4 v = *(const float4 *)(col + (size_t)jj * ld);
+                const float rj = rs[jj];
+                if (j <= i) acc.x += v.x * rj;
+                if (j <= i + 1) acc.y += v.y * rj;
+                if (j <= i + 2) acc.z += v.z * rj;
+                if (j <= i + 3) acc.w += v.w * rj;
+            }
         }
     }
-    *(float4 *)(part + (size_t)cb * ld + i) = acc;
+    if (cg > 0) red[cg - 1][rq] = acc;
+    __syncthreads();
+    if (cg == 0 && live) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const float4 o = red[q][rq];
+            acc.x += o.x; acc.y += o.y; acc.z += o.z; acc.w += o.w;
+        }
+        *(float4 *)(part + (size_t)cb * ld + i) = acc;
+    }
 }
 
 // w = D^+ y, y_i = sum of the partials of row i (fixed order)
@@ -1225,7 +1240,7 @@ Error d32_apply(Dense32 &F, const double *r, double *z, cudaStream_t st) {
     int tiles = 0;
     for (int rb = 0; rb < nrb; ++rb) tiles += std::min(ncb, (rb + 1) * (kFr / kFc));
     ktimer_begin(KT_D32_APPLY, st);
-    d32_fwd_kernel<<<(unsigned)tiles, kFr / 4, 0, st>>>(n, ld, ncb, F.X, r, F.part);
+    d32_fwd_kernel<<<(unsigned)tiles, kFr, 0, st>>>(n, ld, ncb, F.X, r, F.part);
     OT_LAUNCHED();
     d32_mid_kernel<<<(unsigned)ceil_div(n, kTT), kTT, 0, st>>>(n, ld, F.part, F.D, F.w);
     OT_LAUNCHED();

@@ -251,28 +251,6 @@ __global__ void beta1_kernel(int m, const int32_t *__restrict__ rp, const double
 }
 
 // beta2_j = r1b_j + sum_i g_ij ; rhs_j = beta2_j - sum_i theta_ij beta1_i / M_i
-__global__ void rhs_kernel(int n, const int32_t *__restrict__ cp, const int32_t *__restrict__ perm,
-                           const int32_t *__restrict__ crow, const double *__restrict__ g,
-                           const double *__restrict__ thc, const double *__restrict__ Minv,
-                           const double *__restrict__ beta1, const double *__restrict__ r1b,
-                           double *__restrict__ beta2, double *__restrict__ rhs, double *part) {
-    __shared__ double sh[kT / 32];
-    double tot = 0;
-    GRID_STRIDE(j, n) {
-        double b2 = r1b ? r1b[j] : 0.0;
-        double vt = 0;
-        for (int k = cp[j]; k < cp[j + 1]; ++k) {
-            b2 += g[perm[k]];
-            const int i = crow[k];
-            vt += thc[k] * (Minv[i] * beta1[i]);
-        }
-        beta2[j] = b2;
-        const double r = b2 - vt;
-        rhs[j] = r;
-        tot += r;
-    }
-    put_sum(tot, part, SC_SUM_A, sh);
-}
 
 __global__ void sum_kernel(int n, const double *__restrict__ x, double *part, int slot) {
     __shared__ double sh[kT / 32];
@@ -327,6 +305,59 @@ template <typename T>
 __device__ __forceinline__ T group_sum(T x, int g) {
     for (int o = g >> 1; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
     return x;
+}
+
+// beta2_j = r1b_j + sum_i g_ij and rhs_j = beta2_j - sum_i theta_ij M_i^-1 beta1_i over the
+// column's pairs, G lanes per column (warp-uniform trip counts: groups past the end contribute
+// nothing but take part in the shuffles)
+template <int G>
+__global__ void rhs_group_kernel(int n, const int32_t *__restrict__ cp, const int32_t *__restrict__ perm,
+                                 const int32_t *__restrict__ crow, const double *__restrict__ g,
+                                 const double *__restrict__ thc, const double *__restrict__ Minv,
+                                 const double *__restrict__ beta1, const double *__restrict__ r1b,
+                                 double *__restrict__ beta2, double *__restrict__ rhs) {
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int lg = threadIdx.x & (G - 1);
+    const int64_t grp = tid / G, ngrp = stride / G, wgrp0 = (tid & ~(int64_t)31) / G;
+    for (int64_t j0 = wgrp0; j0 < n; j0 += ngrp) {
+        const int64_t j = j0 + (grp - wgrp0);
+        double b2 = 0.0, vt = 0.0;
+        if (j < n) {
+            for (int k = cp[j] + lg; k < cp[j + 1]; k += G) {
+                b2 += g[perm[k]];
+                const int i = crow[k];
+                vt += thc[k] * (Minv[i] * beta1[i]);
+            }
+        }
+        b2 = group_sum(b2, G);
+        vt = group_sum(vt, G);
+        if (lg == 0 && j < n) {
+            if (r1b) b2 += r1b[j];
+            beta2[j] = b2;
+            rhs[j] = b2 - vt;
+        }
+    }
+}
+
+// du_i = M_i^-1 (beta1_i - sum_j theta_ij dv_j), G lanes per row
+template <int G>
+__global__ void du_group_kernel(int m, const int32_t *__restrict__ rp, const int32_t *__restrict__ sj,
+                                const double *__restrict__ th, const double *__restrict__ Minv,
+                                const double *__restrict__ beta1, const double *__restrict__ dv,
+                                double *__restrict__ du) {
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int lg = threadIdx.x & (G - 1);
+    const int64_t grp = tid / G, ngrp = stride / G, wgrp0 = (tid & ~(int64_t)31) / G;
+    for (int64_t i0 = wgrp0; i0 < m; i0 += ngrp) {
+        const int64_t i = i0 + (grp - wgrp0);
+        double acc = 0.0;
+        if (i < m)
+            for (int e = rp[i] + lg; e < rp[i + 1]; e += G) acc += th[e] * dv[sj[e]];
+        acc = group_sum(acc, G);
+        if (lg == 0 && i < m) du[i] = Minv[i] * (beta1[i] - acc);
+    }
 }
 
 // every block sums the gridDim partials of `slots` (fixed order: deterministic, identical in
@@ -845,15 +876,6 @@ __global__ void copy_kernel(int n, const double *__restrict__ a, double *__restr
 }
 
 // ------------------------------------------------------------------------ back-substitution
-__global__ void du_kernel(int m, const int32_t *__restrict__ rp, const int32_t *__restrict__ sj,
-                          const double *__restrict__ th, const double *__restrict__ Minv,
-                          const double *__restrict__ beta1, const double *__restrict__ dv, double *__restrict__ du) {
-    GRID_STRIDE(i, m) {
-        double acc = 0;
-        for (int e = rp[i]; e < rp[i + 1]; ++e) acc += th[e] * dv[sj[e]];
-        du[i] = Minv[i] * (beta1[i] - acc);
-    }
-}
 
 __global__ void dsdp_kernel(int64_t psi, const int32_t *__restrict__ si, const int32_t *__restrict__ sj,
                             const double *__restrict__ p, const double *__restrict__ s,
@@ -1151,7 +1173,8 @@ static Error solve_direct(Newton &W, const Support &S, double tol, int max_cg, d
     // near optimality the primal-infeasibility part of the right-hand side is tiny next to the
     // complementarity part, so the direct branch solves far below the PCG tolerance; the incomplete
     // factor is the iterative phase's preconditioner and stops at the PCG tolerance
-    const double target = ic_only ? tol : std::min(tol, 1e-10);
+    const double target = ic_only ? tol : (W.direct_cg_tol > 0 ? std::max(W.direct_cg_tol, std::min(tol, 1e-10))
+                                                               : std::min(tol, 1e-10));
     double *x = W.x64, *r = W.r64, *z = W.z64, *p = W.p64, *q = W.q64;
     double hs[SC_COUNT];
     OT_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * W.n, st));
@@ -1477,9 +1500,13 @@ Error newton_solve(Newton &W, const Support &S, const Rhs &R, double cg_tol, int
     OT_LAUNCHED();
     beta1_kernel<<<gm, kT, 0, st>>>(W.m, S.row_ptr, W.g, R.r1a, W.beta1);
     OT_LAUNCHED();
-    rhs_kernel<<<gn, kT, 0, st>>>(W.n, S.col_ptr, S.col_perm, S.col_row, W.g, W.theta_col, W.Minv, W.beta1, R.r1b,
-                                  W.beta2, W.rhs, W.part);
-    OT_LAUNCHED();
+    {
+        const unsigned gg = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div((int64_t)W.n * 8, kT),
+                                                                             8LL * W.num_sms));
+        rhs_group_kernel<8><<<gg, kT, 0, st>>>(W.n, S.col_ptr, S.col_perm, S.col_row, W.g, W.theta_col, W.Minv,
+                                               W.beta1, R.r1b, W.beta2, W.rhs);
+        OT_LAUNCHED();
+    }
     const bool one = W.onecomp;
     OT_TRY(project(W, W.rhs, one, st));
 
@@ -1500,8 +1527,12 @@ Error newton_solve(Newton &W, const Support &S, const Rhs &R, double cg_tol, int
         }
     }
     OT_TRY(project(W, dv, one, st));
-    du_kernel<<<gm, kT, 0, st>>>(W.m, S.row_ptr, S.j, W.theta, W.Minv, W.beta1, dv, du);
-    OT_LAUNCHED();
+    {
+        const unsigned gg = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div((int64_t)W.m * 8, kT),
+                                                                             8LL * W.num_sms));
+        du_group_kernel<8><<<gg, kT, 0, st>>>(W.m, S.row_ptr, S.j, W.theta, W.Minv, W.beta1, dv, du);
+        OT_LAUNCHED();
+    }
     dsdp_kernel<<<ge, kT, 0, st>>>(S.psi, S.i, S.j, S.p, S.s, R.r2, R.r3, du, dv, ds, dp);
     OT_LAUNCHED();
     if (stats) *stats = ss;

@@ -70,6 +70,7 @@ struct Newton {
     // (tree.cuh); takes precedence over every other solver
     struct TreeSolver *tree = nullptr;
     int fallbacks = 0;        // mixed-precision solves redone in FP64
+    double direct_cg_tol = 0.0;  // > 0: target of the factor-preconditioned CG (else min(tol, 1e-10))
     bool fp64_fallback = true;  // redo a failed mixed-precision solve with FP64 PCG
 };
 

@@ -488,6 +488,7 @@ threshold_kernel(const unsigned long long *__restrict__ hist_ns,   // support re
             if (acc >= (unsigned long long)kmax) { s_bstar = 4 * t + k; break; }
         }
     }
+    __shared__ int s_bg;
     __syncthreads();
     if (t == 0) {
         const int bstar = s_bstar;
@@ -502,13 +503,21 @@ threshold_kernel(const unsigned long long *__restrict__ hist_ns,   // support re
             else Tg = fminf(__fadd_ru(T, __fmul_ru(2.0f, E)), E);
         }
         geo->Tg = Tg;
-        int bg;                                   // bins that can hold keys <= Tg
-        if (Tg < 0.f) bg = bin_of_neg(Tg);
-        else bg = fp64 ? 4095 : 4096;
-        unsigned long long tot = 0;
-        for (int b = 0; b <= bg; ++b) tot += hist_all[b];
-        geo->gather_bound = tot;
+        // bins that can hold keys <= Tg
+        s_bg = Tg < 0.f ? bin_of_neg(Tg) : (fp64 ? 4095 : 4096);
     }
+    __syncthreads();
+    // the gather bound: the pairs (support included) in bins 0 .. bg, summed by the whole block
+    const int bg = s_bg;
+    unsigned long long loc2 = 0;
+    for (int b = t; b <= bg; b += 1024) loc2 += hist_all[b];
+    part[t] = loc2;
+    __syncthreads();
+    for (int o = 512; o > 0; o >>= 1) {
+        if (t < o) part[t] += part[t + o];
+        __syncthreads();
+    }
+    if (t == 0) geo->gather_bound = part[0];
 }
 
 __global__ void recheck_kernel(int m, int n, int kind, unsigned long long count, const int32_t *__restrict__ ci,

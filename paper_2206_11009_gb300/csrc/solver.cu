@@ -1084,7 +1084,8 @@ Error create_impl(const ot_problem *P, const ot_options *O, ot_ipm *h) {
     ot_options &o = h->opt;
     if (!(o.tol > 0) || o.max_iter < 0 || o.max_cg <= 0 || o.max_corr < 0 || !(o.step_scale > 0 && o.step_scale < 1) ||
         (o.precision != 0 && o.precision != 1) || o.jset_refresh < 0 || !std::isfinite(o.jset_cmax) ||
-        o.precond < 0 || o.precond > 1 || !(o.ic_tau >= 0 && o.ic_tau < 1) || o.tc_update < -1 || o.tc_update > 1)
+        o.precond < 0 || o.precond > 1 || !(o.ic_tau >= 0 && o.ic_tau < 1) || o.tc_update < -1 || o.tc_update > 1 ||
+        !(o.direct_cg_tol >= 0 && o.direct_cg_tol < 1))
         return fail(OT_ERR_ARG, "options: out of range");
     if (P->cost < 0 || P->cost > OT_COST_DENSE) return fail(OT_ERR_ARG, "problem: unknown cost kind");
     const bool dense = P->cost == OT_COST_DENSE;
@@ -1295,6 +1296,7 @@ Error create_impl(const ot_problem *P, const ot_options *O, ot_ipm *h) {
     const bool want_warm = (o.warm_u && o.warm_v) || (o.warm_i && o.warm_j && o.warm_npairs > 0);
     OT_TRY(newton_alloc(h->W, m, n, h->S[h->cur].cap, h->num_sms));
     h->W.verbose = h->opt.verbose;
+    h->W.direct_cg_tol = h->opt.direct_cg_tol;
     OT_TRY(complete_feasible(h, st));
     OT_TRY(chol_alloc(h->chol, n));
     int cgs = 0;
