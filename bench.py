@@ -492,7 +492,7 @@ def kernel_table(ktimes, pk_d, src):
             row.update(bound="alu", achieved=work / sec / 1e12, peak=2 * alu_peak / 1e12, unit="TFLOP/s",
                        frac=work / sec / (2 * alu_peak),
                        peak_source=f"152 SMs x 128 FP32 FMA lanes x 2 flops x {mhz:.0f} MHz (unit counts)")
-        elif name in ("pcg32", "pcg64", "ldl_solve", "d32_apply") and work:
+        elif name in ("pcg32", "pcg64", "ldl_solve", "d32_apply", "dcg") and work:
             row.update(bound="hbm", achieved=work / sec / 1e9, peak=hbm_peak, unit="GB/s",
                        frac=work / sec / 1e9 / hbm_peak, peak_source=f"MEASURED_PEAKS.json hbm_gbs ({src})")
         elif name == "ldl_numeric" and work:

@@ -103,7 +103,7 @@ SIGNATURES = {
 }
 
 KERNEL_IDS = ["scan_hist", "scan_gather", "recheck", "pcg64", "pcg32", "ldl_numeric", "ldl_solve",
-              "d32_factor", "d32_apply"]
+              "d32_factor", "d32_apply", "dcg"]
 
 _lib = None
 

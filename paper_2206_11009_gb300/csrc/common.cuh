@@ -52,7 +52,7 @@ inline Error ok() { return Error{OT_OK, std::string()}; }
 // launched on (ot_kernel_timing_enable / ot_kernel_timing_read in the C ABI).
 enum KernelId : int {
     KT_SCAN_HIST = 0, KT_SCAN_GATHER, KT_RECHECK, KT_PCG64, KT_PCG32, KT_LDL_NUMERIC, KT_LDL_SOLVE,
-    KT_D32_FACTOR, KT_D32_APPLY, KT_COUNT
+    KT_D32_FACTOR, KT_D32_APPLY, KT_DCG, KT_COUNT
 };
 void ktimer_begin(int id, cudaStream_t st);
 void ktimer_end(int id, cudaStream_t st);

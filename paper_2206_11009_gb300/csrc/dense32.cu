@@ -206,24 +206,48 @@ __device__ __forceinline__ void d32_micro_panel(int lane, int k, int c0, int nc,
     }
 }
 
-__global__ void __launch_bounds__(kTT)
-d32_diag_kernel(int ld, int k, int bs, float *__restrict__ A, float *__restrict__ D, const float *__restrict__ d0,
-                const float *__restrict__ csum, int np, float eps, float *__restrict__ Linv) {
-    __shared__ float S[kP][kP + 1];
-    __shared__ float Xs[kP][kP + 1];
-    __shared__ float Ts[kP / 2][kP / 2 + 1];
-    __shared__ float g[kP], thr[kP], ids[kP];
+// shared memory of one diagonal-block factorisation (kDiagSmem bytes when carved from a buffer)
+struct DiagSmem {
+    float (*S)[kP + 1];
+    float (*Xs)[kP + 1];
+    float (*Ts)[kP / 2 + 1];
+    float *g, *thr, *ids;
+};
+constexpr int kDiagSmem = (2 * kP * (kP + 1) + (kP / 2) * (kP / 2 + 1) + 3 * kP) * 4;
+
+__device__ __forceinline__ DiagSmem diag_smem(float *buf) {
+    DiagSmem m;
+    m.S = (float (*)[kP + 1])buf;
+    m.Xs = (float (*)[kP + 1])(buf + kP * (kP + 1));
+    m.Ts = (float (*)[kP / 2 + 1])(buf + 2 * kP * (kP + 1));
+    m.g = buf + 2 * kP * (kP + 1) + (kP / 2) * (kP / 2 + 1);
+    m.thr = m.g + kP;
+    m.ids = m.thr + kP;
+    return m;
+}
+
+// The diagonal block at k (bs columns) by one CTA of kTT threads.  The block and the partial sums
+// are read through L2 (__ldcg): in the fused step kernel other CTAs of the same launch wrote them.
+__device__ __forceinline__ void d32_diag_block(const DiagSmem &m, int ld, int k, int bs, float *__restrict__ A,
+                                               float *__restrict__ D, const float *__restrict__ d0,
+                                               const float *__restrict__ csum, int np, float eps,
+                                               float *__restrict__ Linv) {
+    float (*S)[kP + 1] = m.S;
+    float (*Xs)[kP + 1] = m.Xs;
+    float (*Ts)[kP / 2 + 1] = m.Ts;
+    float *g = m.g, *thr = m.thr, *ids = m.ids;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int t = threadIdx.x; t < kP * kP; t += blockDim.x) {
         const int i = t % kP, j = t / kP;
-        S[i][j] = (i > j && i < bs) ? A[(size_t)(k + j) * ld + (k + i)] : 0.f;
+        S[i][j] = (i > j && i < bs) ? __ldcg(A + (size_t)(k + j) * ld + (k + i)) : 0.f;
     }
     // the np partial sums per column come through shared memory (Xs as staging, kP rows at a time)
     // with independent loads; each column then adds its partials in order
     float gs = 0.f;
     for (int q0 = 0; q0 < np; q0 += kP) {
         const int nq = min(kP, np - q0);
-        for (int t = threadIdx.x; t < nq * kP; t += blockDim.x) Xs[t / kP][t % kP] = csum[(q0 + t / kP) * kP + t % kP];
+        for (int t = threadIdx.x; t < nq * kP; t += blockDim.x)
+            Xs[t / kP][t % kP] = __ldcg(csum + (q0 + t / kP) * kP + t % kP);
         __syncthreads();
         if (threadIdx.x < kP && threadIdx.x < bs)
             for (int q = 0; q < nq; ++q) gs += Xs[q][threadIdx.x];
@@ -347,6 +371,21 @@ d32_diag_kernel(int ld, int k, int bs, float *__restrict__ A, float *__restrict_
         const int i = t % bs, j = t / bs;
         Linv[(size_t)j * ld + (k + i)] = Xs[i][j];
     }
+}
+
+// L0 != NULL: first the rows [k, k + bs) of the previous panel's L21 (kept in L0 by the step
+// kernel, whose other CTAs read those rows of A unscaled) go to A
+__global__ void __launch_bounds__(kTT)
+d32_diag_kernel(int ld, int k, int bs, float *__restrict__ A, float *__restrict__ D, const float *__restrict__ d0,
+                const float *__restrict__ csum, int np, float eps, float *__restrict__ Linv,
+                const float *__restrict__ L0) {
+    __shared__ __align__(16) float buf[kDiagSmem / 4];
+    if (L0)
+        for (int t = threadIdx.x; t < kP * kP; t += blockDim.x) {
+            const int r = t % kP, j = t / kP;
+            if (r < bs) A[(size_t)(k - kP + j) * ld + k + r] = L0[j * kP + r];
+        }
+    d32_diag_block(diag_smem(buf), ld, k, bs, A, D, d0, csum, np, eps, Linv);
 }
 
 // rows r in [k+64, n) of the panel (bs = 64 whenever rows remain below the block): 64 rows per
@@ -548,13 +587,15 @@ d32_update1_kernel(int n, int ld, int k, float *__restrict__ A, float *__restric
     }
 }
 
+// the rest of the update from base2 = base + skip * 64 on (skip = 1, or 2 when the block after
+// the next panel went to its own d32_update1_kernel launch)
 __global__ void __launch_bounds__(kTT, 2)
-d32_update_kernel(int n, int ld, int k, float *__restrict__ A, float *__restrict__ X,
+d32_update_kernel(int n, int ld, int k, int skip, float *__restrict__ A, float *__restrict__ X,
                   const float *__restrict__ LD) {
     // two stages: slice s + 1 is fetched into registers while slice s is multiplied
     __shared__ __align__(16) float As[2][kKc][kTile];
     __shared__ __align__(16) float Bs[2][kKc][kTile];
-    const int base = k + kP, base2 = base + kP;
+    const int base = k + kP, base2 = base + skip * kP;
     const int t = (n - base2 + kTile - 1) / kTile;   // row / column tiles from base2 on
     const int tcn = (base + kTile - 1) / kTile;      // column tiles of the rows of L^-1
     const int idx = blockIdx.x;
@@ -666,6 +707,189 @@ d32_update_kernel(int n, int ld, int k, float *__restrict__ A, float *__restrict
             for (int u = 0; u < 8; ++u) {
                 const int r = r0 + tr * 8 + u;
                 if (r < n && (!tri || r > c)) C[(size_t)c * ld + r] -= acc[u][w];
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ fused panel step (SIMT path)
+// One launch per panel k (bs = 64, base = k + 64 < n) does what the next diagonal block waits for,
+// so the panel-to-panel chain is two kernels (this one and the next diagonal block):
+//   strip CTA rb (rows R = base + 64 rb ..): LD[R] = A21[R] L11^-T and L21[R] = LD[R] D1^-1 (the
+//     panel), then the next panel's 64 columns A22[R, R0] -= LD[R] L21[R0]^T (R0 = the next
+//     panel's rows; L21[R0] recomputed in every CTA from the unscaled A21[R0]) together with the
+//     previous panel's update of the same columns, -= LD'[R] L21'[R0]^T, and the fixed-order
+//     partial column sums below the next diagonal block;
+//   X CTA cb (columns C = 64 cb .. of block row k of L^-1): X[k, C] = L11^-1 B[k, C] (the block row),
+//     then X[R0, C] -= L21[R0] X[k, C] + L21'[R0] X[k - 64, C] (the previous panel's part);
+// L21[R0] goes to A with the next diagonal block's kernel (the other CTAs read A21[R0] unscaled).
+// What remains of both updates (rows and columns from base + 128) is d32_update_kernel's (skip 2).
+constexpr int kStepSmem = (5 * kP * kP + kP) * 4;
+
+// acc[u][w] += sum_l a[l][tr * 4 + u] b[l][tc * 4 + w] (64 x 64 operands, [depth][index])
+__device__ __forceinline__ void mm64(const float *__restrict__ a, const float *__restrict__ b, float (&acc)[4][4],
+                                     int tr, int tc) {
+#pragma unroll 16
+    for (int l = 0; l < kP; ++l) {
+        const float4 x = *(const float4 *)(a + l * kP + tr * 4);
+        const float4 y = *(const float4 *)(b + l * kP + tc * 4);
+        const float av[4] = {x.x, x.y, x.z, x.w}, bv[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int w = 0; w < 4; ++w) acc[u][w] += av[u] * bv[w];
+    }
+}
+
+// tile[l][r] = G[(col0 + l) ld + row0 + r] for row0 + r < rlim, else 0 (row0 a multiple of 4)
+__device__ __forceinline__ void load_cm(float *__restrict__ tile, const float *__restrict__ G, int ld, int col0,
+                                        int row0, int rlim) {
+    for (int t = threadIdx.x; t < kP * (kP / 4); t += blockDim.x) {
+        const int l = t / (kP / 4), q = (t % (kP / 4)) * 4;
+        const float *src = G + (size_t)(col0 + l) * ld + row0 + q;
+        float4 v;
+        if (row0 + q + 4 <= rlim) v = *(const float4 *)src;
+        else {
+            v.x = row0 + q < rlim ? src[0] : 0.f;
+            v.y = row0 + q + 1 < rlim ? src[1] : 0.f;
+            v.z = row0 + q + 2 < rlim ? src[2] : 0.f;
+            v.w = row0 + q + 3 < rlim ? src[3] : 0.f;
+        }
+        *(float4 *)(tile + l * kP + q) = v;
+    }
+}
+
+// tile[l][c] = X(row0 + l, c0 + c) = X[(c0 + c) ld + row0 + l] for c0 + c < climit, else 0
+__device__ __forceinline__ void load_rows_of_x(float *__restrict__ tile, const float *__restrict__ X, int ld,
+                                               int row0, int c0, int climit) {
+    for (int t = threadIdx.x; t < kP * (kP / 4); t += blockDim.x) {
+        const int c = t % kP, lq = (t / kP) * 4;
+        float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (c0 + c < climit) w = *(const float4 *)(X + (size_t)(c0 + c) * ld + row0 + lq);
+        tile[(lq + 0) * kP + c] = w.x;
+        tile[(lq + 1) * kP + c] = w.y;
+        tile[(lq + 2) * kP + c] = w.z;
+        tile[(lq + 3) * kP + c] = w.w;
+    }
+}
+
+__global__ void __launch_bounds__(kTT)
+d32_step_kernel(int n, int ld, int k, float *__restrict__ A, float *__restrict__ X,
+                const float *__restrict__ D, const float *__restrict__ Linv, float *__restrict__ LDc,
+                const float *__restrict__ LDprev, float *__restrict__ L0buf, float *__restrict__ csum) {
+    extern __shared__ __align__(16) float sm[];
+    float *Lt = sm, *T1 = sm + kP * kP, *T2 = sm + 2 * kP * kP, *T3 = sm + 3 * kP * kP, *T4 = sm + 4 * kP * kP;
+    float *idv = sm + 5 * kP * kP;
+    const int base = k + kP;
+    const int ts = (n - base + kP - 1) / kP;
+    const bool strip = (int)blockIdx.x < ts;
+    const bool prev = k > 0;
+    const int tr = threadIdx.x & 15, tc = threadIdx.x >> 4;
+    // Lt[l][j] = (L11^-1)_jl; idv = D1^+ (0 for grounded pivots)
+    for (int t = threadIdx.x; t < kP * kP; t += blockDim.x) {
+        const int j = t % kP, l = t / kP;
+        Lt[l * kP + j] = Linv[(size_t)l * ld + (k + j)];
+    }
+    if (threadIdx.x < kP) {
+        const float dj = D[k + threadIdx.x];
+        idv[threadIdx.x] = isinf(dj) ? 0.f : 1.f / dj;
+    }
+    float acc[4][4], acc2[4][4], acc3[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int w = 0; w < 4; ++w) acc[u][w] = acc2[u][w] = acc3[u][w] = 0.f;
+    if (strip) {
+        const int rb = blockIdx.x, r0 = base + rb * kP;
+        load_cm(T1, A, ld, k, r0, n);                         // A21[R]       [l][r]
+        if (rb > 0) load_cm(T2, A, ld, k, base, n);           // A21[R0]      [l][c]
+        if (prev) {
+            load_cm(T3, LDprev, ld, 0, r0, n);                // LD'[R]       [j][r]
+            load_cm(T4, A, ld, k - kP, base, n);              // L21'[R0]     [j][c]
+        }
+        __syncthreads();
+        mm64(T1, Lt, acc, tr, tc);                            // LD(r, j), r = tr*4+u, j = tc*4+w
+        if (rb > 0) mm64(T2, Lt, acc2, tr, tc);               // LD(R0_r, j)
+        __syncthreads();
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const int j = tc * 4 + w;
+            const float id = idv[j];
+            const bool inf = id == 0.f;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int r = r0 + tr * 4 + u;
+                const float ldv = inf ? 0.f : acc[u][w];
+                if (r < n) {
+                    LDc[(size_t)j * ld + r] = ldv;
+                    if (rb == 0) L0buf[j * kP + tr * 4 + u] = acc[u][w] * id;
+                    else A[(size_t)(k + j) * ld + r] = acc[u][w] * id;
+                }
+                T1[j * kP + tr * 4 + u] = ldv;                                 // A operand [j][r]
+                T2[j * kP + tr * 4 + u] = (rb == 0 ? acc[u][w] : acc2[u][w]) * id;  // B operand [j][c]
+            }
+        }
+        __syncthreads();
+        mm64(T1, T2, acc3, tr, tc);
+        if (prev) mm64(T3, T4, acc3, tr, tc);
+        // A22[R, R0] -= acc3 below the diagonal; column sums of the rows below the next block
+        float cs[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const int c = base + tc * 4 + w;
+            if (c >= n) continue;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int r = r0 + tr * 4 + u;
+                if (r < n && r > c) {
+                    const float v = A[(size_t)c * ld + r] - acc3[u][w];
+                    A[(size_t)c * ld + r] = v;
+                    if (r >= base + kP) cs[w] += v;
+                }
+            }
+        }
+        // the 16 threads with this tc are one half-warp (lanes tr = 0..15)
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            float v = cs[w];
+#pragma unroll
+            for (int o = 1; o < 16; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (tr == 0) csum[(size_t)rb * kP + tc * 4 + w] = v;
+        }
+    } else {
+        const int cb = (int)blockIdx.x - ts, c0 = cb * kP;
+        const bool before = c0 < k;                           // columns left of the diagonal block
+        if (before) load_rows_of_x(T1, X, ld, k, c0, k);      // B[k, C]      [l][c]
+        load_cm(T2, A, ld, k, base, n);                       // A21[R0]      [l][r]
+        if (prev && before) {
+            load_cm(T3, A, ld, k - kP, base, n);              // L21'[R0]     [j][r]
+            load_rows_of_x(T4, X, ld, k - kP, c0, k);         // X[k - 64, C] [j][c]
+        }
+        __syncthreads();
+        if (before) mm64(Lt, T1, acc, tr, tc);                // X(k + i, c), i = tr*4+u, c = tc*4+w
+        mm64(T2, Lt, acc2, tr, tc);                           // LD(R0_r, j)
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                const int i = tr * 4 + u, c = tc * 4 + w;
+                const float x = before ? acc[u][w] : Lt[c * kP + i];
+                X[(size_t)(c0 + c) * ld + (k + i)] = x;
+                T1[i * kP + c] = x;                                          // B operand [i][c]
+                T2[(tc * 4 + w) * kP + tr * 4 + u] = acc2[u][w] * idv[tc * 4 + w];  // A operand [j][r]
+            }
+        }
+        __syncthreads();
+        mm64(T2, T1, acc3, tr, tc);
+        if (prev && before) mm64(T3, T4, acc3, tr, tc);
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const int c = c0 + tc * 4 + w;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int r = base + tr * 4 + u;
+                if (r < n) X[(size_t)c * ld + r] -= acc3[u][w];
             }
         }
     }
@@ -981,16 +1205,17 @@ Error d32_alloc(Dense32 &F, int32_t n) {
     const size_t big = sizeof(float) * (size_t)F.ld * n;
     OT_CUDA(cudaMalloc((void **)&F.A, big));
     OT_CUDA(cudaMalloc((void **)&F.X, big));
-    OT_CUDA(cudaMalloc((void **)&F.LD, 2 * sizeof(float) * (size_t)F.ld * kP));
+    OT_CUDA(cudaMalloc((void **)&F.LD, 3 * sizeof(float) * (size_t)F.ld * kP));
     OT_CUDA(cudaMalloc((void **)&F.Linv, sizeof(float) * (size_t)F.ld * kP));
     OT_CUDA(cudaMalloc((void **)&F.D, sizeof(float) * n));
     OT_CUDA(cudaMalloc((void **)&F.d0, sizeof(float) * n));
     OT_CUDA(cudaMalloc((void **)&F.csum, sizeof(float) * kP * (size_t)ceil_div(n, kP)));
+    OT_CUDA(cudaMalloc((void **)&F.L0, sizeof(float) * kP * kP));
     OT_CUDA(cudaMalloc((void **)&F.w, sizeof(float) * n));
     OT_CUDA(cudaMalloc((void **)&F.part, sizeof(float) * (size_t)F.ld * (size_t)ceil_div(n, kFc)));
     // lower bound of the unwritten upper parts, so that nothing uninitialised is ever read
     OT_CUDA(cudaMemset(F.A, 0, big));
-    OT_CUDA(cudaMemset(F.LD, 0, 2 * sizeof(float) * (size_t)F.ld * kP));
+    OT_CUDA(cudaMemset(F.LD, 0, 3 * sizeof(float) * (size_t)F.ld * kP));
     OT_CUDA(cudaMemset(F.Linv, 0, sizeof(float) * (size_t)F.ld * kP));
     // one process-wide limit, the largest any n of this path needs (a per-n value set by one
     // handle could undercut another handle's launch on another thread)
@@ -999,6 +1224,8 @@ Error d32_alloc(Dense32 &F, int32_t n) {
     std::call_once(once, [] {
         attr_err = cudaFuncSetAttribute(d32_assemble_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)(sizeof(unsigned long long) * kSlice));
+        if (attr_err == cudaSuccess)
+            attr_err = cudaFuncSetAttribute(d32_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kStepSmem);
     });
     if (attr_err != cudaSuccess) return fail(OT_ERR_CUDA, cudaGetErrorString(attr_err));
     if (n > kMaxN) return fail(OT_ERR_ARG, "dense32: n above the supported size");
@@ -1008,7 +1235,7 @@ Error d32_alloc(Dense32 &F, int32_t n) {
 void d32_free(Dense32 &F) {
     if (F.graph) cudaGraphExecDestroy(F.graph);
     for (void *p : {(void *)F.A, (void *)F.X, (void *)F.LD, (void *)F.Linv, (void *)F.D, (void *)F.d0, (void *)F.csum,
-                    (void *)F.w, (void *)F.part, (void *)F.tc, (void *)F.tc_err})
+                    (void *)F.L0, (void *)F.w, (void *)F.part, (void *)F.tc, (void *)F.tc_err})
         if (p) cudaFree(p);
     if (F.tc_err_host) cudaFreeHost(F.tc_err_host);
     F = Dense32();
@@ -1119,19 +1346,68 @@ static Error d32_build(Dense32 &F, float eps, cudaGraph_t g, int64_t *nodes) {
     Dag c;
     c.g = g;
     cudaGraphNode_t prev = c.memset0(F.X, (size_t)ld * n, {});
-    cudaGraphNode_t u1 = nullptr, u2 = nullptr;   // the previous panel's two update parts
-    int np = 1;  // partial column sums feeding the next diagonal block
-    // the chain diag -> panel / invrow -> first update part runs ahead of the bulk update, whose
-    // CTAs would otherwise take the SMs the chain's small grids wait for
     int lo_prio = 0, hi_prio = 0;
     if (cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio) != cudaSuccess) lo_prio = hi_prio = 0;
+    if (!F.use_tc) {
+        // SIMT: the first diagonal block, then one fused step per panel (which also factors the next
+        // diagonal block) on the chain, the rest of each panel's update (from base + 128) beside
+        // it.  The step of panel p waits for the rest-update of panel p - 2 (which covered its
+        // columns); the rest-updates run in order.  Three LD buffers: the rest-update of panel p
+        // still reads its own while the steps of p + 1 and p + 2 write theirs.
+        const int bs0 = std::min(kP, n);
+        prev = c.kernel({prev}, d32_colsum_kernel, (unsigned)bs0, kTT, n, ld, bs0, (const float *)F.A, F.csum);
+        cudaGraphNode_t chain = c.kernel({prev}, d32_diag_kernel, 1u, kTT, ld, 0, bs0, F.A, F.D, (const float *)F.d0,
+                                         (const float *)F.csum, 1, eps, F.Linv, (const float *)nullptr);
+        c.priority(chain, hi_prio);
+        cudaGraphNode_t rest1 = nullptr, rest2 = nullptr;   // rest-updates of panels p - 1 and p - 2
+        int k = 0, p = 0;
+        for (; k + kP < n; k += kP, ++p) {
+            const int base = k + kP;
+            const int ts = (int)ceil_div(n - base, kP), tx = (int)ceil_div(base, kP);
+            float *LDc = F.LD + (size_t)(p % 3) * ld * kP;
+            const float *LDprev = F.LD + (size_t)((p + 2) % 3) * ld * kP;
+            const cudaGraphNode_t sn =
+                c.kernel_smem({chain, rest2}, d32_step_kernel, (unsigned)(ts + tx), kTT, (unsigned)kStepSmem, n, ld,
+                              k, F.A, F.X, (const float *)F.D, (const float *)F.Linv, LDc, LDprev, F.L0, F.csum);
+            c.priority(sn, hi_prio);
+            const cudaGraphNode_t dn =
+                c.kernel({sn}, d32_diag_kernel, 1u, kTT, ld, base, std::min(kP, n - base), F.A, F.D,
+                         (const float *)F.d0, (const float *)F.csum, ts, eps, F.Linv, (const float *)F.L0);
+            c.priority(dn, hi_prio);
+            const int b2 = base + 2 * kP;
+            const int t2 = b2 < n ? (int)ceil_div(n - b2, kTile) : 0, tcn = (int)ceil_div(base, kTile);
+            const int n2 = t2 * (t2 + 1) / 2 + t2 * tcn;
+            cudaGraphNode_t rest = nullptr;
+            if (n2 > 0) {
+                rest = c.kernel({sn, rest1}, d32_update_kernel, (unsigned)n2, kTT, n, ld, k, 2, F.A, F.X,
+                                (const float *)LDc);
+                c.priority(rest, lo_prio);
+            } else {
+                rest = c.join({sn, rest1});
+            }
+            rest2 = rest1;
+            rest1 = rest;
+            chain = dn;
+        }
+        // the last panel: its diagonal block came with the last step (or is the first block); its
+        // block row of L^-1, then the end of the graph after all writes
+        const int bs = n - k;
+        const cudaGraphNode_t ir = c.kernel({chain}, d32_invrow_kernel, (unsigned)ceil_div(n, kP), kTT, ld, k, bs,
+                                            F.X, (const float *)F.Linv);
+        c.priority(ir, hi_prio);
+        prev = c.join({ir, rest1, rest2});
+    } else {
+    // tensor cores: per panel diag -> panel / invrow -> first update part (the next panel's block) on
+    // the chain, the bulk update of the rest beside it (the next panel's first part waits for it)
+    cudaGraphNode_t u1 = nullptr, u2 = nullptr;
+    int np = 1;  // partial column sums feeding the next diagonal block
     for (int k = 0, p = 0; k < n; k += kP, ++p) {
         const int bs = std::min(kP, n - k), base = k + bs;
-        float *LDp = F.LD + (size_t)(p & 1) * ld * kP;   // double-buffered: the rest of the previous
-                                                          // update may still read the other half
+        float *LDp = F.LD + (size_t)(p % 3) * ld * kP;
         if (k == 0) prev = c.kernel({prev}, d32_colsum_kernel, (unsigned)bs, kTT, n, ld, bs, (const float *)F.A, F.csum);
         const cudaGraphNode_t dg = c.kernel({k == 0 ? prev : u1}, d32_diag_kernel, 1u, kTT, ld, k, bs, F.A, F.D,
-                                            (const float *)F.d0, (const float *)F.csum, np, eps, F.Linv);
+                                            (const float *)F.d0, (const float *)F.csum, np, eps, F.Linv,
+                                            (const float *)nullptr);
         c.priority(dg, hi_prio);
         std::vector<cudaGraphNode_t> ready;
         if (base < n)
@@ -1141,46 +1417,40 @@ static Error d32_build(Dense32 &F, float eps, cudaGraph_t g, int64_t *nodes) {
                                  (const float *)F.Linv));
         for (cudaGraphNode_t r : ready) c.priority(r, hi_prio);
         if (u2) ready.push_back(u2);
-        if (base < n) {
-            const int ts = (int)ceil_div(n - base, kP), tx = (int)ceil_div(base, kP);
-            u1 = c.kernel(ready, d32_update1_kernel, (unsigned)(ts + tx), kTT, n, ld, k, F.A, F.X,
-                          (const float *)LDp, F.csum);
-            c.priority(u1, hi_prio);
-            const int base2 = base + kP;
-            const int t2 = base2 < n ? (int)ceil_div(n - base2, kTile) : 0, tcn = (int)ceil_div(base, kTile);
-            const int n2 = t2 * (t2 + 1) / 2 + t2 * tcn;
-            if (n2 > 0 && F.use_tc) {
-                // the operands of this panel's bulk update split for the tensor cores (buffers by
-                // panel parity: the previous panel's update may still read the other half)
-                const int T = (int)ceil_div(n - base2, kTcM), nb = (int)ceil_div(n - base2, kTcN);
-                const int nx = (int)ceil_div(base, kTcN);
-                float *LDs = F.tc + (size_t)(p & 1) * tc_per_parity(n);
-                float *PAs = LDs + tc_a_floats(n), *PBs = PAs + tc_a_floats(n), *XBs = PBs + tc_b_floats(n);
-                const float *panel = F.A + (size_t)k * ld;
-                std::vector<cudaGraphNode_t> sp;
-                sp.push_back(c.kernel(ready, d32_tc_split_kernel<kTcM, false>, (unsigned)T, kTT, n, ld,
-                                      (const float *)LDp, base2, LDs));
-                sp.push_back(c.kernel(ready, d32_tc_split_kernel<kTcN, false>, (unsigned)nb, kTT, n, ld, panel, base2,
-                                      PBs));
-                sp.push_back(c.kernel(ready, d32_tc_split_kernel<kTcM, false>, (unsigned)T, kTT, n, ld, panel, base2,
-                                      PAs));
-                sp.push_back(c.kernel(ready, d32_tc_split_kernel<kTcN, true>, (unsigned)nx, kTT, base, ld,
-                                      (const float *)(F.X + k), 0, XBs));
-                for (cudaGraphNode_t q : sp) c.priority(q, lo_prio);
-                u2 = c.kernel_smem(sp, d32_tc_update_kernel, (unsigned)(T * (T + 1) + T * nx), kTcThreads,
-                                   (unsigned)kTcSmem, n, ld, base, base2, T, (const float *)LDs, (const float *)PBs,
-                                   (const float *)PAs, (const float *)XBs, F.A, F.X, F.tc_err);
-            } else {
-                u2 = n2 > 0 ? c.kernel(ready, d32_update_kernel, (unsigned)n2, kTT, n, ld, k, F.A, F.X,
-                                       (const float *)LDp)
-                            : nullptr;
-            }
-            c.priority(u2, lo_prio);
-            np = ts;
-        } else {
+        if (base >= n) {
             // the last panel: join everything so the graph ends after all writes
             prev = c.join(ready);
+            break;
         }
+        const int ts = (int)ceil_div(n - base, kP), tx = (int)ceil_div(base, kP);
+        np = ts;
+        u1 = c.kernel(ready, d32_update1_kernel, (unsigned)(ts + tx), kTT, n, ld, k, F.A, F.X, (const float *)LDp,
+                      F.csum);
+        c.priority(u1, hi_prio);
+        const int base2 = base + kP;
+        u2 = nullptr;
+        if (base2 < n) {
+            // the operands of this panel's bulk update split for the tensor cores (buffers by panel
+            // parity: the previous panel's update may still read the other half)
+            const int T = (int)ceil_div(n - base2, kTcM), nb = (int)ceil_div(n - base2, kTcN);
+            const int nx = (int)ceil_div(base, kTcN);
+            float *LDs = F.tc + (size_t)(p & 1) * tc_per_parity(n);
+            float *PAs = LDs + tc_a_floats(n), *PBs = PAs + tc_a_floats(n), *XBs = PBs + tc_b_floats(n);
+            const float *panel = F.A + (size_t)k * ld;
+            std::vector<cudaGraphNode_t> sp;
+            sp.push_back(c.kernel(ready, d32_tc_split_kernel<kTcM, false>, (unsigned)T, kTT, n, ld, (const float *)LDp,
+                                  base2, LDs));
+            sp.push_back(c.kernel(ready, d32_tc_split_kernel<kTcN, false>, (unsigned)nb, kTT, n, ld, panel, base2, PBs));
+            sp.push_back(c.kernel(ready, d32_tc_split_kernel<kTcM, false>, (unsigned)T, kTT, n, ld, panel, base2, PAs));
+            sp.push_back(c.kernel(ready, d32_tc_split_kernel<kTcN, true>, (unsigned)nx, kTT, base, ld,
+                                  (const float *)(F.X + k), 0, XBs));
+            for (cudaGraphNode_t q : sp) c.priority(q, lo_prio);
+            u2 = c.kernel_smem(sp, d32_tc_update_kernel, (unsigned)(T * (T + 1) + T * nx), kTcThreads,
+                               (unsigned)kTcSmem, n, ld, base, base2, T, (const float *)LDs, (const float *)PBs,
+                               (const float *)PAs, (const float *)XBs, F.A, F.X, F.tc_err);
+            c.priority(u2, lo_prio);
+        }
+    }
     }
     if (c.err != cudaSuccess) return fail(OT_ERR_CUDA, cudaGetErrorString(c.err));
     *nodes = c.nodes;

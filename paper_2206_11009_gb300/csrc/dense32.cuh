@@ -21,7 +21,8 @@ struct Dense32 {
     int32_t n = 0, ld = 0;       // ld: column stride (n rounded up to a multiple of 32)
     float *A = nullptr;          // ld x n column-major; strictly lower part: S_M, then L
     float *X = nullptr;          // ld x n; lower part with the unit diagonal: L^-1
-    float *LD = nullptr;         // 2 x ld x 64 panel scratch (L21 D1), alternate panels
+    float *LD = nullptr;         // 3 x ld x 64 panel scratch (L21 D1), panels in turn
+    float *L0 = nullptr;         // 64 x 64: the next panel's rows of L21, until the next diagonal kernel stores them
     float *Linv = nullptr;       // ld x 64: inverse diagonal blocks, block k in rows k..k+63
     float *D = nullptr;          // n pivots (+inf: grounded)
     float *d0 = nullptr;         // n diagonal entries of S_M (the reference of the pivot rule)

@@ -1213,8 +1213,13 @@ static Error solve_direct(Newton &W, const Support &S, double tol, int max_cg, d
         const int G = avg >= 12 ? 16 : (avg >= 6 ? 8 : 4);
         const unsigned gmr = (unsigned)std::min<int64_t>(ceil_div((int64_t)W.m * G, kT), 8LL * W.num_sms);
         const unsigned gnc = (unsigned)std::min<int64_t>(ceil_div((int64_t)W.n * G, kT), kMaxPartBlocks);
+        // algorithmic bytes of one operator application and step: per support pair theta (8), an
+        // index (4) and a gathered vector entry (8) in each pass; per row the offset, M^-1 and w;
+        // per column the offset, q, p twice and the step's reads of x, r and writes of x, r
+        const double dcg_bytes = 40.0 * (double)S.psi + 20.0 * (double)W.m + 68.0 * (double)W.n;
         auto issue = [&](int k) -> Error {
             const int cur = (k & 1) ? SC_RZ1 : SC_RZ0, nxt = (k & 1) ? SC_RZ0 : SC_RZ1;
+            ktimer_begin(KT_DCG, st);
             if (G == 16) {
                 mvg_rows_kernel<16><<<gmr, kT, 0, st>>>(W.m, S.row_ptr, S.j, W.theta, W.Minv, p, W.w64);
                 OT_LAUNCHED();
@@ -1231,6 +1236,8 @@ static Error solve_direct(Newton &W, const Support &S, double tol, int max_cg, d
             OT_LAUNCHED();
             dcg_step2_kernel<<<gn, kT, 0, st>>>(W.n, (int)gnc, W.scal, cur, p, q, x, r, W.part);
             OT_LAUNCHED();
+            ktimer_end(KT_DCG, st);
+            ktimer_add_work(KT_DCG, dcg_bytes);
             OT_TRY(precond(r, z));
             dot_kernel<<<gn, kT, 0, st>>>(W.n, r, z, W.part, nxt);
             OT_LAUNCHED();
