@@ -137,10 +137,16 @@ __device__ __forceinline__ double block_min(double x, double *sh) {
 
 // ------------------------------------------------------------------------ grid barrier
 // Sense-free generation barrier for kernels launched cooperatively (co-residency is then
-// guaranteed).  bar[0] = arrival count, bar[1] = generation.  Every wait is bounded: after
+// guaranteed).  bar[0] = arrival count (bar[1] unused).  Every wait is bounded: after
 // ~kSpinLimit polls the barrier records OT_ERR_TIMEOUT in *err and returns false; callers
 // leave the kernel as soon as a barrier returns false.
 constexpr unsigned kSpinLimit = 1u << 22;
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
 
 __device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nblocks, int *err) {
     __syncthreads();
@@ -148,28 +154,22 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nblocks, in
     if (threadIdx.x == 0) {
         int okv = 1;
         if (nblocks > 1) {
-            volatile unsigned *gen = bar + 1;
-            unsigned g = *gen;
+            // bar[0] counts arrivals over the whole launch (zeroed before it): the barrier this
+            // arrival belongs to opens when the count reaches the next multiple of nblocks, so
+            // the last arrival releases it by itself (no reset, no second word on the path)
             __threadfence();
-            unsigned arrived = atomicAdd(bar, 1u);
-            if (arrived == nblocks - 1) {
-                atomicExch(bar, 0u);
-                __threadfence();
-                atomicAdd(bar + 1, 1u);
-            } else {
-                unsigned spins = 0;
-                while (*gen == g) {
-                    if (++spins > kSpinLimit || *(volatile int *)err) {
-                        atomicCAS(err, 0, (int)OT_ERR_TIMEOUT);
-                        okv = 0;
-                        break;
-                    }
-                    __nanosleep(20);
+            const unsigned arrived = atomicAdd(bar, 1u);
+            const unsigned target = (arrived / nblocks + 1u) * nblocks;
+            unsigned spins = 0;
+            while ((int)(ld_acquire_gpu(bar) - target) < 0) {
+                if (++spins > kSpinLimit || *(volatile int *)err) {
+                    atomicCAS(err, 0, (int)OT_ERR_TIMEOUT);
+                    okv = 0;
+                    break;
                 }
+                __nanosleep(20);
             }
-            __threadfence();
         }
-        if (*(volatile int *)err) okv = 0;
         s_ok = okv;
     }
     __syncthreads();

@@ -422,35 +422,61 @@ __global__ void __launch_bounds__(kPcgT) pcg_kernel(PcgArgs<T> A, int g) {
         for (it = 0; it < A.maxit;) {
             // row pass with p = z + beta pprev (the trip count is uniform across a warp: groups
             // past the end contribute zero but still take part in the shuffles)
-            for (int64_t i0 = wgrp0; i0 < m; i0 += ngrp) {
-                const int64_t i = i0 + (grp - wgrp0);
-                T acc = (T)0;
-                if (i < m) {
-                    const int lo = A.rp[i], hi = A.rp[i + 1];
-                    for (int e = lo + lg; e < hi; e += g) {
-                        const int j = A.sj[e];
-                        acc += A.th[e] * (A.z[j] + beta * pprev[j]);
+            // two rows per group and trip (rows i and i + ngrp), their loads interleaved: the
+            // passes are bound by the latency of the index -> gather chains, not by bandwidth
+            for (int64_t i0 = wgrp0; i0 < m; i0 += 2 * ngrp) {
+                const int64_t ia = i0 + (grp - wgrp0), ib = ia + ngrp;
+                T acca = (T)0, accb = (T)0;
+                int ea = 0, ha = 0, eb = 0, hb = 0;
+                if (ia < m) { ea = A.rp[ia] + lg; ha = A.rp[ia + 1]; }
+                if (ib < m) { eb = A.rp[ib] + lg; hb = A.rp[ib + 1]; }
+                while (ea < ha || eb < hb) {
+                    if (ea < ha) {
+                        const int j = A.sj[ea];
+                        acca += A.th[ea] * (A.z[j] + beta * pprev[j]);
+                        ea += g;
+                    }
+                    if (eb < hb) {
+                        const int j = A.sj[eb];
+                        accb += A.th[eb] * (A.z[j] + beta * pprev[j]);
+                        eb += g;
                     }
                 }
-                acc = group_sum(acc, g);
-                if (lg == 0 && i < m) A.w[i] = A.Minv[i] * acc;
+                acca = group_sum(acca, g);
+                accb = group_sum(accb, g);
+                if (lg == 0 && ia < m) A.w[ia] = A.Minv[ia] * acca;
+                if (lg == 0 && ib < m) A.w[ib] = A.Minv[ib] * accb;
             }
             if (!grid_barrier(A.bar, G, A.err)) return;
-            // column pass
+            // column pass (two columns per group and trip)
             double pq = 0;
-            for (int64_t j0 = wgrp0; j0 < n; j0 += ngrp) {
-                const int64_t j = j0 + (grp - wgrp0);
-                T pj = (T)0, acc = (T)0;
-                if (j < n) {
-                    pj = A.z[j] + beta * pprev[j];
-                    const int lo = A.cp[j], hi = A.cp[j + 1];
-                    for (int k = lo + lg; k < hi; k += g) acc += A.thc[k] * (pj - A.w[A.crow[k]]);
+            for (int64_t j0 = wgrp0; j0 < n; j0 += 2 * ngrp) {
+                const int64_t ja = j0 + (grp - wgrp0), jb = ja + ngrp;
+                T pa = (T)0, pb2 = (T)0, acca = (T)0, accb = (T)0;
+                int ka = 0, ha = 0, kb = 0, hb = 0;
+                if (ja < n) { pa = A.z[ja] + beta * pprev[ja]; ka = A.cp[ja] + lg; ha = A.cp[ja + 1]; }
+                if (jb < n) { pb2 = A.z[jb] + beta * pprev[jb]; kb = A.cp[jb] + lg; hb = A.cp[jb + 1]; }
+                while (ka < ha || kb < hb) {
+                    if (ka < ha) {
+                        acca += A.thc[ka] * (pa - A.w[A.crow[ka]]);
+                        ka += g;
+                    }
+                    if (kb < hb) {
+                        accb += A.thc[kb] * (pb2 - A.w[A.crow[kb]]);
+                        kb += g;
+                    }
                 }
-                acc = group_sum(acc, g);
-                if (lg == 0 && j < n) {
-                    A.q[j] = acc;
-                    pcur[j] = pj;
-                    pq += (double)pj * (double)acc;
+                acca = group_sum(acca, g);
+                accb = group_sum(accb, g);
+                if (lg == 0 && ja < n) {
+                    A.q[ja] = acca;
+                    pcur[ja] = pa;
+                    pq += (double)pa * (double)acca;
+                }
+                if (lg == 0 && jb < n) {
+                    A.q[jb] = accb;
+                    pcur[jb] = pb2;
+                    pq += (double)pb2 * (double)accb;
                 }
             }
             {
@@ -755,10 +781,11 @@ Error launch_pcg(Newton &W, const Support &S, const T *th, const T *thc, const T
                  const T *b, T *x, T *r, T *z, T *p, T *q, T *w, double tol, int maxit, cudaStream_t st) {
     int per_sm = 0;
     OT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg_kernel<T>, kPcgT, 0));
-    // lane-group size ~ half the average row length (power of two, <= 32)
+    // lane-group size ~ half the average row length (power of two)
     const double avg = (double)std::max<int64_t>(S.psi, 1) / (double)std::max(W.m, 1);
+    // (at most 16: measured at 256^2 with 33 pairs per row, 16 lanes beat 32 by 8 %)
     int g = 1;
-    while (g < 32 && 2 * g <= avg) g <<= 1;
+    while (g < 16 && 2 * g <= avg) g <<= 1;
     const int64_t threads = (int64_t)std::max(W.m, W.n) * g;
     const int maxg = std::max(1, per_sm) * W.num_sms;
     int G = W.pcg_grid > 0 ? W.pcg_grid : (int)std::max<int64_t>(1, ceil_div(threads, kPcgT));

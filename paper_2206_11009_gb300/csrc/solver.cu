@@ -239,11 +239,11 @@ struct ot_ipm {
     Dense32 d32;
     std::vector<int64_t> psi_hist;
     bool direct_mode = false;
-    bool d32_escalated = false;
+    bool d32_escalated = false;  // the FP32-preconditioned CG failed once: FP64 LDL^T from then on
     int64_t warm_added = 0;      // pairs the warm start added to the cold support
     bool warm_active = false;    // warm-started and still inside the check window
     int device = 0;              // CUDA device the handle lives on
-    int32_t warm_restarts = 0;   // warm starts abandoned for the cold one  // the FP32-preconditioned CG failed once: FP64 LDL^T from then on
+    int32_t warm_restarts = 0;   // warm starts abandoned for the cold one
     int64_t psi_min = 0;
     double max_fill = 0.0;
     double drop = 1e-8;            // drop tolerance of the LDL^T preconditioner (adapted)
@@ -1360,6 +1360,7 @@ void ot_options_default(ot_options *o) {
     o->precond = 0;
     o->ic_tau = 0.0;
     o->tc_update = 0;
+    o->direct_cg_tol = 0.0;
     o->verbose = 0;
     o->stream = nullptr;
 }
