@@ -3,7 +3,7 @@
 Workload: one 64x64 image pair (m = n = 4096, 16.8M variables), seeded log-normal Gaussian
 random-field marginals, squared-Euclidean pixel cost, solved to relative gap 1e-6 with the mixed
 precision path (FP32 pricing scan + FP64 recheck, FP32 dense factorisation preconditioning an
-FP64 CG) and the multiscale warm start (the 32x32 binned problem solved first, its duals seeding
+FP64 CG, which stops at relative residual 1e-6) and the multiscale warm start (the 32x32 binned problem solved first, its duals seeding
 the initial support).  A step = ot_ipm_create + ot_ipm_solve of that instance (the coarse solve
 happens inside create), timed wall-clock with the device synchronised on both sides.  The cold
 mixed solve, the plain FP64 path (cold and multiscale) and the learned network's warm start are
@@ -200,10 +200,36 @@ def config_dict(args):
                         "GRF marginals, squared-Euclidean cost, rel. gap 1e-6, multiscale warm start + mixed "
                         "precision, create + solve timed",
             "k": args.k, "m": args.k * args.k, "n": args.k * args.k, "tol": 1e-6,
-            "l2": "flushed between steps (256 MiB write)", "seed": 0}
+            "l2": "flushed between steps (256 MiB write)", "seed": 0, "direct_cg_tol": 1e-6}
 
 
 # ------------------------------------------------------------------------------ GPU arm
+def pcg_at(torch, synth, k: int, seed: int, steps: int):
+    """The FP32 Jacobi PCG (one cooperative launch per refinement) and the FP64 one on the Newton
+    system of a k x k pair's iterate `steps`: microseconds per CG iteration and algorithmic bytes
+    per second (theta, index and gathered entry per pair in both passes, plus the vectors)."""
+    from paper_2206_11009_gb300 import Solver, kernel_timing
+    inst = synth.image_pair(k, seed)
+    out = {"k": k, "seed": seed, "iterate": steps}
+    with Solver(inst.a, inst.b, grid=(k, k), tol=1e-6, precision=1) as s:
+        for _ in range(steps):
+            s.step()
+        out["psi"] = int(len(s.state()[0]))
+        pk_d, _ = peaks()
+        for name, solver in (("pcg32", "mixed"), ("pcg64", "pcg64")):
+            s.newton_direction(solver, cg_tol=1e-8, max_cg=3000)
+            torch.cuda.synchronize()
+            kernel_timing(True)
+            its = s.newton_direction(solver, cg_tol=1e-8, max_cg=3000)[4]
+            torch.cuda.synchronize()
+            ms, cnt, work = kernel_timing()[name]
+            kernel_timing(False)
+            gbs = work / (ms * 1e-3) / 1e9 if ms > 0 else None
+            out[name] = {"cg_iters": its, "us_per_iter": ms * 1e3 / max(its, 1), "achieved_gbs": gbs,
+                         "frac_hbm": gbs / pk_d.get("hbm_gbs", 6800.0) if gbs else None}
+    return out
+
+
 def pricing_at(torch, synth, k: int, seed: int, reps: int = 5):
     """Pricing + selection on a k x k pair with the duals and support of its 4th IPM iteration;
     full-call throughput and the scan pass against the FP32 ALU peak (4 lane-ops per pair)."""
@@ -280,6 +306,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-big-pricing", action="store_true")
     ap.add_argument("--no-c3", action="store_true")
+    ap.add_argument("--no-pcg256", action="store_true")
     args = ap.parse_args()
     world, rank, local = dist_init()
     if args.impl == "reference":
@@ -310,7 +337,8 @@ def main():
     a_dev, b_dev = a_pin.cuda(), b_pin.cuda()      # inputs resident in HBM for the device-timed value
     # the configuration measured: mixed precision and the multiscale warm start (one coarser level
     # solved first to relative tolerance 1e-3); ot_ipm_create is inside every timed region
-    MAIN = dict(tol=1e-6, precision=1, multiscale=1, ms_tol=1e-3)
+    # the factor-preconditioned CG stops at relative residual 1e-6 (direct_cg_tol)
+    MAIN = dict(tol=1e-6, precision=1, multiscale=1, ms_tol=1e-3, direct_cg_tol=1e-6)
 
     def timed_solve(a, b, want_solution=False, **opts):
         """Wall time of create + solve (+ solution read-back), synchronised on both sides."""
@@ -346,11 +374,13 @@ def main():
         e2e_times.append(t)
         h2d = a_np.nbytes + b_np.nbytes
         d2h = I.nbytes + J.nbytes + P.nbytes + u.nbytes + v.nbytes
-    launches_per_step = (kernel_launches() - launches0) / 2.0
+    # every step runs two solves (device inputs for `value`, host buffers for `e2e`): the kernels of
+    # the `value` solves are half of those counted over the region
+    launches_per_solve = (kernel_launches() - launches0) / (2.0 * max(args.steps, 1))
     torch.cuda.synchronize()
     ktimes = kernel_timing()
     kernel_timing(False)
-    launches = int(launches_per_step * args.steps)
+    launches = int(round(launches_per_solve * args.steps))
     clk = clocks.stop(local)
     barrier(world)
     t_dev = max_over_ranks(statistics.mean(dev_times), world)
@@ -364,7 +394,7 @@ def main():
     plain = None
     if not args.no_plain:
         plain = summary(*timed_solve(a_dev, b_dev, tol=1e-6, precision=0)[:2])
-    mixed_cold = summary(*timed_solve(a_dev, b_dev, tol=1e-6, precision=1)[:2])
+    mixed_cold = summary(*timed_solve(a_dev, b_dev, tol=1e-6, precision=1, direct_cg_tol=1e-6)[:2])
     plain_ms = None if args.no_plain else summary(*timed_solve(a_dev, b_dev, tol=1e-6, precision=0, multiscale=1,
                                                               ms_tol=1e-3)[:2])
     learned = None
@@ -406,6 +436,7 @@ def main():
     gcols = pairs / (price_ms * 1e-3) / 1e9
 
     big = None if args.no_big_pricing else pricing_at(torch, synth, 256, 10000)
+    pcg256 = None if args.no_pcg256 else pcg_at(torch, synth, 256, 10000, 25)
 
     # config 3: the 128x128 pair with 5 % spikes (mixed precision, one solve)
     c3 = None
@@ -433,7 +464,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": t_dev * 1e3, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic", "config": config_dict(args),
         "e2e": {"value": t_e2e, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
-        "gpu_launches": int(launches),
+        "gpu_launches": int(launches), "gpu_launches_per_solve": int(round(launches_per_solve)),
         "e2e_steps_s": e2e_times, "value_steps_s": dev_times,
         "solve": {"status": r0.status, "iters": r0.iters, "direct_iters": r0.direct_iters, "cg_iters": r0.cg_iters,
                   "rel_gap": r0.rel_gap, "r1_l1": r0.r1_l1, "obj": r0.obj, "psi": r0.psi, "max_fill_pct": r0.max_fill},
@@ -448,6 +479,7 @@ def main():
         "pricing": {"gcols_per_s": gcols, "ms_per_call": price_ms, "pairs": pairs, "kernels": ptable,
                     "roofline_gcols_per_s": roof_gcols, "frac_full_call": gcols / roof_gcols,
                     "at_256x256": big},
+        "pcg_at_256x256": pcg256,
         "config3_128x128_spikes": c3,
         "kernels": table,
         "roofline": roof,
@@ -505,9 +537,9 @@ def kernel_table(ktimes, pk_d, src):
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel as it stands, and the
 # summary under profiles/ that gives the command; a kernel changed since then reports null.
 NCU_TRAFFIC = {
-    # one FP32 factorisation (n = 4096, all 317 launches of its graph): 1,667.3 MB read + 0.37 MB
-    # written; profiles/d32_factor_64x64.md
-    "d32_factor": 1.6677e9,
+    # one FP32 factorisation (n = 4096, all 190 kernel launches of its graph): 1,600.5 MB read +
+    # 0.24 MB written; profiles/d32_factor_64x64.md
+    "d32_factor": 1.6007e9,
 }
 
 
