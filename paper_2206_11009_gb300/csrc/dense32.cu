@@ -108,8 +108,8 @@ d32_colsum_kernel(int n, int ld, int bs, const float *__restrict__ A, float *__r
 // One CTA factors the diagonal block in micro-panels of 8 columns.  Warp 0 eliminates a
 // micro-panel with its 64 rows in registers (lane q: rows q and q+32; shuffles only): each pivot
 // is minus the sum of the column's remaining entries plus its below-block sum (np fixed-order
-// partials in csum[p * kP + l]), and the later columns of the micro-panel and their below-block
-// sums are updated as it goes.  Then all warps apply the micro-panel's rank-8 update to the rest of
+// partials in csum[p * kP + l]), kept as sums of same-sign terms by a recurrence over the
+// micro-panel's own 8 x 8 block (the warp-wide sums are taken once per micro-panel).  Then all warps apply the micro-panel's rank-8 update to the rest of
 // the block (two barriers per micro-panel instead of one per column).  Columns stay unscaled until
 // the end (l_ij = S_ij / d_j).  The inverse of the unit block is formed afterwards by 8x8 block
 // rows: X_II = L_II^-1 by warp 0, X_IJ = -X_II sum_K L_IK X_KJ by all threads.
@@ -120,8 +120,7 @@ static_assert(kTT / 32 == kP / kMp && kTT == 4 * kP, "one warp per 8x8 diagonal 
 // registers (lane q: rows q and q + 32).  prev >= 0: the micro-panel's columns first receive the
 // rank-8 update of the micro-panel starting at prev (eliminated by this warp just before), in the
 // same order as the other warps apply it to the later columns.  kFull: nc == kMp known at compile
-// time, so the whole micro-panel is one straight-line block and the shuffles of successive
-// columns overlap.
+// time, so the whole micro-panel is one straight-line block.
 template <bool kFull>
 __device__ __forceinline__ void d32_micro_panel(int lane, int k, int c0, int nc, int prev, float (*S)[kP + 1],
                                                 float *g, const float *thr, float *ids, float *D) {
@@ -163,33 +162,76 @@ __device__ __forceinline__ void d32_micro_panel(int lane, int k, int c0, int nc,
             }
         }
     }
+    // The pivots without a warp reduction on their chain.  With W_c the sum of column c's entries in
+    // the rows from c0 + 8 on (in the block, and below it through g) and B the micro-panel's own
+    // 8 x 8 lower part, eliminating column c changes, for every later column j of the micro-panel,
+    //   B[r][j] -= B[r][c] l_jc  (r > j),   W_j -= W_c l_jc,   g_j -= g_c l_jc,   l_jc = B[j][c] / d_c,
+    // and d_j = -(sum_{r > j} B[r][j] + W_j).  Every W and every B entry below the diagonal stays a
+    // sum of non-positive terms (an M-matrix's Schur complements), so the pivots keep the
+    // cancellation-free form.  The 8 initial W sums are reduced together, B is broadcast once,
+    // and the 8-step recurrence runs on scalars in every lane.
+    const bool lo_half = c0 < 32;   // the micro-panel's rows c0 .. c0 + 7 sit in one half
+    float W[kMp], B[kMp][kMp];
+#pragma unroll
+    for (int jj = 0; jj < kMp; ++jj) {
+        W[jj] = (lane >= c0 + kMp ? v0[jj] : 0.f) + (lane + 32 >= c0 + kMp ? v1[jj] : 0.f);
+#pragma unroll
+        for (int r = 0; r < kMp; ++r) B[r][jj] = 0.f;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int jj = 0; jj < kMp; ++jj) W[jj] += __shfl_xor_sync(full, W[jj], o);
+#pragma unroll
+    for (int jj = 0; jj < kMp; ++jj) {
+        W[jj] += gm[jj];
+#pragma unroll
+        for (int r = jj + 1; r < kMp; ++r) B[r][jj] = __shfl_sync(full, lo_half ? v0[jj] : v1[jj], (c0 + r) & 31);
+    }
+    float L[kMp][kMp];   // L[j][c] = l_jc of the micro-panel (j > c)
+#pragma unroll
+    for (int jj = 0; jj < kMp; ++jj)
+#pragma unroll
+        for (int c = 0; c < kMp; ++c) L[jj][c] = 0.f;
 #pragma unroll
     for (int jj = 0; jj < kMp; ++jj) {
         dv[jj] = INFINITY;
         iv[jj] = 0.f;
         if (jj < ncc) {
-            const int j = c0 + jj;
-            float sum = (lane > j ? v0[jj] : 0.f) + (lane + 32 > j ? v1[jj] : 0.f);
+            float sum = W[jj];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(full, sum, o);
-            const float d = -(sum + gm[jj]);
+            for (int r = jj + 1; r < kMp; ++r) sum += B[r][jj];
+            const float d = -sum;
             const bool inf = !(d > tl[jj]);
             const float id = inf ? 0.f : 1.f / d;
-            const float l0 = (lane > j) ? v0[jj] * id : 0.f, l1 = (lane + 32 > j) ? v1[jj] * id : 0.f;
 #pragma unroll
-            for (int jj2 = jj + 1; jj2 < kMp; ++jj2) {
-                if (jj2 < ncc) {
-                    const int r = c0 + jj2;   // the row whose column-j entry multiplies
-                    const float srj = __shfl_sync(full, r < 32 ? v0[jj] : v1[jj], r & 31);
-                    if (lane > r) v0[jj2] -= l0 * srj;
-                    if (lane + 32 > r) v1[jj2] -= l1 * srj;
-                    gm[jj2] -= (srj * id) * gm[jj];
-                }
+            for (int j2 = jj + 1; j2 < kMp; ++j2) {
+                const float l = B[j2][jj] * id;
+                L[j2][jj] = l;
+#pragma unroll
+                for (int r = j2 + 1; r < kMp; ++r) B[r][j2] -= B[r][jj] * l;
+                W[j2] -= W[jj] * l;
+                gm[j2] -= gm[jj] * l;
             }
-            v0[jj] = inf ? 0.f : v0[jj];
-            v1[jj] = inf ? 0.f : v1[jj];
             dv[jj] = inf ? INFINITY : d;
             iv[jj] = id;
+        }
+    }
+    // each lane's own rows, in the same order: S_ij -= S_ic l_jc for c < j, rows below j only
+#pragma unroll
+    for (int jj = 1; jj < kMp; ++jj) {
+        const int j = c0 + jj;
+#pragma unroll
+        for (int c = 0; c < jj; ++c) {
+            if (lane > j) v0[jj] -= v0[c] * L[jj][c];
+            if (lane + 32 > j) v1[jj] -= v1[c] * L[jj][c];
+        }
+    }
+#pragma unroll
+    for (int jj = 0; jj < kMp; ++jj) {
+        if (dv[jj] == INFINITY) {   // a grounded column: its entries no longer enter anything
+            v0[jj] = 0.f;
+            v1[jj] = 0.f;
         }
     }
 #pragma unroll
