@@ -95,23 +95,6 @@ __global__ void res_rows_kernel(int m, const int32_t *__restrict__ rp, const dou
     put_sum(l1, part, SC_R1A_L1, sh);
 }
 
-__global__ void res_cols_kernel(int n, const int32_t *__restrict__ cp, const int32_t *__restrict__ perm,
-                                const double *__restrict__ p, const double *__restrict__ b,
-                                double *__restrict__ r1b, double *part) {
-    __shared__ double sh[kT / 32];
-    double sq = 0, l1 = 0;
-    GRID_STRIDE(j, n) {
-        double acc = 0;
-        for (int k = cp[j]; k < cp[j + 1]; ++k) acc += p[perm[k]];
-        const double r = b[j] - acc;
-        r1b[j] = r;
-        sq += r * r;
-        l1 += fabs(r);
-    }
-    put_sum(sq, part, SC_R1B_SQ, sh);
-    put_sum(l1, part, SC_R1B_L1, sh);
-}
-
 __global__ void res_entries_kernel(int64_t psi, const int32_t *__restrict__ si, const int32_t *__restrict__ sj,
                                    const double *__restrict__ c, const double *__restrict__ p,
                                    const double *__restrict__ s, const double *__restrict__ u,
@@ -142,47 +125,6 @@ __global__ void theta_kernel(int64_t psi, const double *__restrict__ p, const do
         const double t = p[e] / s[e];
         th[e] = t;
         th32[e] = (float)t;
-    }
-}
-
-// M_i = sum_j theta_ij; excl_ij = sum of the OTHER entries of row i (prefix + suffix, never a
-// subtraction, so a dominant theta does not cancel: S_jj = sum_i theta_ij excl_ij / M_i).
-__global__ void theta_rows_kernel(int m, const int32_t *__restrict__ rp, const double *__restrict__ th,
-                                  double *__restrict__ excl, double *__restrict__ M, double *__restrict__ Minv,
-                                  float *__restrict__ Minv32) {
-    GRID_STRIDE(i, m) {
-        const int lo = rp[i], hi = rp[i + 1];
-        double pre = 0;
-        for (int e = lo; e < hi; ++e) { excl[e] = pre; pre += th[e]; }
-        double suf = 0;
-        for (int e = hi - 1; e >= lo; --e) { excl[e] += suf; suf += th[e]; }
-        M[i] = pre;
-        const double mi = pre > 0 ? 1.0 / pre : 0.0;
-        Minv[i] = mi;
-        Minv32[i] = (float)mi;
-    }
-}
-
-__global__ void theta_cols_kernel(int n, const int32_t *__restrict__ cp, const int32_t *__restrict__ perm,
-                                  const int32_t *__restrict__ crow, const double *__restrict__ th,
-                                  const double *__restrict__ excl, const double *__restrict__ Minv,
-                                  double *__restrict__ thc, float *__restrict__ thc32, double *__restrict__ N,
-                                  double *__restrict__ Dinv, float *__restrict__ Dinv32, double *__restrict__ Sdiag) {
-    GRID_STRIDE(j, n) {
-        double nsum = 0, d = 0;
-        for (int k = cp[j]; k < cp[j + 1]; ++k) {
-            const int e = perm[k];
-            const double t = th[e];
-            thc[k] = t;
-            thc32[k] = (float)t;
-            nsum += t;
-            d += t * excl[e] * Minv[crow[k]];
-        }
-        N[j] = nsum;
-        Sdiag[j] = d;
-        const double di = d > 0 ? 1.0 / d : 0.0;  // columns with D = 0 are private stars: masked
-        Dinv[j] = di;
-        Dinv32[j] = (float)di;
     }
 }
 
@@ -240,17 +182,6 @@ __global__ void g_kernel(int64_t psi, const double *__restrict__ th, const doubl
         g[e] = th[e] * (a - b);
     }
 }
-
-__global__ void beta1_kernel(int m, const int32_t *__restrict__ rp, const double *__restrict__ g,
-                             const double *__restrict__ r1a, double *__restrict__ beta1) {
-    GRID_STRIDE(i, m) {
-        double acc = r1a ? r1a[i] : 0.0;
-        for (int e = rp[i]; e < rp[i + 1]; ++e) acc += g[e];
-        beta1[i] = acc;
-    }
-}
-
-// beta2_j = r1b_j + sum_i g_ij ; rhs_j = beta2_j - sum_i theta_ij beta1_i / M_i
 
 __global__ void sum_kernel(int n, const double *__restrict__ x, double *part, int slot) {
     __shared__ double sh[kT / 32];
@@ -357,6 +288,151 @@ __global__ void du_group_kernel(int m, const int32_t *__restrict__ rp, const int
             for (int e = rp[i] + lg; e < rp[i + 1]; e += G) acc += th[e] * dv[sj[e]];
         acc = group_sum(acc, G);
         if (lg == 0 && i < m) du[i] = Minv[i] * (beta1[i] - acc);
+    }
+}
+
+// Lane-group forms (G lanes per row or column, warp-uniform trip counts; groups past the end take
+// part in the shuffles with nothing) of the per-row / per-column loops of the residuals, of Theta's
+// row and column sums and of beta1: one thread per row or column walked long rows serially.
+
+// r1b_j = b_j - sum_i p_ij over the column, with the block partials of |r1b|^2 and |r1b|_1
+template <int G>
+__global__ void res_cols_group_kernel(int n, const int32_t *__restrict__ cp, const int32_t *__restrict__ perm,
+                                      const double *__restrict__ p, const double *__restrict__ b,
+                                      double *__restrict__ r1b, double *part) {
+    __shared__ double sh[kT / 32];
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int lg = threadIdx.x & (G - 1);
+    const int64_t grp = tid / G, ngrp = stride / G, wgrp0 = (tid & ~(int64_t)31) / G;
+    double sq = 0, l1 = 0;
+    for (int64_t j0 = wgrp0; j0 < n; j0 += ngrp) {
+        const int64_t j = j0 + (grp - wgrp0);
+        double acc = 0.0;
+        if (j < n)
+            for (int k = cp[j] + lg; k < cp[j + 1]; k += G) acc += p[perm[k]];
+        acc = group_sum(acc, G);
+        if (lg == 0 && j < n) {
+            const double r = b[j] - acc;
+            r1b[j] = r;
+            sq += r * r;
+            l1 += fabs(r);
+        }
+    }
+    put_sum(sq, part, SC_R1B_SQ, sh);
+    put_sum(l1, part, SC_R1B_L1, sh);
+}
+
+// M_i = sum_j theta_ij, Minv; excl_ij = the sum of the OTHER entries of row i (a forward exclusive
+// scan plus a backward one, never a subtraction, so a dominant theta does not cancel:
+// S_jj = sum_i theta_ij excl_ij / M_i)
+template <int G>
+__global__ void theta_rows_group_kernel(int m, const int32_t *__restrict__ rp, const double *__restrict__ th,
+                                        double *__restrict__ excl, double *__restrict__ M,
+                                        double *__restrict__ Minv, float *__restrict__ Minv32) {
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int lg = threadIdx.x & (G - 1);
+    const int64_t grp = tid / G, ngrp = stride / G, wgrp0 = (tid & ~(int64_t)31) / G;
+    const unsigned full = 0xffffffffu;
+    for (int64_t i0 = wgrp0; i0 < m; i0 += ngrp) {
+        const int64_t i = i0 + (grp - wgrp0);
+        const int lo = i < m ? rp[i] : 0, hi = i < m ? rp[i + 1] : 0;
+        // trips of the longest row among the warp's groups (every lane takes part in the shuffles)
+        int trips = (hi - lo + G - 1) / G;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) trips = max(trips, __shfl_xor_sync(full, trips, o));
+        double carry = 0.0;
+        for (int c = 0; c < trips; ++c) {
+            const int e = lo + c * G + lg;
+            const double t = e < hi ? th[e] : 0.0;
+            double x = t;
+#pragma unroll
+            for (int o = 1; o < G; o <<= 1) {
+                const double y = __shfl_up_sync(full, x, o, G);
+                if (lg >= o) x += y;
+            }
+            double ex = __shfl_up_sync(full, x, 1, G);
+            ex = lg == 0 ? 0.0 : ex;
+            if (e < hi) excl[e] = carry + ex;
+            carry += __shfl_sync(full, x, G - 1, G);
+        }
+        __syncwarp();
+        double suf = 0.0;
+        for (int c = trips - 1; c >= 0; --c) {
+            const int e = lo + c * G + lg;
+            const double t = e < hi ? th[e] : 0.0;
+            double x = t;
+#pragma unroll
+            for (int o = 1; o < G; o <<= 1) {
+                const double y = __shfl_down_sync(full, x, o, G);
+                if (lg + o < G) x += y;
+            }
+            double ex = __shfl_down_sync(full, x, 1, G);
+            ex = lg == G - 1 ? 0.0 : ex;
+            if (e < hi) excl[e] += suf + ex;
+            suf += __shfl_sync(full, x, 0, G);
+        }
+        if (lg == 0 && i < m) {
+            M[i] = carry;
+            const double mi = carry > 0 ? 1.0 / carry : 0.0;
+            Minv[i] = mi;
+            Minv32[i] = (float)mi;
+        }
+    }
+}
+
+// theta in column order, N_j = the column's sum, the Jacobi diagonal of S_M
+template <int G>
+__global__ void theta_cols_group_kernel(int n, const int32_t *__restrict__ cp, const int32_t *__restrict__ perm,
+                                        const int32_t *__restrict__ crow, const double *__restrict__ th,
+                                        const double *__restrict__ excl, const double *__restrict__ Minv,
+                                        double *__restrict__ thc, float *__restrict__ thc32, double *__restrict__ N,
+                                        double *__restrict__ Dinv, float *__restrict__ Dinv32,
+                                        double *__restrict__ Sdiag) {
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int lg = threadIdx.x & (G - 1);
+    const int64_t grp = tid / G, ngrp = stride / G, wgrp0 = (tid & ~(int64_t)31) / G;
+    for (int64_t j0 = wgrp0; j0 < n; j0 += ngrp) {
+        const int64_t j = j0 + (grp - wgrp0);
+        double nsum = 0, d = 0;
+        if (j < n)
+            for (int k = cp[j] + lg; k < cp[j + 1]; k += G) {
+                const int e = perm[k];
+                const double t = th[e];
+                thc[k] = t;
+                thc32[k] = (float)t;
+                nsum += t;
+                d += t * excl[e] * Minv[crow[k]];
+            }
+        nsum = group_sum(nsum, G);
+        d = group_sum(d, G);
+        if (lg == 0 && j < n) {
+            N[j] = nsum;
+            Sdiag[j] = d;
+            const double di = d > 0 ? 1.0 / d : 0.0;  // columns with D = 0 are private stars: masked
+            Dinv[j] = di;
+            Dinv32[j] = (float)di;
+        }
+    }
+}
+
+// beta1_i = r1a_i + sum_j g_ij over the row
+template <int G>
+__global__ void beta1_group_kernel(int m, const int32_t *__restrict__ rp, const double *__restrict__ g,
+                                   const double *__restrict__ r1a, double *__restrict__ beta1) {
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int lg = threadIdx.x & (G - 1);
+    const int64_t grp = tid / G, ngrp = stride / G, wgrp0 = (tid & ~(int64_t)31) / G;
+    for (int64_t i0 = wgrp0; i0 < m; i0 += ngrp) {
+        const int64_t i = i0 + (grp - wgrp0);
+        double acc = 0.0;
+        if (i < m)
+            for (int e = rp[i] + lg; e < rp[i + 1]; e += G) acc += g[e];
+        acc = group_sum(acc, G);
+        if (lg == 0 && i < m) beta1[i] = acc + (r1a ? r1a[i] : 0.0);
     }
 }
 
@@ -1421,10 +1497,13 @@ Error support_costs(Newton &W, const CostDev &cd, const Support &S, cudaStream_t
 
 Error residuals(Newton &W, const Support &S, const double *a_s, const double *b_s, const double *u,
                 const double *v, cudaStream_t st) {
-    const unsigned gm = grid_of(W.m, W.num_sms), gn = grid_of(W.n, W.num_sms), ge = grid_of(S.psi, W.num_sms);
+    const unsigned gm = grid_of(W.m, W.num_sms), ge = grid_of(S.psi, W.num_sms);
+    // 8 lanes per column; at most kMaxPartBlocks blocks (one partial slot each)
+    const unsigned gn = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div((int64_t)W.n * 8, kT),
+                                                                          std::min(8 * W.num_sms, kMaxPartBlocks)));
     res_rows_kernel<<<gm, kT, 0, st>>>(W.m, S.row_ptr, S.p, a_s, W.r1a, W.part);
     OT_LAUNCHED();
-    res_cols_kernel<<<gn, kT, 0, st>>>(W.n, S.col_ptr, S.col_perm, S.p, b_s, W.r1b, W.part);
+    res_cols_group_kernel<8><<<gn, kT, 0, st>>>(W.n, S.col_ptr, S.col_perm, S.p, b_s, W.r1b, W.part);
     OT_LAUNCHED();
     res_entries_kernel<<<ge, kT, 0, st>>>(S.psi, S.i, S.j, W.c, S.p, S.s, u, v, W.r2, W.part);
     OT_LAUNCHED();
@@ -1442,11 +1521,18 @@ Error schur_setup(Newton &W, const Support &S, cudaStream_t st) {
     const unsigned gm = grid_of(W.m, W.num_sms), gn = grid_of(W.n, W.num_sms), ge = grid_of(S.psi, W.num_sms);
     theta_kernel<<<ge, kT, 0, st>>>(S.psi, S.p, S.s, W.theta, W.theta32);
     OT_LAUNCHED();
-    theta_rows_kernel<<<gm, kT, 0, st>>>(W.m, S.row_ptr, W.theta, W.excl, W.M, W.Minv, W.Minv32);
-    OT_LAUNCHED();
-    theta_cols_kernel<<<gn, kT, 0, st>>>(W.n, S.col_ptr, S.col_perm, S.col_row, W.theta, W.excl, W.Minv,
-                                         W.theta_col, W.theta32_col, W.N, W.Dinv, W.Dinv32, W.Sdiag);
-    OT_LAUNCHED();
+    {
+        const unsigned g8m = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div((int64_t)W.m * 8, kT),
+                                                                              8LL * W.num_sms));
+        const unsigned g8n = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div((int64_t)W.n * 8, kT),
+                                                                              8LL * W.num_sms));
+        theta_rows_group_kernel<8><<<g8m, kT, 0, st>>>(W.m, S.row_ptr, W.theta, W.excl, W.M, W.Minv, W.Minv32);
+        OT_LAUNCHED();
+        theta_cols_group_kernel<8><<<g8n, kT, 0, st>>>(W.n, S.col_ptr, S.col_perm, S.col_row, W.theta, W.excl,
+                                                        W.Minv, W.theta_col, W.theta32_col, W.N, W.Dinv, W.Dinv32,
+                                                        W.Sdiag);
+        OT_LAUNCHED();
+    }
     const int nn = W.m + W.n;
     const unsigned gnn = grid_of(nn, W.num_sms);
     uf_init_kernel<<<gnn, kT, 0, st>>>(nn, W.parent);
@@ -1532,8 +1618,12 @@ Error newton_solve(Newton &W, const Support &S, const Rhs &R, double cg_tol, int
     const unsigned gm = grid_of(W.m, W.num_sms), gn = grid_of(W.n, W.num_sms), ge = grid_of(S.psi, W.num_sms);
     g_kernel<<<ge, kT, 0, st>>>(S.psi, W.theta, S.p, R.r2, R.r3, W.g);
     OT_LAUNCHED();
-    beta1_kernel<<<gm, kT, 0, st>>>(W.m, S.row_ptr, W.g, R.r1a, W.beta1);
-    OT_LAUNCHED();
+    {
+        const unsigned g8m = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div((int64_t)W.m * 8, kT),
+                                                                              8LL * W.num_sms));
+        beta1_group_kernel<8><<<g8m, kT, 0, st>>>(W.m, S.row_ptr, W.g, R.r1a, W.beta1);
+        OT_LAUNCHED();
+    }
     {
         const unsigned gg = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div((int64_t)W.n * 8, kT),
                                                                              8LL * W.num_sms));
