@@ -2,6 +2,8 @@
 // arrays (pricing candidates, support entries: 1e3 .. 1e7 items).
 #include "primitives.cuh"
 
+#include <mutex>
+
 namespace ot {
 
 Arena *&active_arena() {
@@ -161,11 +163,125 @@ radix_scatter_kernel(const uint64_t *__restrict__ kin, const uint32_t *__restric
     }
 }
 
+// Up to kSmallN items: the whole sort in one CTA, both buffers and the per-warp digit counters in
+// shared memory, one launch for all passes.  Warp w owns items [w * 256, w * 256 + 256), taken 32
+// at a time in index order; per pass a counting sweep (warp-private digit counts: the lane that
+// leads each group of equal digits adds the group's size), the exclusive offsets of (digit, warp)
+// in digit-major order, and a scatter sweep in the same order (stable).
+constexpr int kSmallN = 8192;
+constexpr int kSmallThreads = 1024;
+constexpr int kSmallWarps = kSmallThreads / 32;
+constexpr int kSmallSteps = kSmallN / kSmallThreads;   // 32-item steps per warp
+constexpr int kSmallSmem = kSmallN * (8 + 8 + 4 + 4) + kSmallWarps * 256 * 4 + 256 * 4;
+
+__global__ void __launch_bounds__(kSmallThreads, 1)
+radix_small_kernel(uint64_t *__restrict__ keys, uint32_t *__restrict__ vals, int n, int passes) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    uint64_t *K0 = (uint64_t *)sm, *K1 = K0 + kSmallN;
+    uint32_t *V0 = (uint32_t *)(K1 + kSmallN), *V1 = V0 + kSmallN;
+    uint32_t (*cnt)[256] = (uint32_t (*)[256])(V1 + kSmallN);
+    uint32_t *dtot = (uint32_t *)(cnt + kSmallWarps);
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int i = threadIdx.x; i < n; i += kSmallThreads) {
+        K0[i] = keys[i];
+        V0[i] = vals[i];
+    }
+    __syncthreads();
+    for (int p = 0; p < passes; ++p) {
+        const int shift = 8 * p;
+        for (int d = lane; d < 256; d += 32) cnt[w][d] = 0u;
+        __syncwarp();
+        for (int k = 0; k < kSmallSteps; ++k) {
+            const int idx = w * (kSmallSteps * 32) + k * 32 + lane;
+            const bool valid = idx < n;
+            const unsigned d = valid ? (unsigned)(K0[idx] >> shift) & 255u : 256u;
+            const unsigned peers = __match_any_sync(full, d);
+            if (valid && (peers & lt) == 0u) cnt[w][d] += (uint32_t)__popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        if (threadIdx.x < 256) {
+            const int d = threadIdx.x;
+            uint32_t run = 0;
+            for (int ww = 0; ww < kSmallWarps; ++ww) {
+                const uint32_t c = cnt[ww][d];
+                cnt[ww][d] = run;
+                run += c;
+            }
+            dtot[d] = run;
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {   // exclusive scan of the 256 digit totals, 8 per lane
+            uint32_t v[8], t = 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                v[q] = dtot[lane * 8 + q];
+                t += v[q];
+            }
+            uint32_t x = t;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(full, x, o);
+                if (lane >= o) x += y;
+            }
+            uint32_t pre = x - t;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                dtot[lane * 8 + q] = pre;
+                pre += v[q];
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < 256) {
+            const uint32_t b = dtot[threadIdx.x];
+            for (int ww = 0; ww < kSmallWarps; ++ww) cnt[ww][threadIdx.x] += b;
+        }
+        __syncthreads();
+        for (int k = 0; k < kSmallSteps; ++k) {
+            const int idx = w * (kSmallSteps * 32) + k * 32 + lane;
+            const bool valid = idx < n;
+            const uint64_t key = valid ? K0[idx] : 0ull;
+            const uint32_t val = valid ? V0[idx] : 0u;
+            const unsigned d = valid ? (unsigned)(key >> shift) & 255u : 256u;
+            const unsigned peers = __match_any_sync(full, d);
+            const uint32_t rank = (uint32_t)__popc(peers & lt);
+            const uint32_t base = valid ? cnt[w][d] : 0u;
+            __syncwarp();
+            if (valid) {
+                K1[base + rank] = key;
+                V1[base + rank] = val;
+                if (rank == 0u) cnt[w][d] = base + (uint32_t)__popc(peers);
+            }
+            __syncwarp();
+        }
+        __syncthreads();
+        uint64_t *tk = K0; K0 = K1; K1 = tk;
+        uint32_t *tv = V0; V0 = V1; V1 = tv;
+    }
+    for (int i = threadIdx.x; i < n; i += kSmallThreads) {
+        keys[i] = K0[i];
+        vals[i] = V0[i];
+    }
+}
+
 }  // namespace
 
 Error radix_sort_pairs(uint64_t *keys, uint32_t *vals, int64_t n, int key_bits, cudaStream_t st) {
     if (n <= 1 || key_bits <= 0) return ok();
     if (n > 0x7fffffffLL) return fail(OT_ERR_ARG, "radix_sort_pairs: too many items");
+    if (n <= kSmallN) {
+        static std::once_flag once;
+        static cudaError_t attr = cudaSuccess;
+        std::call_once(once, [] {
+            attr = cudaFuncSetAttribute(radix_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmallSmem);
+        });
+        if (attr != cudaSuccess) return fail(OT_ERR_CUDA, cudaGetErrorString(attr));
+        radix_small_kernel<<<1, kSmallThreads, kSmallSmem, st>>>(keys, vals, (int)n, (key_bits + 7) / 8);
+        OT_LAUNCHED();
+        return ok();
+    }
     const int passes = (key_bits + 7) / 8;
     const int nb = (int)ceil_div(n, kSortTile);
     DevTemp<uint64_t> k2;
