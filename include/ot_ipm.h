@@ -380,10 +380,11 @@ int64_t ot_kernel_launches(void);
  * gathered vector entry per support pair in both passes, plus the row/column vectors), FP64 flops
  * for the LDL^T numeric factorisation (n^3/3 when dense), bytes for the LDL^T solves (L read
  * twice), FP32 flops for the FP32 dense factorisation with its inverse factor (n^3/3 + n^3/3) and
- * bytes for its application (the triangle of L^-1 read twice), and bytes for the operator of the
- * FP64 CG that refines a factor-preconditioned solve (per iteration: theta, index and gathered
- * vector entry per support pair in the row and the column pass, the per-row and per-column
- * vectors, and the step's update of x and r):
+ * bytes for its application (the triangle of L^-1 read twice), and bytes for the FP64 CG that
+ * refines a factor-preconditioned solve (per iteration: theta, index and gathered vector entry
+ * per support pair in the row and the column pass, the per-row and per-column vectors, the
+ * step's update of x and r, and -- with the FP32 dense factor, whose CG runs as one persistent
+ * launch that includes the factor's application -- the triangle of L^-1 read twice):
  *   0 pricing scan (histogram pass)   1 pricing scan (gather pass)   2 FP64 recheck
  *   3 PCG FP64 (persistent kernel)    4 PCG FP32                     5 LDL^T numeric (FP64)
  *   6 LDL^T solve (FP64)              7 FP32 dense LDL^T + L^-1      8 FP32 dense apply

@@ -1268,6 +1268,276 @@ static Error solve_mixed(Newton &W, const Support &S, double tol, int max_cg, do
 // few iterations recover FP64 accuracy (iterative refinement in conjugate-gradient form).
 constexpr int kD32MaxCg = 60;
 
+// ------------------------------------------------------------------------ persistent refinement CG
+// The FP64 CG preconditioned by the FP32 dense factor (z = L^-T D^+ L^-1 r through X = L^-1), all
+// iterations in one cooperative launch: per iteration the row pass, the column pass with p.q, the
+// step with r.r, the convergence test, the three stages of the preconditioner (partial products of
+// X r by 512 x 64 tiles, their row sums scaled by D^+, the column products of X^T), r.z and the new
+// direction, seven grid barriers.  Every block sums the partials of a dot product in the same fixed
+// order, so all take the same decisions.  Same arithmetic as the launch-per-stage loop.
+constexpr int kCgT = 512;
+constexpr int kCgRows = 512, kCgCols = 64;   // preconditioner tile: 128 row quads x 4 column groups
+
+struct D32CgArgs {
+    int m, n, ld, ncb;
+    const int32_t *rp, *sj, *cp, *crow;
+    const double *th, *thc, *Minv, *rhs;
+    const float *X, *D;
+    float *part, *w32;
+    double *x, *r, *z, *p, *q, *w64;
+    double *red;          // 3 slots x gridDim partial sums
+    unsigned *bar;
+    int *err;
+    double target2;       // stop when r.r <= target2 * b.b
+    int maxit;
+    double *scal;         // SC_PCG_ITERS, SC_PCG_RELRES
+};
+
+// part[cb ld + i] = sum over the tile's columns j <= i of X_ij r_j, for the lower-triangle tiles
+__device__ __forceinline__ void cg_fwd(const D32CgArgs &A, const double *__restrict__ r, float *rs, float4 *red4) {
+    const int n = A.n, ld = A.ld, ncb = A.ncb;
+    const int per = kCgRows / kCgCols;
+    const int nrb = (n + kCgRows - 1) / kCgRows;
+    int tiles = 0;
+    for (int rb = 0; rb < nrb; ++rb) tiles += min(ncb, (rb + 1) * per);
+    const int rq = threadIdx.x & (kCgRows / 4 - 1), cgp = threadIdx.x / (kCgRows / 4);
+    for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+        int idx = t, rb = 0;
+        while (idx >= min(ncb, (rb + 1) * per)) { idx -= min(ncb, (rb + 1) * per); ++rb; }
+        const int cb = idx, c0 = cb * kCgCols, i = rb * kCgRows + rq * 4;
+        if (threadIdx.x < kCgCols) rs[threadIdx.x] = c0 + (int)threadIdx.x < n ? (float)r[c0 + threadIdx.x] : 0.f;
+        __syncthreads();
+        const bool live = i < n && i + 3 >= c0;
+        const int jn = min(kCgCols, n - c0);
+        const int jlo = cgp * (kCgCols / 4), jhi = min(jlo + kCgCols / 4, jn);
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (live) {
+            const float *col = A.X + (size_t)c0 * ld + i;
+            for (int jj = jlo; jj < jhi; ++jj) {
+                const int j = c0 + jj;
+                const float4 v = *(const float4 *)(col + (size_t)jj * ld);
+                const float rj = rs[jj];
+                if (j <= i) acc.x += v.x * rj;
+                if (j <= i + 1) acc.y += v.y * rj;
+                if (j <= i + 2) acc.z += v.z * rj;
+                if (j <= i + 3) acc.w += v.w * rj;
+            }
+        }
+        if (cgp > 0) red4[(cgp - 1) * (kCgRows / 4) + rq] = acc;
+        __syncthreads();
+        if (cgp == 0 && live) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const float4 o = red4[q * (kCgRows / 4) + rq];
+                acc.x += o.x; acc.y += o.y; acc.z += o.z; acc.w += o.w;
+            }
+            *(float4 *)(A.part + (size_t)cb * ld + i) = acc;
+        }
+        __syncthreads();
+    }
+}
+
+// w32_i = D_i^+ sum_cb part[cb ld + i]
+__device__ __forceinline__ void cg_mid(const D32CgArgs &A) {
+    GRID_STRIDE(i, A.n) {
+        const int last = (int)i / kCgCols;
+        float y = 0.f;
+        for (int cb = 0; cb <= last; ++cb) y += A.part[(size_t)cb * A.ld + i];
+        const float d = A.D[i];
+        A.w32[i] = isinf(d) ? 0.f : y / d;
+    }
+}
+
+// z_j = sum_{i >= j} X_ij w32_i (one warp per column); returns this thread's part of r.z
+__device__ __forceinline__ double cg_bwd(const D32CgArgs &A, const double *__restrict__ r) {
+    const int n = A.n, lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    double rz = 0.0;
+    for (int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < n; j += warps) {
+        const float *col = A.X + (size_t)j * A.ld;
+        float acc = 0.f;
+        const int i0 = (int)j & ~3;
+        for (int i = i0 + lane * 4; i < n; i += 128) {
+            const float4 v = *(const float4 *)(col + i);
+            if (i >= j && i + 3 < n) {
+                acc += v.x * A.w32[i] + v.y * A.w32[i + 1] + v.z * A.w32[i + 2] + v.w * A.w32[i + 3];
+            } else {
+                if (i >= j && i < n) acc += v.x * A.w32[i];
+                if (i + 1 >= j && i + 1 < n) acc += v.y * A.w32[i + 1];
+                if (i + 2 >= j && i + 2 < n) acc += v.z * A.w32[i + 2];
+                if (i + 3 >= j && i + 3 < n) acc += v.w * A.w32[i + 3];
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) {
+            const double zj = (double)acc;
+            A.z[j] = zj;
+            rz += r[j] * zj;
+        }
+    }
+    return rz;
+}
+
+template <int LG>
+__global__ void __launch_bounds__(kCgT) d32_cg_kernel(D32CgArgs A) {
+    __shared__ double sh[kCgT / 32];
+    __shared__ double s_val[3];
+    __shared__ float rs[kCgCols];
+    __shared__ float4 red4[3 * (kCgRows / 4)];
+    const unsigned G = gridDim.x;
+    const int n = A.n, m = A.m;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)G * blockDim.x;
+    const int lg = threadIdx.x & (LG - 1);
+    const int64_t grp = tid / LG, ngrp = stride / LG, wgrp0 = (tid & ~(int64_t)31) / LG;
+    double *P0 = A.red, *P1 = A.red + G, *P2 = A.red + 2 * G;
+    // x = 0, r = rhs, z = M^-1 r, p = z
+    double rr = 0.0;
+    for (int64_t j = tid; j < n; j += stride) {
+        const double bj = A.rhs[j];
+        A.x[j] = 0.0;
+        A.r[j] = bj;
+        rr += bj * bj;
+    }
+    if (!grid_barrier(A.bar, G, A.err)) return;
+    cg_fwd(A, A.r, rs, red4);
+    if (!grid_barrier(A.bar, G, A.err)) return;
+    cg_mid(A);
+    if (!grid_barrier(A.bar, G, A.err)) return;
+    double rz = cg_bwd(A, A.r);
+    {
+        const double s1 = block_sum(rz, sh), s2 = block_sum(rr, sh);
+        if (threadIdx.x == 0) { P1[blockIdx.x] = s1; P2[blockIdx.x] = s2; }
+    }
+    if (!grid_barrier(A.bar, G, A.err)) return;
+    for (int64_t j = tid; j < n; j += stride) A.p[j] = A.z[j];
+    sum_partials(A.red + G, G, 2, s_val + 1);
+    rz = s_val[1];
+    const double bb = s_val[2];
+    rr = bb;
+    // once converged, one more iteration refines x (as the launch-per-stage loop, which runs one
+    // iteration ahead of its test, does); the count and the residual reported are those of the test
+    int it = 0;
+    bool extra = false;
+    double rr_test = rr;
+    if (bb > 0.0 && rz > 0.0 && A.maxit > 0) {
+        for (;;) {
+            // the new direction p must be complete before the row pass gathers it
+            if (!grid_barrier(A.bar, G, A.err)) return;
+            for (int64_t i0 = wgrp0; i0 < m; i0 += ngrp) {
+                const int64_t i = i0 + (grp - wgrp0);
+                double acc = 0.0;
+                if (i < m)
+                    for (int e = A.rp[i] + lg; e < A.rp[i + 1]; e += LG) acc += A.th[e] * A.p[A.sj[e]];
+                acc = group_sum(acc, LG);
+                if (lg == 0 && i < m) A.w64[i] = A.Minv[i] * acc;
+            }
+            if (!grid_barrier(A.bar, G, A.err)) return;
+            double pq = 0.0;
+            for (int64_t j0 = wgrp0; j0 < n; j0 += ngrp) {
+                const int64_t j = j0 + (grp - wgrp0);
+                double acc = 0.0, pj = 0.0;
+                if (j < n) {
+                    pj = A.p[j];
+                    for (int k = A.cp[j] + lg; k < A.cp[j + 1]; k += LG) acc += A.thc[k] * (pj - A.w64[A.crow[k]]);
+                }
+                acc = group_sum(acc, LG);
+                if (lg == 0 && j < n) {
+                    A.q[j] = acc;
+                    pq += pj * acc;
+                }
+            }
+            {
+                const double s0 = block_sum(pq, sh);
+                if (threadIdx.x == 0) P0[blockIdx.x] = s0;
+            }
+            if (!grid_barrier(A.bar, G, A.err)) return;
+            sum_partials(A.red, G, 1, s_val);
+            pq = s_val[0];
+            if (!(pq > 0.0)) break;   // breakdown: the step would be a no-op
+            const double alpha = rz > 0.0 ? rz / pq : 0.0;
+            double rrn = 0.0;
+            for (int64_t j = tid; j < n; j += stride) {
+                A.x[j] += alpha * A.p[j];
+                const double rj = A.r[j] - alpha * A.q[j];
+                A.r[j] = rj;
+                rrn += rj * rj;
+            }
+            {
+                const double s2 = block_sum(rrn, sh);
+                if (threadIdx.x == 0) P2[blockIdx.x] = s2;
+            }
+            if (!grid_barrier(A.bar, G, A.err)) return;
+            sum_partials(A.red + 2 * G, G, 1, s_val + 2);
+            rr = s_val[2];
+            if (extra) break;
+            ++it;
+            rr_test = rr;
+            if (it >= A.maxit) break;
+            if (rr <= A.target2 * bb) extra = true;
+            cg_fwd(A, A.r, rs, red4);
+            if (!grid_barrier(A.bar, G, A.err)) return;
+            cg_mid(A);
+            if (!grid_barrier(A.bar, G, A.err)) return;
+            double rzn = cg_bwd(A, A.r);
+            {
+                const double s1 = block_sum(rzn, sh);
+                if (threadIdx.x == 0) P1[blockIdx.x] = s1;
+            }
+            if (!grid_barrier(A.bar, G, A.err)) return;
+            sum_partials(A.red + G, G, 1, s_val + 1);
+            rzn = s_val[1];
+            const double beta = (rz > 0.0 && rzn > 0.0) ? rzn / rz : 0.0;
+            for (int64_t j = tid; j < n; j += stride) A.p[j] = A.z[j] + beta * A.p[j];
+            rz = rzn;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        A.scal[SC_PCG_ITERS] = (double)it;
+        A.scal[SC_PCG_RELRES] = bb > 0.0 ? sqrt(rr_test / bb) : 0.0;
+    }
+}
+
+
+// the persistent form of solve_direct's loop for the FP32 dense preconditioner
+static Error solve_d32_persistent(Newton &W, const Support &S, double target, int cap, double *dv, SolveStats *ss,
+                                  cudaStream_t st) {
+    Dense32 &F = *W.d32;
+    const double avg = (double)S.psi / (double)std::max(1, std::min(W.m, W.n));
+    const int LG = avg >= 12 ? 16 : (avg >= 6 ? 8 : 4);
+    const void *fn = LG == 16 ? (const void *)d32_cg_kernel<16>
+                   : (LG == 8 ? (const void *)d32_cg_kernel<8> : (const void *)d32_cg_kernel<4>);
+    int per_sm = 0;
+    OT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kCgT, 0));
+    const int maxg = std::max(1, per_sm) * W.num_sms;
+    const int64_t want = std::max<int64_t>(ceil_div((int64_t)std::max(W.m, W.n) * LG, kCgT),
+                                           ceil_div((int64_t)W.n, kCgT / 32));
+    const int G = (int)std::max<int64_t>(1, std::min<int64_t>(want, std::min(maxg, kMaxPartBlocks / 3)));
+    OT_CUDA(cudaMemsetAsync(W.bar, 0, 2 * sizeof(unsigned), st));
+    OT_CUDA(cudaMemsetAsync(W.err, 0, sizeof(int), st));
+    D32CgArgs A{W.m, W.n, F.ld, (int)ceil_div(W.n, kCgCols), S.row_ptr, S.j, S.col_ptr, S.col_row, W.theta,
+                W.theta_col, W.Minv, W.rhs, F.X, F.D, F.part, F.w, dv, W.r64, W.z64, W.p64, W.q64, W.w64, W.part,
+                W.bar, W.err, target * target, cap, W.scal};
+    void *args[] = {&A};
+    ktimer_begin(KT_DCG, st);
+    OT_CUDA(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kCgT), args, 0, st));
+    OT_LAUNCHED();
+    ktimer_end(KT_DCG, st);
+    double hs[SC_COUNT];
+    OT_TRY(read_scalars(W, hs, st));
+    int errv = 0;
+    OT_CUDA(cudaMemcpy(&errv, W.err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (errv) return fail(OT_ERR_TIMEOUT, "refinement CG: grid barrier wait limit reached");
+    ss->cg_iters = (int)hs[SC_PCG_ITERS];
+    ss->direct = 0;
+    ss->relres = hs[SC_PCG_RELRES];
+    // per iteration: the operator's bytes (as the stage-per-launch form) plus the triangle of L^-1 twice
+    ktimer_add_work(KT_DCG, ss->cg_iters * (40.0 * (double)S.psi + 20.0 * (double)W.m + 68.0 * (double)W.n +
+                                            4.0 * (double)W.n * (double)W.n));
+    return ok();
+}
+
 static Error solve_direct(Newton &W, const Support &S, double tol, int max_cg, double *dv, SolveStats *ss,
                           cudaStream_t st) {
     const unsigned gm = grid_of(W.m, W.num_sms), gn = grid_of(W.n, W.num_sms);
@@ -1278,6 +1548,7 @@ static Error solve_direct(Newton &W, const Support &S, double tol, int max_cg, d
     // factor is the iterative phase's preconditioner and stops at the PCG tolerance
     const double target = ic_only ? tol : (W.direct_cg_tol > 0 ? std::max(W.direct_cg_tol, std::min(tol, 1e-10))
                                                                : std::min(tol, 1e-10));
+    if (W.d32 && !C && !W.tree) return solve_d32_persistent(W, S, target, std::min(max_cg, kD32MaxCg), dv, ss, st);
     double *x = W.x64, *r = W.r64, *z = W.z64, *p = W.p64, *q = W.q64;
     double hs[SC_COUNT];
     OT_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * W.n, st));
