@@ -230,6 +230,91 @@ __global__ void bv_jump_kernel(int V, const int32_t *__restrict__ parent, int32_
     }
 }
 
+// All Boruvka rounds in one cooperative launch: the same five stages per round as the kernels
+// above, separated by grid barriers instead of launches, and the round / jump-pass decisions taken
+// by every block from flags that a barrier has published (one fresh flag word per round and per
+// jump pass, zeroed before the launch, so no block can see a flag reset under it).
+struct BvArgs {
+    int64_t psi;
+    int m, V, max_passes;             // jump passes per round at most (chains of 64 steps each)
+    const int32_t *si, *sj, *row_ptr;
+    const double *p;
+    int32_t *comp, *parent;
+    unsigned long long *bestp, *bestk;
+    uint8_t *flag;
+    int *changed;                     // [64]: a component hooked in round r
+    int *more;                        // [64 * max_passes]: a chain outlived jump pass k of round r
+    unsigned *bar;
+    int *err;                         // barrier timeout; 2 = a round needed more jump passes
+};
+
+__global__ void __launch_bounds__(256) bv_coop_kernel(BvArgs A) {
+    const unsigned G = gridDim.x;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (int64_t)G * blockDim.x;
+    for (int64_t v = tid; v < A.V; v += stride) {
+        A.comp[v] = (int32_t)v;
+        A.parent[v] = (int32_t)v;
+    }
+    if (!grid_barrier(A.bar, G, A.err)) return;
+    for (int round = 0; round < 64; ++round) {
+        for (int64_t v = tid; v < A.V; v += stride) {
+            A.bestp[v] = 0ull;
+            A.bestk[v] = ~0ull;
+        }
+        if (!grid_barrier(A.bar, G, A.err)) return;
+        for (int64_t e = tid; e < A.psi; e += stride) {
+            const int cu = A.comp[A.si[e]], cv = A.comp[A.m + A.sj[e]];
+            if (cu == cv) continue;
+            const unsigned long long b = (unsigned long long)__double_as_longlong(A.p[e]);
+            atomicMax(&A.bestp[cu], b);
+            atomicMax(&A.bestp[cv], b);
+        }
+        if (!grid_barrier(A.bar, G, A.err)) return;
+        for (int64_t e = tid; e < A.psi; e += stride) {
+            const int cu = A.comp[A.si[e]], cv = A.comp[A.m + A.sj[e]];
+            if (cu == cv) continue;
+            const unsigned long long b = (unsigned long long)__double_as_longlong(A.p[e]);
+            const unsigned long long jl = (unsigned long long)A.si[e] + (unsigned long long)A.sj[e] * (unsigned long long)A.m;
+            if (A.bestp[cu] == b) atomicMin(&A.bestk[cu], jl);
+            if (A.bestp[cv] == b) atomicMin(&A.bestk[cv], jl);
+        }
+        if (!grid_barrier(A.bar, G, A.err)) return;
+        for (int64_t c = tid; c < A.V; c += stride) {
+            if (A.comp[c] != c || A.bestp[c] == 0ull) continue;
+            const unsigned long long jl = A.bestk[c];
+            const int i = (int)(jl % (unsigned long long)A.m), j = (int)(jl / (unsigned long long)A.m);
+            int lo = A.row_ptr[i], hi = A.row_ptr[i + 1];
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (A.sj[mid] < j) lo = mid + 1; else hi = mid;
+            }
+            A.flag[lo] = 0;
+            const int ci = A.comp[i], cj = A.comp[A.m + j];
+            const int other = ci == (int)c ? cj : ci;
+            const bool mutual = A.bestk[other] == jl && A.bestp[other] == A.bestp[c];
+            if (!mutual || (int)c < other) A.parent[c] = other;
+            A.changed[round] = 1;
+        }
+        if (!grid_barrier(A.bar, G, A.err)) return;
+        for (int pass = 0;; ++pass) {
+            int *more = A.more + (int64_t)round * A.max_passes + pass;
+            for (int64_t v = tid; v < A.V; v += stride) {
+                int r = A.comp[v];
+                for (int s = 0; s < 64 && A.parent[r] != r; ++s) r = A.parent[r];
+                A.comp[v] = r;
+                if (A.parent[r] != r) *more = 1;
+            }
+            if (!grid_barrier(A.bar, G, A.err)) return;
+            if (!*(volatile int *)more) break;
+            if (pass + 1 >= A.max_passes) {
+                if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(A.err, 0, 2);
+                return;
+            }
+        }
+        if (!*(volatile int *)(A.changed + round)) break;
+    }
+}
+
 __global__ void bv_init_kernel(int V, int32_t *__restrict__ comp, int32_t *__restrict__ parent) {
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x) {
         comp[v] = v;
@@ -423,6 +508,41 @@ Error removal_flags(const Support &S, int32_t m, int32_t n, const double *a_s, c
         OT_TRY(comp.alloc(V, st)); OT_TRY(parent.alloc(V, st));
         OT_TRY(bestp.alloc(V, st)); OT_TRY(bestk.alloc(V, st));
         OT_TRY(flags.alloc(2, st));
+        // one cooperative launch when the device can hold its grid; else the launch-per-stage rounds
+        bool done = false;
+        {
+            const int max_passes = V / 64 + 2;
+            DevTemp<int> chg, more, err;
+            DevTemp<unsigned> bar;
+            OT_TRY(chg.alloc(64, st)); OT_TRY(more.alloc((int64_t)64 * max_passes, st));
+            OT_TRY(err.alloc(1, st)); OT_TRY(bar.alloc(2, st));
+            OT_CUDA(cudaMemsetAsync(chg.p, 0, sizeof(int) * 64, st));
+            OT_CUDA(cudaMemsetAsync(more.p, 0, sizeof(int) * 64 * (size_t)max_passes, st));
+            OT_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
+            OT_CUDA(cudaMemsetAsync(bar.p, 0, 2 * sizeof(unsigned), st));
+            int dev = 0, sms = 0, per_sm = 0;
+            OT_CUDA(cudaGetDevice(&dev));
+            OT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+            OT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bv_coop_kernel, 256, 0));
+            const int64_t want = ceil_div(std::max<int64_t>(psi, V), 256);
+            const int G = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)std::max(per_sm, 0) * sms));
+            if (per_sm > 0) {
+                BvArgs A{psi, m, V, max_passes, S.i, S.j, S.row_ptr, S.p, comp.p, parent.p, bestp.p, bestk.p, flag,
+                         chg.p, more.p, bar.p, err.p};
+                void *args[] = {&A};
+                OT_CUDA(cudaLaunchCooperativeKernel((const void *)bv_coop_kernel, dim3(G), dim3(256), args, 0, st));
+                OT_LAUNCHED();
+                int ev = 0;
+                OT_CUDA(cudaMemcpyAsync(&ev, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+                OT_CUDA(cudaStreamSynchronize(st));
+                if (ev == (int)OT_ERR_TIMEOUT) return fail(OT_ERR_TIMEOUT, "removal guard: grid barrier wait limit reached");
+                done = ev == 0;
+            }
+        }
+        if (!done) {
+        // the flags of the forest edges are reset again by the rounds below
+        removal_cand_kernel<<<grid_for(psi), 256, 0, st>>>(psi, S.i, S.j, S.p, S.s, a_s, b_s, rm_p_frac, flag);
+        OT_LAUNCHED();
         bv_init_kernel<<<grid_for(V), 256, 0, st>>>(V, comp.p, parent.p);
         OT_LAUNCHED();
         int hf[2] = {1, 0};
@@ -444,6 +564,7 @@ Error removal_flags(const Support &S, int32_t m, int32_t n, const double *a_s, c
                 OT_CUDA(cudaMemcpyAsync(hf, flags.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
                 OT_CUDA(cudaStreamSynchronize(st));
             } while (hf[1]);
+        }
         }
     }
     count_flags_kernel<<<grid_for(psi), 256, 0, st>>>(psi, flag, f32.p);
