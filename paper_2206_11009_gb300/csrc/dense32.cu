@@ -279,14 +279,42 @@ __device__ __forceinline__ void d32_diag_block(const DiagSmem &m, int ld, int k,
     float (*Ts)[kP / 2 + 1] = m.Ts;
     float *g = m.g, *thr = m.thr, *ids = m.ids;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int t = threadIdx.x; t < kP * kP; t += blockDim.x) {
-        const int i = t % kP, j = t / kP;
-        S[i][j] = (i > j && i < bs) ? __ldcg(A + (size_t)(k + j) * ld + (k + i)) : 0.f;
+    // every global load of the block, of the first kP rows of partial sums and of the diagonal
+    // is issued before the first of them is used (kTT = 4 kP threads: 16 block entries each)
+    constexpr int kPer = kP * kP / kTT;
+    const int nq0 = min(kP, np);
+    float sv[kPer], cv[kPer];
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+        const int t = (int)threadIdx.x + q * kTT, i = t % kP, j = t / kP;
+        sv[q] = (i > j && i < bs) ? __ldcg(A + (size_t)(k + j) * ld + (k + i)) : 0.f;
     }
-    // the np partial sums per column come through shared memory (Xs as staging, kP rows at a time)
-    // with independent loads; each column then adds its partials in order
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+        const int t = (int)threadIdx.x + q * kTT;
+        cv[q] = t < nq0 * kP ? __ldcg(csum + t) : 0.f;
+    }
+    const float d0v = (int)threadIdx.x < bs ? d0[k + threadIdx.x] : 0.f;
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+        const int t = (int)threadIdx.x + q * kTT;
+        S[t % kP][t / kP] = sv[q];
+        Xs[t / kP][t % kP] = cv[q];
+    }
+    __syncthreads();
+    // each column's partials: four threads take every fourth row, then one adds the four in order
+    // (further chunks of kP rows, for n above 4096, the same way)
     float gs = 0.f;
-    for (int q0 = 0; q0 < np; q0 += kP) {
+    {
+        const int c = threadIdx.x % kP, h = threadIdx.x / kP;
+        float part = 0.f;
+        for (int q = h; q < nq0; q += kTT / kP) part += Xs[q][c];
+        float *red = &Ts[0][0];   // free until the block inverse: [4][kP] here
+        red[h * kP + c] = part;
+        __syncthreads();
+        if (threadIdx.x < kP && (int)threadIdx.x < bs) gs = red[c] + red[kP + c] + red[2 * kP + c] + red[3 * kP + c];
+    }
+    for (int q0 = kP; q0 < np; q0 += kP) {
         const int nq = min(kP, np - q0);
         for (int t = threadIdx.x; t < nq * kP; t += blockDim.x)
             Xs[t / kP][t % kP] = __ldcg(csum + (q0 + t / kP) * kP + t % kP);
@@ -297,7 +325,7 @@ __device__ __forceinline__ void d32_diag_block(const DiagSmem &m, int ld, int k,
     }
     if (threadIdx.x < kP) {
         g[threadIdx.x] = gs;
-        thr[threadIdx.x] = threadIdx.x < bs ? eps * d0[k + threadIdx.x] : 0.f;
+        thr[threadIdx.x] = eps * d0v;
     }
     __syncthreads();
     // micro-panel 0, then per step: warp 0 updates and eliminates the next micro-panel while the
