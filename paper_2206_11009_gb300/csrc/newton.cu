@@ -1521,7 +1521,13 @@ static Error solve_d32_persistent(Newton &W, const Support &S, double target, in
                 W.bar, W.err, target * target, cap, W.scal};
     void *args[] = {&A};
     ktimer_begin(KT_DCG, st);
-    OT_CUDA(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kCgT), args, 0, st));
+    const cudaError_t le = cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kCgT), args, 0, st);
+    if (le == cudaErrorCooperativeLaunchTooLarge) {   // the device cannot hold the grid now
+        cudaGetLastError();
+        ktimer_end(KT_DCG, st);
+        return fail(OT_ERR_UNSUPPORTED, "refinement CG: cooperative grid not resident");
+    }
+    OT_CUDA(le);
     OT_LAUNCHED();
     ktimer_end(KT_DCG, st);
     double hs[SC_COUNT];
@@ -1548,7 +1554,10 @@ static Error solve_direct(Newton &W, const Support &S, double tol, int max_cg, d
     // factor is the iterative phase's preconditioner and stops at the PCG tolerance
     const double target = ic_only ? tol : (W.direct_cg_tol > 0 ? std::max(W.direct_cg_tol, std::min(tol, 1e-10))
                                                                : std::min(tol, 1e-10));
-    if (W.d32 && !C && !W.tree) return solve_d32_persistent(W, S, target, std::min(max_cg, kD32MaxCg), dv, ss, st);
+    if (W.d32 && !C && !W.tree) {
+        const Error e = solve_d32_persistent(W, S, target, std::min(max_cg, kD32MaxCg), dv, ss, st);
+        if (e.code != OT_ERR_UNSUPPORTED) return e;   // else the launch-per-stage loop below
+    }
     double *x = W.x64, *r = W.r64, *z = W.z64, *p = W.p64, *q = W.q64;
     double hs[SC_COUNT];
     OT_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * W.n, st));

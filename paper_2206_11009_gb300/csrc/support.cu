@@ -530,8 +530,15 @@ Error removal_flags(const Support &S, int32_t m, int32_t n, const double *a_s, c
                 BvArgs A{psi, m, V, max_passes, S.i, S.j, S.row_ptr, S.p, comp.p, parent.p, bestp.p, bestk.p, flag,
                          chg.p, more.p, bar.p, err.p};
                 void *args[] = {&A};
-                OT_CUDA(cudaLaunchCooperativeKernel((const void *)bv_coop_kernel, dim3(G), dim3(256), args, 0, st));
-                OT_LAUNCHED();
+                const cudaError_t le =
+                    cudaLaunchCooperativeKernel((const void *)bv_coop_kernel, dim3(G), dim3(256), args, 0, st);
+                if (le == cudaErrorCooperativeLaunchTooLarge) {
+                    cudaGetLastError();
+                    OT_CUDA(cudaMemsetAsync(err.p, 0xff, sizeof(int), st));   // -1: not launched
+                } else {
+                    OT_CUDA(le);
+                    OT_LAUNCHED();
+                }
                 int ev = 0;
                 OT_CUDA(cudaMemcpyAsync(&ev, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
                 OT_CUDA(cudaStreamSynchronize(st));
