@@ -976,9 +976,9 @@ d32_step_kernel(int n, int ld, int k, float *__restrict__ A, float *__restrict__
 // (M = 128, N = 64, K = 8 each), and all four warps read the accumulator back (each warp its 32
 // lanes) and subtract it from C.  Every wait is bounded: a wait that gives up records the failure
 // in *err, waits once more for its own copies or MMAs, releases the tensor memory and returns.
-constexpr int kTcM = 128, kTcN = 64;                  // tile rows, tile columns
+constexpr int kTcM = 128, kTcN = 256;                 // tile rows, tile columns
 constexpr int kTcApiece = kTcM * kP * 4;              // one A piece (hi or lo): 32 KB
-constexpr int kTcBpiece = kTcN * kP * 4;              // one B piece: 16 KB
+constexpr int kTcBpiece = kTcN * kP * 4;              // one B piece: 64 KB
 constexpr int kTcSmem = 2 * kTcApiece + 2 * kTcBpiece + 64;
 constexpr int kTcThreads = 128;
 constexpr long long kTcWaitLimit = 1LL << 24;
@@ -1052,19 +1052,21 @@ d32_tc_split_kernel(int rows, int ld, const float *__restrict__ src, int row0, f
 // rows of L^-1 (C = X, columns below base).  Operand pieces: trailing A = split L D rows, B =
 // split panel rows (64-row blocks); inverse A = split panel rows (128-row blocks), B = split rows
 // of L^-1 (64-column blocks).
-__global__ void __launch_bounds__(kTcThreads, 2)
+__global__ void __launch_bounds__(kTcThreads, 1)
 d32_tc_update_kernel(int n, int ld, int base, int base2, int T, const float *__restrict__ LDs,
                      const float *__restrict__ PBs, const float *__restrict__ PAs, const float *__restrict__ XBs,
                      float *__restrict__ A, float *__restrict__ X, int *__restrict__ err) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    const int idx = blockIdx.x, ntri = T * (T + 1);
+    // triangle tiles: T row tiles x TJ column tiles, of which row tile ti needs the column tiles
+    // starting before its last row (tj < (ti + 1) kTcM / kTcN); then T x tcx tiles of L^-1's rows
+    const int TJ = (int)ceil_div(T * kTcM, kTcN), ntri = T * TJ;
+    const int idx = blockIdx.x;
     const bool tri = idx < ntri;
     int ti, tj;
     if (tri) {
-        ti = (int)floorf((sqrtf(4.f * (float)idx + 1.f) - 1.f) * 0.5f);
-        while ((ti + 1) * (ti + 2) <= idx) ++ti;
-        while (ti * (ti + 1) > idx) --ti;
-        tj = idx - ti * (ti + 1);
+        ti = idx / TJ;
+        tj = idx % TJ;
+        if (tj * kTcN >= (ti + 1) * kTcM) return;   // above the diagonal: uniform, nothing started
     } else {
         const int tcx = (int)ceil_div(base, kTcN);
         ti = (idx - ntri) / tcx;
@@ -1143,11 +1145,18 @@ d32_tc_update_kernel(int n, int ld, int base, int base2, int T, const float *__r
     }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok) {
-        // warp w: TMEM lanes (tile rows) 32 w .. 32 w + 31, all 64 columns in two loads
+        // warp w: TMEM lanes (tile rows) 32 w .. 32 w + 31, all kTcN columns, 32 per load
         float *C = tri ? A : X;
         const int r = r0 + warp * 32 + lane;
+#pragma unroll 1
+        for (int part = 0; part < kTcN / 32; ++part) {
+            // the 32 C values first (all loads in flight together), then the accumulator, then stores
+            float cv[32];
 #pragma unroll
-        for (int part = 0; part < 2; ++part) {
+            for (int j = 0; j < 32; ++j) {
+                const int c = c0 + part * 32 + j;
+                cv[j] = (r < n && c < climit && (!tri || r > c)) ? C[(size_t)c * ld + r] : 0.f;
+            }
             uint32_t v[32];
             const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(part * 32);
             asm volatile(
@@ -1165,7 +1174,7 @@ d32_tc_update_kernel(int n, int ld, int base, int base2, int T, const float *__r
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
                     const int c = c0 + part * 32 + j;
-                    if (c < climit && (!tri || r > c)) C[(size_t)c * ld + r] -= __uint_as_float(v[j]);
+                    if (c < climit && (!tri || r > c)) C[(size_t)c * ld + r] = cv[j] - __uint_as_float(v[j]);
                 }
             }
         }
@@ -1515,7 +1524,8 @@ static Error d32_build(Dense32 &F, float eps, cudaGraph_t g, int64_t *nodes) {
             sp.push_back(c.kernel(ready, d32_tc_split_kernel<kTcN, true>, (unsigned)nx, kTT, base, ld,
                                   (const float *)(F.X + k), 0, XBs));
             for (cudaGraphNode_t q : sp) c.priority(q, lo_prio);
-            u2 = c.kernel_smem(sp, d32_tc_update_kernel, (unsigned)(T * (T + 1) + T * nx), kTcThreads,
+            const int TJ = (int)ceil_div(T * kTcM, kTcN);
+            u2 = c.kernel_smem(sp, d32_tc_update_kernel, (unsigned)(T * TJ + T * nx), kTcThreads,
                                (unsigned)kTcSmem, n, ld, base, base2, T, (const float *)LDs, (const float *)PBs,
                                (const float *)PAs, (const float *)XBs, F.A, F.X, F.tc_err);
             c.priority(u2, lo_prio);
