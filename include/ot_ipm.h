@@ -154,12 +154,12 @@ typedef struct {
      * (Section 4.3) is unchanged. */
     int32_t precond;
     double ic_tau;
-    /* Bulk update of the FP32 dense factorisation on the tensor cores: 1 = tcgen05 MMAs in split
-     * TF32 (a = a_hi + a_lo, three products per term, FP32 accumulation in tensor memory; FP32
-     * accuracy), operands pre-split per panel and fetched by bulk copies; 0 or -1 = the FP32 SIMT
-     * update (the default: a rank-64 update reads and writes the trailing matrix once per panel,
-     * about 16 flops per byte, so the tensor-core form is bound by that traffic and its per-tile
-     * latency; it measured 306 ms against 99 ms per factorisation at n = 16384). */
+    /* Bulk update of the FP32 dense factorisation: 1 = on the tensor cores (tcgen05 MMAs in split
+     * TF32, a = a_hi + a_lo, three products per term, FP32 accumulation in tensor memory: FP32
+     * accuracy; operands pre-split per panel, fetched by bulk copies; persistent warp-specialised
+     * CTAs with two accumulators), -1 = the FP32 SIMT update with the fused panel step, 0 = the
+     * tensor cores from n = 8192 on, SIMT below (the default; measured per factorisation:
+     * n = 16384 75 ms against 93 ms, n = 4096 2.9 ms either way). */
     int32_t tc_update;
     /* Relative residual at which the CG preconditioned by a factorisation (the FP32 dense factor,
      * the direct branch) stops: 0 = min(CG tolerance, 1e-10) (near-exact Newton directions);

@@ -980,7 +980,8 @@ constexpr int kTcM = 128, kTcN = 256;                 // tile rows, tile columns
 constexpr int kTcApiece = kTcM * kP * 4;              // one A piece (hi or lo): 32 KB
 constexpr int kTcBpiece = kTcN * kP * 4;              // one B piece: 64 KB
 constexpr int kTcSmem = 2 * kTcApiece + 2 * kTcBpiece + 64;
-constexpr int kTcThreads = 128;
+constexpr int kTcThreads = 160;   // four epilogue warps and one producer warp
+constexpr int kTcAutoN = 8192;    // tc_mode 0: the tensor-core update from this n on
 constexpr long long kTcWaitLimit = 1LL << 24;
 
 __device__ __forceinline__ uint32_t tc_smem_u32(const void *ptr) { return (uint32_t)__cvta_generic_to_shared(ptr); }
@@ -1047,141 +1048,191 @@ d32_tc_split_kernel(int rows, int ld, const float *__restrict__ src, int row0, f
     }
 }
 
-// One CTA per tile.  Tiles [0, T (T + 1)): the trailing triangle from base2 (row block ti of 128,
-// column block tj of 64 with tj <= 2 ti + 1; C = A, rows > columns); then T x tcx tiles of the
-// rows of L^-1 (C = X, columns below base).  Operand pieces: trailing A = split L D rows, B =
-// split panel rows (64-row blocks); inverse A = split panel rows (128-row blocks), B = split rows
-// of L^-1 (64-column blocks).
-__global__ void __launch_bounds__(kTcThreads, 1)
+// Tile t of one panel's bulk update: tiles [0, T TJ) are the trailing triangle from base2 (row
+// tile ti of 128, column tile tj of 256; only those that start left of the row tile's last row),
+// then T x tcx tiles of the rows of L^-1 (C = X, columns below base).  False: nothing to do.
+__device__ __forceinline__ bool tc_tile(int t, int n, int base, int base2, int T, int TJ, int tcx, bool &tri, int &ti,
+                                        int &tj, int &r0, int &c0, int &climit) {
+    const int ntri = T * TJ;
+    tri = t < ntri;
+    if (tri) {
+        ti = t / TJ;
+        tj = t % TJ;
+        if (tj * kTcN >= (ti + 1) * kTcM) return false;
+    } else {
+        ti = (t - ntri) / tcx;
+        tj = (t - ntri) % tcx;
+    }
+    r0 = base2 + ti * kTcM;
+    c0 = tri ? base2 + tj * kTcN : tj * kTcN;
+    climit = tri ? n : base;
+    return r0 < n && c0 < climit;
+}
+
+__device__ __forceinline__ int tc_next(int t, int step, int ntiles, int n, int base, int base2, int T, int TJ,
+                                       int tcx) {
+    bool tri;
+    int ti, tj, r0, c0, cl;
+    while (t < ntiles && !tc_tile(t, n, base, base2, T, TJ, tcx, tri, ti, tj, r0, c0, cl)) t += step;
+    return t;
+}
+
+// Persistent CTAs (one per SM), each taking tiles gridDim.x apart, warp-specialised: warp 4 (one
+// lane) brings each tile's four operand pieces with two bulk copies on an mbarrier and issues its
+// 3 x 8 MMAs into one of two tensor-memory accumulators, committing them to that accumulator's
+// "full" mbarrier; warps 0-3 (tensor-memory lanes 0-127) wait for it, subtract the accumulator
+// from C and arrive on its "empty" mbarrier.  So tile i + 1's copies and MMAs run while tile i's
+// epilogue does; the single operand stage is refilled once tile i's MMAs are done.  Every wait
+// is bounded: one that gives up records the failure in *err and the CTA winds down (its own
+// copies and MMAs waited for once more) before it releases the tensor memory.  Operand pieces:
+// trailing A = split L D rows, B = split panel rows (256-row blocks); inverse A = split panel rows
+// (128-row blocks), B = split rows of L^-1.
+constexpr int kTcWarps = 5;
+__device__ __forceinline__ void tc_arrive(uint32_t mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(mbar) : "memory");
+}
+
+__global__ void __launch_bounds__(kTcWarps * 32, 1)
 d32_tc_update_kernel(int n, int ld, int base, int base2, int T, const float *__restrict__ LDs,
                      const float *__restrict__ PBs, const float *__restrict__ PAs, const float *__restrict__ XBs,
                      float *__restrict__ A, float *__restrict__ X, int *__restrict__ err) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    // triangle tiles: T row tiles x TJ column tiles, of which row tile ti needs the column tiles
-    // starting before its last row (tj < (ti + 1) kTcM / kTcN); then T x tcx tiles of L^-1's rows
-    const int TJ = (int)ceil_div(T * kTcM, kTcN), ntri = T * TJ;
-    const int idx = blockIdx.x;
-    const bool tri = idx < ntri;
-    int ti, tj;
-    if (tri) {
-        ti = idx / TJ;
-        tj = idx % TJ;
-        if (tj * kTcN >= (ti + 1) * kTcM) return;   // above the diagonal: uniform, nothing started
-    } else {
-        const int tcx = (int)ceil_div(base, kTcN);
-        ti = (idx - ntri) / tcx;
-        tj = (idx - ntri) % tcx;
-    }
-    const int r0 = base2 + ti * kTcM;
-    const int c0 = tri ? base2 + tj * kTcN : tj * kTcN;
-    const int climit = tri ? n : base;
-    if (r0 >= n || c0 >= climit) return;   // outside the matrix: uniform over the CTA, nothing started
-    uint64_t *mb_load = (uint64_t *)(smem + 2 * kTcApiece + 2 * kTcBpiece);
-    uint64_t *mb_mma = mb_load + 1;
-    uint32_t *tslot = (uint32_t *)(mb_load + 2);
+    const int TJ = (int)ceil_div(T * kTcM, kTcN), tcx = (int)ceil_div(base, kTcN);
+    const int ntiles = T * TJ + T * tcx, step = (int)gridDim.x;
+    const int first = tc_next((int)blockIdx.x, step, ntiles, n, base, base2, T, TJ, tcx);
+    if (first >= ntiles) return;   // no tile for this CTA: uniform, nothing started
+    uint64_t *mbs = (uint64_t *)(smem + 2 * kTcApiece + 2 * kTcBpiece);
+    // [0] load, [1..2] full (per accumulator), [3..4] empty (per accumulator)
+    uint32_t *tslot = (uint32_t *)(mbs + 5);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     :: "r"(tc_smem_u32(tslot)), "r"(kTcN) : "memory");
+                     :: "r"(tc_smem_u32(tslot)), "r"(2 * kTcN) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
+    const uint32_t mbl = tc_smem_u32(mbs), sbase = tc_smem_u32(smem);
+    const uint32_t mfull[2] = {tc_smem_u32(mbs + 1), tc_smem_u32(mbs + 2)};
+    const uint32_t mempty[2] = {tc_smem_u32(mbs + 3), tc_smem_u32(mbs + 4)};
     if (threadIdx.x == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(tc_smem_u32(mb_load)) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(tc_smem_u32(mb_mma)) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mbl) : "memory");
+        for (int q = 0; q < 2; ++q) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mfull[q]) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" :: "r"(mempty[q]) : "memory");
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tslot;
-    const float *pa = (tri ? LDs : PAs) + (size_t)(2 * ti) * kTcM * kP;
-    const float *pb = (tri ? PBs : XBs) + (size_t)(2 * tj) * kTcN * kP;
-    int ok = 1;
-    if (threadIdx.x == 0) {
-        const uint32_t mbl = tc_smem_u32(mb_load), sbase = tc_smem_u32(smem);
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                     :: "r"(mbl), "r"((uint32_t)(2 * kTcApiece + 2 * kTcBpiece)) : "memory");
-        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                     :: "r"(sbase), "l"(pa), "r"((uint32_t)(2 * kTcApiece)), "r"(mbl) : "memory");
-        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                     :: "r"(sbase + 2 * kTcApiece), "l"(pb), "r"((uint32_t)(2 * kTcBpiece)), "r"(mbl) : "memory");
-        if (!tc_wait(mbl, 0)) {
-            ok = 0;
-            atomicExch(err, 1);
-            tc_wait(mbl, 0);   // the copies target this CTA's shared memory: give them time to land
-        }
-        if (ok) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t ah = sbase, al = sbase + kTcApiece;
-            const uint32_t bh = sbase + 2 * kTcApiece, bl = bh + kTcBpiece;
-            const uint32_t lboA = (kTcM / 8) * 128, lboB = (kTcN / 8) * 128;
+    if (warp == 4) {
+        if (lane == 0) {
+            int i = 0, failed = 0;
+            for (int t = first; t < ntiles && !failed; t = tc_next(t + step, step, ntiles, n, base, base2, T, TJ, tcx), ++i) {
+                const int bsel = i & 1;
+                // the stage is free once the previous tile's MMAs are done
+                if (i >= 1 && !tc_wait(mfull[(i - 1) & 1], (uint32_t)(((i - 1) >> 1) & 1))) { failed = 1; break; }
+                bool tri;
+                int ti, tj, r0, c0, cl;
+                tc_tile(t, n, base, base2, T, TJ, tcx, tri, ti, tj, r0, c0, cl);
+                const float *pa = (tri ? LDs : PAs) + (size_t)(2 * ti) * kTcM * kP;
+                const float *pb = (tri ? PBs : XBs) + (size_t)(2 * tj) * kTcN * kP;
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                             :: "r"(mbl), "r"((uint32_t)(2 * kTcApiece + 2 * kTcBpiece)) : "memory");
+                asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                             :: "r"(sbase), "l"(pa), "r"((uint32_t)(2 * kTcApiece)), "r"(mbl) : "memory");
+                asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                             :: "r"(sbase + 2 * kTcApiece), "l"(pb), "r"((uint32_t)(2 * kTcBpiece)), "r"(mbl) : "memory");
+                if (!tc_wait(mbl, (uint32_t)(i & 1))) {
+                    failed = 1;
+                    tc_wait(mbl, (uint32_t)(i & 1));   // the copies target this CTA's shared memory
+                    break;
+                }
+                // the accumulator is free once the epilogue of tile i - 2 is done
+                if (i >= 2 && !tc_wait(mempty[bsel], (uint32_t)(((i - 2) >> 1) & 1))) { failed = 1; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t acc = tmem + (uint32_t)(bsel * kTcN);
+                const uint32_t ah = sbase, al = sbase + kTcApiece;
+                const uint32_t bh = sbase + 2 * kTcApiece, bl = bh + kTcBpiece;
+                const uint32_t lboA = (kTcM / 8) * 128, lboB = (kTcN / 8) * 128;
 #pragma unroll
-            for (int ks = 0; ks < kP / 8; ++ks) {
-                const uint32_t ka = (uint32_t)ks * 2 * lboA, kb = (uint32_t)ks * 2 * lboB;
-                const uint64_t dah = tc_desc(ah + ka, lboA), dal = tc_desc(al + ka, lboA);
-                const uint64_t dbh = tc_desc(bh + kb, lboB), dbl = tc_desc(bl + kb, lboB);
-                asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                             " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
-                             :: "r"(tmem), "l"(dah), "l"(dbh), "r"(kTcIdesc), "r"(ks > 0 ? 1u : 0u) : "memory");
-                asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                             " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
-                             :: "r"(tmem), "l"(dah), "l"(dbl), "r"(kTcIdesc), "r"(1u) : "memory");
-                asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                             " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
-                             :: "r"(tmem), "l"(dal), "l"(dbh), "r"(kTcIdesc), "r"(1u) : "memory");
+                for (int ks = 0; ks < kP / 8; ++ks) {
+                    const uint32_t ka = (uint32_t)ks * 2 * lboA, kb = (uint32_t)ks * 2 * lboB;
+                    const uint64_t dah = tc_desc(ah + ka, lboA), dal = tc_desc(al + ka, lboA);
+                    const uint64_t dbh = tc_desc(bh + kb, lboB), dbl = tc_desc(bl + kb, lboB);
+                    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                                 " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+                                 :: "r"(acc), "l"(dah), "l"(dbh), "r"(kTcIdesc), "r"(ks > 0 ? 1u : 0u) : "memory");
+                    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                                 " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+                                 :: "r"(acc), "l"(dah), "l"(dbl), "r"(kTcIdesc), "r"(1u) : "memory");
+                    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                                 " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+                                 :: "r"(acc), "l"(dal), "l"(dbh), "r"(kTcIdesc), "r"(1u) : "memory");
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                             :: "r"(mfull[bsel]) : "memory");
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                         :: "r"(tc_smem_u32(mb_mma)) : "memory");
+            if (failed) atomicExch(err, 1);
+            // before the CTA ends: the last MMAs issued must be complete (bounded)
+            if (i >= 1) tc_wait(mfull[(i - 1) & 1], (uint32_t)(((i - 1) >> 1) & 1));
         }
-    }
-    ok = __syncthreads_and(ok);
-    if (ok) {
-        const bool done = tc_wait(tc_smem_u32(mb_mma), 0);
-        ok = __syncthreads_and(done ? 1 : 0);
-        if (!ok) {
-            if (threadIdx.x == 0) atomicExch(err, 1);
-            tc_wait(tc_smem_u32(mb_mma), 0);   // the MMAs write this CTA's tensor memory
-        }
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (ok) {
-        // warp w: TMEM lanes (tile rows) 32 w .. 32 w + 31, all kTcN columns, 32 per load
-        float *C = tri ? A : X;
-        const int r = r0 + warp * 32 + lane;
-#pragma unroll 1
-        for (int part = 0; part < kTcN / 32; ++part) {
-            // the 32 C values first (all loads in flight together), then the accumulator, then stores
-            float cv[32];
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const int c = c0 + part * 32 + j;
-                cv[j] = (r < n && c < climit && (!tri || r > c)) ? C[(size_t)c * ld + r] : 0.f;
-            }
-            uint32_t v[32];
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(part * 32);
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-                "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-                "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
-                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-                  "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
-                  "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
-                  "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-                : "r"(taddr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (r < n) {
+    } else {
+        // epilogue warps: warp w owns tensor-memory lanes (tile rows) 32 w .. 32 w + 31
+        int i = 0;
+        for (int t = first; t < ntiles; t = tc_next(t + step, step, ntiles, n, base, base2, T, TJ, tcx), ++i) {
+            const int bsel = i & 1;
+            bool tri;
+            int ti, tj, r0, c0, climit;
+            tc_tile(t, n, base, base2, T, TJ, tcx, tri, ti, tj, r0, c0, climit);
+            float *C = tri ? A : X;
+            const int r = r0 + warp * 32 + lane;
+            float cv[2][32];
+            auto load_part = [&](float (&dst)[32], int part) {
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
                     const int c = c0 + part * 32 + j;
-                    if (c < climit && (!tri || r > c)) C[(size_t)c * ld + r] = cv[j] - __uint_as_float(v[j]);
+                    dst[j] = (r < n && c < climit && (!tri || r > c)) ? C[(size_t)c * ld + r] : 0.f;
+                }
+            };
+            load_part(cv[0], 0);   // while the MMAs run
+            if (!tc_wait(mfull[bsel], (uint32_t)((i >> 1) & 1))) {
+                if (lane == 0) atomicExch(err, 1);
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t accrow = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(bsel * kTcN);
+#pragma unroll 2
+            for (int part = 0; part < kTcN / 32; ++part) {
+                if (part + 1 < kTcN / 32) load_part(cv[(part + 1) & 1], part + 1);
+                uint32_t v[32];
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                    "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+                    "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                      "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                      "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+                      "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                    : "r"(accrow + (uint32_t)(part * 32)));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (r < n) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int c = c0 + part * 32 + j;
+                        if (c < climit && (!tri || r > c)) C[(size_t)c * ld + r] = cv[part & 1][j] - __uint_as_float(v[j]);
+                    }
                 }
             }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) tc_arrive(mempty[bsel]);
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kTcN) : "memory");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(2 * kTcN) : "memory");
 }
 
 // partial sums of y = X r: CTA (rb, cb) covers rows [rb*256, +256) (four per thread, float4 loads)
@@ -1427,6 +1478,9 @@ static Error d32_build(Dense32 &F, float eps, cudaGraph_t g, int64_t *nodes) {
     cudaGraphNode_t prev = c.memset0(F.X, (size_t)ld * n, {});
     int lo_prio = 0, hi_prio = 0;
     if (cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio) != cudaSuccess) lo_prio = hi_prio = 0;
+    int sms = 0, dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        sms = 1;
     if (!F.use_tc) {
         // SIMT: the first diagonal block, then one fused step per panel (which also factors the next
         // diagonal block) on the chain, the rest of each panel's update (from base + 128) beside
@@ -1525,7 +1579,8 @@ static Error d32_build(Dense32 &F, float eps, cudaGraph_t g, int64_t *nodes) {
                                   (const float *)(F.X + k), 0, XBs));
             for (cudaGraphNode_t q : sp) c.priority(q, lo_prio);
             const int TJ = (int)ceil_div(T * kTcM, kTcN);
-            u2 = c.kernel_smem(sp, d32_tc_update_kernel, (unsigned)(T * TJ + T * nx), kTcThreads,
+            const int tiles = T * TJ + T * nx;   // persistent CTAs: one per SM at most
+            u2 = c.kernel_smem(sp, d32_tc_update_kernel, (unsigned)std::max(1, std::min(tiles, sms)), kTcThreads,
                                (unsigned)kTcSmem, n, ld, base, base2, T, (const float *)LDs, (const float *)PBs,
                                (const float *)PAs, (const float *)XBs, F.A, F.X, F.tc_err);
             c.priority(u2, lo_prio);
@@ -1541,7 +1596,7 @@ Error d32_factor(Dense32 &F, float eps, cudaStream_t st) {
     if (F.tc_err_host && *F.tc_err_host)
         return fail(OT_ERR_TIMEOUT, "dense32: a bounded wait of the tensor-core update gave up");
     if (!F.graph || F.eps != eps) {
-        const bool want_tc = F.tc_mode > 0;
+        const bool want_tc = F.tc_mode > 0 || (F.tc_mode == 0 && F.n >= kTcAutoN);
         if (want_tc && !F.tc) {
             OT_CUDA(cudaMalloc((void **)&F.tc, sizeof(float) * 2 * tc_per_parity(F.n)));
             OT_CUDA(cudaMalloc((void **)&F.tc_err, sizeof(int)));

@@ -32,8 +32,9 @@ struct Dense32 {
     float eps = 0.f;
     cudaGraphExec_t graph = nullptr;  // the factorisation's launch sequence for this n
     int64_t graph_nodes = 0;
-    // bulk update on the tensor cores (split TF32, tcgen05): tc_mode 1 = on, otherwise the FP32 SIMT
-    // update (read when the launch sequence is built); split operands, double-buffered by panel
+    // bulk update on the tensor cores (split TF32, tcgen05): tc_mode 1 = on, -1 = the FP32 SIMT
+    // update, 0 = on from n = 8192 (read when the launch sequence is built); split operands,
+    // double-buffered by panel
     int tc_mode = 0;
     bool use_tc = false;
     float *tc = nullptr;
