@@ -399,10 +399,14 @@ int ot_kernel_timing_read(double *ms, int64_t *count, double *work, int32_t cap)
  *   input  x (B, 2, k, k): log(a m / sum a), log(b m / sum b), NCHW, FP32
  *   blocks l = 0..3: h <- silu(rmsnorm_c(conv3x3(h; W_l, b_l, dilation 2^l)) * g_l), 2->32->32->32->32
  *   head:  y = conv3x3(h; W_4, b_4), 32 -> 2: the predicted (u, v) / k^2
- * Convolutions take BF16 operands and accumulate in FP32; parameters (FP32, the flat order: per
- * layer W[cout][cin][3][3], b[cout], then g[cout] for the normalised blocks) are the caller's at
- * creation.  All x / y / target / gradient pointers are DEVICE pointers; one handle is one
- * stream's state and is not thread-safe. */
+ * Convolutions take BF16 operands and accumulate in FP32; those of the three 32 -> 32 blocks
+ * (forward, data gradient, weight gradient) are implicit GEMMs on the tensor cores (tcgen05, FP32
+ * accumulators in tensor memory), the 2 -> 32 and 32 -> 2 ones run on the FP32 pipes.  Parameters
+ * (FP32, the flat order: per layer W[cout][cin][3][3], b[cout], then g[cout] for the normalised
+ * blocks) are the caller's at creation.  All x / y / target / gradient pointers are DEVICE
+ * pointers; one handle is one stream's state and is not thread-safe.  ot_cnn_forward and
+ * ot_cnn_backward synchronise the stream once at the end: a tensor-core kernel whose bounded wait
+ * gave up is reported there as OT_ERR_TIMEOUT. */
 typedef struct ot_cnn ot_cnn_t;
 
 /* Number of parameters for `channels` hidden channels (only 32 is built; -1 otherwise). */

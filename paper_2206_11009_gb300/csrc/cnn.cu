@@ -16,6 +16,7 @@
 
 #include "common.cuh"
 #include "ot_ipm.h"
+#include "tc05.cuh"
 
 namespace ot {
 namespace {
@@ -224,6 +225,258 @@ conv_bwd_weight_kernel(int B, int H, int Wd, int dil, const __nv_bfloat16 *__res
     }
 }
 
+// ---- the 32 -> 32 convolutions on the tensor cores (implicit GEMM)
+// BF16 operands in shared memory, FP32 accumulators in tensor memory, one elected thread issuing
+// the MMAs.  Operands are K-major without swizzle: core matrices of 8 rows x 8 BF16 (16 bytes),
+// core matrix (row / 8, k / 8) of an R-row operand at byte ((k / 8)(R / 8) + row / 8) 128, its row
+// row % 8 at 16-byte steps, so the leading byte offset is (R / 8) 128 and one MMA (K = 16) spans
+// two core-matrix columns.
+//   conv:   D[pixel, o] = sum_{t, c} A[pixel, t 32 + c] Wop[o, t 32 + c], A the pixel's 9 taps x 32
+//           channels (zero outside the image): M = 128 pixels, N = 32, K = 288 (18 MMAs).  The data
+//           gradient is the same product over the output gradient with the taps mirrored.
+//   wgrad:  D[t 32 + c, o] = sum_pixel A[t 32 + c, pixel] dz[o, pixel] over a chunk of 128 pixels:
+//           rows padded to 384 (three M = 128 tiles), N = 32, K = 128 (8 MMAs per tile).
+constexpr int kCvM = 128, kCvN = 32, kCvK = 9 * 32;
+constexpr int kCvAbytes = kCvM * kCvK * 2;     // 73,728
+constexpr int kCvBbytes = kCvN * kCvK * 2;     // 18,432: one layer's weight operand
+constexpr int kCvSmem = kCvAbytes + kCvBbytes + 16;
+constexpr uint32_t kCvIdesc = tc_idesc(1u, kCvM, kCvN);
+constexpr int kWgRows = 384, kWgK = 128;        // weight-gradient rows (288 used), pixels per chunk
+constexpr int kWgAbytes = kWgRows * kWgK * 2;  // 98,304
+constexpr int kWgBbytes = kCvN * kWgK * 2;     // 8,192
+constexpr int kWgSmem = kWgAbytes + kWgBbytes + 16;
+constexpr int kWgStride = 32 * 32 * 9 + 32;    // one chunk's partial row: dW then db
+
+// byte offset of element (row, k) in a K-major operand of R rows
+__device__ __forceinline__ int cv_off(int row, int k, int R) {
+    return ((k >> 3) * (R >> 3) + (row >> 3)) * 128 + (row & 7) * 16 + (k & 7) * 2;
+}
+
+// Weight operands of the three 32 -> 32 layers in the layout above, forward (Wop[o, t 32 + c] =
+// W[o, c, t]) and mirrored for the data gradient (Wop'[c, t 32 + o] = W[o, c, 8 - t]); operand
+// (layer l, mirrored f) at wop + (2 l + f) 32 288.
+__global__ void conv_wop_kernel(const float *__restrict__ w, int64_t off1, int64_t off2, int64_t off3,
+                                __nv_bfloat16 *__restrict__ wop) {
+    const int per = kCvN * kCvK;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < 6 * per; q += gridDim.x * blockDim.x) {
+        const int op = q / per, e = q % per, l = op >> 1, f = op & 1;
+        const float *W = w + (l == 0 ? off1 : l == 1 ? off2 : off3);
+        const int r = e / kCvK, k = e % kCvK, t = k >> 5, c = k & 31;
+        const float v = f ? W[(c * 32 + r) * 9 + (8 - t)] : W[(r * 32 + c) * 9 + t];
+        wop[(int64_t)op * per + cv_off(r, k, kCvN) / 2] = __float2bfloat16(v);
+    }
+}
+
+// out[b, o, y, x] = bias[o] + sum_{c, t} Wop[o, t 32 + c] in[b, c, y + oy_t, x + ox_t] (zero
+// padding, offsets (t / 3 - 1, t % 3 - 1) dil; bias may be NULL).  Persistent CTAs of 128
+// threads take 128-pixel tiles gridDim.x apart: each thread gathers its pixel's 288 inputs into
+// the A operand (16-byte stores), thread 0 issues the 18 MMAs and commits them to an mbarrier,
+// and warp w reads accumulator lanes 32 w .. 32 w + 31 (its pixels) back.  The wait is bounded:
+// a CTA in which it gives up records that in *err, waits once more for its MMAs and stops.
+__global__ void __launch_bounds__(kCvM)
+conv_tc_kernel(int B, int H, int Wd, int dil, const __nv_bfloat16 *__restrict__ in,
+               const __nv_bfloat16 *__restrict__ wop, const float *__restrict__ bias, float *__restrict__ out,
+               int *__restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char *sA = smem, *sB = smem + kCvAbytes;
+    uint64_t *mb = (uint64_t *)(sB + kCvBbytes);
+    uint32_t *tslot = (uint32_t *)(mb + 1);
+    const int HW = H * Wd;
+    const int64_t P = (int64_t)B * HW, ntiles = (P + kCvM - 1) / kCvM;
+    const int warp = threadIdx.x >> 5, p = threadIdx.x;
+    for (int q = threadIdx.x; q < kCvBbytes / 16; q += blockDim.x) ((uint4 *)sB)[q] = ((const uint4 *)wop)[q];
+    if (warp == 0) tc_alloc(tslot, kCvN);
+    const uint32_t a0 = tc_smem_u32(sA), b0 = tc_smem_u32(sB), mbar = tc_smem_u32(mb);
+    if (threadIdx.x == 0) {
+        tc_mbar_init(mbar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    const unsigned short *src16 = (const unsigned short *)in;
+    int it = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+        const int64_t pix = tile * kCvM + p;
+        const bool valid = pix < P;
+        const int b = valid ? (int)(pix / HW) : 0;
+        const int yx = valid ? (int)(pix % HW) : 0, y = yx / Wd, x = yx % Wd;
+        const unsigned short *src = src16 + (int64_t)b * 32 * HW;
+#pragma unroll 1
+        for (int t = 0; t < 9; ++t) {
+            const int yy = y + (t / 3 - 1) * dil, xx = x + (t % 3 - 1) * dil;
+            const bool ok = valid && yy >= 0 && yy < H && xx >= 0 && xx < Wd;
+            const int off = ok ? yy * Wd + xx : 0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                uint32_t w4[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int c = q * 8 + 2 * e;
+                    const uint32_t lo = ok ? src[(int64_t)c * HW + off] : 0u;
+                    const uint32_t hi = ok ? src[(int64_t)(c + 1) * HW + off] : 0u;
+                    w4[e] = lo | (hi << 16);
+                }
+                *(uint4 *)(sA + cv_off(p, t * 32 + q * 8, kCvM)) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+            }
+        }
+        // the generic-proxy stores above must be visible to the MMAs (async proxy)
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_fence_before();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tc_fence_after();
+            const uint32_t lboA = (kCvM / 8) * 128, lboB = (kCvN / 8) * 128;
+#pragma unroll
+            for (int ks = 0; ks < kCvK / 16; ++ks)
+                tc_mma<true>(tmem, tc_desc(a0 + ks * 2 * lboA, lboA), tc_desc(b0 + ks * 2 * lboB, lboB), kCvIdesc,
+                             ks > 0);
+            tc_commit(mbar);
+        }
+        const bool done = tc_wait(mbar, (uint32_t)(it & 1));
+        if (__syncthreads_or(!done)) {
+            if (threadIdx.x == 0) {
+                atomicExch(err, 1);
+                tc_wait(mbar, (uint32_t)(it & 1));   // its MMAs read this CTA's shared memory
+            }
+            break;
+        }
+        tc_fence_after();
+        float v[32];
+        tc_ld32(tmem + ((uint32_t)(warp * 32) << 16), v);
+        if (valid) {
+            float *dst = out + (int64_t)b * 32 * HW + yx;
+#pragma unroll
+            for (int o = 0; o < 32; ++o) dst[(int64_t)o * HW] = (bias ? bias[o] : 0.f) + v[o];
+        }
+        tc_fence_before();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tc_dealloc(tmem, kCvN);
+}
+
+// Partial weight and bias gradients of a 32 -> 32 convolution over chunk blockIdx.x of 128 pixels:
+// part[chunk kWgStride + (o 32 + c) 9 + t] = sum_pixel dz[b, o, pixel] in[b, c, pixel + offset_t]
+// and part[chunk kWgStride + 9216 + o] = sum_pixel dz[b, o, pixel] (FP32, a fixed order).  dz is
+// rounded to BF16 for the MMAs.  The A operand is built in items of (row, 8 pixels), 32 items per
+// warp pass: lanes 8 j + r take rows 8 R + r of one row octet R and pixel groups 4 G + j, so each
+// phase of eight 16-byte stores covers eight distinct bank groups and each load instruction touches
+// 8 channel planes in runs of 4 pixel groups.  Same waits and clean-up as conv_tc_kernel.
+__global__ void __launch_bounds__(kCvM)
+conv_wgrad_tc_kernel(int B, int H, int Wd, int dil, const __nv_bfloat16 *__restrict__ in,
+                     const float *__restrict__ dz, float *__restrict__ part, int *__restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ int sb[kWgK], sy[kWgK], sx[kWgK];
+    __shared__ float sbias[kCvM];
+    unsigned char *sA = smem, *sB = smem + kWgAbytes;
+    uint64_t *mb = (uint64_t *)(sB + kWgBbytes);
+    uint32_t *tslot = (uint32_t *)(mb + 1);
+    const int HW = H * Wd;
+    const int64_t P = (int64_t)B * HW, p0 = (int64_t)blockIdx.x * kWgK;
+    const int np = (int)(P - p0 < kWgK ? P - p0 : kWgK);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp == 0) tc_alloc(tslot, 128);
+    for (int i = threadIdx.x; i < kWgK; i += blockDim.x) {
+        const int64_t pix = p0 + (i < np ? i : 0);
+        const int yx = (int)(pix % HW);
+        sb[i] = (int)(pix / HW);
+        sy[i] = yx / Wd;
+        sx[i] = yx % Wd;
+    }
+    if (threadIdx.x == 0) {
+        tc_mbar_init(tc_smem_u32(mb), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    // A: 192 warp passes of 32 items; rows 288.. are zero
+    const unsigned short *in16 = (const unsigned short *)in;
+    for (int qb = warp; qb < (kWgRows / 8) * (kWgK / 32); qb += kCvM / 32) {
+        const int row = (qb % (kWgRows / 8)) * 8 + (lane & 7), kg = (qb / (kWgRows / 8)) * 4 + (lane >> 3);
+        uint32_t w4[4] = {0u, 0u, 0u, 0u};
+        if (row < kCvK) {
+            const int t = row >> 5, c = row & 31;
+            const int oy = (t / 3 - 1) * dil, ox = (t % 3 - 1) * dil;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int i = kg * 8 + e;
+                uint32_t v = 0u;
+                if (i < np) {
+                    const int yy = sy[i] + oy, xx = sx[i] + ox;
+                    if (yy >= 0 && yy < H && xx >= 0 && xx < Wd)
+                        v = in16[((int64_t)sb[i] * 32 + c) * HW + yy * Wd + xx];
+                }
+                w4[e >> 1] |= v << ((e & 1) * 16);
+            }
+        }
+        *(uint4 *)(sA + cv_off(row, kg * 8, kWgRows)) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+    }
+    // B: thread (o = tid % 32, pixel groups tid / 32 + 4 u), rounded to BF16; the FP32 sum of the
+    // thread's 32 values (in pixel order) is its share of the bias gradient
+    {
+        const int o = threadIdx.x & 31;
+        float bs = 0.f;
+#pragma unroll 1
+        for (int u = 0; u < 4; ++u) {
+            const int kg = (threadIdx.x >> 5) + 4 * u;
+            uint32_t w4[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int i = kg * 8 + e;
+                const float v = i < np ? dz[((int64_t)sb[i] * 32 + o) * HW + sy[i] * Wd + sx[i]] : 0.f;
+                bs += v;
+                w4[e >> 1] |= (uint32_t)__bfloat16_as_ushort(__float2bfloat16(v)) << ((e & 1) * 16);
+            }
+            *(uint4 *)(sB + cv_off(o, kg * 8, kCvN)) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+        }
+        sbias[threadIdx.x] = bs;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot, mbar = tc_smem_u32(mb);
+    if (threadIdx.x == 0) {
+        const uint32_t a0 = tc_smem_u32(sA), b0 = tc_smem_u32(sB);
+        const uint32_t lboA = (kWgRows / 8) * 128, lboB = (kCvN / 8) * 128;
+#pragma unroll
+        for (int mt = 0; mt < kWgRows / 128; ++mt)
+#pragma unroll
+            for (int ks = 0; ks < kWgK / 16; ++ks)
+                tc_mma<true>(tmem + (uint32_t)(mt * kCvN), tc_desc(a0 + mt * 16 * 128 + ks * 2 * lboA, lboA),
+                             tc_desc(b0 + ks * 2 * lboB, lboB), kCvIdesc, ks > 0);
+        tc_commit(mbar);
+    }
+    float *prow = part + (int64_t)blockIdx.x * kWgStride;
+    if (warp == 0) prow[32 * 32 * 9 + lane] = ((sbias[lane] + sbias[lane + 32]) + sbias[lane + 64]) + sbias[lane + 96];
+    const bool done = tc_wait(mbar, 0u);
+    if (__syncthreads_or(!done)) {
+        if (threadIdx.x == 0) {
+            atomicExch(err, 1);
+            tc_wait(mbar, 0u);
+        }
+    } else {
+        tc_fence_after();
+#pragma unroll 1
+        for (int mt = 0; mt < kWgRows / 128; ++mt) {
+            float v[32];
+            tc_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(mt * kCvN), v);
+            const int row = mt * 128 + warp * 32 + lane;
+            if (row < kCvK) {
+                const int t = row >> 5, c = row & 31;
+#pragma unroll
+                for (int o = 0; o < 32; ++o) prow[(o * 32 + c) * 9 + t] = v[o];
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tc_dealloc(tmem, 128);
+}
+
 // out[j] = sum over nblk partial rows (fixed order); row stride `stride`
 __global__ void reduce_rows_kernel(int64_t count, int nblk, int64_t stride, const float *__restrict__ part,
                                    float *__restrict__ out) {
@@ -293,6 +546,9 @@ struct ot_cnn {
     cudaStream_t st = nullptr;
     float *w = nullptr, *m = nullptr, *v = nullptr;   // FP32 master weights and Adam moments
     __nv_bfloat16 *wb = nullptr;                      // BF16 copy
+    __nv_bfloat16 *wop = nullptr;   // tensor-core weight operands of layers 1-3 (forward, mirrored)
+    int *derr = nullptr;            // set by a tensor-core kernel whose wait gave up
+    int sms = 1;
     // activations of the last forward (B, k)
     int B = 0, k = 0;
     int64_t cap_pix = 0;
@@ -300,6 +556,7 @@ struct ot_cnn {
     float *z[kLayers] = {};           // conv outputs (z[4] = prediction)
     float *r[kLayers] = {};           // RMS of the normalised blocks
     float *g1 = nullptr, *g2 = nullptr;  // gradient ping-pong (B x C x HW)
+    __nv_bfloat16 *gb = nullptr;         // BF16 copy of a gradient (the data gradient's operand)
     float *part = nullptr;
     int64_t cap_part = 0;
     float *lpart = nullptr;
@@ -348,7 +605,9 @@ void free_acts(ot_cnn *c) {
     }
     if (c->g1) cudaFree(c->g1);
     if (c->g2) cudaFree(c->g2);
+    if (c->gb) cudaFree(c->gb);
     c->g1 = c->g2 = nullptr;
+    c->gb = nullptr;
     c->cap_pix = 0;
 }
 
@@ -365,11 +624,12 @@ int ensure_acts(ot_cnn *c, int B, int k) {
                 return cnn_fail(c, OT_ERR_OOM, "ot_cnn: activation allocation failed");
         }
         if (cudaMalloc((void **)&c->g1, sizeof(float) * C * pix) != cudaSuccess ||
-            cudaMalloc((void **)&c->g2, sizeof(float) * C * pix) != cudaSuccess)
+            cudaMalloc((void **)&c->g2, sizeof(float) * C * pix) != cudaSuccess ||
+            cudaMalloc((void **)&c->gb, sizeof(__nv_bfloat16) * C * pix) != cudaSuccess)
             return cnn_fail(c, OT_ERR_OOM, "ot_cnn: gradient allocation failed");
         c->cap_pix = pix;
     }
-    const int64_t nblk = (pix + kChunk - 1) / kChunk;
+    const int64_t nblk = (pix + kWgK - 1) / kWgK;   // chunk partials (128-pixel chunks, the most)
     const int64_t need = nblk * ((int64_t)c->ch * c->ch * 9 + c->ch) + blocks_for(pix, kPix) * (int64_t)c->ch;
     if (need > c->cap_part) {
         if (c->part) cudaFree(c->part);
@@ -388,6 +648,24 @@ int refresh_bf16(ot_cnn *c) {
     to_bf16_kernel<<<blocks_for(c->nparam, 256), 256, 0, c->st>>>(c->nparam, c->w, c->wb);
     if (cudaGetLastError() != cudaSuccess) return cnn_fail(c, OT_ERR_CUDA, "ot_cnn: launch failed");
     g_launches.fetch_add(1, std::memory_order_relaxed);
+    conv_wop_kernel<<<blocks_for(6 * kCvN * kCvK, 256), 256, 0, c->st>>>(c->w, c->L[1].W, c->L[2].W, c->L[3].W, c->wop);
+    if (cudaGetLastError() != cudaSuccess) return cnn_fail(c, OT_ERR_CUDA, "ot_cnn: launch failed");
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return OT_OK;
+}
+
+// tensor-core weight operand of 32 -> 32 layer l (1..3), forward or mirrored
+const __nv_bfloat16 *wop_of(const ot_cnn *c, int l, int mirrored) {
+    return c->wop + (int64_t)(2 * (l - 1) + mirrored) * kCvN * kCvK;
+}
+
+// a tensor-core kernel's wait that gave up (bounded waits; the flag is read after a synchronisation)
+int check_tc(ot_cnn *c, const char *where) {
+    int h = 0;
+    if (cudaMemcpyAsync(&h, c->derr, sizeof(int), cudaMemcpyDeviceToHost, c->st) != cudaSuccess ||
+        cudaStreamSynchronize(c->st) != cudaSuccess)
+        return cnn_fail(c, OT_ERR_CUDA, std::string(where) + ": synchronisation failed");
+    if (h) return cnn_fail(c, OT_ERR_TIMEOUT, std::string(where) + ": a tensor-core wait gave up");
     return OT_OK;
 }
 
@@ -423,13 +701,25 @@ int ot_cnn_create(int32_t channels, const float *params, void *stream, ot_cnn_t 
     const size_t nb = sizeof(float) * c->nparam;
     if (cudaMalloc((void **)&c->w, nb) != cudaSuccess || cudaMalloc((void **)&c->m, nb) != cudaSuccess ||
         cudaMalloc((void **)&c->v, nb) != cudaSuccess ||
-        cudaMalloc((void **)&c->wb, sizeof(__nv_bfloat16) * c->nparam) != cudaSuccess) {
+        cudaMalloc((void **)&c->wb, sizeof(__nv_bfloat16) * c->nparam) != cudaSuccess ||
+        cudaMalloc((void **)&c->wop, sizeof(__nv_bfloat16) * 6 * kCvN * kCvK) != cudaSuccess ||
+        cudaMalloc((void **)&c->derr, sizeof(int)) != cudaSuccess) {
         ot_cnn_destroy(c);
         return cnn_fail(nullptr, OT_ERR_OOM, "ot_cnn_create: weight allocation failed");
     }
     cudaMemcpyAsync(c->w, params, nb, cudaMemcpyHostToDevice, c->st);
     cudaMemsetAsync(c->m, 0, nb, c->st);
     cudaMemsetAsync(c->v, 0, nb, c->st);
+    cudaMemsetAsync(c->derr, 0, sizeof(int), c->st);
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaFuncSetAttribute(conv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kCvSmem) != cudaSuccess ||
+            cudaFuncSetAttribute(conv_wgrad_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kWgSmem) != cudaSuccess) {
+            ot_cnn_destroy(c);
+            return cnn_fail(nullptr, OT_ERR_CUDA, "ot_cnn_create: device query failed");
+        }
+    }
     int rc = refresh_bf16(c);
     if (rc == OT_OK && cudaStreamSynchronize(c->st) != cudaSuccess) rc = cnn_fail(c, OT_ERR_CUDA, "ot_cnn_create: copy failed");
     if (rc != OT_OK) {
@@ -458,6 +748,7 @@ int ot_cnn_forward(ot_cnn_t *c, int32_t batch, int32_t k, const float *x, float 
     to_bf16_kernel<<<blocks_for(2 * pix, 256), 256, 0, st>>>(2 * pix, x, c->h[0]);
     CNN_LAUNCHED(c);
     const unsigned gp = blocks_for(pix, kPix);
+    const unsigned tc_grid = (unsigned)std::min<int64_t>((pix + kCvM - 1) / kCvM, 2LL * c->sms);
     for (int l = 0; l < kLayers; ++l) {
         const Layer &Ly = c->L[l];
         const __nv_bfloat16 *wl = c->wb + Ly.W;
@@ -465,7 +756,8 @@ int ot_cnn_forward(ot_cnn_t *c, int32_t batch, int32_t k, const float *x, float 
         if (l == 0)
             conv_fwd_kernel<2, 32><<<gp, kPix, 0, st>>>(batch, k, k, Ly.dil, c->h[0], wl, bl, c->z[0]);
         else if (l < kLayers - 1)
-            conv_fwd_kernel<32, 32><<<gp, kPix, 0, st>>>(batch, k, k, Ly.dil, c->h[l], wl, bl, c->z[l]);
+            conv_tc_kernel<<<tc_grid, kCvM, kCvSmem, st>>>(batch, k, k, Ly.dil, c->h[l], wop_of(c, l, 0), bl, c->z[l],
+                                                         c->derr);
         else
             conv_fwd_kernel<32, 2><<<gp, kPix, 0, st>>>(batch, k, k, Ly.dil, c->h[l], wl, bl, c->z[l]);
         CNN_LAUNCHED(c);
@@ -476,7 +768,7 @@ int ot_cnn_forward(ot_cnn_t *c, int32_t batch, int32_t k, const float *x, float 
     }
     if (y && cudaMemcpyAsync(y, c->z[kLayers - 1], sizeof(float) * 2 * pix, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
         return cnn_fail(c, OT_ERR_CUDA, "ot_cnn_forward: copy failed");
-    return OT_OK;
+    return check_tc(c, "ot_cnn_forward");
 }
 
 int ot_cnn_loss(ot_cnn_t *c, const float *target, float *dy, float *loss) {
@@ -501,6 +793,8 @@ int ot_cnn_backward(ot_cnn_t *c, const float *dy, float *grad, float *dx) {
     cudaStream_t st = c->st;
     const unsigned gp = blocks_for(pix, kPix);
     const int nchunk = (int)((pix + kChunk - 1) / kChunk);
+    const int nchunk_tc = (int)((pix + kWgK - 1) / kWgK);
+    const unsigned tc_grid = (unsigned)std::min<int64_t>((pix + kCvM - 1) / kCvM, 2LL * c->sms);
     const float *gcur = dy;   // gradient with respect to the current layer's output
     float *bufs[2] = {c->g1, c->g2};
     int flip = 0;
@@ -521,27 +815,31 @@ int ot_cnn_backward(ot_cnn_t *c, const float *dy, float *grad, float *dx) {
         if (l == 0)
             conv_bwd_weight_kernel<2, 32><<<nchunk, 256, 0, st>>>(B, k, k, Ly.dil, c->h[0], dz, c->part);
         else if (l < kLayers - 1)
-            conv_bwd_weight_kernel<32, 32><<<nchunk, 256, 0, st>>>(B, k, k, Ly.dil, c->h[l], dz, c->part);
+            conv_wgrad_tc_kernel<<<nchunk_tc, kCvM, kWgSmem, st>>>(B, k, k, Ly.dil, c->h[l], dz, c->part, c->derr);
         else
             conv_bwd_weight_kernel<32, 2><<<nchunk, 256, 0, st>>>(B, k, k, Ly.dil, c->h[l], dz, c->part);
         CNN_LAUNCHED(c);
         // W and bias are contiguous in the flat layout: one pass over the partial rows
-        reduce_rows_kernel<<<blocks_for(stride, 256), 256, 0, st>>>(stride, nchunk, stride, c->part, grad + Ly.W);
+        const int nparts = (l > 0 && l < kLayers - 1) ? nchunk_tc : nchunk;
+        reduce_rows_kernel<<<blocks_for(stride, 256), 256, 0, st>>>(stride, nparts, stride, c->part, grad + Ly.W);
         CNN_LAUNCHED(c);
         if (l > 0 || dx) {
             float *out = (l == 0) ? dx : bufs[flip];
             flip ^= 1;
             if (l == 0)
                 conv_bwd_data_kernel<2, 32><<<gp, kPix, 0, st>>>(B, k, k, Ly.dil, dz, wl, out);
-            else if (l < kLayers - 1)
-                conv_bwd_data_kernel<32, 32><<<gp, kPix, 0, st>>>(B, k, k, Ly.dil, dz, wl, out);
-            else
+            else if (l < kLayers - 1) {
+                to_bf16_kernel<<<blocks_for(32 * pix, 256), 256, 0, st>>>(32 * pix, dz, c->gb);
+                CNN_LAUNCHED(c);
+                conv_tc_kernel<<<tc_grid, kCvM, kCvSmem, st>>>(B, k, k, Ly.dil, c->gb, wop_of(c, l, 1), nullptr, out,
+                                                             c->derr);
+            } else
                 conv_bwd_data_kernel<32, 2><<<gp, kPix, 0, st>>>(B, k, k, Ly.dil, dz, wl, out);
             CNN_LAUNCHED(c);
             gcur = out;
         }
     }
-    return OT_OK;
+    return check_tc(c, "ot_cnn_backward");
 }
 
 int ot_cnn_adam(ot_cnn_t *c, const float *grad, float lr, float beta1, float beta2, float eps, int32_t step) {
@@ -558,7 +856,8 @@ const char *ot_cnn_last_error(const ot_cnn_t *c) { return c ? c->err.c_str() : g
 void ot_cnn_destroy(ot_cnn_t *c) {
     if (!c) return;
     free_acts(c);
-    for (void *p : {(void *)c->w, (void *)c->m, (void *)c->v, (void *)c->wb, (void *)c->part, (void *)c->lpart})
+    for (void *p : {(void *)c->w, (void *)c->m, (void *)c->v, (void *)c->wb, (void *)c->wop, (void *)c->derr,
+                    (void *)c->part, (void *)c->lpart})
         if (p) cudaFree(p);
     delete c;
 }

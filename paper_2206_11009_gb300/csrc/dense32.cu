@@ -13,6 +13,7 @@
 // The sequence depends on n only, so it is captured once into a CUDA graph.
 #include "dense32.cuh"
 #include "primitives.cuh"
+#include "tc05.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -982,41 +983,14 @@ constexpr int kTcBpiece = kTcN * kP * 4;              // one B piece: 64 KB
 constexpr int kTcSmem = 2 * kTcApiece + 2 * kTcBpiece + 64;
 constexpr int kTcThreads = 160;   // four epilogue warps and one producer warp
 constexpr int kTcAutoN = 8192;    // tc_mode 0: the tensor-core update from this n on
-constexpr long long kTcWaitLimit = 1LL << 24;
-
-__device__ __forceinline__ uint32_t tc_smem_u32(const void *ptr) { return (uint32_t)__cvta_generic_to_shared(ptr); }
-
 __device__ __forceinline__ float tc_tf32(float x) {
     uint32_t r;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
     return __uint_as_float(r);
 }
 
-// shared-memory matrix descriptor: start, leading (K) and stride (M / N) byte offsets >> 4,
-// descriptor version 1 at bit 46, no swizzle
-__device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo) {
-    uint64_t d = (uint64_t)((addr >> 4) & 0x3FFFu);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((128u >> 4) & 0x3FFFu) << 32;
-    d |= (uint64_t)1 << 46;
-    return d;
-}
-
-// kind::tf32 instruction descriptor: D = F32, A = B = TF32, both K-major, N = 64, M = 128
-constexpr uint32_t kTcIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
-                              ((uint32_t)(kTcM >> 4) << 24);
-
-__device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity) {
-    for (long long i = 0; i < kTcWaitLimit; ++i) {
-        uint32_t done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-            " selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
-        if (done) return true;
-    }
-    return false;
-}
+// kind::tf32 instruction descriptor: D = F32, A = B = TF32, both K-major, M = 128, N = 256
+constexpr uint32_t kTcIdesc = tc_idesc(2u, kTcM, kTcN);
 
 // Rows [row0 + b RB, +RB) of an operand, depth 64, split into TF32 hi / lo pieces in the layout
 // above: piece (b, hi) at out + 2 b P, (b, lo) at out + (2 b + 1) P (P = RB * 64 floats).  The
@@ -1088,9 +1062,6 @@ __device__ __forceinline__ int tc_next(int t, int step, int ntiles, int n, int b
 // trailing A = split L D rows, B = split panel rows (256-row blocks); inverse A = split panel rows
 // (128-row blocks), B = split rows of L^-1.
 constexpr int kTcWarps = 5;
-__device__ __forceinline__ void tc_arrive(uint32_t mbar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(mbar) : "memory");
-}
 
 __global__ void __launch_bounds__(kTcWarps * 32, 1)
 d32_tc_update_kernel(int n, int ld, int base, int base2, int T, const float *__restrict__ LDs,

@@ -51,8 +51,12 @@ def test_features_match_reference():
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("k,B", [(12, 2), (19, 3)])
+@pytest.mark.parametrize("k,B", [(12, 2), (19, 3), (64, 12)])
 def test_forward_backward_match_reference(k, B):
+    """Ragged tiles (288 and 1,083 pixels: tiles of 128 pixels, chunks of 128 for the weight
+    gradient), dilations up to 8 on a 12-pixel image (most taps outside), and 64x64 x 12 = 384 tiles:
+    more than the 2 x 152 persistent CTAs of the tensor-core convolution, so some take a second
+    tile (the mbarrier's second phase)."""
     from paper_2206_11009_gb300.learn import WarmNet
     th = _theta(11)
     rng = np.random.default_rng(k)
