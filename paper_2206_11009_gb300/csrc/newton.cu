@@ -227,6 +227,8 @@ struct PcgArgs {
     double tol;
     int maxit;
     double *scal;  // SC_PCG_ITERS, SC_PCG_RELRES
+    int *bnd;      // lane-group boundaries: rows at bnd[0 ..], columns at bnd[bnd_cap ..]
+    int64_t bnd_cap;
 };
 
 constexpr int kPcgT = 512;   // threads per PCG block
@@ -451,7 +453,11 @@ __device__ __forceinline__ void sum_partials(const double *part, unsigned G, int
 }
 
 // Jacobi-preconditioned CG on S_M, persistent cooperative kernel.  Rows and columns are handled
-// by lane groups of g threads (g ~ the average row/column length).  With p_k = z_k + beta_k p_{k-1}
+// by lane groups of g threads (g ~ the average row/column length), each group a contiguous range
+// of rows (and one of columns) of equal weight, pairs + g per row (the per-row reduction costs
+// about one trip): group q starts at the first row i with rp[i] + g i >= q (psi + g m) / ngrp.
+// Contiguous ranges keep neighbouring pixels together (the gathers stay local) and bound a group's
+// excess over the mean by one row.  With p_k = z_k + beta_k p_{k-1}
 // formed on the fly from z and the previous direction (double buffer), one iteration is
 //   row pass:    w_i = M_i^-1 sum_j theta_ij p_j                                   | barrier
 //   column pass: p_j stored; q_j = sum_i theta_ij (p_j - w_i); partial p.q           | barrier
@@ -467,9 +473,30 @@ __global__ void __launch_bounds__(kPcgT) pcg_kernel(PcgArgs<T> A, int g) {
     const int64_t stride = (int64_t)G * blockDim.x;
     const int lg = threadIdx.x & (g - 1);                 // lane within its group
     const int64_t grp = tid / g, ngrp = stride / g;
-    const int64_t wgrp0 = (tid & ~(int64_t)31) / g;          // first group of this warp
     double *P0 = A.part, *P1 = A.part + G, *P2 = A.part + 2 * G;
 
+    // the group boundaries (lane 0 of each group searches its own; group 0 also writes the ends)
+    if (lg == 0) {
+        const int64_t dr = (int64_t)A.rp[m] + (int64_t)g * m, dc = (int64_t)A.cp[n] + (int64_t)g * n;
+        const int64_t tr = grp * dr / ngrp, tc = grp * dc / ngrp;
+        int64_t lo = 0, hi = m;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if ((int64_t)A.rp[mid] + (int64_t)g * mid >= tr) hi = mid; else lo = mid + 1;
+        }
+        A.bnd[grp] = (int)lo;
+        lo = 0;
+        hi = n;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if ((int64_t)A.cp[mid] + (int64_t)g * mid >= tc) hi = mid; else lo = mid + 1;
+        }
+        A.bnd[A.bnd_cap + grp] = (int)lo;
+        if (grp == 0) {
+            A.bnd[ngrp] = m;
+            A.bnd[A.bnd_cap + ngrp] = n;
+        }
+    }
     double bb = 0, rz = 0;
     for (int64_t j = tid; j < n; j += stride) {
         const T bj = A.b[j];
@@ -490,6 +517,10 @@ __global__ void __launch_bounds__(kPcgT) pcg_kernel(PcgArgs<T> A, int g) {
     bb = s_val[0];
     rz = s_val[1];
     const double tol2 = A.tol * A.tol * bb;
+    // this group's rows [r0, r0 + nr) and columns [c0, c0 + nc); trip counts uniform over the warp
+    const int r0 = A.bnd[grp], nr = A.bnd[grp + 1] - r0;
+    const int c0 = A.bnd[A.bnd_cap + grp], nc = A.bnd[A.bnd_cap + grp + 1] - c0;
+    const int rtrips = __reduce_max_sync(0xffffffffu, nr), ctrips = __reduce_max_sync(0xffffffffu, nc);
     int it = 0;
     double rr = bb;
     T beta = (T)0;
@@ -497,15 +528,16 @@ __global__ void __launch_bounds__(kPcgT) pcg_kernel(PcgArgs<T> A, int g) {
     if (bb > 0.0 && rz > 0.0) {
         for (it = 0; it < A.maxit;) {
             // row pass with p = z + beta pprev (the trip count is uniform across a warp: groups
-            // past the end contribute zero but still take part in the shuffles)
-            // two rows per group and trip (rows i and i + ngrp), their loads interleaved: the
+            // past their range contribute zero but still take part in the shuffles)
+            // two rows per group and trip (rows i and i + 1), their loads interleaved: the
             // passes are bound by the latency of the index -> gather chains, not by bandwidth
-            for (int64_t i0 = wgrp0; i0 < m; i0 += 2 * ngrp) {
-                const int64_t ia = i0 + (grp - wgrp0), ib = ia + ngrp;
+            for (int t = 0; t < rtrips; t += 2) {
+                const int ia = r0 + t, ib = ia + 1;
+                const bool va = t < nr, vb = t + 1 < nr;
                 T acca = (T)0, accb = (T)0;
                 int ea = 0, ha = 0, eb = 0, hb = 0;
-                if (ia < m) { ea = A.rp[ia] + lg; ha = A.rp[ia + 1]; }
-                if (ib < m) { eb = A.rp[ib] + lg; hb = A.rp[ib + 1]; }
+                if (va) { ea = A.rp[ia] + lg; ha = A.rp[ia + 1]; }
+                if (vb) { eb = A.rp[ib] + lg; hb = A.rp[ib + 1]; }
                 while (ea < ha || eb < hb) {
                     if (ea < ha) {
                         const int j = A.sj[ea];
@@ -520,18 +552,19 @@ __global__ void __launch_bounds__(kPcgT) pcg_kernel(PcgArgs<T> A, int g) {
                 }
                 acca = group_sum(acca, g);
                 accb = group_sum(accb, g);
-                if (lg == 0 && ia < m) A.w[ia] = A.Minv[ia] * acca;
-                if (lg == 0 && ib < m) A.w[ib] = A.Minv[ib] * accb;
+                if (lg == 0 && va) A.w[ia] = A.Minv[ia] * acca;
+                if (lg == 0 && vb) A.w[ib] = A.Minv[ib] * accb;
             }
             if (!grid_barrier(A.bar, G, A.err)) return;
             // column pass (two columns per group and trip)
             double pq = 0;
-            for (int64_t j0 = wgrp0; j0 < n; j0 += 2 * ngrp) {
-                const int64_t ja = j0 + (grp - wgrp0), jb = ja + ngrp;
+            for (int t = 0; t < ctrips; t += 2) {
+                const int ja = c0 + t, jb = ja + 1;
+                const bool va = t < nc, vb = t + 1 < nc;
                 T pa = (T)0, pb2 = (T)0, acca = (T)0, accb = (T)0;
                 int ka = 0, ha = 0, kb = 0, hb = 0;
-                if (ja < n) { pa = A.z[ja] + beta * pprev[ja]; ka = A.cp[ja] + lg; ha = A.cp[ja + 1]; }
-                if (jb < n) { pb2 = A.z[jb] + beta * pprev[jb]; kb = A.cp[jb] + lg; hb = A.cp[jb + 1]; }
+                if (va) { pa = A.z[ja] + beta * pprev[ja]; ka = A.cp[ja] + lg; ha = A.cp[ja + 1]; }
+                if (vb) { pb2 = A.z[jb] + beta * pprev[jb]; kb = A.cp[jb] + lg; hb = A.cp[jb + 1]; }
                 while (ka < ha || kb < hb) {
                     if (ka < ha) {
                         acca += A.thc[ka] * (pa - A.w[A.crow[ka]]);
@@ -544,12 +577,12 @@ __global__ void __launch_bounds__(kPcgT) pcg_kernel(PcgArgs<T> A, int g) {
                 }
                 acca = group_sum(acca, g);
                 accb = group_sum(accb, g);
-                if (lg == 0 && ja < n) {
+                if (lg == 0 && va) {
                     A.q[ja] = acca;
                     pcur[ja] = pa;
                     pq += (double)pa * (double)acca;
                 }
-                if (lg == 0 && jb < n) {
+                if (lg == 0 && vb) {
                     A.q[jb] = accb;
                     pcur[jb] = pb2;
                     pq += (double)pb2 * (double)accb;
@@ -866,12 +899,14 @@ Error launch_pcg(Newton &W, const Support &S, const T *th, const T *thc, const T
     const int maxg = std::max(1, per_sm) * W.num_sms;
     int G = W.pcg_grid > 0 ? W.pcg_grid : (int)std::max<int64_t>(1, ceil_div(threads, kPcgT));
     G = std::min(G, std::min(maxg, kMaxPartBlocks / 3));
+    // the boundary arrays hold ngrp + 1 = G kPcgT / g + 1 entries per half
+    G = (int)std::min<int64_t>(G, std::max<int64_t>(1, (W.pcg_bnd_cap - 1) * g / kPcgT));
     OT_CUDA(cudaMemsetAsync(W.bar, 0, 2 * sizeof(unsigned), st));
     OT_CUDA(cudaMemsetAsync(W.err, 0, sizeof(int), st));
     T *pb = (T *)W.pcg_pb;
     if (sizeof(T) == 4) pb = (T *)W.pcg_pb32;
     PcgArgs<T> A{W.m, W.n, S.row_ptr, S.j, S.col_ptr, S.col_row, th, thc, Minv, Dinv, b, x, r, z, p, pb, q, w,
-                 W.part, W.bar, W.err, tol, maxit, W.scal};
+                 W.part, W.bar, W.err, tol, maxit, W.scal, W.pcg_bnd, W.pcg_bnd_cap};
     const int kid = sizeof(T) == 8 ? KT_PCG64 : KT_PCG32;
     const int R = W.pcg_cluster;
     cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -1726,6 +1761,9 @@ Error newton_alloc(Newton &W, int32_t m, int32_t n, int64_t cap, int num_sms) {
         OT_TRY(dev_alloc(p, n));
     for (float **p : {&W.Dinv32, &W.b32, &W.x32, &W.r32, &W.z32, &W.p32, &W.q32, &W.pcg_pb32}) OT_TRY(dev_alloc(p, n));
     OT_TRY(dev_alloc(&W.pcg_pb, n));
+    // grid PCG lane groups: G kPcgT / g <= (blocks per SM <= 2048 / kPcgT) x SMs x kPcgT
+    W.pcg_bnd_cap = (int64_t)(2048 / kPcgT) * std::max(num_sms, 1) * kPcgT + 1;
+    OT_TRY(dev_alloc(&W.pcg_bnd, 2 * W.pcg_bnd_cap));
     OT_TRY(dev_alloc(&W.parent, (int64_t)m + n));
     OT_TRY(dev_alloc(&W.comp_sum, (int64_t)m + n));
     OT_TRY(dev_alloc(&W.comp_cnt, (int64_t)m + n));
@@ -1758,7 +1796,7 @@ void newton_free(Newton &W) {
                     W.theta_col, W.theta32_col, W.flag, W.r1a, W.beta1, W.M, W.Minv, W.du, W.du2, W.du3, W.w64,
                     W.Minv32, W.w32, W.r1b, W.beta2, W.N, W.Dinv, W.Sdiag, W.rhs, W.dv, W.dv2, W.dv3, W.res64, W.y64,
                     W.x64, W.r64, W.z64, W.p64, W.q64, W.Dinv32, W.b32, W.x32, W.r32, W.z32, W.p32, W.q32, W.pcg_pb, W.pcg_pb32,
-                    W.parent, W.comp_sum, W.comp_cnt, W.part, W.scal, W.bar, W.err};
+                    W.pcg_bnd, W.parent, W.comp_sum, W.comp_cnt, W.part, W.scal, W.bar, W.err};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (W.hscal) cudaFreeHost(W.hscal);

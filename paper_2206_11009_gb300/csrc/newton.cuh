@@ -55,6 +55,8 @@ struct Newton {
     double last_pcg_ms = 0.0;
     double *pcg_pb = nullptr;     // second direction buffer of the PCG (fp64 / fp32)
     float *pcg_pb32 = nullptr;
+    int *pcg_bnd = nullptr;       // grid PCG: first row (then first column) of each lane group
+    int64_t pcg_bnd_cap = 0;      // entries per half of pcg_bnd
     double pcg_bytes_per_iter = 0.0;
     int pcg_cluster = 0;       // CTAs of the FP32 cluster PCG (0: not available on this device)
     int pcg_cluster_smem = 0;  // dynamic shared memory of one of its CTAs
