@@ -542,9 +542,9 @@ def kernel_table(ktimes, pk_d, src):
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel as it stands, and the
 # summary under profiles/ that gives the command; a kernel changed since then reports null.
 NCU_TRAFFIC = {
-    # one FP32 factorisation (n = 4096, all 190 kernel launches of its graph): 1,600.6 MB read +
-    # 0.23 MB written; profiles/d32_factor_64x64.md
-    "d32_factor": 1.6008e9,
+    # one FP32 factorisation (n = 4096, all 190 kernel launches of its graph): 1,600.5 MB read +
+    # 0.15 MB written; profiles/d32_factor_64x64.md
+    "d32_factor": 1.6007e9,
 }
 
 

@@ -273,7 +273,7 @@ __device__ __forceinline__ DiagSmem diag_smem(float *buf) {
 // are read through L2 (__ldcg): in the fused step kernel other CTAs of the same launch wrote them.
 __device__ __forceinline__ void d32_diag_block(const DiagSmem &m, int ld, int k, int bs, float *__restrict__ A,
                                                float *__restrict__ D, const float *__restrict__ d0,
-                                               const float *__restrict__ csum, int np, float eps,
+                                               const float *__restrict__ csum, int np, int per, float eps,
                                                float *__restrict__ Linv) {
     float (*S)[kP + 1] = m.S;
     float (*Xs)[kP + 1] = m.Xs;
@@ -292,8 +292,14 @@ __device__ __forceinline__ void d32_diag_block(const DiagSmem &m, int ld, int k,
     }
 #pragma unroll
     for (int q = 0; q < kPer; ++q) {
-        const int t = (int)threadIdx.x + q * kTT;
-        cv[q] = t < nq0 * kP ? __ldcg(csum + t) : 0.f;
+        // strip t / kP's sum: its per (1 or 2) partial rows added in order
+        const int t = (int)threadIdx.x + q * kTT, row = t / kP, col = t % kP;
+        float v = 0.f;
+        if (t < nq0 * kP) {
+            v = __ldcg(csum + (size_t)(row * per) * kP + col);
+            if (per == 2) v += __ldcg(csum + (size_t)(row * per + 1) * kP + col);
+        }
+        cv[q] = v;
     }
     const float d0v = (int)threadIdx.x < bs ? d0[k + threadIdx.x] : 0.f;
 #pragma unroll
@@ -317,8 +323,12 @@ __device__ __forceinline__ void d32_diag_block(const DiagSmem &m, int ld, int k,
     }
     for (int q0 = kP; q0 < np; q0 += kP) {
         const int nq = min(kP, np - q0);
-        for (int t = threadIdx.x; t < nq * kP; t += blockDim.x)
-            Xs[t / kP][t % kP] = __ldcg(csum + (q0 + t / kP) * kP + t % kP);
+        for (int t = threadIdx.x; t < nq * kP; t += blockDim.x) {
+            const int row = q0 + t / kP, col = t % kP;
+            float v = __ldcg(csum + (size_t)(row * per) * kP + col);
+            if (per == 2) v += __ldcg(csum + (size_t)(row * per + 1) * kP + col);
+            Xs[t / kP][col] = v;
+        }
         __syncthreads();
         if (threadIdx.x < kP && threadIdx.x < bs)
             for (int q = 0; q < nq; ++q) gs += Xs[q][threadIdx.x];
@@ -448,7 +458,7 @@ __device__ __forceinline__ void d32_diag_block(const DiagSmem &m, int ld, int k,
 // kernel, whose other CTAs read those rows of A unscaled) go to A
 __global__ void __launch_bounds__(kTT)
 d32_diag_kernel(int ld, int k, int bs, float *__restrict__ A, float *__restrict__ D, const float *__restrict__ d0,
-                const float *__restrict__ csum, int np, float eps, float *__restrict__ Linv,
+                const float *__restrict__ csum, int np, int per, float eps, float *__restrict__ Linv,
                 const float *__restrict__ L0) {
     __shared__ __align__(16) float buf[kDiagSmem / 4];
     if (L0)
@@ -456,7 +466,7 @@ d32_diag_kernel(int ld, int k, int bs, float *__restrict__ A, float *__restrict_
             const int r = t % kP, j = t / kP;
             if (r < bs) A[(size_t)(k - kP + j) * ld + k + r] = L0[j * kP + r];
         }
-    d32_diag_block(diag_smem(buf), ld, k, bs, A, D, d0, csum, np, eps, Linv);
+    d32_diag_block(diag_smem(buf), ld, k, bs, A, D, d0, csum, np, per, eps, Linv);
 }
 
 // rows r in [k+64, n) of the panel (bs = 64 whenever rows remain below the block): 64 rows per
@@ -785,17 +795,23 @@ d32_update_kernel(int n, int ld, int k, int skip, float *__restrict__ A, float *
 
 // ------------------------------------------------------------------ fused panel step (SIMT path)
 // One launch per panel k (bs = 64, base = k + 64 < n) does what the next diagonal block waits for,
-// so the panel-to-panel chain is two kernels (this one and the next diagonal block):
-//   strip CTA rb (rows R = base + 64 rb ..): LD[R] = A21[R] L11^-T and L21[R] = LD[R] D1^-1 (the
-//     panel), then the next panel's 64 columns A22[R, R0] -= LD[R] L21[R0]^T (R0 = the next
-//     panel's rows; L21[R0] recomputed in every CTA from the unscaled A21[R0]) together with the
-//     previous panel's update of the same columns, -= LD'[R] L21'[R0]^T, and the fixed-order
-//     partial column sums below the next diagonal block;
-//   X CTA cb (columns C = 64 cb .. of block row k of L^-1): X[k, C] = L11^-1 B[k, C] (the block row),
-//     then X[R0, C] -= L21[R0] X[k, C] + L21'[R0] X[k - 64, C] (the previous panel's part);
+// so the panel-to-panel chain is two kernels (this one and the next diagonal block).  Its units are
+// 64-row strips and 64-column blocks, each split over two CTAs (CTA 2 s + h takes half h of unit s),
+// so that a CTA's dependent products are 2.5 instead of 4 64x64x64 ones and about 130 CTAs share the
+// SMs instead of 65:
+//   strip s (rows R = base + 64 s ..), half rows R_h = R[32 h, 32 h + 32): LD[R_h] = A21[R_h] L11^-T
+//     and L21[R_h] = LD[R_h] D1^-1 (the panel), then the next panel's 64 columns A22[R_h, R0] -=
+//     LD[R_h] L21[R0]^T (R0 = the next panel's rows; L21[R0] recomputed in every CTA from the
+//     unscaled A21[R0]) together with the previous panel's update of the same columns, -= LD'[R_h]
+//     L21'[R0]^T, and the fixed-order partial column sums below the next diagonal block (one row of
+//     csum per half: row 2 s + h);
+//   X block s - ts (columns C = 64 (s - ts) .. of block row k of L^-1), half columns C_h:
+//     X[k, C_h] = L11^-1 B[k, C_h] (the block row), then X[R0, C_h] -= L21[R0] X[k, C_h] +
+//     L21'[R0] X[k - 64, C_h] (the previous panel's part);
 // L21[R0] goes to A with the next diagonal block's kernel (the other CTAs read A21[R0] unscaled).
 // What remains of both updates (rows and columns from base + 128) is d32_update_kernel's (skip 2).
 constexpr int kStepSmem = (5 * kP * kP + kP) * 4;
+constexpr int kHalf = kP / 2;
 
 // acc[u][w] += sum_l a[l][tr * 4 + u] b[l][tc * 4 + w] (64 x 64 operands, [depth][index])
 __device__ __forceinline__ void mm64(const float *__restrict__ a, const float *__restrict__ b, float (&acc)[4][4],
@@ -812,11 +828,43 @@ __device__ __forceinline__ void mm64(const float *__restrict__ a, const float *_
     }
 }
 
-// tile[l][r] = G[(col0 + l) ld + row0 + r] for row0 + r < rlim, else 0 (row0 a multiple of 4)
+// 32 x 64 outputs: acc[u][w] += sum_l a[l][tr * 2 + u] b[l][tc * 4 + w] (a's first 32 indices)
+__device__ __forceinline__ void mm_r32(const float *__restrict__ a, const float *__restrict__ b, float (&acc)[2][4],
+                                       int tr, int tc) {
+#pragma unroll 16
+    for (int l = 0; l < kP; ++l) {
+        const float2 x = *(const float2 *)(a + l * kP + tr * 2);
+        const float4 y = *(const float4 *)(b + l * kP + tc * 4);
+        const float av[2] = {x.x, x.y}, bv[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+#pragma unroll
+            for (int w = 0; w < 4; ++w) acc[u][w] += av[u] * bv[w];
+    }
+}
+
+// 64 x 32 outputs: acc[u][w] += sum_l a[l][tr * 4 + u] b[l][tc * 2 + w] (b's first 32 indices)
+__device__ __forceinline__ void mm_c32(const float *__restrict__ a, const float *__restrict__ b, float (&acc)[4][2],
+                                       int tr, int tc) {
+#pragma unroll 16
+    for (int l = 0; l < kP; ++l) {
+        const float4 x = *(const float4 *)(a + l * kP + tr * 4);
+        const float2 y = *(const float2 *)(b + l * kP + tc * 2);
+        const float av[4] = {x.x, x.y, x.z, x.w}, bv[2] = {y.x, y.y};
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int w = 0; w < 2; ++w) acc[u][w] += av[u] * bv[w];
+    }
+}
+
+// tile[l][r] = G[(col0 + l) ld + row0 + r] for r < R and row0 + r < rlim, else 0 (row0 a multiple
+// of 4; depth 64, tile stride 64)
+template <int R>
 __device__ __forceinline__ void load_cm(float *__restrict__ tile, const float *__restrict__ G, int ld, int col0,
                                         int row0, int rlim) {
-    for (int t = threadIdx.x; t < kP * (kP / 4); t += blockDim.x) {
-        const int l = t / (kP / 4), q = (t % (kP / 4)) * 4;
+    for (int t = threadIdx.x; t < kP * (R / 4); t += blockDim.x) {
+        const int l = t / (R / 4), q = (t % (R / 4)) * 4;
         const float *src = G + (size_t)(col0 + l) * ld + row0 + q;
         float4 v;
         if (row0 + q + 4 <= rlim) v = *(const float4 *)src;
@@ -830,11 +878,13 @@ __device__ __forceinline__ void load_cm(float *__restrict__ tile, const float *_
     }
 }
 
-// tile[l][c] = X(row0 + l, c0 + c) = X[(c0 + c) ld + row0 + l] for c0 + c < climit, else 0
+// tile[l][c] = X(row0 + l, c0 + c) = X[(c0 + c) ld + row0 + l] for c < C and c0 + c < climit, else
+// 0 (depth 64, tile stride 64)
+template <int C>
 __device__ __forceinline__ void load_rows_of_x(float *__restrict__ tile, const float *__restrict__ X, int ld,
                                                int row0, int c0, int climit) {
-    for (int t = threadIdx.x; t < kP * (kP / 4); t += blockDim.x) {
-        const int c = t % kP, lq = (t / kP) * 4;
+    for (int t = threadIdx.x; t < C * (kP / 4); t += blockDim.x) {
+        const int c = t % C, lq = (t / C) * 4;
         float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
         if (c0 + c < climit) w = *(const float4 *)(X + (size_t)(c0 + c) * ld + row0 + lq);
         tile[(lq + 0) * kP + c] = w.x;
@@ -853,7 +903,8 @@ d32_step_kernel(int n, int ld, int k, float *__restrict__ A, float *__restrict__
     float *idv = sm + 5 * kP * kP;
     const int base = k + kP;
     const int ts = (n - base + kP - 1) / kP;
-    const bool strip = (int)blockIdx.x < ts;
+    const int unit = (int)blockIdx.x >> 1, h = (int)blockIdx.x & 1;
+    const bool strip = unit < ts;
     const bool prev = k > 0;
     const int tr = threadIdx.x & 15, tc = threadIdx.x >> 4;
     // Lt[l][j] = (L11^-1)_jl; idv = D1^+ (0 for grounded pivots)
@@ -865,22 +916,38 @@ d32_step_kernel(int n, int ld, int k, float *__restrict__ A, float *__restrict__
         const float dj = D[k + threadIdx.x];
         idv[threadIdx.x] = isinf(dj) ? 0.f : 1.f / dj;
     }
-    float acc[4][4], acc2[4][4], acc3[4][4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int w = 0; w < 4; ++w) acc[u][w] = acc2[u][w] = acc3[u][w] = 0.f;
     if (strip) {
-        const int rb = blockIdx.x, r0 = base + rb * kP;
-        load_cm(T1, A, ld, k, r0, n);                         // A21[R]       [l][r]
-        if (rb > 0) load_cm(T2, A, ld, k, base, n);           // A21[R0]      [l][c]
+        const int rb = unit, rh = base + rb * kP + h * kHalf;   // this half's first row
+        float acc[2][4], acc2[4][4], acc3[2][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                acc2[u][w] = 0.f;
+                if (u < 2) acc[u][w] = acc3[u][w] = 0.f;
+            }
+        // the A22[R_h, R0] entries this thread updates, loaded with the operands (no other CTA of
+        // this launch, and no rest-update running beside it, writes them)
+        float cur[2][4];
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const int c = base + tc * 4 + w;
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int r = rh + tr * 2 + u;
+                cur[u][w] = (c < n && r < n && r > c) ? A[(size_t)c * ld + r] : 0.f;
+            }
+        }
+        if (rb > 0) load_cm<kHalf>(T1, A, ld, k, rh, n);       // A21[R_h]     [l][r], r < 32
+        load_cm<kP>(T2, A, ld, k, base, n);                     // A21[R0]      [l][c]
         if (prev) {
-            load_cm(T3, LDprev, ld, 0, r0, n);                // LD'[R]       [j][r]
-            load_cm(T4, A, ld, k - kP, base, n);              // L21'[R0]     [j][c]
+            load_cm<kHalf>(T3, LDprev, ld, 0, rh, n);           // LD'[R_h]     [j][r]
+            load_cm<kP>(T4, A, ld, k - kP, base, n);            // L21'[R0]     [j][c]
         }
         __syncthreads();
-        mm64(T1, Lt, acc, tr, tc);                            // LD(r, j), r = tr*4+u, j = tc*4+w
-        if (rb > 0) mm64(T2, Lt, acc2, tr, tc);               // LD(R0_r, j)
+        // LD(R_h row tr*2+u, j = tc*4+w) (the first strip's rows are R0's: read from T2)
+        mm_r32(rb > 0 ? T1 : T2 + h * kHalf, Lt, acc, tr, tc);
+        mm64(T2, Lt, acc2, tr, tc);                             // LD(R0 row tr*4+u, j = tc*4+w)
         __syncthreads();
 #pragma unroll
         for (int w = 0; w < 4; ++w) {
@@ -888,32 +955,33 @@ d32_step_kernel(int n, int ld, int k, float *__restrict__ A, float *__restrict__
             const float id = idv[j];
             const bool inf = id == 0.f;
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int r = r0 + tr * 4 + u;
+            for (int u = 0; u < 2; ++u) {
+                const int rr = tr * 2 + u, r = rh + rr;
                 const float ldv = inf ? 0.f : acc[u][w];
                 if (r < n) {
                     LDc[(size_t)j * ld + r] = ldv;
-                    if (rb == 0) L0buf[j * kP + tr * 4 + u] = acc[u][w] * id;
+                    if (rb == 0) L0buf[j * kP + h * kHalf + rr] = acc[u][w] * id;
                     else A[(size_t)(k + j) * ld + r] = acc[u][w] * id;
                 }
-                T1[j * kP + tr * 4 + u] = ldv;                                 // A operand [j][r]
-                T2[j * kP + tr * 4 + u] = (rb == 0 ? acc[u][w] : acc2[u][w]) * id;  // B operand [j][c]
+                T1[j * kP + rr] = ldv;                                      // A operand [j][r]
             }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) T2[j * kP + tr * 4 + u] = acc2[u][w] * id;   // B operand [j][c]
         }
         __syncthreads();
-        mm64(T1, T2, acc3, tr, tc);
-        if (prev) mm64(T3, T4, acc3, tr, tc);
-        // A22[R, R0] -= acc3 below the diagonal; column sums of the rows below the next block
+        mm_r32(T1, T2, acc3, tr, tc);
+        if (prev) mm_r32(T3, T4, acc3, tr, tc);
+        // A22[R_h, R0] -= acc3 below the diagonal; column sums of the rows below the next block
         float cs[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int w = 0; w < 4; ++w) {
             const int c = base + tc * 4 + w;
             if (c >= n) continue;
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int r = r0 + tr * 4 + u;
+            for (int u = 0; u < 2; ++u) {
+                const int r = rh + tr * 2 + u;
                 if (r < n && r > c) {
-                    const float v = A[(size_t)c * ld + r] - acc3[u][w];
+                    const float v = cur[u][w] - acc3[u][w];
                     A[(size_t)c * ld + r] = v;
                     if (r >= base + kP) cs[w] += v;
                 }
@@ -925,42 +993,61 @@ d32_step_kernel(int n, int ld, int k, float *__restrict__ A, float *__restrict__
             float v = cs[w];
 #pragma unroll
             for (int o = 1; o < 16; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (tr == 0) csum[(size_t)rb * kP + tc * 4 + w] = v;
+            if (tr == 0) csum[(size_t)(2 * rb + h) * kP + tc * 4 + w] = v;
         }
     } else {
-        const int cb = (int)blockIdx.x - ts, c0 = cb * kP;
+        const int cb = unit - ts, c0 = cb * kP, ch = c0 + h * kHalf;   // this half's first column
         const bool before = c0 < k;                           // columns left of the diagonal block
-        if (before) load_rows_of_x(T1, X, ld, k, c0, k);      // B[k, C]      [l][c]
-        load_cm(T2, A, ld, k, base, n);                       // A21[R0]      [l][r]
+        float acc[4][2], acc2[4][4], acc3[4][2];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                acc2[u][w] = 0.f;
+                if (w < 2) acc[u][w] = acc3[u][w] = 0.f;
+            }
+        // the X[R0, C_h] entries this thread updates, loaded with the operands
+        float cur[4][2];
+#pragma unroll
+        for (int w = 0; w < 2; ++w)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int r = base + tr * 4 + u;
+                cur[u][w] = r < n ? X[(size_t)(ch + tc * 2 + w) * ld + r] : 0.f;
+            }
+        if (before) load_rows_of_x<kHalf>(T1, X, ld, k, ch, k);     // B[k, C_h]      [l][c], c < 32
+        load_cm<kP>(T2, A, ld, k, base, n);                          // A21[R0]        [l][r]
         if (prev && before) {
-            load_cm(T3, A, ld, k - kP, base, n);              // L21'[R0]     [j][r]
-            load_rows_of_x(T4, X, ld, k - kP, c0, k);         // X[k - 64, C] [j][c]
+            load_cm<kP>(T3, A, ld, k - kP, base, n);                 // L21'[R0]       [j][r]
+            load_rows_of_x<kHalf>(T4, X, ld, k - kP, ch, k);         // X[k - 64, C_h] [j][c]
         }
         __syncthreads();
-        if (before) mm64(Lt, T1, acc, tr, tc);                // X(k + i, c), i = tr*4+u, c = tc*4+w
-        mm64(T2, Lt, acc2, tr, tc);                           // LD(R0_r, j)
+        if (before) mm_c32(Lt, T1, acc, tr, tc);              // X(k + i, c), i = tr*4+u, c = tc*2+w
+        mm64(T2, Lt, acc2, tr, tc);                           // LD(R0_r, j), r = tr*4+u, j = tc*4+w
         __syncthreads();
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
 #pragma unroll
-            for (int w = 0; w < 4; ++w) {
-                const int i = tr * 4 + u, c = tc * 4 + w;
-                const float x = before ? acc[u][w] : Lt[c * kP + i];
-                X[(size_t)(c0 + c) * ld + (k + i)] = x;
+            for (int w = 0; w < 2; ++w) {
+                const int i = tr * 4 + u, c = tc * 2 + w;
+                const float x = before ? acc[u][w] : Lt[(h * kHalf + c) * kP + i];
+                X[(size_t)(ch + c) * ld + (k + i)] = x;
                 T1[i * kP + c] = x;                                          // B operand [i][c]
-                T2[(tc * 4 + w) * kP + tr * 4 + u] = acc2[u][w] * idv[tc * 4 + w];  // A operand [j][r]
             }
+#pragma unroll
+            for (int w = 0; w < 4; ++w)
+                T2[(tc * 4 + w) * kP + tr * 4 + u] = acc2[u][w] * idv[tc * 4 + w];  // A operand [j][r]
         }
         __syncthreads();
-        mm64(T2, T1, acc3, tr, tc);
-        if (prev && before) mm64(T3, T4, acc3, tr, tc);
+        mm_c32(T2, T1, acc3, tr, tc);
+        if (prev && before) mm_c32(T3, T4, acc3, tr, tc);
 #pragma unroll
-        for (int w = 0; w < 4; ++w) {
-            const int c = c0 + tc * 4 + w;
+        for (int w = 0; w < 2; ++w) {
+            const int c = ch + tc * 2 + w;
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int r = base + tr * 4 + u;
-                if (r < n) X[(size_t)c * ld + r] -= acc3[u][w];
+                if (r < n) X[(size_t)c * ld + r] = cur[u][w] - acc3[u][w];
             }
         }
     }
@@ -1310,7 +1397,8 @@ Error d32_alloc(Dense32 &F, int32_t n) {
     OT_CUDA(cudaMalloc((void **)&F.Linv, sizeof(float) * (size_t)F.ld * kP));
     OT_CUDA(cudaMalloc((void **)&F.D, sizeof(float) * n));
     OT_CUDA(cudaMalloc((void **)&F.d0, sizeof(float) * n));
-    OT_CUDA(cudaMalloc((void **)&F.csum, sizeof(float) * kP * (size_t)ceil_div(n, kP)));
+    // partial column sums: up to two rows (one per half strip) per 64-row strip
+    OT_CUDA(cudaMalloc((void **)&F.csum, sizeof(float) * 2 * kP * (size_t)ceil_div(n, kP)));
     OT_CUDA(cudaMalloc((void **)&F.L0, sizeof(float) * kP * kP));
     OT_CUDA(cudaMalloc((void **)&F.w, sizeof(float) * n));
     OT_CUDA(cudaMalloc((void **)&F.part, sizeof(float) * (size_t)F.ld * (size_t)ceil_div(n, kFc)));
@@ -1461,7 +1549,7 @@ static Error d32_build(Dense32 &F, float eps, cudaGraph_t g, int64_t *nodes) {
         const int bs0 = std::min(kP, n);
         prev = c.kernel({prev}, d32_colsum_kernel, (unsigned)bs0, kTT, n, ld, bs0, (const float *)F.A, F.csum);
         cudaGraphNode_t chain = c.kernel({prev}, d32_diag_kernel, 1u, kTT, ld, 0, bs0, F.A, F.D, (const float *)F.d0,
-                                         (const float *)F.csum, 1, eps, F.Linv, (const float *)nullptr);
+                                         (const float *)F.csum, 1, 1, eps, F.Linv, (const float *)nullptr);
         c.priority(chain, hi_prio);
         cudaGraphNode_t rest1 = nullptr, rest2 = nullptr;   // rest-updates of panels p - 1 and p - 2
         int k = 0, p = 0;
@@ -1471,12 +1559,12 @@ static Error d32_build(Dense32 &F, float eps, cudaGraph_t g, int64_t *nodes) {
             float *LDc = F.LD + (size_t)(p % 3) * ld * kP;
             const float *LDprev = F.LD + (size_t)((p + 2) % 3) * ld * kP;
             const cudaGraphNode_t sn =
-                c.kernel_smem({chain, rest2}, d32_step_kernel, (unsigned)(ts + tx), kTT, (unsigned)kStepSmem, n, ld,
+                c.kernel_smem({chain, rest2}, d32_step_kernel, (unsigned)(2 * (ts + tx)), kTT, (unsigned)kStepSmem, n, ld,
                               k, F.A, F.X, (const float *)F.D, (const float *)F.Linv, LDc, LDprev, F.L0, F.csum);
             c.priority(sn, hi_prio);
             const cudaGraphNode_t dn =
                 c.kernel({sn}, d32_diag_kernel, 1u, kTT, ld, base, std::min(kP, n - base), F.A, F.D,
-                         (const float *)F.d0, (const float *)F.csum, ts, eps, F.Linv, (const float *)F.L0);
+                         (const float *)F.d0, (const float *)F.csum, ts, 2, eps, F.Linv, (const float *)F.L0);
             c.priority(dn, hi_prio);
             const int b2 = base + 2 * kP;
             const int t2 = b2 < n ? (int)ceil_div(n - b2, kTile) : 0, tcn = (int)ceil_div(base, kTile);
@@ -1510,7 +1598,7 @@ static Error d32_build(Dense32 &F, float eps, cudaGraph_t g, int64_t *nodes) {
         float *LDp = F.LD + (size_t)(p % 3) * ld * kP;
         if (k == 0) prev = c.kernel({prev}, d32_colsum_kernel, (unsigned)bs, kTT, n, ld, bs, (const float *)F.A, F.csum);
         const cudaGraphNode_t dg = c.kernel({k == 0 ? prev : u1}, d32_diag_kernel, 1u, kTT, ld, k, bs, F.A, F.D,
-                                            (const float *)F.d0, (const float *)F.csum, np, eps, F.Linv,
+                                            (const float *)F.d0, (const float *)F.csum, np, 1, eps, F.Linv,
                                             (const float *)nullptr);
         c.priority(dg, hi_prio);
         std::vector<cudaGraphNode_t> ready;
