@@ -270,7 +270,8 @@ __device__ __forceinline__ DiagSmem diag_smem(float *buf) {
 }
 
 // The diagonal block at k (bs columns) by one CTA of kTT threads.  The block and the partial sums
-// are read through L2 (__ldcg): in the fused step kernel other CTAs of the same launch wrote them.
+// are read through L2 (__ldcg).  The partial column sums below the block come as np strips of
+// `per` rows each (per = 2: the step kernel's two half-strip CTAs), added in a fixed order.
 __device__ __forceinline__ void d32_diag_block(const DiagSmem &m, int ld, int k, int bs, float *__restrict__ A,
                                                float *__restrict__ D, const float *__restrict__ d0,
                                                const float *__restrict__ csum, int np, int per, float eps,
