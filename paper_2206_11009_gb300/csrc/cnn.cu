@@ -5,7 +5,9 @@
 //   head:           y <- conv3x3(h; W_4, b_4), C -> 2: predicted (u, v) / k^2
 // Layouts: activations NCHW; conv inputs stored in BF16, pre-normalisation outputs and all
 // gradients in FP32; weights kept in FP32 (Adam's master copy) with a BF16 copy for the
-// convolutions.  Every reduction runs in a fixed order (per-block partials, then one pass).
+// convolutions.  The 32 -> 32 convolutions (forward, data and weight gradient) are implicit GEMMs
+// on the tensor cores; the 2 -> 32 and 32 -> 2 ones run on the FP32 pipes.  Every reduction runs
+// in a fixed order (per-block partials, then one pass).
 #include <cuda_bf16.h>
 
 #include <cmath>
