@@ -290,6 +290,35 @@ def test_min_reduced_cost_hand_fixture():
     assert certificate.min_reduced_cost(costs.Cost.dense(C), ubar, v) == 0.0
 
 
+def test_c_transform_lower_bound_hand_fixture():
+    """a^T u + b^T v with u the c-transform of v, worked out by hand:
+       C = [[4, 1, 3], [2, 5, 0]], a = (0.4, 0.6), b = (0.2, 0.3, 0.5), v = (0, 3, -1)
+       u = (min(4, -2, 4), min(2, 2, 1)) = (-2, 1); a^T u = -0.2, b^T v = 0.4  ->  0.2,
+       below the optimum 0.9 (row 1: 0.5 to column 2 at 0 and 0.1 to column 0 at 2; row 0: 0.3 to
+       column 1 at 1 and 0.1 to column 0 at 4)."""
+    C = np.array([[4.0, 1.0, 3.0], [2.0, 5.0, 0.0]])
+    a, b = np.array([0.4, 0.6]), np.array([0.2, 0.3, 0.5])
+    v = np.array([0.0, 3.0, -1.0])
+    lb = certificate.c_transform_lower_bound(costs.Cost.dense(C), a, b, v)
+    assert abs(lb - 0.2) <= 1e-15
+    r = netsimplex.solve(costs.Cost.dense(C), a, b)
+    assert abs(r.obj - 0.9) <= 1e-15 and lb <= r.obj
+
+
+@pytest.mark.parametrize("k,seed", [(6, 0), (9, 1)])
+def test_c_transform_lower_bound_weak_duality_and_tightness(k, seed):
+    """Weak duality: for any v the bound is at most OPT; at an optimal v it equals OPT (the
+    c-transform of v* is at least u* entrywise, so the bound is at least a^T u* + b^T v* = OPT)."""
+    inst = synth.image_pair(k, seed)
+    c = costs.square_grid(k)
+    r = netsimplex.solve(c, inst.a, inst.b)
+    assert abs(certificate.c_transform_lower_bound(c, inst.a, inst.b, r.v) - r.obj) <= 1e-12 * r.obj
+    rng = synth.uniform01(seed + 77, 5 * k * k)
+    for t in range(5):
+        v = r.v + (rng[t * k * k:(t + 1) * k * k] - 0.5) * (1.0 + t)
+        assert certificate.c_transform_lower_bound(c, inst.a, inst.b, v) <= r.obj * (1 + 1e-12)
+
+
 @pytest.mark.parametrize("kind", ["sqeuclid", "euclid", "l1", "linf"])
 def test_min_reduced_cost_matches_python_loops(kind):
     """Against pure-Python loops over every pair, on point sets with a row count that spans
