@@ -305,6 +305,21 @@ def test_c_transform_lower_bound_hand_fixture():
     assert abs(r.obj - 0.9) <= 1e-15 and lb <= r.obj
 
 
+def test_forest_test_and_marginal_residual_hand_fixtures():
+    """The bipartite graph rows {0, 1} x columns {0, 1}: the path 0-0', 0-1', 1-1' is a tree, adding
+    1-0' closes the 4-cycle; a repeated edge is a 2-cycle.  Residual by hand: a = (0.5, 0.5),
+    b = (0.25, 0.75), P on (0,0), (0,1), (1,1) = (0.25, 0.2, 0.5) -> row sums (0.45, 0.5), column
+    sums (0.25, 0.7) -> |0.05| + 0 + 0 + |0.05| = 0.1."""
+    assert certificate.is_forest(2, 2, [0, 0, 1], [0, 1, 1])
+    assert not certificate.is_forest(2, 2, [0, 0, 1, 1], [0, 1, 1, 0])
+    assert not certificate.is_forest(2, 2, [0, 0], [1, 1])
+    assert certificate.is_forest(3, 2, [], [])
+    res = certificate.marginal_residual_l1(2, 2, np.array([0, 0, 1]), np.array([0, 1, 1]),
+                                           np.array([0.25, 0.2, 0.5]), np.array([0.5, 0.5]),
+                                           np.array([0.25, 0.75]))
+    assert abs(res - 0.1) <= 1e-15
+
+
 @pytest.mark.parametrize("k,seed", [(6, 0), (9, 1)])
 def test_c_transform_lower_bound_weak_duality_and_tightness(k, seed):
     """Weak duality: for any v the bound is at most OPT; at an optimal v it equals OPT (the
